@@ -1,0 +1,968 @@
+// FP64 CPU oracle for Bernstein bounds for caustics (Fan et al., TOG 2025).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the plain, slow reference that the
+// CUDA path is checked against.  Only the test-suite, the smoke check and the
+// CPU-baseline leg of the benchmark load it; the library path never does.  It
+// shares no code, header or table with the CUDA sources.
+//
+// What it follows, step by step:
+//   * Sec. 4.1, Eq. (1) and Eq. "eq_bbound": classical Bernstein coefficients
+//     on a simplex; a ratio p/q is bounded by the min/max of b(p)/b(q) when all
+//     b(q) are non-zero and share a sign; otherwise the reciprocal rule, then the
+//     universal set.  Products use the textbook weights C(m;a)C(n;b)/C(m+n;a+b),
+//     elevation and directional derivatives their textbook formulas.
+//   * Sec. 4.3, Eqs. "eq_xi", "eq_ni", "eq_rct", "eq_refr_rational": the vertex,
+//     interpolated normal, reflected direction and the Moller-form receiver
+//     coordinates as polynomials in the cell's barycentric coordinates.
+//   * Sec. 4.4, Eqs. "eq_dwda" and "eq_irr_term3a": irradiance through the GGT
+//     chain rule, det(du_k/du_1) = M / Q^3, and the non-rational |d_0|^3 carried
+//     by a remainder variable xi (Sec. 4.3, "Remainder variables") around a chord
+//     of f(s) = s^(-3/2).
+//   * Sec. 4.5, Eq. "eq_pertuple_b": per-tuple bound m * max over covering pieces.
+//   * Sec. 6.1 "Bound storage": uniform texture-space grid, splat to every
+//     overlapped cell.
+//   * Sec. 5.3, Algorithm 1, and Sec. 5.4: independent selection of each tuple
+//     with P = min(gamma * E~, 1), estimate sum E(T)/P over selected tuples.
+//   * Sec. 6.1 "Root-finding": Newton's method with deterministic initialization.
+//
+// Readings where the paper is silent (cell split order, chord closed form,
+// forward culling, grid inclusion, RNG, Newton details) are listed in the
+// repository's design notes; the code below states each one where it is used.
+//
+// Precision: every quantity is double.  Where a floating-point value decides an
+// integer and the CUDA path takes that decision in float32 (grid cell of a box
+// edge, selection r < P), this file repeats the same float32 operation.
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <thread>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Small vector algebra
+// ---------------------------------------------------------------------------
+struct V3 {
+  double x, y, z;
+};
+inline V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+inline V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+inline double norm(V3 a) { return std::sqrt(dot(a, a)); }
+
+// ---------------------------------------------------------------------------
+// Classical Bernstein polynomials on the 1-simplex (dim 1) or 2-simplex (dim 2)
+// Coefficient order (dim 2): g1 = 0..n outer, g2 = 0..n-g1 inner, g0 = n-g1-g2.
+// ---------------------------------------------------------------------------
+// Pascal's triangle up to degree 96, built once (exact integers up to 2^53).
+constexpr int kMaxDeg = 96;
+struct BinomTable {
+  double t[kMaxDeg + 1][kMaxDeg + 1];
+  BinomTable() {
+    for (int n = 0; n <= kMaxDeg; ++n)
+      for (int k = 0; k <= kMaxDeg; ++k)
+        t[n][k] = (k == 0 || k == n) ? 1.0 : (k > n ? 0.0 : t[n - 1][k - 1] + t[n - 1][k]);
+  }
+};
+const BinomTable kBinom;
+double binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  return kBinom.t[n][k];
+}
+
+struct Poly {
+  int dim = 2;
+  int n = 0;
+  std::vector<double> c;  // classical Bernstein coefficients
+};
+
+int psize(int dim, int n) { return dim == 1 ? n + 1 : (n + 1) * (n + 2) / 2; }
+int pidx(int dim, int n, int g1, int g2) {
+  if (dim == 1) return g1;
+  return g1 * (n + 1) - g1 * (g1 - 1) / 2 + g2;
+}
+// multinomial n! / (g0! g1! g2!)
+double multinom(int n, int g1, int g2) { return binom(n, g1) * binom(n - g1, g2); }
+
+template <class F>
+void for_each_index(int dim, int n, F f) {
+  if (dim == 1) {
+    for (int g1 = 0; g1 <= n; ++g1) f(g1, 0);
+  } else {
+    for (int g1 = 0; g1 <= n; ++g1)
+      for (int g2 = 0; g2 <= n - g1; ++g2) f(g1, g2);
+  }
+}
+
+Poly pconst(int dim, int n, double v) {
+  Poly p;
+  p.dim = dim;
+  p.n = n;
+  p.c.assign(psize(dim, n), v);  // partition of unity
+  return p;
+}
+
+// Degree-1 polynomial from its values at the simplex corners (linear precision).
+Poly paffine(double f0, double f1, double f2) {
+  Poly p;
+  p.dim = 2;
+  p.n = 1;
+  p.c.assign(3, 0.0);
+  p.c[pidx(2, 1, 0, 0)] = f0;
+  p.c[pidx(2, 1, 1, 0)] = f1;
+  p.c[pidx(2, 1, 0, 1)] = f2;
+  return p;
+}
+
+// Product in classical form: (pq)_g = sum_{a+b=g} C(m;a) C(n;b) / C(m+n;g) p_a q_b.
+Poly pmul(const Poly& p, const Poly& q) {
+  Poly r;
+  r.dim = p.dim;
+  r.n = p.n + q.n;
+  r.c.assign(psize(r.dim, r.n), 0.0);
+  for_each_index(p.dim, p.n, [&](int a1, int a2) {
+    double pa = p.c[pidx(p.dim, p.n, a1, a2)];
+    double wa = multinom(p.n, a1, a2);
+    for_each_index(q.dim, q.n, [&](int b1, int b2) {
+      int g1 = a1 + b1, g2 = a2 + b2;
+      double w = wa * multinom(q.n, b1, b2) / multinom(r.n, g1, g2);
+      r.c[pidx(r.dim, r.n, g1, g2)] += w * pa * q.c[pidx(q.dim, q.n, b1, b2)];
+    });
+  });
+  return r;
+}
+
+// Degree elevation by one: b'_g = sum_i (g_i / (n+1)) b_{g - e_i}.
+Poly pelevate(const Poly& p) {
+  Poly r;
+  r.dim = p.dim;
+  r.n = p.n + 1;
+  r.c.assign(psize(r.dim, r.n), 0.0);
+  for_each_index(r.dim, r.n, [&](int g1, int g2) {
+    int g0 = r.n - g1 - g2;
+    double s = 0.0;
+    if (g0 >= 1) s += (double)g0 / r.n * p.c[pidx(p.dim, p.n, g1, g2)];
+    if (g1 >= 1) s += (double)g1 / r.n * p.c[pidx(p.dim, p.n, g1 - 1, g2)];
+    if (g2 >= 1) s += (double)g2 / r.n * p.c[pidx(p.dim, p.n, g1, g2 - 1)];
+    r.c[pidx(r.dim, r.n, g1, g2)] = s;
+  });
+  return r;
+}
+
+Poly pelevate_to(Poly p, int n) {
+  while (p.n < n) p = pelevate(p);
+  return p;
+}
+
+Poly padd(Poly p, Poly q, double sq = 1.0) {
+  int n = std::max(p.n, q.n);
+  p = pelevate_to(p, n);
+  q = pelevate_to(q, n);
+  for (size_t i = 0; i < p.c.size(); ++i) p.c[i] += sq * q.c[i];
+  return p;
+}
+
+Poly pscale(Poly p, double s) {
+  for (auto& v : p.c) v *= s;
+  return p;
+}
+
+// Derivative along the j-th barycentric direction (d/dmu_j with mu_0 = 1 - mu_1 - mu_2):
+// coefficient at b (degree n-1) = n (b_{b+e_j} - b_{b+e_0}).
+Poly pderiv(const Poly& p, int j) {
+  Poly r;
+  r.dim = p.dim;
+  r.n = p.n - 1;
+  r.c.assign(psize(r.dim, r.n), 0.0);
+  for_each_index(r.dim, r.n, [&](int b1, int b2) {
+    double up = (j == 1) ? p.c[pidx(p.dim, p.n, b1 + 1, b2)] : p.c[pidx(p.dim, p.n, b1, b2 + 1)];
+    double base = p.c[pidx(p.dim, p.n, b1, b2)];
+    r.c[pidx(r.dim, r.n, b1, b2)] = p.n * (up - base);
+  });
+  return r;
+}
+
+// Direct evaluation sum_g b_g C(n;g) mu^g.
+double peval(const Poly& p, double m1, double m2) {
+  double m0 = 1.0 - m1 - m2;
+  double s = 0.0;
+  for_each_index(p.dim, p.n, [&](int g1, int g2) {
+    int g0 = p.n - g1 - g2;
+    s += p.c[pidx(p.dim, p.n, g1, g2)] * multinom(p.n, g1, g2) * std::pow(m0, g0) *
+         std::pow(m1, g1) * std::pow(m2, g2);
+  });
+  return s;
+}
+
+double pmin(const Poly& p) { return *std::min_element(p.c.begin(), p.c.end()); }
+double pmax(const Poly& p) { return *std::max_element(p.c.begin(), p.c.end()); }
+
+// +1 / -1 when every coefficient is non-zero with that sign, 0 otherwise (Eq. eq_bbound).
+int psign(const Poly& p) {
+  bool pos = true, neg = true;
+  for (double v : p.c) {
+    if (!(v > 0.0)) pos = false;
+    if (!(v < 0.0)) neg = false;
+  }
+  return pos ? 1 : (neg ? -1 : 0);
+}
+
+struct PV {  // polynomial 3-vector
+  Poly x, y, z;
+};
+PV pv_affine(V3 a, V3 b, V3 c) { return {paffine(a.x, b.x, c.x), paffine(a.y, b.y, c.y), paffine(a.z, b.z, c.z)}; }
+Poly pv_dot(const PV& a, const PV& b) { return padd(padd(pmul(a.x, b.x), pmul(a.y, b.y)), pmul(a.z, b.z)); }
+Poly pv_dotc(const PV& a, V3 b) { return padd(padd(pscale(a.x, b.x), pscale(a.y, b.y)), pscale(a.z, b.z)); }
+PV pv_mul(const Poly& s, const PV& a) { return {pmul(s, a.x), pmul(s, a.y), pmul(s, a.z)}; }
+PV pv_sub(const PV& a, const PV& b, double sb = 1.0) { return {padd(a.x, b.x, -sb), padd(a.y, b.y, -sb), padd(a.z, b.z, -sb)}; }
+PV pv_subc(const PV& a, V3 c) {
+  PV r = a;
+  for (auto& v : r.x.c) v -= c.x;
+  for (auto& v : r.y.c) v -= c.y;
+  for (auto& v : r.z.c) v -= c.z;
+  return r;
+}
+PV pv_crossc(const PV& a, V3 b) {  // a x b, b constant
+  return {padd(pscale(a.y, b.z), pscale(a.z, b.y), -1.0), padd(pscale(a.z, b.x), pscale(a.x, b.z), -1.0),
+          padd(pscale(a.x, b.y), pscale(a.y, b.x), -1.0)};
+}
+
+// ---------------------------------------------------------------------------
+// Scene views (own definitions; the field layout is the documented interface)
+// ---------------------------------------------------------------------------
+}  // namespace
+
+extern "C" {
+typedef struct {
+  int32_t n_verts, n_tris;
+  const float *px, *py, *pz, *nx, *ny, *nz;
+  const int32_t *i0, *i1, *i2;
+  int32_t kind;  // 0 reflect, 1 refract
+  float eta;     // n_incident / n_transmitted
+} orc_surface;
+typedef struct {
+  float p0[3], e1[3], e2[3];
+} orc_receiver;
+typedef struct {
+  int32_t n;
+  const float *x, *y, *z, *intensity;
+} orc_emitters;
+typedef struct {
+  int32_t emitter, tri0, tri1;
+  uint32_t cell;   // base-4 digits of the cell path, most significant first
+  uint32_t flags;  // bits 0..7 flags, bits 24..29 depth
+  int32_t pad;
+  double u_lo, u_hi, v_lo, v_hi, e_lo, e_hi;
+  double q_cond, m_cond;  // min|b| / max|b| of Q and M (diagnostics for tolerance rules)
+} orc_record;
+}
+
+namespace {
+
+enum : uint32_t {
+  F_LIVE = 1u,
+  F_SPLIT = 2u,
+  F_CULL_BEHIND = 4u,
+  F_CULL_EMPTY = 8u,
+  F_FOLD = 16u,
+  F_POS_UNBOUNDED = 32u,
+  F_TIR = 128u,
+};
+
+struct Tri {
+  V3 p[3], n[3];
+};
+
+Tri get_tri(const orc_surface* s, int t) {
+  Tri T;
+  int id[3] = {s->i0[t], s->i1[t], s->i2[t]};
+  for (int k = 0; k < 3; ++k) {
+    int v = id[k];
+    T.p[k] = {(double)s->px[v], (double)s->py[v], (double)s->pz[v]};
+    T.n[k] = {(double)s->nx[v], (double)s->ny[v], (double)s->nz[v]};
+  }
+  return T;
+}
+
+struct Rec {
+  V3 p0, e1, e2;
+};
+Rec get_rec(const orc_receiver* r) {
+  return {{r->p0[0], r->p0[1], r->p0[2]}, {r->e1[0], r->e1[1], r->e1[2]}, {r->e2[0], r->e2[1], r->e2[2]}};
+}
+
+struct UV {
+  double u, v;
+};
+
+// Cell corners for a base-4 path (Sec. 6.1 "Domain subdivision", on the simplex):
+// children of (C0,C1,C2) are (C0,m01,m02), (m01,C1,m12), (m02,m12,C2), (m12,m02,m01).
+void child_corners(const UV in[3], int k, UV out[3]) {
+  UV m01 = {(in[0].u + in[1].u) / 2, (in[0].v + in[1].v) / 2};
+  UV m02 = {(in[0].u + in[2].u) / 2, (in[0].v + in[2].v) / 2};
+  UV m12 = {(in[1].u + in[2].u) / 2, (in[1].v + in[2].v) / 2};
+  if (k == 0) { out[0] = in[0]; out[1] = m01; out[2] = m02; }
+  if (k == 1) { out[0] = m01; out[1] = in[1]; out[2] = m12; }
+  if (k == 2) { out[0] = m02; out[1] = m12; out[2] = in[2]; }
+  if (k == 3) { out[0] = m12; out[1] = m02; out[2] = m01; }
+}
+
+void cell_corners(uint32_t id, int depth, UV C[3]) {
+  C[0] = {0, 0};
+  C[1] = {1, 0};
+  C[2] = {0, 1};
+  for (int d = depth - 1; d >= 0; --d) {
+    int k = (id >> (2 * d)) & 3;
+    UV o[3];
+    child_corners(C, k, o);
+    C[0] = o[0]; C[1] = o[1]; C[2] = o[2];
+  }
+}
+
+// Chord of f(s) = s^(-3/2) on [s_lo, s_hi] and the range [dlo, dhi] of f - r.
+// f is convex and decreasing: the chord lies above f, so f - r <= 0 with the
+// minimum where f'(s*) = a.  A degenerate interval gives a = 0, b = f, d = 0.
+void chord_inv32(double s_lo, double s_hi, double* a, double* b, double* dlo, double* dhi) {
+  auto f = [](double s) { return 1.0 / (s * std::sqrt(s)); };
+  if (!(s_hi > s_lo)) {
+    *a = 0.0;
+    *b = f(s_lo);
+    *dlo = 0.0;
+    *dhi = 0.0;
+    return;
+  }
+  *a = (f(s_hi) - f(s_lo)) / (s_hi - s_lo);
+  *b = f(s_lo) - *a * s_lo;
+  double ss = std::pow(-*a / 1.5, -0.4);
+  ss = std::min(std::max(ss, s_lo), s_hi);
+  *dlo = std::min(0.0, f(ss) - (*a * ss + *b));
+  *dhi = 0.0;
+}
+
+// Ratio bound [min, max] of b(p)/b(q) (same degree; q must have uniform sign).
+void ratio_bound(const Poly& p, const Poly& q, double* lo, double* hi) {
+  double l = std::numeric_limits<double>::infinity(), h = -l;
+  for (size_t i = 0; i < p.c.size(); ++i) {
+    double r = p.c[i] / q.c[i];
+    l = std::min(l, r);
+    h = std::max(h, r);
+  }
+  *lo = l;
+  *hi = h;
+}
+
+// Reciprocal rule (Sec. 4.1): when q has mixed signs but p does not, q/p is
+// bounded; p/q then lies in 1/[r_lo, r_hi] (two rays when 0 is inside).  The
+// result is returned already intersected with [0,1] as its hull; empty -> lo > hi.
+void reciprocal_bound01(const Poly& p, const Poly& q, double* lo, double* hi) {
+  if (psign(p) == 0) {
+    *lo = 0.0;
+    *hi = 1.0;  // universal set, intersected with [0,1]
+    return;
+  }
+  double rl, rh;
+  ratio_bound(q, p, &rl, &rh);
+  double L = 1.0, H = 0.0;  // empty
+  auto add = [&](double a, double b) {  // add [a,b] ∩ [0,1] to the hull
+    a = std::max(a, 0.0);
+    b = std::min(b, 1.0);
+    if (a <= b) {
+      L = std::min(L, a);
+      H = std::max(H, b);
+    }
+  };
+  const double inf = std::numeric_limits<double>::infinity();
+  if (rl > 0.0 || rh < 0.0) {
+    add(1.0 / rh, 1.0 / rl);
+  } else {
+    // r in [rl, 0] -> p/q in (-inf, 1/rl];  r in [0, rh] -> p/q in [1/rh, inf)
+    add(-inf, rl < 0.0 ? 1.0 / rl : -inf);
+    add(rh > 0.0 ? 1.0 / rh : inf, inf);
+  }
+  *lo = L;
+  *hi = H;
+}
+
+struct Ctx {
+  const orc_surface* s1;
+  Rec rec;
+  const orc_emitters* em;
+  int irradiance;
+  int max_total_depth;
+};
+
+double cond_of(const Poly& p) {
+  double mn = std::numeric_limits<double>::infinity(), mx = 0.0;
+  for (double v : p.c) {
+    mn = std::min(mn, std::fabs(v));
+    mx = std::max(mx, std::fabs(v));
+  }
+  return mx > 0 ? mn / mx : 0.0;
+}
+
+// Bound one cell of one (emitter, triangle) tuple for single reflection.
+void bound_cell_reflect(const Ctx& cx, int e, int t, uint32_t id, int depth, std::vector<orc_record>& out) {
+  UV C[3];
+  cell_corners(id, depth, C);
+  Tri T = get_tri(cx.s1, t);
+  V3 x0 = {cx.em->x[e], cx.em->y[e], cx.em->z[e]};
+  double I0 = cx.em->intensity[e];
+  V3 e11 = T.p[1] - T.p[0], e12 = T.p[2] - T.p[0];
+  V3 n1d = T.n[1] - T.n[0], n2d = T.n[2] - T.n[0];
+  V3 xc[3], nc[3];
+  for (int k = 0; k < 3; ++k) {
+    xc[k] = T.p[0] + C[k].u * e11 + C[k].v * e12;  // Eq. eq_xi
+    nc[k] = T.n[0] + C[k].u * n1d + C[k].v * n2d;  // Eq. eq_ni
+  }
+  PV x1 = pv_affine(xc[0], xc[1], xc[2]);
+  PV n1 = pv_affine(nc[0], nc[1], nc[2]);
+  PV d0 = pv_subc(x1, x0);
+  // Eq. eq_refr_rational, reflection: d~ = (n.n) d0 - 2 (d0.n) n
+  Poly nn = pv_dot(n1, n1);
+  Poly dn = pv_dot(d0, n1);
+  PV dt = pv_sub(pv_mul(nn, d0), pv_mul(dn, n1), 2.0);
+  // Eq. eq_rct with receiver (p_k0, e_k1, e_k2)
+  const Rec& R = cx.rec;
+  PV w = pv_subc(x1, R.p0);
+  PV dxe2 = pv_crossc(dt, R.e2);
+  Poly Q = pv_dotc(dxe2, R.e1);
+  Poly Pu = pv_dot(dxe2, w);
+  Poly Pv = pv_dot(pv_crossc(w, R.e1), dt);
+  Poly Tn = pv_dotc(pv_crossc(w, R.e1), R.e2);  // t = Tn / Q (forward distance)
+
+  orc_record r;
+  std::memset(&r, 0, sizeof(r));
+  r.emitter = e;
+  r.tri0 = t;
+  r.tri1 = -1;
+  r.cell = id;
+  r.flags = (uint32_t)depth << 24;
+  r.q_cond = cond_of(Q);
+
+  int sq = psign(Q);
+  if (sq == 0) {
+    if (depth < cx.max_total_depth) {  // split and bound the four children
+      r.flags |= F_SPLIT;
+      out.push_back(r);
+      for (int k = 0; k < 4; ++k) bound_cell_reflect(cx, e, t, id * 4u + (uint32_t)k, depth + 1, out);
+      return;
+    }
+    // After the split limit: reciprocal rule / universal set, irradiance unbounded.
+    Poly Q4 = pelevate_to(Q, 4);
+    reciprocal_bound01(Pu, Q4, &r.u_lo, &r.u_hi);
+    reciprocal_bound01(Pv, Q4, &r.v_lo, &r.v_hi);
+    r.e_lo = 0.0;
+    r.e_hi = std::numeric_limits<double>::infinity();
+    if (r.u_lo > r.u_hi || r.v_lo > r.v_hi) {
+      r.flags |= F_CULL_EMPTY;
+    } else {
+      r.flags |= F_LIVE | F_POS_UNBOUNDED;
+    }
+    out.push_back(r);
+    return;
+  }
+  // Forward culling: the hit is behind x1 on the whole cell when t < 0 everywhere.
+  int st = psign(Tn);
+  if (st != 0 && st != sq) {
+    r.flags |= F_CULL_BEHIND;
+    out.push_back(r);
+    return;
+  }
+  Poly Q4 = pelevate(Q);
+  double ul, uh, vl, vh;
+  ratio_bound(Pu, Q4, &ul, &uh);
+  ratio_bound(Pv, Q4, &vl, &vh);
+  r.u_lo = std::max(ul, 0.0);
+  r.u_hi = std::min(uh, 1.0);
+  r.v_lo = std::max(vl, 0.0);
+  r.v_hi = std::min(vh, 1.0);
+  if (r.u_lo > r.u_hi || r.v_lo > r.v_hi) {
+    r.flags |= F_CULL_EMPTY;
+    out.push_back(r);
+    return;
+  }
+  r.flags |= F_LIVE;
+  if (!cx.irradiance) {
+    r.e_lo = 0.0;
+    r.e_hi = std::numeric_limits<double>::infinity();
+    out.push_back(r);
+    return;
+  }
+  // Eq. eq_irr_term3a: det(du_k/dmu) = M / Q^3 with a = Pu, b = Pv.
+  Poly a1 = pderiv(Pu, 1), a2 = pderiv(Pu, 2);
+  Poly b1 = pderiv(Pv, 1), b2 = pderiv(Pv, 2);
+  Poly q1 = pderiv(Q, 1), q2 = pderiv(Q, 2);
+  Poly X = padd(pmul(a1, b2), pmul(a2, b1), -1.0);
+  Poly Y = padd(pmul(a1, q2), pmul(a2, q1), -1.0);
+  Poly Z = padd(pmul(q1, b2), pmul(q2, b1), -1.0);
+  Poly M = padd(padd(pmul(Q, X), pmul(Pv, Y), -1.0), pmul(Pu, Z), -1.0);
+  r.m_cond = cond_of(M);
+  int sm = psign(M);
+  // Eq. eq_dwda: E = I0 * |d0.N1|/|d0|^3 * |N1|... collapsed to
+  //   E = I0 |C1| |detA| |Q|^3 s^(-3/2) / (|N_k| |M|),  s = d0.d0,
+  // with C1 = (p10 - x0).N1 (N1 = e11 x e12, constant on the triangle),
+  // detA = det[C1 - C0, C2 - C0] (cell -> triangle barycentrics).
+  V3 N1 = cross(e11, e12);
+  double C1 = dot(T.p[0] - x0, N1);
+  V3 Nk = cross(R.e1, R.e2);
+  double detA = (C[1].u - C[0].u) * (C[2].v - C[0].v) - (C[1].v - C[0].v) * (C[2].u - C[0].u);
+  double K = I0 * std::fabs(C1) * std::fabs(detA) / norm(Nk);
+  if (sm == 0) {
+    r.flags |= F_FOLD;
+    r.e_lo = 0.0;
+    r.e_hi = std::numeric_limits<double>::infinity();
+    out.push_back(r);
+    return;
+  }
+  Poly s = pv_dot(d0, d0);
+  double a, b, dlo, dhi;
+  chord_inv32(pmin(s), pmax(s), &a, &b, &dlo, &dhi);
+  Poly Q3 = pmul(pmul(Q, Q), Q);
+  if (sq < 0) Q3 = pscale(Q3, -1.0);  // |Q|^3 on a cell where Q has one sign
+  Poly Mn = pelevate_to(M, 11);
+  if (sm < 0) Mn = pscale(Mn, -1.0);
+  double lo = std::numeric_limits<double>::infinity(), hi = -lo;
+  for (int j = 0; j < 2; ++j) {  // remainder variable xi in {0, 1}: delta = dlo, dhi
+    Poly F = padd(pscale(s, a), pconst(2, 2, b + (j == 0 ? dlo : dhi)));
+    Poly N = pmul(Q3, F);
+    double l, h;
+    ratio_bound(N, Mn, &l, &h);
+    lo = std::min(lo, l);
+    hi = std::max(hi, h);
+  }
+  r.e_lo = K * lo;
+  r.e_hi = K * hi;
+  out.push_back(r);
+}
+
+void decode_work(int64_t i, int n_tris, int depth, int* e, int* t, uint32_t* c) {
+  int64_t per = (int64_t)1 << (2 * depth);
+  *c = (uint32_t)(i % per);
+  int64_t tup = i / per;
+  *t = (int)(tup % n_tris);
+  *e = (int)(tup / n_tris);
+}
+
+template <class F>
+void parallel_for(int64_t n, int n_threads, F f) {
+  if (n_threads <= 1 || n < 2 * n_threads) {
+    f(0, (int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  int64_t chunk = (n + n_threads - 1) / n_threads;
+  for (int k = 0; k < n_threads; ++k) {
+    int64_t a = k * chunk, b = std::min(n, a + chunk);
+    if (a >= b) break;
+    th.emplace_back([=]() { f(k, a, b); });
+  }
+  for (auto& x : th) x.join();
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+  }
+  for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+// Uniform in [0,1) with 24 bits, from the first output word.
+float philox_uniform(uint64_t seed, int64_t point, uint64_t key) {
+  uint32_t ctr[4] = {(uint32_t)point, (uint32_t)((uint64_t)point >> 32), (uint32_t)key, (uint32_t)(key >> 32)};
+  uint32_t k[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  philox4x32_10(ctr, k, o);
+  return (float)(o[0] >> 8) * (1.0f / 16777216.0f);
+}
+
+// float32 product rounded toward +inf, emulated exactly: the double product of
+// two floats is exact, then rounded up to the next float when needed.
+float fmul_ru32(float a, float b) {
+  double p = (double)a * (double)b;
+  float f = (float)p;
+  if ((double)f < p) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// Path evaluation within a tuple (rational form, forward-mode derivatives)
+// ---------------------------------------------------------------------------
+struct PathEval {
+  double uk, vk;       // receiver coordinates of the hit
+  double J[2][2];      // d(uk,vk)/d(u1,v1)
+  double t, Q;         // ray parameter numerator/denominator sign info
+  double E;            // irradiance I0 dOmega0/dA_k (GGT), V = F = 1
+  bool ok;
+};
+
+PathEval eval_reflect(const Tri& T, V3 x0, double I0, const Rec& R, double u, double v) {
+  PathEval P;
+  V3 e1 = T.p[1] - T.p[0], e2 = T.p[2] - T.p[0];
+  V3 dn1 = T.n[1] - T.n[0], dn2 = T.n[2] - T.n[0];
+  V3 x = T.p[0] + u * e1 + v * e2;
+  V3 n = T.n[0] + u * dn1 + v * dn2;
+  V3 d0 = x - x0;
+  V3 dx[2] = {e1, e2}, dnn[2] = {dn1, dn2};
+  double nn = dot(n, n), dn = dot(d0, n);
+  V3 dt = nn * d0 - 2.0 * dn * n;
+  V3 w = x - R.p0;
+  V3 g = cross(R.e2, R.e1);
+  double Q = dot(dt, g);
+  V3 he2w = cross(R.e2, w), hwe1 = cross(w, R.e1);
+  double A = dot(dt, he2w), B = dot(hwe1, dt);
+  double dA[2], dB[2], dQ[2];
+  for (int j = 0; j < 2; ++j) {
+    double dnn_j = 2.0 * dot(n, dnn[j]);
+    double ddn_j = dot(dx[j], n) + dot(d0, dnn[j]);
+    V3 ddt = dnn_j * d0 + nn * dx[j] - 2.0 * (ddn_j * n + dn * dnn[j]);
+    dQ[j] = dot(ddt, g);
+    dA[j] = dot(ddt, he2w) + dot(dt, cross(R.e2, dx[j]));
+    dB[j] = dot(cross(dx[j], R.e1), dt) + dot(hwe1, ddt);
+  }
+  P.Q = Q;
+  P.t = dot(hwe1, R.e2) / Q;
+  P.uk = A / Q;
+  P.vk = B / Q;
+  for (int j = 0; j < 2; ++j) {
+    P.J[0][j] = (dA[j] * Q - A * dQ[j]) / (Q * Q);
+    P.J[1][j] = (dB[j] * Q - B * dQ[j]) / (Q * Q);
+  }
+  double detJ = P.J[0][0] * P.J[1][1] - P.J[0][1] * P.J[1][0];
+  V3 N1 = cross(e1, e2);
+  double C1 = dot(T.p[0] - x0, N1);
+  double s = dot(d0, d0);
+  P.E = I0 * std::fabs(C1) / (s * std::sqrt(s) * norm(cross(R.e1, R.e2)) * std::fabs(detJ));
+  P.ok = std::isfinite(P.uk) && std::isfinite(P.vk) && std::isfinite(detJ) && Q != 0.0;
+  return P;
+}
+
+// Independent direct-geometry evaluator: normalized normal, vector reflection,
+// ray/plane hit, and the Jacobian by forward-mode dual numbers through those
+// operations.  Used only by the pins (containment sweeps).
+struct Dual {
+  double v, d[2];
+};
+Dual dmk(double v, double a, double b) { return {v, {a, b}}; }
+Dual operator+(Dual a, Dual b) { return {a.v + b.v, {a.d[0] + b.d[0], a.d[1] + b.d[1]}}; }
+Dual operator-(Dual a, Dual b) { return {a.v - b.v, {a.d[0] - b.d[0], a.d[1] - b.d[1]}}; }
+Dual operator*(Dual a, Dual b) { return {a.v * b.v, {a.d[0] * b.v + a.v * b.d[0], a.d[1] * b.v + a.v * b.d[1]}}; }
+Dual operator/(Dual a, Dual b) {
+  double iv = 1.0 / b.v;
+  return {a.v * iv, {(a.d[0] - a.v * iv * b.d[0]) * iv, (a.d[1] - a.v * iv * b.d[1]) * iv}};
+}
+Dual dsqrt(Dual a) {
+  double s = std::sqrt(a.v);
+  return {s, {a.d[0] / (2 * s), a.d[1] / (2 * s)}};
+}
+Dual dc(double v) { return {v, {0, 0}}; }
+struct DV3 {
+  Dual x, y, z;
+};
+DV3 operator+(DV3 a, DV3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+DV3 operator-(DV3 a, DV3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+DV3 operator*(Dual s, DV3 a) { return {s * a.x, s * a.y, s * a.z}; }
+Dual ddot(DV3 a, DV3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+DV3 dconst(V3 a) { return {dc(a.x), dc(a.y), dc(a.z)}; }
+
+bool eval_direct_reflect(const Tri& T, V3 x0, double I0, const Rec& R, double u, double v, double* uk,
+                         double* vk, double* E, double* tt) {
+  Dual U = dmk(u, 1, 0), W = dmk(v, 0, 1);
+  DV3 p0 = dconst(T.p[0]), e1 = dconst(T.p[1] - T.p[0]), e2 = dconst(T.p[2] - T.p[0]);
+  DV3 x = p0 + U * e1 + W * e2;
+  DV3 n = dconst(T.n[0]) + U * dconst(T.n[1] - T.n[0]) + W * dconst(T.n[2] - T.n[0]);
+  Dual ln = dsqrt(ddot(n, n));
+  DV3 nh = {n.x / ln, n.y / ln, n.z / ln};
+  DV3 d = x - dconst(x0);
+  DV3 r = d - (dc(2.0) * ddot(d, nh)) * nh;  // mirror reflection of the incident direction
+  V3 Nk = cross(R.e1, R.e2);
+  DV3 Nkd = dconst(Nk);
+  Dual t = ddot(dconst(R.p0) - x, Nkd) / ddot(r, Nkd);
+  DV3 X = x + t * r;
+  // receiver coordinates via the dual basis of (e1, e2) in the receiver plane
+  double g11 = dot(R.e1, R.e1), g12 = dot(R.e1, R.e2), g22 = dot(R.e2, R.e2);
+  double det = g11 * g22 - g12 * g12;
+  DV3 rel = X - dconst(R.p0);
+  Dual a = ddot(rel, dconst(R.e1)), b = ddot(rel, dconst(R.e2));
+  Dual Uk = (dc(g22) * a - dc(g12) * b) / dc(det);
+  Dual Vk = (dc(g11) * b - dc(g12) * a) / dc(det);
+  double detJ = Uk.d[0] * Vk.d[1] - Uk.d[1] * Vk.d[0];
+  V3 N1 = cross(T.p[1] - T.p[0], T.p[2] - T.p[0]);
+  V3 dd = {d.x.v, d.y.v, d.z.v};
+  double s = dot(dd, dd);
+  // GGT (Eq. eq_dwda): dOmega0/dA1 |dx1/du1| = |d0.N1| / |d0|^3, |du_k/dx_k| = 1/|N_k|
+  *E = I0 * std::fabs(dot(dd, N1)) / (s * std::sqrt(s)) / (std::fabs(detJ) * norm(Nk));
+  *uk = Uk.v;
+  *vk = Vk.v;
+  *tt = t.v;
+  return std::isfinite(Uk.v) && std::isfinite(Vk.v);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI (loaded by the tests through ctypes)
+// ===========================================================================
+extern "C" {
+
+// Bernstein helpers exposed for the pins.  dim in {1,2}; coefficient order as above.
+int orc_bb_size(int dim, int n) { return psize(dim, n); }
+void orc_bb_mul(int dim, int m, const double* p, int n, const double* q, double* out) {
+  Poly P{dim, m, std::vector<double>(p, p + psize(dim, m))};
+  Poly Qp{dim, n, std::vector<double>(q, q + psize(dim, n))};
+  Poly R = pmul(P, Qp);
+  std::copy(R.c.begin(), R.c.end(), out);
+}
+void orc_bb_elevate(int dim, int n, const double* p, double* out) {
+  Poly P{dim, n, std::vector<double>(p, p + psize(dim, n))};
+  Poly R = pelevate(P);
+  std::copy(R.c.begin(), R.c.end(), out);
+}
+void orc_bb_deriv(int n, const double* p, int j, double* out) {
+  Poly P{2, n, std::vector<double>(p, p + psize(2, n))};
+  Poly R = pderiv(P, j);
+  std::copy(R.c.begin(), R.c.end(), out);
+}
+double orc_bb_eval(int dim, int n, const double* p, double m1, double m2) {
+  Poly P{dim, n, std::vector<double>(p, p + psize(dim, n))};
+  return peval(P, m1, m2);
+}
+void orc_chord_inv32(double s_lo, double s_hi, double* out4) {
+  chord_inv32(s_lo, s_hi, &out4[0], &out4[1], &out4[2], &out4[3]);
+}
+void orc_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) { philox4x32_10(ctr, key, out); }
+float orc_philox_uniform(uint64_t seed, int64_t point, uint64_t key) { return philox_uniform(seed, point, key); }
+void orc_cell_corners(uint32_t id, int depth, double* out6) {
+  UV C[3];
+  cell_corners(id, depth, C);
+  for (int k = 0; k < 3; ++k) {
+    out6[2 * k] = C[k].u;
+    out6[2 * k + 1] = C[k].v;
+  }
+}
+
+// Bound the given base cells (flat work indices, or all when work == NULL).
+// Records of cells that split follow their parent (flag SPLIT) in depth-first
+// order.  Returns 0, or -2 when cap is too small (n_out then holds the need).
+int orc_bound(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, int32_t depth,
+              int32_t max_extra_split, int32_t irradiance, const int64_t* work, int64_t n_work,
+              orc_record* out, int64_t cap, int64_t* n_out, int32_t n_threads) {
+  if (s1->kind != 0) return -4;
+  Ctx cx{s1, get_rec(rec), em, irradiance, depth + max_extra_split};
+  int64_t total = work ? n_work : (int64_t)em->n * s1->n_tris * ((int64_t)1 << (2 * depth));
+  int nt = std::max(1, (int)n_threads);
+  std::vector<std::vector<orc_record>> parts(nt);
+  parallel_for(total, nt, [&](int k, int64_t a, int64_t b) {
+    auto& v = parts[k];
+    for (int64_t i = a; i < b; ++i) {
+      int e, t;
+      uint32_t c;
+      decode_work(work ? work[i] : i, s1->n_tris, depth, &e, &t, &c);
+      bound_cell_reflect(cx, e, t, c, depth, v);
+    }
+  });
+  int64_t n = 0;
+  for (auto& v : parts) n += (int64_t)v.size();
+  *n_out = n;
+  if (n > cap) return -2;
+  int64_t o = 0;
+  for (auto& v : parts)
+    for (auto& r : v) out[o++] = r;
+  return 0;
+}
+
+// Index (Sec. 6.1 "Bound storage"): for each LIVE record, the closed range of
+// grid cells its box overlaps, i = floor(u*G) clamped to [0, G-1] (float32
+// product, as the CUDA path takes this decision).  Per (grid cell, tuple key)
+// the tuple bound is m * max over covering records (Eq. eq_pertuple_b), kept in
+// float32 (round-up product).  Keys: emitter<<48 | (tri1+1)<<24 | tri0.
+int orc_index(const float* u_lo, const float* u_hi, const float* v_lo, const float* v_hi, const float* e_hi,
+              const int32_t* emitter, const int32_t* tri0, const int32_t* tri1, const uint32_t* flags, int64_t n,
+              int32_t G, float m, int64_t* offsets, uint64_t* key, float* etilde, int64_t cap, int64_t* n_out) {
+  std::vector<std::map<uint64_t, float>> cells((size_t)G * G);
+  for (int64_t r = 0; r < n; ++r) {
+    if (!(flags[r] & F_LIVE)) continue;
+    auto gi = [&](float x) {
+      float p = x * (float)G;  // float32 product
+      int i = (int)std::floor(p);
+      return std::min(G - 1, std::max(0, i));
+    };
+    int i0 = gi(u_lo[r]), i1 = gi(u_hi[r]), j0 = gi(v_lo[r]), j1 = gi(v_hi[r]);
+    uint64_t k = ((uint64_t)(uint32_t)emitter[r] << 48) | ((uint64_t)(uint32_t)(tri1[r] + 1) << 24) |
+                 (uint64_t)(uint32_t)tri0[r];
+    for (int j = j0; j <= j1; ++j)
+      for (int i = i0; i <= i1; ++i) {
+        auto& mp = cells[(size_t)j * G + i];
+        auto it = mp.find(k);
+        if (it == mp.end())
+          mp[k] = e_hi[r];
+        else
+          it->second = std::max(it->second, e_hi[r]);
+      }
+  }
+  int64_t tot = 0;
+  offsets[0] = 0;
+  for (size_t g = 0; g < cells.size(); ++g) {
+    tot += (int64_t)cells[g].size();
+    offsets[g + 1] = tot;
+  }
+  *n_out = tot;
+  if (tot > cap) return -2;
+  int64_t o = 0;
+  for (auto& mp : cells)
+    for (auto& kv : mp) {
+      key[o] = kv.first;
+      etilde[o] = fmul_ru32(m, kv.second);
+      ++o;
+    }
+  return 0;
+}
+
+// Algorithm 1 (Sec. 5.3) with P = min(gamma E~, 1) (Sec. 5.4): one uniform per
+// (point, tuple) from Philox4x32-10 keyed by the seed, counter (point, key);
+// select when r < P.  The probability is the float32 product rounded up, so
+// P > 0 whenever E~ > 0 (unbiasedness condition of Sec. 5.3).
+int orc_sample(const int64_t* offsets, const uint64_t* key, const float* etilde, int32_t G, const float* su,
+               const float* sv, int64_t n_points, float gamma, uint64_t seed, int64_t* wl_point, uint64_t* wl_key,
+               float* wl_p, int64_t cap, int64_t* n_out, int64_t* n_U) {
+  int64_t o = 0, nu = 0;
+  for (int64_t p = 0; p < n_points; ++p) {
+    auto gi = [&](float x) {
+      int i = (int)std::floor(x * (float)G);
+      return std::min(G - 1, std::max(0, i));
+    };
+    int64_t g = (int64_t)gi(sv[p]) * G + gi(su[p]);
+    for (int64_t j = offsets[g]; j < offsets[g + 1]; ++j) {
+      ++nu;
+      float P = std::min(fmul_ru32(gamma, etilde[j]), 1.0f);
+      float r = philox_uniform(seed, p, key[j]);
+      if (r < P) {
+        if (o < cap) {
+          wl_point[o] = p;
+          wl_key[o] = key[j];
+          wl_p[o] = P;
+        }
+        ++o;
+      }
+    }
+  }
+  *n_out = o;
+  *n_U = nu;
+  return o > cap ? -2 : 0;
+}
+
+// Newton root-finding in the tuple's triangle (Sec. 6.1, deterministic init):
+// start at the centroid, newton_iters damped steps (step clamped to 0.5 in
+// barycentric units; early exit when the step is below 1e-6), then
+// polish_iters full steps; accept when the hit is within tol scene units of the
+// target, u1 lies in the closed triangle and the hit is in front (t > 0).
+// contrib = E(root) / P.  status: 1 root, 0 none.
+int orc_solve(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, const int64_t* wl_point,
+              const uint64_t* wl_key, const float* wl_p, int64_t n_wl, const float* su, const float* sv,
+              int32_t newton_iters, int32_t polish_iters, double tol, double* contrib, double* root_u,
+              double* root_v, int32_t* status, int32_t n_threads) {
+  Rec R = get_rec(rec);
+  parallel_for(n_wl, std::max(1, (int)n_threads), [&](int, int64_t a, int64_t b) {
+    for (int64_t i = a; i < b; ++i) {
+      uint64_t k = wl_key[i];
+      int e = (int)(k >> 48), t = (int)(k & 0xFFFFFFu);
+      Tri T = get_tri(s1, t);
+      V3 x0 = {em->x[e], em->y[e], em->z[e]};
+      double I0 = em->intensity[e];
+      double tu = su[wl_point[i]], tv = sv[wl_point[i]];
+      double u = 1.0 / 3.0, v = 1.0 / 3.0;
+      bool bad = false;
+      for (int it = 0; it < newton_iters + polish_iters; ++it) {
+        PathEval P = eval_reflect(T, x0, I0, R, u, v);
+        double det = P.J[0][0] * P.J[1][1] - P.J[0][1] * P.J[1][0];
+        if (!P.ok || !(det != 0.0) || !std::isfinite(det)) {
+          bad = true;
+          break;
+        }
+        double fu = P.uk - tu, fv = P.vk - tv;
+        double du = -(P.J[1][1] * fu - P.J[0][1] * fv) / det;
+        double dv = -(-P.J[1][0] * fu + P.J[0][0] * fv) / det;
+        double mx = std::max(std::fabs(du), std::fabs(dv));
+        bool damped = it < newton_iters;
+        if (damped && mx > 0.5) {
+          du *= 0.5 / mx;
+          dv *= 0.5 / mx;
+        }
+        u += du;
+        v += dv;
+        if (!std::isfinite(u) || !std::isfinite(v)) {
+          bad = true;
+          break;
+        }
+        if (damped && mx < 1e-6) it = newton_iters - 1;  // converged: go to the polish steps
+      }
+      contrib[i] = 0.0;
+      status[i] = 0;
+      root_u[i] = u;
+      root_v[i] = v;
+      if (bad) continue;
+      PathEval P = eval_reflect(T, x0, I0, R, u, v);
+      if (!P.ok) continue;
+      double fu = P.uk - tu, fv = P.vk - tv;
+      V3 res = fu * R.e1 + fv * R.e2;
+      bool inside = u >= 0.0 && v >= 0.0 && u + v <= 1.0;
+      if (norm(res) < tol && inside && P.t > 0.0 && std::isfinite(P.E)) {
+        status[i] = 1;
+        contrib[i] = P.E / (double)wl_p[i];
+      }
+    }
+  });
+  return 0;
+}
+
+// Rational-form path evaluation at given (u1, v1) of one tuple (for pins).
+int orc_eval_path(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, int32_t e, int32_t t,
+                  const double* u, const double* v, int64_t n, double* uk, double* vk, double* E, double* tt) {
+  Rec R = get_rec(rec);
+  Tri T = get_tri(s1, t);
+  V3 x0 = {em->x[e], em->y[e], em->z[e]};
+  for (int64_t i = 0; i < n; ++i) {
+    PathEval P = eval_reflect(T, x0, em->intensity[e], R, u[i], v[i]);
+    uk[i] = P.uk;
+    vk[i] = P.vk;
+    E[i] = P.E;
+    tt[i] = P.t;
+  }
+  return 0;
+}
+
+// Direct-geometry evaluation (normalized normals, vector reflection, duals).
+int orc_eval_direct(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, int32_t e, int32_t t,
+                    const double* u, const double* v, int64_t n, double* uk, double* vk, double* E, double* tt) {
+  Rec R = get_rec(rec);
+  Tri T = get_tri(s1, t);
+  V3 x0 = {em->x[e], em->y[e], em->z[e]};
+  for (int64_t i = 0; i < n; ++i)
+    eval_direct_reflect(T, x0, em->intensity[e], R, u[i], v[i], &uk[i], &vk[i], &E[i], &tt[i]);
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+"""Seeded synthetic scene generators (input data only).
+
+This module builds the meshes, emitters, receivers and shading points that both
+the CUDA path and the CPU oracle consume.  It holds none of the bounding,
+sampling or solving arithmetic: every array it returns is plain input data,
+generated in float64 with numpy and stored as float32 (the precision the
+kernels read).  The paper's scenes (Plane, Sphere, Slab, Pool; Sec. 6, Table
+"tab:perf") are not available, so these generators stand in for them with the
+same kind of geometry:
+
+* ``heightfield``   -- a mirror heightfield on [-1,1]^2 made of seeded
+  sinusoids (+ optional per-vertex noise), standing in for the Plane scene
+  (single reflection, interpolated normals).
+* ``gerstner``      -- a water surface made of seeded Gerstner waves over a
+  pool floor, standing in for the Pool scene (single refraction).
+* ``slab``          -- a glass slab whose top and bottom faces are seeded
+  heightfields, standing in for the Slab scene (two refractions).
+
+Triangles use the (N+1)^2 vertex grid with the quad diagonal alternating by
+quad parity; all triangles are counter-clockwise seen from +z.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, Optional
+
+import numpy as np
+
+SURFACE_REFLECT = 0
+SURFACE_REFRACT = 1
+
+
+@dataclasses.dataclass
+class Surface:
+    """Triangle mesh with per-vertex normals (SoA float32, int32 indices)."""
+    px: np.ndarray
+    py: np.ndarray
+    pz: np.ndarray
+    nx: np.ndarray
+    ny: np.ndarray
+    nz: np.ndarray
+    i0: np.ndarray
+    i1: np.ndarray
+    i2: np.ndarray
+    kind: int = SURFACE_REFLECT
+    eta: float = 1.0   # ratio of indices of refraction, incident side / transmitted side
+
+    @property
+    def n_verts(self) -> int:
+        return int(self.px.shape[0])
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.i0.shape[0])
+
+
+@dataclasses.dataclass
+class Receiver:
+    """Planar receiver parallelogram p0 + u*e1 + v*e2, (u,v) in [0,1]^2."""
+    p0: np.ndarray
+    e1: np.ndarray
+    e2: np.ndarray
+
+
+@dataclasses.dataclass
+class Emitters:
+    """Point emitters (positions and isotropic intensities), float32."""
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    intensity: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+
+@dataclasses.dataclass
+class Scene:
+    name: str
+    s1: Surface
+    s2: Optional[Surface]
+    receiver: Receiver
+    emitters: Emitters
+    depth: int
+    su: np.ndarray          # shading points, receiver texture coordinates
+    sv: np.ndarray
+    grid_res: int = 512
+    extra: Dict = dataclasses.field(default_factory=dict)
+
+
+def _grid_triangles(n: int) -> np.ndarray:
+    """Indices (2 n^2, 3) of the (n+1)^2 vertex grid; diagonal alternates per quad parity."""
+    tris = np.empty((2 * n * n, 3), dtype=np.int64)
+    k = 0
+    for j in range(n):
+        for i in range(n):
+            v00 = j * (n + 1) + i
+            v10 = v00 + 1
+            v01 = v00 + (n + 1)
+            v11 = v01 + 1
+            if (i + j) % 2 == 0:
+                tris[k] = (v00, v10, v11)
+                tris[k + 1] = (v00, v11, v01)
+            else:
+                tris[k] = (v00, v10, v01)
+                tris[k + 1] = (v10, v11, v01)
+            k += 2
+    return tris
+
+
+def _sinusoids(rng: np.random.Generator, n_waves: int, amp_total: float):
+    kmag = rng.uniform(math.pi, 3.0 * math.pi, n_waves)
+    ang = rng.uniform(0.0, 2.0 * math.pi, n_waves)
+    phase = rng.uniform(0.0, 2.0 * math.pi, n_waves)
+    kx = kmag * np.cos(ang)
+    ky = kmag * np.sin(ang)
+    amp = np.full(n_waves, amp_total / n_waves)
+    return kx, ky, phase, amp
+
+
+def _face_average_normals(P: np.ndarray, tris: np.ndarray) -> np.ndarray:
+    """Area-weighted average of face normals at each vertex, normalized."""
+    e1 = P[tris[:, 1]] - P[tris[:, 0]]
+    e2 = P[tris[:, 2]] - P[tris[:, 0]]
+    fn = np.cross(e1, e2)            # length = 2 * area
+    N = np.zeros_like(P)
+    for c in range(3):
+        np.add.at(N, tris[:, c], fn)
+    return N / np.linalg.norm(N, axis=1, keepdims=True)
+
+
+def _to_surface(P: np.ndarray, N: np.ndarray, tris: np.ndarray, kind: int, eta: float) -> Surface:
+    f = np.float32
+    return Surface(px=P[:, 0].astype(f), py=P[:, 1].astype(f), pz=P[:, 2].astype(f),
+                   nx=N[:, 0].astype(f), ny=N[:, 1].astype(f), nz=N[:, 2].astype(f),
+                   i0=tris[:, 0].astype(np.int32), i1=tris[:, 1].astype(np.int32),
+                   i2=tris[:, 2].astype(np.int32), kind=kind, eta=float(eta))
+
+
+def heightfield(n: int, seed: int, n_waves: int = 4, amp_total: float = 0.05,
+                noise: float = 0.0, normals: str = "analytic", extent: float = 1.0,
+                z0: float = 0.0, kind: int = SURFACE_REFLECT, eta: float = 1.0,
+                flip_normals: bool = False) -> Surface:
+    """Heightfield z = z0 + sum_i A sin(k_i . (x,y) + phi_i) (+ U[-noise,noise]) on [-extent,extent]^2.
+
+    ``normals='analytic'`` uses the normalized gradient normal of the smooth
+    sinusoid sum; ``'face'`` uses the normalized area-weighted average of the
+    face normals (needed once per-vertex noise is added).
+    """
+    rng = np.random.default_rng(seed)
+    kx, ky, ph, amp = _sinusoids(rng, n_waves, amp_total)
+    xs = np.linspace(-extent, extent, n + 1)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")     # row j = y index, column i = x index
+    X = X.reshape(-1)
+    Y = Y.reshape(-1)
+    arg = np.outer(X, kx) + np.outer(Y, ky) + ph
+    Z = z0 + (np.sin(arg) * amp).sum(axis=1)
+    if noise > 0.0:
+        Z = Z + rng.uniform(-noise, noise, Z.shape[0])
+    P = np.stack([X, Y, Z], axis=1)
+    tris = _grid_triangles(n)
+    if normals == "analytic":
+        zx = (np.cos(arg) * amp * kx).sum(axis=1)
+        zy = (np.cos(arg) * amp * ky).sum(axis=1)
+        N = np.stack([-zx, -zy, np.ones_like(zx)], axis=1)
+        N /= np.linalg.norm(N, axis=1, keepdims=True)
+    elif normals == "face":
+        N = _face_average_normals(P, tris)
+    elif normals == "flat_up":
+        N = np.tile(np.array([0.0, 0.0, 1.0]), (P.shape[0], 1))
+    else:
+        raise ValueError(normals)
+    if flip_normals:
+        N = -N
+    return _to_surface(P, N, tris, kind, eta)
+
+
+def gerstner(n: int, seed: int, n_waves: int = 16, extent: float = 2.0, steep: float = 0.02,
+             lam_lo: float = 0.2, lam_hi: float = 1.0, eta: float = 1.0 / 1.33) -> Surface:
+    """Water surface as a sum of Gerstner waves (k_i A_i = steep, Q_i = 1) on [-extent,extent]^2.
+
+    Normals are the analytic normals of the displaced surface, normalized.
+    """
+    rng = np.random.default_rng(seed)
+    lam = rng.uniform(lam_lo, lam_hi, n_waves)
+    k = 2.0 * math.pi / lam
+    A = steep / k
+    ang = rng.uniform(0.0, 2.0 * math.pi, n_waves)
+    ph = rng.uniform(0.0, 2.0 * math.pi, n_waves)
+    Dx, Dy = np.cos(ang), np.sin(ang)
+    xs = np.linspace(-extent, extent, n + 1)
+    X, Y = np.meshgrid(xs, xs, indexing="xy")
+    X = X.reshape(-1)
+    Y = Y.reshape(-1)
+    arg = np.outer(X, k * Dx) + np.outer(Y, k * Dy) + ph
+    C, S = np.cos(arg), np.sin(arg)
+    Px = X + (A * Dx * C).sum(axis=1)
+    Py = Y + (A * Dy * C).sum(axis=1)
+    Pz = (A * S).sum(axis=1)
+    # Tangents of the displaced surface; normal = dP/dx x dP/dy.
+    WA = k * A
+    tx = np.stack([1.0 - (WA * Dx * Dx * S).sum(1), -(WA * Dx * Dy * S).sum(1), (WA * Dx * C).sum(1)], 1)
+    ty = np.stack([-(WA * Dx * Dy * S).sum(1), 1.0 - (WA * Dy * Dy * S).sum(1), (WA * Dy * C).sum(1)], 1)
+    N = np.cross(tx, ty)
+    N /= np.linalg.norm(N, axis=1, keepdims=True)
+    P = np.stack([Px, Py, Pz], axis=1)
+    return _to_surface(P, N, _grid_triangles(n), SURFACE_REFRACT, eta)
+
+
+def point_emitters(positions, intensity=1.0) -> Emitters:
+    P = np.asarray(positions, dtype=np.float64).reshape(-1, 3)
+    I = np.broadcast_to(np.asarray(intensity, dtype=np.float64), (P.shape[0],))
+    f = np.float32
+    return Emitters(P[:, 0].astype(f), P[:, 1].astype(f), P[:, 2].astype(f), I.astype(f))
+
+
+def area_quad_emitters(center, size: float, strata: int, seed: int) -> Emitters:
+    """Axis-aligned horizontal quad light, one jittered sample per stratum, I0 = 1/strata^2 each."""
+    rng = np.random.default_rng(seed)
+    c = np.asarray(center, dtype=np.float64)
+    pts = []
+    for j in range(strata):
+        for i in range(strata):
+            a = (i + rng.uniform()) / strata - 0.5
+            b = (j + rng.uniform()) / strata - 0.5
+            pts.append((c[0] + a * size, c[1] + b * size, c[2]))
+    return point_emitters(pts, 1.0 / (strata * strata))
+
+
+def receiver_square(center_z: float, half: float, cx: float = 0.0, cy: float = 0.0,
+                    half_y: Optional[float] = None) -> Receiver:
+    hy = half if half_y is None else half_y
+    p0 = np.array([cx - half, cy - hy, center_z], dtype=np.float32)
+    e1 = np.array([2.0 * half, 0.0, 0.0], dtype=np.float32)
+    e2 = np.array([0.0, 2.0 * hy, 0.0], dtype=np.float32)
+    return Receiver(p0, e1, e2)
+
+
+def shading_points(nx: int, ny: int, seed: int, jitter: float = 0.25):
+    """Pixel centres of an nx x ny grid over [0,1]^2 plus a seeded jitter of +-jitter pixel."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(nx, dtype=np.float64)
+    j = np.arange(ny, dtype=np.float64)
+    I, J = np.meshgrid(i, j, indexing="xy")
+    su = (I.reshape(-1) + 0.5 + rng.uniform(-jitter, jitter, nx * ny)) / nx
+    sv = (J.reshape(-1) + 0.5 + rng.uniform(-jitter, jitter, nx * ny)) / ny
+    return su.astype(np.float32), sv.astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Workloads.  Sizes follow the paper-shaped configurations:
+#   mirror32   : 32^2 mirror (2048 tris), light (0,0,2), 64^2 points, depth 2
+#   mirror256  : 256^2 mirror (131,072 tris), 0.2x0.2 area light with 4x4
+#                strata at z=2, 1024^2 points, depth 3
+#   water420   : 420^2 Gerstner water (352,800 tris), 4 lights, floor 1 below,
+#                1920x1080 points, depth 3
+#   slab48     : glass slab with two 48^2 faces, light (0,0,2), 512^2 points, depth 2
+# Reflection receivers sit at z=+1 facing the mirror (reflected rays travel up).
+# ---------------------------------------------------------------------------
+
+def mirror(n: int, seed: int, n_waves: int, noise: float, normals: str, emitters: Emitters,
+           points: int, depth: int, name: str, receiver_z: float = 1.0, point_seed: Optional[int] = None,
+           points_y: Optional[int] = None) -> Scene:
+    s1 = heightfield(n, seed, n_waves=n_waves, amp_total=0.05, noise=noise, normals=normals)
+    rec = receiver_square(receiver_z, 1.5)
+    py = points if points_y is None else points_y
+    su, sv = shading_points(points, py, seed + 1000 if point_seed is None else point_seed)
+    return Scene(name, s1, None, rec, emitters, depth, su, sv)
+
+
+def config(name: str, **kw) -> Scene:
+    """Named workloads (see module docstring)."""
+    if name == "mirror32":
+        em = point_emitters([(0.0, 0.0, 2.0)], 1.0)
+        return mirror(32, 1, 4, 0.0, "analytic", em, kw.get("points", 64), kw.get("depth", 2), name,
+                      receiver_z=kw.get("receiver_z", 1.0))
+    if name == "mirror256":
+        em = area_quad_emitters((0.0, 0.0, 2.0), 0.2, 4, seed=2)
+        return mirror(256, 2, 6, 0.01, "face", em, kw.get("points", 1024), kw.get("depth", 3), name)
+    if name == "tiny":
+        # A few triangles: exhaustive enumeration fits in milliseconds.
+        n = kw.get("n", 4)
+        em = point_emitters(kw.get("lights", [(0.1, -0.05, 2.0)]), 1.0)
+        return mirror(n, kw.get("seed", 7), 4, 0.0, "analytic", em, kw.get("points", 16),
+                      kw.get("depth", 1), name)
+    if name == "flat":
+        # Flat mirror z=0 with flat normals: the image-point closed form applies.
+        n = kw.get("n", 4)
+        s1 = heightfield(n, 0, n_waves=1, amp_total=0.0, normals="flat_up")
+        h = kw.get("h", 2.0)
+        em = point_emitters([(0.0, 0.0, h)], 1.0)
+        rec = receiver_square(kw.get("c", 1.0), 1.5)
+        su, sv = shading_points(kw.get("points", 16), kw.get("points", 16), 3)
+        return Scene(name, s1, None, rec, em, kw.get("depth", 1), su, sv)
+    raise KeyError(name)
