@@ -451,23 +451,30 @@ void bound_cell_reflect(const Ctx& cx, int e, int t, uint32_t id, int depth, std
 
   int sq = psign(Q);
   if (sq == 0) {
+    // Mixed-sign denominator (Sec. 4.1): bound the reciprocal q/p where p has one sign; the
+    // result (possibly two rays) is intersected with the receiver region [0,1] as a hull, and
+    // the universal set when p also has mixed signs.  A cell whose reciprocal bound misses
+    // the receiver is culled; otherwise it is split (up to the extra-split limit) and, at the
+    // limit, kept with this box and an unbounded irradiance.
+    Poly Q4 = pelevate_to(Q, 4);
+    reciprocal_bound01(Pu, Q4, &r.u_lo, &r.u_hi);
+    reciprocal_bound01(Pv, Q4, &r.v_lo, &r.v_hi);
+    if (r.u_lo > r.u_hi || r.v_lo > r.v_hi) {
+      r.u_lo = r.u_hi = r.v_lo = r.v_hi = 0.0;
+      r.flags |= F_CULL_EMPTY;
+      out.push_back(r);
+      return;
+    }
     if (depth < cx.max_total_depth) {  // split and bound the four children
+      r.u_lo = r.u_hi = r.v_lo = r.v_hi = 0.0;
       r.flags |= F_SPLIT;
       out.push_back(r);
       for (int k = 0; k < 4; ++k) bound_cell_reflect(cx, e, t, id * 4u + (uint32_t)k, depth + 1, out);
       return;
     }
-    // After the split limit: reciprocal rule / universal set, irradiance unbounded.
-    Poly Q4 = pelevate_to(Q, 4);
-    reciprocal_bound01(Pu, Q4, &r.u_lo, &r.u_hi);
-    reciprocal_bound01(Pv, Q4, &r.v_lo, &r.v_hi);
     r.e_lo = 0.0;
     r.e_hi = std::numeric_limits<double>::infinity();
-    if (r.u_lo > r.u_hi || r.v_lo > r.v_hi) {
-      r.flags |= F_CULL_EMPTY;
-    } else {
-      r.flags |= F_LIVE | F_POS_UNBOUNDED;
-    }
+    r.flags |= F_LIVE | F_POS_UNBOUNDED;
     out.push_back(r);
     return;
   }
@@ -857,7 +864,7 @@ int orc_sample(const int64_t* offsets, const uint64_t* key, const float* etilde,
     int64_t g = (int64_t)gi(sv[p]) * G + gi(su[p]);
     for (int64_t j = offsets[g]; j < offsets[g + 1]; ++j) {
       ++nu;
-      float P = std::min(fmul_ru32(gamma, etilde[j]), 1.0f);
+      float P = std::fmin(fmul_ru32(gamma, etilde[j]), 1.0f);  // fmin: a NaN product (0 * inf) selects
       float r = philox_uniform(seed, p, key[j]);
       if (r < P) {
         if (o < cap) {
