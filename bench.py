@@ -1,0 +1,436 @@
+"""Benchmark: one step = the whole path (bound -> index -> sample -> solve) over one
+synthetic area-lit mirror workload, timed on the GPU with CUDA events.
+
+Workload (N=1): 256^2 mirror heightfield (131,072 triangles, 6 seeded sinusoids
++ U[-0.01,0.01] noise, face-averaged normals), a 0.2 x 0.2 quad light at z=2 as
+16 stratified point samples, subdivision depth 3: 134,217,728 (emitter,
+triangle, cell) bounds per step; 1024^2 jittered shading points on the receiver
+z=+1, 512^2 grid.  Multi-GPU: replicas (each rank runs the same workload;
+`value` sums the ranks' work over the slowest rank's time).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
+bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bounded cells/s; caustic shading samples/s at 1e-4 rel err; p50/p99 latency"
+WORKLOAD = ("mirror256: 256^2 mirror heightfield (131,072 tris, 6 sinusoids + noise 0.01), area light "
+            "0.2x0.2 at z=2 as 16 stratified samples, depth 3 (134,217,728 cells/step), 1024^2 shading "
+            "points, grid 512, reflection, FP32 with outward rounding")
+
+
+# ----------------------------------------------------------------------------- algorithmic work
+def nc(n: int) -> int:
+    return (n + 1) * (n + 2) // 2
+
+
+def bound_fma_per_cell() -> int:
+    """FMAs of the canonical scaled-Bernstein value chain of one reflection cell (products as
+    convolutions: nc(M)*nc(N) FMAs), excluding error tracking and ratio logic."""
+    f = 0
+    f += 2 * 3 * nc(1) * nc(1)                          # n.n, d0.n
+    f += 3 * 2 * nc(2) * nc(1)                          # d~ = (n.n) d0 - 2 (d0.n) n
+    f += 2 * (3 * nc(1) * nc(0) + 3 * 2 * nc(1) * nc(0))  # D(n.n), D(d0.n) along 2 edges
+    f += 2 * 3 * (2 * nc(1) * nc(1) + 2 * nc(2) * nc(0))  # D d~
+    f += 3 * nc(3) + 2 * 3 * nc(2)                      # Q, DQ
+    f += 2 * 3 * nc(3) * nc(1)                          # A, B
+    f += 2 * 2 * 3 * (nc(2) * nc(1) + nc(3) * nc(0))    # DA, DB
+    f += 2 * nc(3) * nc(3) + nc(3) * nc(6)              # X, Q X
+    f += 2 * (2 * nc(3) * nc(2) + nc(4) * nc(5))        # Y, B Y, Z, A Z
+    f += 3 * nc(1) * nc(1)                              # s = d0.d0
+    f += nc(3) * nc(3) + nc(6) * nc(3)                  # Q^2, Q^3
+    f += 3 * nc(9) * nc(2)                              # N0, N1 and the elevated M per output coefficient
+    return f
+
+
+BOUND_FLOP_PER_CELL = 2 * bound_fma_per_cell()
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.rows.append([x.strip() for x in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------- reference arm (oracle)
+# Per-point work of the workload: mean |U| (listed tuples) and |S| (selected, gamma calibrated to
+# E|S| = 4) per shading point, as measured by the GPU arm on this workload; used to extrapolate the
+# oracle's per-draw and per-solve costs to a full step.
+U_PER_POINT = 48.0
+S_PER_POINT = 4.0
+
+
+def oracle_step_sample(sc, cells: int, points: int, seed: int, n_threads: int):
+    """One bounded sample of the workload through the FP64 oracle: `cells` contiguous base cells
+    (bound + index) and up to `points` shading points whose grid cells list sampled tuples
+    (Algorithm 1 draws over their lists + Newton on every listed tuple).
+    Returns (s per cell, s per draw, s per solve, description)."""
+    import copy
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    per = 4 ** sc.depth
+    n_base = sc.emitters.n * sc.s1.n_tris * per
+    t0_tuple = int(rng.integers(0, n_base // per - cells // per))
+    work = np.arange(t0_tuple * per, t0_tuple * per + cells, dtype=np.int64)
+    t0 = time.perf_counter()
+    rec = oracle.bound(sc, work=work, n_threads=n_threads)
+    f = oracle.records_to_f32(rec)
+    off, key, et = oracle.index(f["u_lo"], f["u_hi"], f["v_lo"], f["v_hi"], f["e_hi"], f["emitter"], f["tri0"],
+                                f["tri1"], f["flags"], sc.grid_res)
+    t1 = time.perf_counter()
+    G = sc.grid_res
+    g = np.clip(np.floor(sc.sv * np.float32(G)), 0, G - 1).astype(np.int64) * G + \
+        np.clip(np.floor(sc.su * np.float32(G)), 0, G - 1).astype(np.int64)
+    pick = np.nonzero(np.diff(off)[g] > 0)[0][:points]
+    su, sv = sc.su[pick], sc.sv[pick]
+    t2 = time.perf_counter()
+    wp, wk, wP, n_u = oracle.sample(off, key, et, G, su, sv, 1e30, seed)
+    t3 = time.perf_counter()
+    sc2 = copy.copy(sc)
+    sc2.su, sc2.sv = su, sv
+    oracle.solve(sc2, wp, wk, wP, n_threads=n_threads)
+    t4 = time.perf_counter()
+    return ((t1 - t0) / cells, (t3 - t2) / max(1, n_u), (t4 - t3) / max(1, wp.shape[0]),
+            f"{cells} contiguous base cells (bound+index, {t1 - t0:.2f} s), {n_u} draws over {len(pick)} points "
+            f"({t3 - t2:.3f} s), {wp.shape[0]} Newton solves ({t4 - t3:.2f} s)")
+
+
+def oracle_step_seconds(sc, t_cell, t_draw, t_solve, u_per_point=U_PER_POINT, s_per_point=S_PER_POINT):
+    n_cells = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
+    n_points = sc.su.shape[0]
+    return n_cells * t_cell + n_points * (u_per_point * t_draw + s_per_point * t_solve)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2504_19163_gb300 import scenes as S
+    oracle.build()
+    sc = S.config("mirror256")
+    n_threads = os.cpu_count() or 1
+    n_cells_full = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
+    n_points_full = sc.su.shape[0]
+    cells, points = 64 * 256, 256
+    for i in range(args.warmup):
+        oracle_step_sample(sc, cells, points, 100 + i, n_threads)
+    acc = np.zeros(3)
+    desc = ""
+    for i in range(args.steps):
+        a, b, c, desc = oracle_step_sample(sc, cells, points, 1000 + i, n_threads)
+        acc += (a, b, c)
+    t_cell, t_draw, t_solve = acc / args.steps
+    step_s = oracle_step_seconds(sc, t_cell, t_draw, t_solve)
+    value = n_cells_full / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": n_threads, "kind": "oracle",
+                             "sample": f"per step: {desc}; extrapolated to {n_cells_full} cells and "
+                                       f"{n_points_full} points x ({U_PER_POINT} draws + {S_PER_POINT} solves)"},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "shading_samples_per_s": n_points_full / step_s}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2504_19163_gb300 import bnb, build
+    from paper_2504_19163_gb300 import scenes as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    dev = torch.device("cuda", local)
+    sc = S.config("mirror256")
+    if args.emitters and args.emitters < sc.emitters.n:
+        # smaller case of the same workload (profiling): the first N area-light samples
+        e = sc.emitters
+        sc.emitters = S.Emitters(e.x[:args.emitters], e.y[:args.emitters], e.z[:args.emitters],
+                                 e.intensity[:args.emitters])
+    ds = bnb.DeviceScene(sc, dev)
+    n_cells = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
+    n_points = ds.n_points
+    stream = torch.cuda.current_stream(dev)
+
+    # Buffers sized once (first call discovers the capacities), then reused every step.
+    cb = bnb.bound_tuples(ds, sc.depth)
+    idx = bnb.build_index(cb, grid_res=sc.grid_res)
+    # gamma: expected |S| of about 4 per shading point (paper's Plane scene: |S| = 3.4)
+    gamma = calibrate_gamma(bnb, ds, idx, target=4.0)
+    res = bnb.sample_and_solve(ds, idx, gamma, 1)
+    torch.cuda.synchronize()
+    wl_cap = int(res.counters[1].item()) * 2 + 4096
+    cb_ws = bnb._ws(bnb.bnb_bound_tuples_ws(bnb.C.byref(ds.s1), None, bnb.C.byref(ds.em),
+                                            bnb.C.byref(bnb.bnb_bound_cfg(sc.depth, 4, 1, 0))), dev)
+    pre_cap = int(idx.count[1].item()) + idx.count[1].item() // 4 + 4096
+    ix_ws = bnb._ws(bnb.bnb_build_index_ws(bnb.C.byref(cb.c), sc.grid_res, pre_cap), dev)
+    idx = bnb.Index(sc.grid_res, pre_cap, dev)
+    sm_ws = bnb._ws(bnb.bnb_sample_and_solve_ws(bnb.C.byref(ds.s1), n_points, wl_cap), dev)
+    E_out = torch.empty(n_points, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(seed, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        bnb.bound_tuples(ds, sc.depth, out=cb, ws=cb_ws, sync_check=False)
+        if ev is not None:
+            ev[1].record(stream)
+        bnb.build_index(cb, grid_res=sc.grid_res, pre_capacity=pre_cap, capacity=pre_cap, out=idx, ws=ix_ws,
+                        sync_check=False)
+        if ev is not None:
+            ev[2].record(stream)
+        r = bnb.sample_and_solve(ds, idx, gamma, seed, worklist_capacity=wl_cap, E_out=E_out, ws=sm_ws,
+                                 sync_check=False)
+        if ev is not None:
+            ev[3].record(stream)
+        return r
+
+    for i in range(args.warmup):
+        step(1000 + i)
+    torch.cuda.synchronize()
+    st_ok = int(cb.status.item()) == 0 and int(idx.status.item()) == 0
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush (256 MiB > 129 MB L2) outside the timed events
+            r = step(i, evs[i])
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    stage = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs])
+    ms_step = float(stage.sum(axis=1).mean())
+    st_ok = st_ok and int(cb.status.item()) == 0 and int(idx.status.item()) == 0 and int(r.status.item()) == 0
+    counters = r.counters.cpu().numpy()
+    t_total = torch.tensor([ms_step], device=dev)
+    if dist is not None:
+        dist.all_reduce(t_total, op=dist.ReduceOp.MAX)
+    ms_max = float(t_total.item())
+    value = n_cells * world / (ms_max / 1e3)
+
+    # ---- end to end through the public API with host buffers (pinned), copies inside the region
+    host = {k: v.cpu().pin_memory() for k, v in ds.t.items()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    E_host = torch.empty(n_points, dtype=torch.float32).pin_memory()
+    d2h = E_host.numel() * 4
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for i in range(e2e_steps):
+        flush.zero_()
+        e0.record(stream)
+        for k, v in host.items():
+            ds.t[k].copy_(v, non_blocking=True)
+        step(500 + i)
+        E_host.copy_(E_out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e_ms /= e2e_steps
+    e2e_t = torch.tensor([e2e_ms], device=dev)
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = n_cells * world / (float(e2e_t.item()) / 1e3)
+
+    # ---- roofline of the dominant kernel (bound pass)
+    bound_ms = float(stage[:, 0].mean())
+    props = torch.cuda.get_device_properties(dev)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    achieved = BOUND_FLOP_PER_CELL * n_cells / (bound_ms / 1e3) / 1e12
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "bound_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            traffic = json.load(open(tr_path)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if sc.emitters.n == 16 else
+                       WORKLOAD.replace("16 stratified samples", f"{sc.emitters.n} of 16 stratified samples"),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single",
+                       "l2": "flushed between steps (256 MiB write, outside the events)",
+                       "gamma": gamma, "cells_per_step": n_cells, "points_per_step": n_points,
+                       "status_ok": st_ok},
+            "shading_samples_per_s": n_points * world / (ms_max / 1e3),
+            "stage_ms": {"bound": bound_ms, "index": float(stage[:, 1].mean()),
+                         "sample_solve": float(stage[:, 2].mean())},
+            "per_point": {"U": counters[0] / n_points, "S": counters[1] / n_points, "roots": counters[2] / n_points},
+            "roofline": {"bound": "alu", "kernel": "bound_base_k<float>", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                         "flop_per_cell": BOUND_FLOP_PER_CELL,
+                         "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                       f"(max SM clock of MEASURED_PEAKS.json)"},
+            "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": launches_per_step(n_points, sc.grid_res) * args.steps,
+            "clocks": clk.summary()}
+    if not args.no_cpu_baseline and rank == 0 and world == 1 and not args.emitters:
+        line["cpu_baseline"] = cpu_baseline(counters[0] / n_points, counters[1] / n_points)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def scan_launches(n: int) -> int:
+    tiles = (n + 2047) // 2048
+    if tiles <= 1:
+        return 2
+    return 1 + scan_launches(tiles) + 2
+
+
+def launches_per_step(n_points: int, G: int) -> int:
+    bound = 1 + 1 + 4                                # pack, base, 4 split levels
+    index = 2 + scan_launches(G * G) + 3 + scan_launches(G * G) + 2
+    sample = 1 + 1 + scan_launches(n_points) + 1 + 1 + 1
+    return bound + index + sample
+
+
+def calibrate_gamma(bnb, ds, idx, target: float) -> float:
+    """gamma such that the mean expected |S| = mean sum_U min(gamma E~, 1) is `target` (Sec. 5.4:
+    one-to-one map between gamma and E|S|), by bisection on log gamma over the device index."""
+    import torch
+    off = idx.offsets
+    su, sv = ds.t["su"], ds.t["sv"]
+    G = idx.grid_res
+    gi = torch.clamp(torch.floor(su * G), 0, G - 1).long()
+    gj = torch.clamp(torch.floor(sv * G), 0, G - 1).long()
+    g = gj * G + gi
+    cnt = (off[1:] - off[:-1])
+    n = int(idx.count[0].item())
+    et = idx.etilde[:n].double()
+    cell_of = torch.repeat_interleave(torch.arange(G * G, device=off.device), cnt)
+    w = torch.bincount(g, minlength=G * G).double()
+    lo, hi = -60.0, 60.0
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        p = torch.clamp(et * (2.0 ** mid), max=1.0)
+        per_cell = torch.zeros(G * G, dtype=torch.float64, device=off.device).index_add_(0, cell_of, p)
+        mean = float((per_cell * w).sum() / w.sum())
+        if mean < target:
+            lo = mid
+        else:
+            hi = mid
+    return float(2.0 ** hi)
+
+
+def cpu_baseline(u_per_point: float, s_per_point: float) -> dict:
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        return pool.apply(_cpu_baseline_worker, ("mirror256", u_per_point, s_per_point))
+
+
+def _cpu_baseline_worker(name, u_per_point, s_per_point):
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2504_19163_gb300 import scenes as S
+    oracle.build()
+    sc = S.config(name)
+    n_threads = os.cpu_count() or 1
+    t_cell, t_draw, t_solve, desc = oracle_step_sample(sc, 64 * 2048, 1024, 7, n_threads)
+    step_s = oracle_step_seconds(sc, t_cell, t_draw, t_solve, u_per_point, s_per_point)
+    n_cells = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
+    return {"value": n_cells / step_s, "unit": "cells/s", "cores": n_threads, "kind": "oracle",
+            "sample": f"{desc} on {n_threads} threads; extrapolated to {n_cells} cells and {sc.su.shape[0]} "
+                      f"points x ({u_per_point:.1f} draws + {s_per_point:.2f} solves, this run's |U|, |S|)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--emitters", type=int, default=0, help="use only the first N area-light samples (profiling case)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

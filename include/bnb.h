@@ -1,0 +1,195 @@
+/*
+ * bnb.h -- C ABI of libbnb: GB300 (sm_103a) kernels for Bernstein bounds for
+ * caustics (Fan, Wang, Wang, Li, Guo, Yan, Guo, Guo; ACM TOG 44(4), 2025).
+ *
+ * Three calls make up the path:
+ *   bnb_bound_tuples      precomputation pass (Sec. 3 "Overall pipeline",
+ *                         Secs. 4.3-4.5): per (emitter, specular triangle,
+ *                         subdivision cell) a conservative receiver box U_k and
+ *                         irradiance bound [E_lo, E_hi].
+ *   bnb_build_index       bound storage (Sec. 6.1 "Bound storage"): the boxes
+ *                         binned into a uniform texture-space grid; per grid
+ *                         cell the sorted list of tuples with the per-tuple
+ *                         bound E~ = m * max E_hi (Eq. eq_pertuple_b).
+ *   bnb_sample_and_solve  rendering pass (Sec. 5, Algorithm 1; Sec. 6.1
+ *                         "Root-finding"): per shading point, select each
+ *                         listed tuple with P = min(gamma E~, 1) (Sec. 5.4),
+ *                         solve for the path with Newton's method and return
+ *                         sum E(T)/P.
+ *
+ * Conventions (all calls):
+ *   - Every array pointer is a DEVICE pointer owned by the caller; the library
+ *     never allocates device memory.  Scratch comes from the caller's workspace
+ *     `ws` of `ws_bytes` bytes (256-byte aligned), sized by the matching
+ *     *_ws() query.  Small structs (receiver, cfgs) are read on the host.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls enqueue kernels on it and return without synchronizing.
+ *   - Return values are host-detected: BNB_OK, or BNB_ERR_INVALID for a bad
+ *     argument (nothing is launched), BNB_ERR_UNSUPPORTED, or BNB_ERR_CUDA when
+ *     a launch fails.  Conditions only the device can see (an output or
+ *     workspace too small) are written to the device word `*status` of the
+ *     output struct (0 = ok, BNB_ERR_CAPACITY) and the device counters hold the
+ *     size that was needed; the outputs are then incomplete and the caller
+ *     re-calls with larger buffers.  The library does not reset `*status`: the
+ *     caller zeroes it (and the counters) before a call.
+ *   - No C++ exception crosses the ABI.  Calls on different streams with
+ *     disjoint outputs and workspaces may run concurrently.
+ */
+#ifndef BNB_H_
+#define BNB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define BNB_OK 0
+#define BNB_ERR_INVALID (-1)
+#define BNB_ERR_CAPACITY (-2)
+#define BNB_ERR_CUDA (-3)
+#define BNB_ERR_UNSUPPORTED (-4)
+#define BNB_ERR_TIMEOUT (-5)
+
+/* Surface kinds (scattering type at the specular vertex, Eq. eq_refr_rational). */
+#define BNB_REFLECT 0
+#define BNB_REFRACT 1
+
+/* Cell record flags (bits 0..7); bits 24..29 of `flags` hold the cell depth. */
+#define BNB_CELL_LIVE 1u           /* box and irradiance bound valid, box meets [0,1]^2 */
+#define BNB_CELL_SPLIT 2u          /* superseded by its four children (denominator sign test failed) */
+#define BNB_CELL_CULL_BEHIND 4u    /* every path of the cell hits the receiver plane behind x1 (t < 0) */
+#define BNB_CELL_CULL_EMPTY 8u     /* the box misses the receiver region [0,1]^2 */
+#define BNB_CELL_FOLD 16u          /* Jacobian numerator changes sign: E_hi = +inf */
+#define BNB_CELL_POS_UNBOUNDED 32u /* reciprocal rule / universal set used after the split limit */
+#define BNB_CELL_QSIGN_FP64 64u    /* the float32 sign test was inconclusive; float64 decided it */
+#define BNB_CELL_TIR 128u          /* refraction: total internal reflection on the whole cell */
+#define BNB_CELL_DEPTH_SHIFT 24
+
+/* A triangle mesh with per-vertex normals (Table 1: p_{i,0..2}, n_{i,0..2}).
+ * SoA float32 device arrays of n_verts entries; int32 index arrays of n_tris.
+ * Normals are interpolated un-normalized (Eq. eq_ni); they need not be unit. */
+typedef struct bnb_surface {
+  int32_t n_verts, n_tris;
+  const float *px, *py, *pz;
+  const float *nx, *ny, *nz;
+  const int32_t *i0, *i1, *i2;
+  int32_t kind; /* BNB_REFLECT or BNB_REFRACT */
+  float eta;    /* refraction: index of the incident side / index of the transmitted side */
+} bnb_surface;
+
+/* Planar receiver T_k: x = p0 + u e1 + v e2 with texture coordinates (u,v) in
+ * [0,1]^2 (host values).  Eq. eq_rct maps a path to (u,v). */
+typedef struct bnb_receiver {
+  float p0[3], e1[3], e2[3];
+} bnb_receiver;
+
+/* Point emitters x_0 with isotropic intensity I_0 (device arrays of n).  Each
+ * emitter is part of the tuple key (Sec. 3: multiple emitters are treated as
+ * part of the tuple); area lights are passed as their stratified samples. */
+typedef struct bnb_emitters {
+  int32_t n;
+  const float *x, *y, *z, *intensity;
+} bnb_emitters;
+
+typedef struct bnb_bound_cfg {
+  int32_t depth;           /* base 4-way subdivision depth D of T1's domain: 4^D cells per tuple (0..10) */
+  int32_t max_extra_split; /* extra splits of a cell whose denominator sign test fails (0..4) */
+  int32_t irradiance;      /* 1: irradiance bound (Sec. 4.4); 0: position only, e_hi = +inf */
+  int32_t fp64;            /* 1: the whole bound pass in float64 (same arithmetic, u = 2^-53) */
+} bnb_bound_cfg;
+
+/* Per-cell bound records, SoA device arrays of `capacity` entries.  Slots
+ * [0, n_base) hold the base cells in work order
+ *     w = (emitter * n_tris + tri) * 4^depth + cell
+ * (the 4^depth cells of one tuple are contiguous); children of split cells
+ * are appended after n_base in no particular order.  Boxes are in receiver
+ * texture coordinates, clipped to [0,1]^2, rounded outward. */
+typedef struct bnb_cell_bounds {
+  int64_t capacity;
+  int64_t *count;  /* device int64: records produced (n_base + children); may exceed capacity */
+  int32_t *status; /* device int32: BNB_OK or BNB_ERR_CAPACITY */
+  float *u_lo, *u_hi, *v_lo, *v_hi, *e_lo, *e_hi;
+  int32_t *emitter, *tri0, *tri1; /* tri1 = -1 for single scattering */
+  uint32_t *cell;                 /* base-4 digits of the cell path, most significant first */
+  uint32_t *flags;                /* BNB_CELL_* | depth << BNB_CELL_DEPTH_SHIFT */
+  float *e_hi_min;                /* optional (NULL: not written): the exact-arithmetic Bernstein bound
+                                     that e_hi rounds outward lies in [e_hi_min, e_hi]; 0 when e_hi = +inf */
+  /* host fields, written by bnb_bound_tuples for the index pass */
+  int64_t n_base;
+  int32_t depth;
+  int32_t n_emitters;
+  int32_t n_tris;
+} bnb_cell_bounds;
+
+/* Texture-space grid index (CSR).  Tuple keys: emitter << 48 | (tri1 + 1) << 24 | tri0. */
+typedef struct bnb_index {
+  int32_t grid_res; /* G: G x G cells over [0,1]^2, cell (i,j) = j * G + i */
+  int64_t capacity; /* entries key/etilde can hold */
+  int64_t *count;   /* device int64[2]: [0] entries in the index, [1] pre-merge entries needed */
+  int32_t *status;  /* device int32: BNB_OK or BNB_ERR_CAPACITY */
+  int64_t *offsets; /* device, G*G + 1 */
+  uint64_t *key;    /* device, capacity; ascending within each grid cell */
+  float *etilde;    /* device, capacity; per-tuple bound E~ (may be +inf) */
+} bnb_index;
+
+typedef struct bnb_sample_cfg {
+  float gamma;                /* P = min(gamma * E~, 1) (Sec. 5.4) */
+  uint64_t seed;              /* Philox4x32-10 key; counter = (point, tuple key) */
+  int32_t newton_iters;       /* damped float32 Newton steps (<= 64) */
+  int32_t polish_iters;       /* float64 polish steps (<= 8) */
+  float tol;                  /* acceptance: |hit - target| < tol scene units */
+  int64_t worklist_capacity;  /* selected (point, tuple) pairs the workspace holds */
+} bnb_sample_cfg;
+
+typedef struct bnb_sample_stats {
+  int64_t *counters;  /* device int64[4]: |U| summed, |S| summed (= worklist entries needed), roots found, 0 */
+  int32_t *status;    /* device int32: BNB_OK or BNB_ERR_CAPACITY */
+  int32_t *sel_count; /* optional device int32[n_points]: |S| per shading point (NULL: not written) */
+} bnb_sample_stats;
+
+/* Precomputation pass.  Bounds every (emitter, triangle of s1, cell) with
+ * Secs. 4.3-4.4: x1, n1 (Eqs. eq_xi, eq_ni), the reflected direction (Eq.
+ * eq_refr_rational), receiver coordinates (Eq. eq_rct) and irradiance (Eqs.
+ * eq_dwda, eq_irr_term3a) as Bernstein forms on the cell, their ratio bound
+ * (Eq. eq_bbound), |d0|^-3 carried by a remainder variable (Sec. 4.3).  s2 must
+ * be NULL (one specular vertex).  Requires out->capacity >= n_base =
+ * em->n * s1->n_tris * 4^depth.  ws: bnb_bound_tuples_ws() bytes. */
+int32_t bnb_bound_tuples(const bnb_surface *s1, const bnb_surface *s2, const bnb_receiver *rec,
+                         const bnb_emitters *em, const bnb_bound_cfg *cfg, bnb_cell_bounds *out,
+                         void *ws, size_t ws_bytes, void *stream);
+size_t bnb_bound_tuples_ws(const bnb_surface *s1, const bnb_surface *s2, const bnb_emitters *em,
+                           const bnb_bound_cfg *cfg);
+
+/* Bound storage (Sec. 6.1) over the records of one bnb_bound_tuples call (its
+ * host fields must be set).  m multiplies the bound (Eq. eq_pertuple_b; the
+ * paper uses m = 1).  pre_capacity: pre-merge (grid cell, tuple) entries the
+ * workspace holds; bnb_build_index_ws(cells, grid_res, pre_capacity) bytes. */
+int32_t bnb_build_index(const bnb_cell_bounds *cells, float m, int64_t pre_capacity, bnb_index *out,
+                        void *ws, size_t ws_bytes, void *stream);
+size_t bnb_build_index_ws(const bnb_cell_bounds *cells, int32_t grid_res, int64_t pre_capacity);
+
+/* Rendering pass for n_points shading points (receiver texture coordinates
+ * su, sv, device float arrays).  E_out[p] (device float, n_points) receives the
+ * estimate sum_{T in S} E(T) / P_T (Sec. 5.3) with E the path irradiance
+ * I0 dOmega0/dA_k of Eq. eq_dwda (visibility and Fresnel ignored, Sec. 4.4).
+ * ws: bnb_sample_and_solve_ws(s1, n_points, cfg->worklist_capacity) bytes. */
+int32_t bnb_sample_and_solve(const bnb_surface *s1, const bnb_surface *s2, const bnb_receiver *rec,
+                             const bnb_emitters *em, const bnb_index *index, const float *su, const float *sv,
+                             int64_t n_points, const bnb_sample_cfg *cfg, float *E_out,
+                             bnb_sample_stats *stats, void *ws, size_t ws_bytes, void *stream);
+size_t bnb_sample_and_solve_ws(const bnb_surface *s1, int64_t n_points, int64_t worklist_capacity);
+
+/* Human-readable name of a status code (static string). */
+const char *bnb_status_string(int32_t status);
+
+/* ABI version of this header (increments on any struct or signature change). */
+int32_t bnb_abi_version(void);  /* 2 */
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BNB_H_ */

@@ -1,0 +1,346 @@
+"""Python binding of libbnb (include/bnb.h): argument marshalling only.
+
+The C entry points keep their names (``bnb_bound_tuples``, ``bnb_build_index``,
+``bnb_sample_and_solve`` and the ``*_ws`` queries).  Torch tensors provide the
+device memory and the CUDA stream; every step of the path runs in libbnb's
+kernels.  There is no CPU fallback: importing the library fails loudly when
+``libbnb.so`` has not been built.
+
+Higher-level helpers (``DeviceScene``, ``bound_tuples``, ``build_index``,
+``sample_and_solve``) allocate outputs and workspaces as torch tensors, zero
+the device status words, call the C function, and re-call once with larger
+buffers when the device reports BNB_ERR_CAPACITY.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbnb.so")
+
+BNB_OK, BNB_ERR_INVALID, BNB_ERR_CAPACITY, BNB_ERR_CUDA, BNB_ERR_UNSUPPORTED, BNB_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+BNB_REFLECT, BNB_REFRACT = 0, 1
+LIVE, SPLIT, CULL_BEHIND, CULL_EMPTY, FOLD, POS_UNBOUNDED, QSIGN_FP64, TIR = 1, 2, 4, 8, 16, 32, 64, 128
+DEPTH_SHIFT = 24
+
+vp, i32, i64, u64, f32, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_float, C.c_size_t
+
+
+class bnb_surface(C.Structure):
+    _fields_ = [("n_verts", i32), ("n_tris", i32), ("px", vp), ("py", vp), ("pz", vp), ("nx", vp), ("ny", vp),
+                ("nz", vp), ("i0", vp), ("i1", vp), ("i2", vp), ("kind", i32), ("eta", f32)]
+
+
+class bnb_receiver(C.Structure):
+    _fields_ = [("p0", f32 * 3), ("e1", f32 * 3), ("e2", f32 * 3)]
+
+
+class bnb_emitters(C.Structure):
+    _fields_ = [("n", i32), ("x", vp), ("y", vp), ("z", vp), ("intensity", vp)]
+
+
+class bnb_bound_cfg(C.Structure):
+    _fields_ = [("depth", i32), ("max_extra_split", i32), ("irradiance", i32), ("fp64", i32)]
+
+
+class bnb_cell_bounds(C.Structure):
+    _fields_ = [("capacity", i64), ("count", vp), ("status", vp), ("u_lo", vp), ("u_hi", vp), ("v_lo", vp),
+                ("v_hi", vp), ("e_lo", vp), ("e_hi", vp), ("emitter", vp), ("tri0", vp), ("tri1", vp),
+                ("cell", vp), ("flags", vp), ("e_hi_min", vp), ("n_base", i64), ("depth", i32), ("n_emitters", i32),
+                ("n_tris", i32)]
+
+
+class bnb_index(C.Structure):
+    _fields_ = [("grid_res", i32), ("capacity", i64), ("count", vp), ("status", vp), ("offsets", vp),
+                ("key", vp), ("etilde", vp)]
+
+
+class bnb_sample_cfg(C.Structure):
+    _fields_ = [("gamma", f32), ("seed", u64), ("newton_iters", i32), ("polish_iters", i32), ("tol", f32),
+                ("worklist_capacity", i64)]
+
+
+class bnb_sample_stats(C.Structure):
+    _fields_ = [("counters", vp), ("status", vp), ("sel_count", vp)]
+
+
+_lib = None
+EXPORTS = ["bnb_bound_tuples", "bnb_bound_tuples_ws", "bnb_build_index", "bnb_build_index_ws",
+           "bnb_sample_and_solve", "bnb_sample_and_solve_ws", "bnb_status_string", "bnb_abi_version"]
+
+
+def lib():
+    """Load libbnb.so (raises when it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libbnb.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        L.bnb_bound_tuples.restype = i32
+        L.bnb_bound_tuples.argtypes = [P(bnb_surface), P(bnb_surface), P(bnb_receiver), P(bnb_emitters),
+                                       P(bnb_bound_cfg), P(bnb_cell_bounds), vp, sz, vp]
+        L.bnb_bound_tuples_ws.restype = sz
+        L.bnb_bound_tuples_ws.argtypes = [P(bnb_surface), P(bnb_surface), P(bnb_emitters), P(bnb_bound_cfg)]
+        L.bnb_build_index.restype = i32
+        L.bnb_build_index.argtypes = [P(bnb_cell_bounds), f32, i64, P(bnb_index), vp, sz, vp]
+        L.bnb_build_index_ws.restype = sz
+        L.bnb_build_index_ws.argtypes = [P(bnb_cell_bounds), i32, i64]
+        L.bnb_sample_and_solve.restype = i32
+        L.bnb_sample_and_solve.argtypes = [P(bnb_surface), P(bnb_surface), P(bnb_receiver), P(bnb_emitters),
+                                           P(bnb_index), vp, vp, i64, P(bnb_sample_cfg), vp, P(bnb_sample_stats),
+                                           vp, sz, vp]
+        L.bnb_sample_and_solve_ws.restype = sz
+        L.bnb_sample_and_solve_ws.argtypes = [P(bnb_surface), i64, i64]
+        L.bnb_status_string.restype = C.c_char_p
+        L.bnb_status_string.argtypes = [i32]
+        L.bnb_abi_version.restype = i32
+        _lib = L
+    return _lib
+
+
+# Raw entry points with the C names (argument marshalling only).
+def bnb_bound_tuples(*a):
+    return lib().bnb_bound_tuples(*a)
+
+
+def bnb_bound_tuples_ws(*a):
+    return lib().bnb_bound_tuples_ws(*a)
+
+
+def bnb_build_index(*a):
+    return lib().bnb_build_index(*a)
+
+
+def bnb_build_index_ws(*a):
+    return lib().bnb_build_index_ws(*a)
+
+
+def bnb_sample_and_solve(*a):
+    return lib().bnb_sample_and_solve(*a)
+
+
+def bnb_sample_and_solve_ws(*a):
+    return lib().bnb_sample_and_solve_ws(*a)
+
+
+def bnb_status_string(s: int) -> str:
+    return lib().bnb_status_string(s).decode()
+
+
+class BnbError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str):
+    if rc != BNB_OK:
+        raise BnbError(f"{what}: {bnb_status_string(rc)} ({rc})")
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    # torch's caching allocator returns 512-byte aligned blocks; +256 keeps a zero-size request valid.
+    return torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
+
+
+# ----------------------------------------------------------------------------- device scene
+class DeviceScene:
+    """A scene's inputs resident in device memory, with the C structs pointing at them."""
+
+    def __init__(self, scene, device="cuda"):
+        self.scene = scene
+        self.device = torch.device(device)
+        d = self.device
+        s = scene.s1
+
+        def t(a, dt):
+            return torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(d)
+
+        self.t = dict(px=t(s.px, torch.float32), py=t(s.py, torch.float32), pz=t(s.pz, torch.float32),
+                      nx=t(s.nx, torch.float32), ny=t(s.ny, torch.float32), nz=t(s.nz, torch.float32),
+                      i0=t(s.i0, torch.int32), i1=t(s.i1, torch.int32), i2=t(s.i2, torch.int32),
+                      ex=t(scene.emitters.x, torch.float32), ey=t(scene.emitters.y, torch.float32),
+                      ez=t(scene.emitters.z, torch.float32), ei=t(scene.emitters.intensity, torch.float32),
+                      su=t(scene.su, torch.float32), sv=t(scene.sv, torch.float32))
+        T = self.t
+        self.s1 = bnb_surface(s.n_verts, s.n_tris, _ptr(T["px"]), _ptr(T["py"]), _ptr(T["pz"]), _ptr(T["nx"]),
+                              _ptr(T["ny"]), _ptr(T["nz"]), _ptr(T["i0"]), _ptr(T["i1"]), _ptr(T["i2"]), s.kind,
+                              s.eta)
+        r = scene.receiver
+        self.rec = bnb_receiver((f32 * 3)(*r.p0), (f32 * 3)(*r.e1), (f32 * 3)(*r.e2))
+        self.em = bnb_emitters(scene.emitters.n, _ptr(T["ex"]), _ptr(T["ey"]), _ptr(T["ez"]), _ptr(T["ei"]))
+
+    @property
+    def n_points(self) -> int:
+        return int(self.t["su"].shape[0])
+
+
+# ----------------------------------------------------------------------------- outputs
+class CellBounds:
+    """Cell records (SoA device tensors) plus their bnb_cell_bounds view."""
+
+    def __init__(self, capacity: int, device, with_e_hi_min: bool = False):
+        d = device
+        self.capacity = int(capacity)
+        f = lambda dt: torch.empty(self.capacity, dtype=dt, device=d)
+        self.count = torch.zeros(1, dtype=torch.int64, device=d)
+        self.status = torch.zeros(1, dtype=torch.int32, device=d)
+        self.u_lo, self.u_hi, self.v_lo, self.v_hi = f(torch.float32), f(torch.float32), f(torch.float32), f(torch.float32)
+        self.e_lo, self.e_hi = f(torch.float32), f(torch.float32)
+        self.emitter, self.tri0, self.tri1 = f(torch.int32), f(torch.int32), f(torch.int32)
+        self.cell, self.flags = f(torch.int32), f(torch.int32)
+        self.e_hi_min = f(torch.float32) if with_e_hi_min else None
+        self.c = bnb_cell_bounds(self.capacity, _ptr(self.count), _ptr(self.status), _ptr(self.u_lo),
+                                 _ptr(self.u_hi), _ptr(self.v_lo), _ptr(self.v_hi), _ptr(self.e_lo), _ptr(self.e_hi),
+                                 _ptr(self.emitter), _ptr(self.tri0), _ptr(self.tri1), _ptr(self.cell),
+                                 _ptr(self.flags), _ptr(self.e_hi_min), 0, 0, 0, 0)
+
+    def reset(self):
+        self.count.zero_()
+        self.status.zero_()
+
+    def n_records(self) -> int:
+        return min(int(self.count.item()), self.capacity)
+
+    def to_numpy(self) -> dict:
+        n = self.n_records()
+        g = lambda t: t[:n].cpu().numpy()
+        out = dict(u_lo=g(self.u_lo), u_hi=g(self.u_hi), v_lo=g(self.v_lo), v_hi=g(self.v_hi), e_lo=g(self.e_lo),
+                   e_hi=g(self.e_hi), emitter=g(self.emitter), tri0=g(self.tri0), tri1=g(self.tri1),
+                   cell=g(self.cell).view(np.uint32), flags=g(self.flags).view(np.uint32))
+        if self.e_hi_min is not None:
+            out["e_hi_min"] = g(self.e_hi_min)
+        return out
+
+
+class Index:
+    def __init__(self, grid_res: int, capacity: int, device):
+        d = device
+        self.grid_res = int(grid_res)
+        self.capacity = int(capacity)
+        self.count = torch.zeros(2, dtype=torch.int64, device=d)
+        self.status = torch.zeros(1, dtype=torch.int32, device=d)
+        self.offsets = torch.empty(self.grid_res * self.grid_res + 1, dtype=torch.int64, device=d)
+        self.key = torch.empty(max(1, self.capacity), dtype=torch.int64, device=d)
+        self.etilde = torch.empty(max(1, self.capacity), dtype=torch.float32, device=d)
+        self.c = bnb_index(self.grid_res, self.capacity, _ptr(self.count), _ptr(self.status), _ptr(self.offsets),
+                           _ptr(self.key), _ptr(self.etilde))
+
+    def reset(self):
+        self.count.zero_()
+        self.status.zero_()
+
+    def to_numpy(self):
+        n = min(int(self.count[0].item()), self.capacity)
+        return (self.offsets.cpu().numpy(), self.key[:n].cpu().numpy().view(np.uint64),
+                self.etilde[:n].cpu().numpy())
+
+
+# ----------------------------------------------------------------------------- high-level calls
+def bound_tuples(ds: DeviceScene, depth: int, max_extra_split: int = 4, irradiance: bool = True,
+                 fp64: bool = False, capacity: Optional[int] = None, out: Optional[CellBounds] = None,
+                 ws: Optional[torch.Tensor] = None, stream=None, sync_check: bool = True,
+                 with_e_hi_min: bool = False) -> CellBounds:
+    cfg = bnb_bound_cfg(depth, max_extra_split, int(irradiance), int(fp64))
+    n_base = ds.scene.emitters.n * ds.s1.n_tris * 4 ** depth
+    if out is None:
+        out = CellBounds(capacity if capacity is not None else n_base + n_base // 8 + 1024, ds.device, with_e_hi_min)
+    need = bnb_bound_tuples_ws(C.byref(ds.s1), None, C.byref(ds.em), C.byref(cfg))
+    if ws is None or ws.numel() < need + 256:
+        ws = _ws(need, ds.device)
+    for _ in range(2):
+        out.reset()
+        rc = bnb_bound_tuples(C.byref(ds.s1), None, C.byref(ds.rec), C.byref(ds.em), C.byref(cfg), C.byref(out.c),
+                              _align(ws), C.c_size_t(need), _stream(stream))
+        _check(rc, "bnb_bound_tuples")
+        if not sync_check:
+            return out
+        if int(out.status.item()) == BNB_OK:
+            return out
+        out = CellBounds(int(out.count.item()) + 1024, ds.device, with_e_hi_min)
+    raise BnbError("bnb_bound_tuples: capacity exceeded twice")
+
+
+def _align(ws: torch.Tensor):
+    p = ws.data_ptr()
+    return C.c_void_p((p + 255) // 256 * 256)
+
+
+def build_index(cells: CellBounds, grid_res: int = 512, m: float = 1.0, pre_capacity: Optional[int] = None,
+                capacity: Optional[int] = None, out: Optional[Index] = None, ws: Optional[torch.Tensor] = None,
+                stream=None, sync_check: bool = True) -> Index:
+    dev = cells.u_lo.device
+    n_rec = cells.capacity
+    pre = pre_capacity if pre_capacity is not None else max(4096, n_rec // 4)
+    cap = capacity if capacity is not None else pre
+    for _ in range(3):
+        if out is None or out.capacity < cap:
+            out = Index(grid_res, cap, dev)
+        need = bnb_build_index_ws(C.byref(cells.c), grid_res, pre)
+        if ws is None or ws.numel() < need + 256:
+            ws = _ws(need, dev)
+        out.reset()
+        rc = bnb_build_index(C.byref(cells.c), m, pre, C.byref(out.c), _align(ws), C.c_size_t(need),
+                             _stream(stream))
+        _check(rc, "bnb_build_index")
+        if not sync_check:
+            return out
+        if int(out.status.item()) == BNB_OK:
+            return out
+        pre = max(pre, int(out.count[1].item()) + 1024)
+        cap = max(cap, int(out.count[0].item()) + 1024, pre)
+        out = None
+    raise BnbError("bnb_build_index: capacity exceeded repeatedly")
+
+
+@dataclasses.dataclass
+class SampleResult:
+    E: torch.Tensor
+    counters: torch.Tensor
+    status: torch.Tensor
+    sel_count: Optional[torch.Tensor] = None
+
+
+def sample_and_solve(ds: DeviceScene, index: Index, gamma: float, seed: int, newton_iters: int = 16,
+                     polish_iters: int = 2, tol: float = 1e-5, worklist_capacity: Optional[int] = None,
+                     su: Optional[torch.Tensor] = None, sv: Optional[torch.Tensor] = None,
+                     E_out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None,
+                     sync_check: bool = True, with_sel_count: bool = False) -> SampleResult:
+    su = ds.t["su"] if su is None else su
+    sv = ds.t["sv"] if sv is None else sv
+    n_points = int(su.shape[0])
+    wl = worklist_capacity if worklist_capacity is not None else max(1024, 16 * n_points)
+    counters = torch.zeros(4, dtype=torch.int64, device=ds.device)
+    status = torch.zeros(1, dtype=torch.int32, device=ds.device)
+    E = E_out if E_out is not None else torch.empty(n_points, dtype=torch.float32, device=ds.device)
+    sel = torch.zeros(n_points, dtype=torch.int32, device=ds.device) if with_sel_count else None
+    for _ in range(2):
+        cfg = bnb_sample_cfg(gamma, seed, newton_iters, polish_iters, tol, wl)
+        need = bnb_sample_and_solve_ws(C.byref(ds.s1), n_points, wl)
+        if ws is None or ws.numel() < need + 256:
+            ws = _ws(need, ds.device)
+        counters.zero_()
+        status.zero_()
+        stats = bnb_sample_stats(_ptr(counters), _ptr(status), _ptr(sel))
+        rc = bnb_sample_and_solve(C.byref(ds.s1), None, C.byref(ds.rec), C.byref(ds.em), C.byref(index.c),
+                                  _ptr(su), _ptr(sv), n_points, C.byref(cfg), _ptr(E), C.byref(stats), _align(ws),
+                                  C.c_size_t(need), _stream(stream))
+        _check(rc, "bnb_sample_and_solve")
+        if not sync_check or int(status.item()) == BNB_OK:
+            return SampleResult(E, counters, status, sel)
+        wl = int(counters[1].item()) + 1024
+    raise BnbError("bnb_sample_and_solve: worklist capacity exceeded twice")

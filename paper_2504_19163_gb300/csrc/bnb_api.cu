@@ -1,0 +1,221 @@
+// C ABI of libbnb (declared in include/bnb.h): argument checks, workspace
+// layout and the launch sequence of each call.  No call allocates memory or
+// synchronizes the stream.
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "bnb_internal.cuh"
+
+namespace bnb {
+size_t index_ws_bytes(int32_t G, int64_t pre_cap);
+cudaError_t launch_build_index(const bnb_cell_bounds* c, float m, int64_t pre_cap, bnb_index* out, void* ws,
+                               cudaStream_t st);
+size_t sample_ws_bytes(int64_t n_tris, int64_t n_points, int64_t wl_cap);
+cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_receiver* rec, const bnb_emitters* em,
+                                    const bnb_index* idx, const float* su, const float* sv, int64_t n_points,
+                                    const bnb_sample_cfg* cfg, float* E_out, bnb_sample_stats* stats, void* ws,
+                                    cudaStream_t st);
+}  // namespace bnb
+
+using namespace bnb;
+
+namespace {
+
+constexpr int kMaxBaseDepth = 10;
+constexpr int kMaxExtra = 4;
+
+bool surface_ok(const bnb_surface* s) {
+  if (!s || s->n_tris < 0 || s->n_verts < 0) return false;
+  if (s->n_tris > 0 && (!s->px || !s->py || !s->pz || !s->nx || !s->ny || !s->nz || !s->i0 || !s->i1 || !s->i2))
+    return false;
+  if (s->n_tris > (1 << 24) - 2) return false;  // tuple key holds 24 bits per triangle index
+  return true;
+}
+
+bool emitters_ok(const bnb_emitters* e) {
+  if (!e || e->n < 0 || e->n > 65535) return false;
+  if (e->n > 0 && (!e->x || !e->y || !e->z || !e->intensity)) return false;
+  return true;
+}
+
+bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
+
+int64_t n_base_of(const bnb_surface* s1, const bnb_emitters* em, int depth) {
+  return (int64_t)em->n * (int64_t)s1->n_tris * ((int64_t)1 << (2 * depth));
+}
+
+int64_t split_queue_cap(int64_t n_base) { return 4096 + n_base / 32; }
+
+struct BoundWs {
+  float4* tri;
+  SplitItem* q[2];
+  int64_t* qcount;  // [2]
+  size_t bytes;
+};
+
+BoundWs carve_bound_ws(void* base, int64_t n_tris, int64_t qcap) {
+  BoundWs w{};
+  size_t o = 0;
+  auto take = [&](size_t b) -> char* {
+    char* p = (char*)base + o;
+    o += (size_t)round_up((int64_t)b, 256);
+    return p;
+  };
+  w.tri = (float4*)take((size_t)n_tris * kTriF4 * sizeof(float4));
+  w.q[0] = (SplitItem*)take((size_t)qcap * sizeof(SplitItem));
+  w.q[1] = (SplitItem*)take((size_t)qcap * sizeof(SplitItem));
+  w.qcount = (int64_t*)take(2 * sizeof(int64_t));
+  w.bytes = o;
+  return w;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t bnb_abi_version(void) { return 2; }
+
+const char* bnb_status_string(int32_t s) {
+  switch (s) {
+    case BNB_OK: return "ok";
+    case BNB_ERR_INVALID: return "invalid argument";
+    case BNB_ERR_CAPACITY: return "output or workspace capacity exceeded";
+    case BNB_ERR_CUDA: return "CUDA launch error";
+    case BNB_ERR_UNSUPPORTED: return "unsupported configuration";
+    case BNB_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+size_t bnb_bound_tuples_ws(const bnb_surface* s1, const bnb_surface* s2, const bnb_emitters* em,
+                           const bnb_bound_cfg* cfg) {
+  (void)s2;
+  if (!surface_ok(s1) || !emitters_ok(em) || !cfg || cfg->depth < 0 || cfg->depth > kMaxBaseDepth) return 0;
+  const int64_t nb = n_base_of(s1, em, cfg->depth);
+  return carve_bound_ws(nullptr, s1->n_tris, split_queue_cap(nb)).bytes;
+}
+
+int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
+                         const bnb_emitters* em, const bnb_bound_cfg* cfg, bnb_cell_bounds* out, void* ws,
+                         size_t ws_bytes, void* stream) {
+  if (!surface_ok(s1) || !emitters_ok(em) || !rec || !cfg || !out) return BNB_ERR_INVALID;
+  if (s2 != nullptr) return BNB_ERR_UNSUPPORTED;
+  if (s1->kind != BNB_REFLECT) return BNB_ERR_UNSUPPORTED;
+  if (cfg->depth < 0 || cfg->depth > kMaxBaseDepth || cfg->max_extra_split < 0 || cfg->max_extra_split > kMaxExtra ||
+      cfg->depth + cfg->max_extra_split > kMaxDepth)
+    return BNB_ERR_INVALID;
+  const int64_t nb = n_base_of(s1, em, cfg->depth);
+  if (!out->count || !out->status) return BNB_ERR_INVALID;
+  if (out->capacity < nb) return BNB_ERR_INVALID;
+  if (out->capacity > 0 && (!out->u_lo || !out->u_hi || !out->v_lo || !out->v_hi || !out->e_lo || !out->e_hi ||
+                            !out->emitter || !out->tri0 || !out->tri1 || !out->cell || !out->flags))
+    return BNB_ERR_INVALID;
+  const int64_t qcap = split_queue_cap(nb);
+  const BoundWs need = carve_bound_ws(nullptr, s1->n_tris, qcap);
+  if (ws_bytes < need.bytes || (need.bytes > 0 && (!ws || !aligned256(ws)))) return BNB_ERR_INVALID;
+  out->n_base = nb;
+  out->depth = cfg->depth;
+  out->n_emitters = em->n;
+  out->n_tris = s1->n_tris;
+  if (nb == 0) return BNB_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  BoundWs w = carve_bound_ws(ws, s1->n_tris, qcap);
+  if (launch_pack_tris(s1, w.tri, st) != cudaSuccess) return BNB_ERR_CUDA;
+  if (cudaMemsetAsync(w.qcount, 0, 2 * sizeof(int64_t), st) != cudaSuccess) return BNB_ERR_CUDA;
+  BoundParams P{};
+  P.tri = w.tri;
+  P.n_tris = s1->n_tris;
+  P.n_emitters = em->n;
+  P.ex = em->x;
+  P.ey = em->y;
+  P.ez = em->z;
+  P.ei = em->intensity;
+  for (int c = 0; c < 3; ++c) {
+    P.rp0[c] = rec->p0[c];
+    P.re1[c] = rec->e1[c];
+    P.re2[c] = rec->e2[c];
+  }
+  P.depth = cfg->depth;
+  P.max_depth = cfg->depth + cfg->max_extra_split;
+  P.irradiance = cfg->irradiance ? 1 : 0;
+  P.n_base = nb;
+  P.capacity = out->capacity;
+  P.count = out->count;
+  P.status = out->status;
+  P.u_lo = out->u_lo;
+  P.u_hi = out->u_hi;
+  P.v_lo = out->v_lo;
+  P.v_hi = out->v_hi;
+  P.e_lo = out->e_lo;
+  P.e_hi = out->e_hi;
+  P.emitter = out->emitter;
+  P.tri0 = out->tri0;
+  P.tri1 = out->tri1;
+  P.cell = out->cell;
+  P.flags = out->flags;
+  P.e_hi_min = out->e_hi_min;
+  P.q_cap = qcap;
+  P.q_out = w.q[0];
+  P.q_out_count = w.qcount + 0;
+  const bool fp64 = cfg->fp64 != 0;
+  if (launch_bound_base(P, fp64, st) != cudaSuccess) return BNB_ERR_CUDA;
+  for (int lvl = 0; lvl < cfg->max_extra_split; ++lvl) {
+    const int cur = lvl & 1, nxt = cur ^ 1;
+    if (cudaMemsetAsync(w.qcount + nxt, 0, sizeof(int64_t), st) != cudaSuccess) return BNB_ERR_CUDA;
+    P.q_out = w.q[nxt];
+    P.q_out_count = w.qcount + nxt;
+    if (launch_bound_split(P, w.q[cur], w.qcount + cur, fp64, st) != cudaSuccess) return BNB_ERR_CUDA;
+  }
+  return BNB_OK;
+}
+
+size_t bnb_build_index_ws(const bnb_cell_bounds* cells, int32_t grid_res, int64_t pre_capacity) {
+  (void)cells;
+  if (grid_res < 1 || grid_res > 4096 || pre_capacity < 0) return 0;
+  return index_ws_bytes(grid_res, pre_capacity);
+}
+
+int32_t bnb_build_index(const bnb_cell_bounds* cells, float m, int64_t pre_capacity, bnb_index* out, void* ws,
+                        size_t ws_bytes, void* stream) {
+  if (!cells || !out || !cells->count) return BNB_ERR_INVALID;
+  if (out->grid_res < 1 || out->grid_res > 4096 || !out->count || !out->status || !out->offsets) return BNB_ERR_INVALID;
+  if (out->capacity < 0 || (out->capacity > 0 && (!out->key || !out->etilde))) return BNB_ERR_INVALID;
+  if (pre_capacity < 0 || !(m >= 0.0f)) return BNB_ERR_INVALID;
+  if (cells->depth < 0 || cells->depth > kMaxBaseDepth || cells->n_base < 0) return BNB_ERR_INVALID;
+  if (cells->n_base % ((int64_t)1 << (2 * cells->depth)) != 0) return BNB_ERR_INVALID;
+  if (cells->n_base > 0 && (!cells->u_lo || !cells->u_hi || !cells->v_lo || !cells->v_hi || !cells->e_hi ||
+                            !cells->emitter || !cells->tri0 || !cells->tri1 || !cells->flags))
+    return BNB_ERR_INVALID;
+  const size_t need = index_ws_bytes(out->grid_res, pre_capacity);
+  if (ws_bytes < need || !ws || !aligned256(ws)) return BNB_ERR_INVALID;
+  return launch_build_index(cells, m, pre_capacity, out, ws, (cudaStream_t)stream) == cudaSuccess ? BNB_OK
+                                                                                                  : BNB_ERR_CUDA;
+}
+
+size_t bnb_sample_and_solve_ws(const bnb_surface* s1, int64_t n_points, int64_t worklist_capacity) {
+  if (!surface_ok(s1) || n_points < 0 || worklist_capacity < 0) return 0;
+  return sample_ws_bytes(s1->n_tris, n_points, worklist_capacity);
+}
+
+int32_t bnb_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
+                             const bnb_emitters* em, const bnb_index* index, const float* su, const float* sv,
+                             int64_t n_points, const bnb_sample_cfg* cfg, float* E_out, bnb_sample_stats* stats,
+                             void* ws, size_t ws_bytes, void* stream) {
+  if (!surface_ok(s1) || !emitters_ok(em) || !rec || !index || !cfg || !stats) return BNB_ERR_INVALID;
+  if (s2 != nullptr || s1->kind != BNB_REFLECT) return BNB_ERR_UNSUPPORTED;
+  if (n_points < 0 || (n_points > 0 && (!su || !sv || !E_out))) return BNB_ERR_INVALID;
+  if (!stats->counters || !stats->status || !index->offsets) return BNB_ERR_INVALID;
+  if (index->grid_res < 1 || index->grid_res > 4096) return BNB_ERR_INVALID;
+  if (cfg->worklist_capacity < 0 || cfg->newton_iters < 0 || cfg->newton_iters > 64 || cfg->polish_iters < 0 ||
+      cfg->polish_iters > 8 || !(cfg->gamma >= 0.0f) || !(cfg->tol > 0.0f))
+    return BNB_ERR_INVALID;
+  const size_t need = sample_ws_bytes(s1->n_tris, n_points, cfg->worklist_capacity);
+  if (ws_bytes < need || !ws || !aligned256(ws)) return BNB_ERR_INVALID;
+  return launch_sample_and_solve(s1, rec, em, index, su, sv, n_points, cfg, E_out, stats, ws,
+                                 (cudaStream_t)stream) == cudaSuccess
+             ? BNB_OK
+             : BNB_ERR_CUDA;
+}
+
+}  // extern "C"

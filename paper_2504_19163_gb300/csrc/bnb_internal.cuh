@@ -1,0 +1,55 @@
+// Internal declarations shared by the libbnb translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bnb.h"
+
+namespace bnb {
+
+constexpr int kMaxDepth = 15;  // depth + extra splits: 2 bits per level in a uint32 cell id
+
+// Packed triangle: p0, p1, p2, n0, n1, n2 as 18 floats in 5 float4 (80 bytes, 16-byte aligned).
+constexpr int kTriF4 = 5;
+
+struct SplitItem {
+  int32_t emitter, tri;
+  uint32_t cell;
+  int32_t depth;
+};
+
+struct BoundParams {
+  const float4* tri;  // packed triangles
+  int32_t n_tris, n_emitters;
+  const float *ex, *ey, *ez, *ei;
+  float rp0[3], re1[3], re2[3];
+  int32_t depth, max_depth, irradiance;
+  int64_t n_base;
+  // outputs
+  int64_t capacity;
+  int64_t* count;
+  int32_t* status;
+  float *u_lo, *u_hi, *v_lo, *v_hi, *e_lo, *e_hi;
+  int32_t *emitter, *tri0, *tri1;
+  uint32_t *cell, *flags;
+  float* e_hi_min;  // optional
+  // split queues
+  SplitItem* q_out;
+  int64_t* q_out_count;
+  int64_t q_cap;
+};
+
+// Launchers (bnb_bound.cu)
+cudaError_t launch_pack_tris(const bnb_surface* s, float4* out, cudaStream_t st);
+cudaError_t launch_bound_base(const BoundParams& p, bool fp64, cudaStream_t st);
+cudaError_t launch_bound_split(const BoundParams& p, const SplitItem* q_in, const int64_t* q_in_count, bool fp64,
+                               cudaStream_t st);
+
+// Scan (bnb_index.cu): exclusive prefix sum of n int64 values into out[0..n], out[n] = total.
+size_t scan_ws_bytes(int64_t n);
+cudaError_t launch_exclusive_scan(const int64_t* in, int64_t* out, int64_t n, void* ws, cudaStream_t st);
+
+__host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace bnb

@@ -295,3 +295,49 @@ def config(name: str, **kw) -> Scene:
         su, sv = shading_points(kw.get("points", 16), kw.get("points", 16), 3)
         return Scene(name, s1, None, rec, em, kw.get("depth", 1), su, sv)
     raise KeyError(name)
+
+
+def synthetic_cell_records(n_tuples: int, depth: int, n_tris: int, n_emitters: int, n_overflow: int, seed: int,
+                           grid_res: int = 512):
+    """Seeded synthetic bound records (float32 SoA) in the record layout of the bound pass:
+    4^depth contiguous base records per tuple, then `n_overflow` extra records that repeat
+    tuples of the base part (as split children do).  Boxes cluster per tuple; some edges sit
+    exactly on grid lines, at 0 or at 1; some records are culled; some bounds are +inf."""
+    rng = np.random.default_rng(seed)
+    cpt = 4 ** depth
+    n_base = n_tuples * cpt
+    n = n_base + n_overflow
+    em = np.empty(n, np.int32)
+    t0 = np.empty(n, np.int32)
+    tup_e = rng.integers(0, n_emitters, n_tuples)
+    tup_t = rng.permutation(n_tris)[:n_tuples] if n_tuples <= n_tris else rng.integers(0, n_tris, n_tuples)
+    em[:n_base] = np.repeat(tup_e, cpt)
+    t0[:n_base] = np.repeat(tup_t, cpt)
+    pick = rng.integers(0, n_tuples, n_overflow)
+    em[n_base:] = tup_e[pick]
+    t0[n_base:] = tup_t[pick]
+    centre = rng.uniform(-0.05, 1.05, (n_tuples, 2))
+    c = np.concatenate([np.repeat(centre, cpt, axis=0), centre[pick]], axis=0)
+    c = c + rng.normal(0, 0.004, c.shape)
+    half = rng.exponential(0.002, (n, 2)) + rng.choice([0.0, 0.02], (n, 2), p=[0.97, 0.03])
+    lo = c - half
+    hi = c + half
+    # snap some edges onto grid lines and onto the region boundary
+    snap = rng.random((n, 2)) < 0.05
+    lo[snap] = np.floor(lo[snap] * grid_res) / grid_res
+    snap = rng.random((n, 2)) < 0.05
+    hi[snap] = np.ceil(hi[snap] * grid_res) / grid_res
+    lo = np.clip(lo, 0.0, 1.0).astype(np.float32)
+    hi = np.clip(hi, 0.0, 1.0).astype(np.float32)
+    flags = np.full(n, 1, np.uint32)
+    empty = (lo > hi).any(axis=1)
+    flags[empty] = 8
+    cull = rng.random(n) < 0.05
+    flags[cull] = 4
+    e_hi = rng.lognormal(0.0, 1.0, n).astype(np.float32)
+    e_hi[rng.random(n) < 0.01] = np.inf
+    depths = np.concatenate([np.full(n_base, depth), np.full(n_overflow, depth + 1)]).astype(np.uint32)
+    flags = flags | (depths << np.uint32(24))
+    return dict(u_lo=lo[:, 0], u_hi=hi[:, 0], v_lo=lo[:, 1], v_hi=hi[:, 1], e_lo=np.zeros(n, np.float32),
+                e_hi=e_hi, emitter=em, tri0=t0, tri1=np.full(n, -1, np.int32),
+                cell=np.zeros(n, np.uint32), flags=flags, n_base=n_base, depth=depth)

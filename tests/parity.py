@@ -1,0 +1,105 @@
+"""Comparison rules between the CUDA path and the FP64 oracle (shared by the GPU tests).
+
+The bound pass runs in float32 with rigorous outward rounding, so its results differ from the
+oracle's float64 values by the kernel's own certified error, and only in the safe direction:
+* boxes: GPU lo <= oracle lo + 1e-12 and GPU hi >= oracle hi - 1e-12 for every cell (zero
+  containment violations), widened by at most BOX_TOL32 texture units;
+* irradiance: the kernel reports [e_hi_min, e_hi], a certified enclosure of the exact-arithmetic
+  Bernstein bound; the oracle's E_hi must lie inside it (relative slack 1e-6 for the float32
+  vs float64 chord coefficients) for every finite cell, and the enclosure's width (the price of
+  float32) is reported and bounded at the median and 99th percentile;
+* the float64 mode stores float32 records, so it must agree to 2 float32 ulps.
+Integer decisions taken in float (split, cull, fold) must agree except inside the ambiguity
+bands: denominator coefficients within Q_COND of zero relative to the largest, and fold flags
+where the oracle's M condition is below M_COND (GPU only on the conservative side).
+"""
+import numpy as np
+
+BOX_TOL32 = 1e-4
+ENCL_SLACK = 1e-6
+M_COND = 1e-3
+Q_COND = 1e-10
+ULP2 = 2.0 ** -22
+FLAG_MASK = 0xFF & ~64  # QSIGN_FP64 is a GPU-only diagnostic
+
+
+def depth_of(flags):
+    return (np.asarray(flags).astype(np.int64) >> 24) & 63
+
+
+def compare_bounds(g, o, fp64=False):
+    """g: GPU records (dict of arrays), o: oracle records (structured array).  Returns a report."""
+    gd = depth_of(g["flags"])
+    od = depth_of(o["flags"])
+    gkey = {(int(e), int(t), int(c), int(d)): i for i, (e, t, c, d) in
+            enumerate(zip(g["emitter"], g["tri0"], g["cell"], gd))}
+    okey = {(int(e), int(t), int(c), int(d)): i for i, (e, t, c, d) in
+            enumerate(zip(o["emitter"], o["tri0"], o["cell"], od))}
+    rep = dict(n=len(okey), missing=0, extra=0, flag_mismatch=0, flag_ambiguous=0, box_outside=0,
+               box_widen=[], e_checked=0, encl_viol=0, e_below=0, slack=[], e_rel=[], qsign_fp64=0, live=0,
+               fp64=fp64)
+    has_min = "e_hi_min" in g
+    for k, oi in okey.items():
+        gi = gkey.get(k)
+        if gi is None:
+            if o["q_cond"][oi] < Q_COND or (o["flags"][oi] & 2) == 0:
+                rep["missing"] += 1
+            continue
+        gf = int(g["flags"][gi]) & FLAG_MASK
+        of = int(o["flags"][oi]) & 0xFF
+        if int(g["flags"][gi]) & 64:
+            rep["qsign_fp64"] += 1
+        if gf != of:
+            amb = o["q_cond"][oi] < Q_COND or ((gf & 16) and not (of & 16) and o["m_cond"][oi] < M_COND
+                                                and (gf & ~16) == (of & ~16))
+            rep["flag_ambiguous" if amb else "flag_mismatch"] += 1
+            continue
+        if not (of & 1):
+            continue
+        rep["live"] += 1
+        for a in ("u", "v"):
+            glo, ghi = float(g[a + "_lo"][gi]), float(g[a + "_hi"][gi])
+            olo, ohi = float(o[a + "_lo"][oi]), float(o[a + "_hi"][oi])
+            if glo > olo + 1e-12 or ghi < ohi - 1e-12:
+                rep["box_outside"] += 1
+            rep["box_widen"].append(max(olo - glo, ghi - ohi))
+        oe, ge = float(o["e_hi"][oi]), float(g["e_hi"][gi])
+        if np.isfinite(oe) and np.isfinite(ge):
+            rep["e_checked"] += 1
+            rep["e_rel"].append((ge - oe) / oe)
+            if ge < oe * (1 - ENCL_SLACK):
+                rep["e_below"] += 1
+            if has_min:
+                gm = float(g["e_hi_min"][gi])
+                if oe < gm * (1 - ENCL_SLACK) or oe > ge * (1 + ENCL_SLACK):
+                    rep["encl_viol"] += 1
+                rep["slack"].append(ge / max(gm, 1e-300) - 1.0)
+        elif not np.isfinite(oe) and np.isfinite(ge):
+            rep["e_below"] += 1
+    for k in gkey:
+        if k not in okey:
+            rep["extra"] += 1
+    w = np.array(rep.pop("box_widen") or [0.0])
+    sl = np.array(rep.pop("slack") or [0.0])
+    er = np.array(rep.pop("e_rel") or [0.0])
+    rep.update(box_widen_max=float(w.max()), box_widen_p99=float(np.percentile(w, 99)),
+               slack_median=float(np.median(sl)), slack_p99=float(np.percentile(sl, 99)), slack_max=float(sl.max()),
+               e_rel_median=float(np.median(er)), e_rel_max=float(np.abs(er).max()))
+    return rep
+
+
+def assert_bounds_parity(rep, allow_ambiguous_frac=1e-3, slack_median=2e-4, slack_p99=5e-3):
+    assert rep["missing"] == 0, rep
+    assert rep["extra"] <= 4 * rep["flag_ambiguous"], rep
+    assert rep["flag_mismatch"] == 0, rep
+    assert rep["flag_ambiguous"] <= max(2, allow_ambiguous_frac * rep["n"]), rep
+    assert rep["box_outside"] == 0, rep
+    assert rep["e_below"] == 0, rep
+    if rep["fp64"]:
+        assert rep["box_widen_max"] <= ULP2, rep
+        assert rep["e_rel_max"] <= ULP2, rep
+    else:
+        assert rep["box_widen_max"] <= BOX_TOL32, rep
+        assert rep["encl_viol"] == 0, rep
+        assert rep["slack_median"] <= slack_median and rep["slack_p99"] <= slack_p99, rep
+    assert rep["e_checked"] > 0.9 * rep["live"], rep

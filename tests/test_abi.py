@@ -1,0 +1,94 @@
+"""The C-ABI library loads on a machine without a GPU, exports every function that
+include/*.h declares, and rejects bad arguments on the host (no launch)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bnb():
+    from paper_2504_19163_gb300 import build as B
+    B.build()
+    from paper_2504_19163_gb300 import bnb as M
+    return M
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(bnb_[a-z0-9_]+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(bnb):
+    names = declared_functions()
+    assert {"bnb_bound_tuples", "bnb_build_index", "bnb_sample_and_solve"} <= names
+    L = C.CDLL(bnb.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert set(bnb.EXPORTS) == names
+
+
+def test_status_strings_and_version(bnb):
+    assert bnb.bnb_status_string(0) == "ok"
+    assert "capacity" in bnb.bnb_status_string(-2)
+    assert bnb.lib().bnb_abi_version() == 2
+
+
+def test_workspace_queries_are_host_only(bnb):
+    s = bnb.bnb_surface()
+    s.n_tris = 2048
+    s.n_verts = 33 * 33
+    for f in ("px", "py", "pz", "nx", "ny", "nz", "i0", "i1", "i2"):
+        setattr(s, f, 4096)  # dummy non-null pointers: the queries never dereference them
+    em = bnb.bnb_emitters(1, 4096, 4096, 4096, 4096)
+    cfg = bnb.bnb_bound_cfg(2, 4, 1, 0)
+    wb = bnb.bnb_bound_tuples_ws(C.byref(s), None, C.byref(em), C.byref(cfg))
+    assert wb >= 2048 * 80
+    assert bnb.bnb_build_index_ws(None, 512, 1000) > 512 * 512 * 8 * 3
+    assert bnb.bnb_build_index_ws(None, 0, 1000) == 0
+    assert bnb.bnb_sample_and_solve_ws(C.byref(s), 4096, 10000) > 10000 * 24
+    bad = bnb.bnb_bound_cfg(11, 0, 1, 0)
+    assert bnb.bnb_bound_tuples_ws(C.byref(s), None, C.byref(em), C.byref(bad)) == 0
+
+
+def test_invalid_arguments_rejected_before_launch(bnb):
+    s = bnb.bnb_surface()
+    s.n_tris = 8
+    s.n_verts = 9
+    rec = bnb.bnb_receiver()
+    em = bnb.bnb_emitters(1, None, None, None, None)  # n > 0 with NULL arrays
+    cfg = bnb.bnb_bound_cfg(1, 0, 1, 0)
+    out = bnb.bnb_cell_bounds()
+    rc = bnb.bnb_bound_tuples(C.byref(s), None, C.byref(rec), C.byref(em), C.byref(cfg), C.byref(out), None, 0, None)
+    assert rc == bnb.BNB_ERR_INVALID
+    # a second specular surface is not supported by this build
+    rc = bnb.bnb_bound_tuples(C.byref(s), C.byref(s), C.byref(rec), C.byref(em), C.byref(cfg), C.byref(out), None,
+                              0, None)
+    assert rc in (bnb.BNB_ERR_INVALID, bnb.BNB_ERR_UNSUPPORTED)
+    idx = bnb.bnb_index()
+    assert bnb.bnb_build_index(None, 1.0, 0, C.byref(idx), None, 0, None) == bnb.BNB_ERR_INVALID
+    cells = bnb.bnb_cell_bounds()
+    assert bnb.bnb_build_index(C.byref(cells), 1.0, 0, C.byref(idx), None, 0, None) == bnb.BNB_ERR_INVALID
+    scfg = bnb.bnb_sample_cfg(1.0, 0, 100, 2, 1e-5, 0)  # newton_iters > 64
+    stats = bnb.bnb_sample_stats()
+    rc = bnb.bnb_sample_and_solve(C.byref(s), None, C.byref(rec), C.byref(em), C.byref(idx), None, None, 0,
+                                  C.byref(scfg), None, C.byref(stats), None, 0, None)
+    assert rc == bnb.BNB_ERR_INVALID
+
+
+def test_no_oracle_import_in_library_path():
+    """The product path never imports or links the oracle."""
+    pkg = os.path.join(ROOT, "paper_2504_19163_gb300")
+    for f in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if f.endswith((".py", ".cu", ".cuh", ".h")):
+            src = open(f).read()
+            assert "import oracle" not in src and "from oracle" not in src and "liboracle" not in src, f

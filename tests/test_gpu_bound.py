@@ -1,0 +1,125 @@
+"""GPU parity of the bound pass (bnb_bound_tuples) against the FP64 oracle."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import parity
+from paper_2504_19163_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2504_19163_gb300 import build
+    build.build()
+    from paper_2504_19163_gb300 import bnb
+    assert torch.cuda.is_available()
+    return bnb
+
+
+def run_gpu(B, sc, depth=None, fp64=False, max_extra_split=4, irradiance=True):
+    ds = B.DeviceScene(sc)
+    cb = B.bound_tuples(ds, sc.depth if depth is None else depth, max_extra_split=max_extra_split,
+                        irradiance=irradiance, fp64=fp64, with_e_hi_min=True)
+    torch.cuda.synchronize()
+    assert int(cb.status.item()) == 0
+    return cb, cb.to_numpy()
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_mirror32_parity(B, orc, fp64):
+    """32^2 mirror, point light, depth 2: every cell against the oracle."""
+    sc = S.config("mirror32")
+    cb, g = run_gpu(B, sc, fp64=fp64)
+    o = orc.bound(sc, n_threads=os.cpu_count())
+    assert cb.c.n_base == 2048 * 16
+    rep = parity.compare_bounds(g, o, fp64=fp64)
+    print(rep)
+    parity.assert_bounds_parity(rep)
+
+
+@pytest.mark.parametrize("depth", [0, 1, 3])
+def test_ragged_sizes_and_depths(B, orc, depth):
+    """5x5 mesh (50 triangles), 3 emitters: tuple count not a multiple of any block size."""
+    sc = S.config("tiny", n=5, depth=depth, lights=[(0.1, -0.05, 2.0), (-0.4, 0.3, 1.7), (0.5, 0.5, 2.5)])
+    cb, g = run_gpu(B, sc)
+    o = orc.bound(sc)
+    rep = parity.compare_bounds(g, o)
+    parity.assert_bounds_parity(rep)
+    # base slots are in work order
+    n_base = cb.c.n_base
+    w = np.arange(n_base)
+    per = 4 ** depth
+    assert np.array_equal(g["tri0"][:n_base], (w // per) % 50)
+    assert np.array_equal(g["emitter"][:n_base], w // (per * 50))
+    assert np.array_equal(g["cell"][:n_base], (w % per).astype(np.uint32))
+
+
+def test_flat_mirror_boxes_are_corner_images(B, orc):
+    """Affine map: the box equals the corner images' box (oracle exact), GPU within BOX_TOL32."""
+    sc = S.config("flat", n=4, depth=2)
+    cb, g = run_gpu(B, sc)
+    o = orc.bound(sc)
+    rep = parity.compare_bounds(g, o)
+    parity.assert_bounds_parity(rep)
+    assert rep["live"] == len(o)
+
+
+def test_receiver_behind_all_culled(B):
+    sc = S.config("mirror32", receiver_z=-1.0)
+    cb, g = run_gpu(B, sc)
+    assert not np.any(g["flags"] & B.LIVE)
+    assert np.all((g["flags"] & (B.CULL_BEHIND | B.SPLIT)) != 0)
+
+
+def test_position_only_mode(B, orc):
+    sc = S.config("mirror32")
+    cb, g = run_gpu(B, sc, irradiance=False)
+    o = orc.bound(sc, irradiance=False)
+    live = (g["flags"] & B.LIVE) != 0
+    assert np.all(np.isinf(g["e_hi"][live]))
+    rep = parity.compare_bounds(g, o)
+    assert rep["missing"] == 0 and rep["flag_mismatch"] == 0 and rep["box_outside"] == 0
+    assert rep["box_widen_max"] <= parity.BOX_TOL32
+
+
+def test_no_emitters_is_empty(B):
+    sc = S.config("mirror32")
+    sc.emitters = S.point_emitters(np.zeros((0, 3)), 1.0)
+    ds = B.DeviceScene(sc)
+    cb = B.bound_tuples(ds, 2)
+    torch.cuda.synchronize()
+    assert cb.c.n_base == 0 and int(cb.count.item()) == 0
+    assert int(cb.status.item()) == 0
+
+
+def test_full_size_area_light_sampled(B, orc):
+    """256^2 noisy mirror, 16 area-light samples, depth 3 (134M cells) in one launch; 20000
+    seeded base cells compared with the oracle slot by slot."""
+    sc = S.config("mirror256")
+    ds = B.DeviceScene(sc)
+    cb = B.bound_tuples(ds, sc.depth, with_e_hi_min=True)
+    torch.cuda.synchronize()
+    assert int(cb.status.item()) == 0
+    n_base = cb.c.n_base
+    assert n_base == 16 * 131072 * 64
+    rng = np.random.default_rng(99)
+    work = np.sort(rng.choice(n_base, 20000, replace=False))
+    wt = torch.as_tensor(work, device="cuda")
+    g = {k: getattr(cb, k)[wt].cpu().numpy() for k in
+         ("u_lo", "u_hi", "v_lo", "v_hi", "e_lo", "e_hi", "emitter", "tri0", "tri1", "e_hi_min")}
+    g["cell"] = cb.cell[wt].cpu().numpy().view(np.uint32)
+    g["flags"] = cb.flags[wt].cpu().numpy().view(np.uint32)
+    o = orc.bound(sc, work=work, n_threads=os.cpu_count())
+    # base records only (children of split cells follow their parent in the oracle's output);
+    # they come out in work order, like the GPU slots
+    o_base = o[parity.depth_of(o["flags"]) == sc.depth]
+    assert len(o_base) == len(work)
+    assert np.array_equal(o_base["tri0"], g["tri0"]) and np.array_equal(o_base["emitter"], g["emitter"])
+    assert np.array_equal(o_base["cell"], g["cell"])
+    rep = parity.compare_bounds(g, o_base)
+    print(rep)
+    parity.assert_bounds_parity(rep)
