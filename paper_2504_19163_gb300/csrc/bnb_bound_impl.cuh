@@ -40,14 +40,22 @@ namespace bnb {
 
 // ------------------------------------------------------------------ helpers
 template <typename T>
-__device__ __forceinline__ T cup(double x) {  // constant rounded up into T (x >= 0)
+__host__ __device__ constexpr T cup(double x) {  // constant rounded up into T (x >= 0)
   return (T)(x * (1.0 + 4.0 * FP<T>::u));
 }
 
 template <typename T>
-__device__ __forceinline__ T tiny_pos() {
+__host__ __device__ constexpr T tiny_pos() {
   return sizeof(T) == 4 ? (T)1e-30 : (T)1e-290;
 }
+
+// gamma_k and multinomials as compile-time constants.
+template <typename T, int K>
+constexpr T GAM = gam<T>(K);
+template <typename T, int N, int I>
+constexpr T MULT = (T)mult_c(N, I);
+template <typename T, int N, int I>
+constexpr T MULTUP = cup<T>(mult_c(N, I));
 
 __device__ __forceinline__ void load_tri(const float4* __restrict__ tri, int t, float (&p)[3][3], float (&n)[3][3]) {
   const float4* b = tri + (int64_t)t * kTriF4;
@@ -136,7 +144,7 @@ template <typename T, bool DERIV>
 __device__ __forceinline__ void make_leaves(const T (&p)[3][3], const T (&n)[3][3], const T (&x0)[3], const T (&cu)[3],
                                             const T (&cv)[3], Leaves<T>& L) {
   using F = FP<T>;
-  const T g3 = gam<T>(3), g4 = gam<T>(4), uu = (T)FP<T>::u, up2 = (T)(1.0 + 2.0 * FP<T>::u);
+  constexpr T g3 = GAM<T, 3>, g4 = GAM<T, 4>, uu = (T)FP<T>::u, up2 = (T)(1.0 + 2.0 * FP<T>::u);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const T e1 = p[1][c] - p[0][c], e2 = p[2][c] - p[0][c];
@@ -196,8 +204,10 @@ __device__ __forceinline__ void scale2(TP<T, N>& p) {  // exact doubling
 template <typename T, int N>
 __device__ __forceinline__ void add_const(TP<T, N>& p, T c, T cerr) {
   using F = FP<T>;
-#pragma unroll
-  for (int i = 0; i < nc(N); ++i) p.c[i] = F::fma_rn(c, (T)mult_c(N, i), p.c[i]);
+  static_for<nc(N)>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    p.c[i] = F::fma_rn(c, MULT<T, N, i>, p.c[i]);
+  });
   const T mag = F::add_ru(F::add_ru(fabs(c), p.B), p.E);
   p.E = F::add_ru(F::add_ru(p.E, cerr), F::mul_ru((T)FP<T>::u, mag));
   p.B = F::add_ru(F::add_ru(p.B, fabs(c)), cerr);
@@ -326,7 +336,7 @@ __device__ __forceinline__ TP<T, 0> cross_comp(T a1, T b2, T a2, T b1) {  // a1*
   using F = FP<T>;
   const T v = F::fma_rn(a1, b2, -(a2 * b1));
   const T mag = F::fma_ru(fabs(a1), fabs(b2), F::mul_ru(fabs(a2), fabs(b1)));
-  return tconst<T>(v, F::mul_ru(gam<T>(2), mag));
+  return tconst<T>(v, F::mul_ru(GAM<T, 2>, mag));
 }
 
 template <typename T>
@@ -338,28 +348,6 @@ __device__ __forceinline__ TP<T, 3> q_of(const Dir<T>& D, const T (&e1)[3], cons
 #pragma unroll
   for (int c = 0; c < 3; ++c) mac(Q, D.DT[c], g[c]);
   return Q;
-}
-
-// Float64 recheck of the denominator sign (decides whether the cell must be split).
-static __device__ __noinline__ int q_sign_fp64(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0f)[3],
-                                        const float (&e1f)[3], const float (&e2f)[3], uint32_t id, int depth) {
-  double p[3][3], n[3][3], x0[3], e1[3], e2[3], cu[3], cv[3];
-  for (int a = 0; a < 3; ++a) {
-    for (int b = 0; b < 3; ++b) {
-      p[a][b] = pf[a][b];
-      n[a][b] = nf[a][b];
-    }
-    x0[a] = x0f[a];
-    e1[a] = e1f[a];
-    e2[a] = e2f[a];
-  }
-  cell_corners<double>(id, depth, cu, cv);
-  Leaves<double> L;
-  make_leaves<double, false>(p, n, x0, cu, cv, L);
-  Dir<double> D;
-  reflect_dir<double, false>(L, D);
-  TP<double, 3> Q = q_of<double>(D, e1, e2);
-  return cert_sign(Q);
 }
 
 // ------------------------------------------------------------------ ratio helpers
@@ -381,9 +369,9 @@ __device__ __forceinline__ T widen_hi(T x) {
 }
 
 // Interval of coefficient i of a tracked polynomial (scaled form).
-template <typename T, int N>
-__device__ __forceinline__ void coef_iv(const TP<T, N>& p, int i, T& lo, T& hi) {
-  const T C = cup<T>(mult_c(N, i));
+template <int i, typename T, int N>
+__device__ __forceinline__ void coef_iv(const TP<T, N>& p, T& lo, T& hi) {
+  constexpr T C = MULTUP<T, N, i>;
   lo = FP<T>::fma_rd(-p.E, C, p.c[i]);
   hi = FP<T>::fma_ru(p.E, C, p.c[i]);
 }
@@ -395,6 +383,7 @@ struct Term2 {
   static constexpr int gg2 = g2_of(M + 2, G) - g2_of(2, Bi);
   static constexpr bool valid = gg1 >= 0 && gg2 >= 0 && gg1 + gg2 <= M;
   static constexpr int a = valid ? idx_of(M, gg1, gg2) : 0;
+  static constexpr double c2 = mult_c(2, Bi);
 };
 
 template <typename T, int M, int G, int... Bi>
@@ -406,7 +395,7 @@ __device__ __forceinline__ void coef3(const T* __restrict__ p, const T* __restri
   mm = T(0);
   ((Term2<M, G, Bi>::valid ? (n0 = FP<T>::fma_rn(f0[Bi], p[Term2<M, G, Bi>::a], n0),
                               n1 = FP<T>::fma_rn(f1[Bi], p[Term2<M, G, Bi>::a], n1),
-                              mm = FP<T>::fma_rn((T)mult_c(2, Bi), m[Term2<M, G, Bi>::a], mm), 0)
+                              mm = FP<T>::fma_rn((T)Term2<M, G, Bi>::c2, m[Term2<M, G, Bi>::a], mm), 0)
                            : 0),
    ...);
 }
@@ -424,7 +413,7 @@ __device__ __forceinline__ void irr_step(const TP<T, 9>& Q3, const T (&F0)[6], c
                                          IrrAcc<T>& acc) {
   T n0, n1, mm;
   coef3<T, 9, G>(Q3.c, F0, F1, M.c, n0, n1, mm, std::make_integer_sequence<int, 6>{});
-  const T C = cup<T>(mult_c(11, G));
+  constexpr T C = MULTUP<T, 11, G>;
   const T ml = FP<T>::fma_rd(-acc.EM, C, mm), mh = FP<T>::fma_ru(acc.EM, C, mm);
   if (!(ml > tiny_pos<T>())) acc.unbounded = true;
   const T rl = FP<T>::rcp_rn(ml), rh = FP<T>::rcp_rn(mh);
@@ -530,8 +519,10 @@ __device__ void recip01(const TP<T, 4>& P4, const TP<T, 4>& Q4, int sp, T& lo, T
   hi = T(1);
   if (sp == 0) return;  // universal set
   T mn = F::inf(), mx = -F::inf();
-  for (int i = 0; i < nc(4); ++i) {
-    const T C = cup<T>(mult_c(4, i));
+  bool bad = false;
+  static_for<nc(4)>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr T C = MULTUP<T, 4, i>;
     T pl = F::fma_rd(-P4.E, C, P4.c[i]), ph = F::fma_ru(P4.E, C, P4.c[i]);
     T ql = F::fma_rd(-Q4.E, C, Q4.c[i]), qh = F::fma_ru(Q4.E, C, Q4.c[i]);
     if (sp < 0) {  // divide by the positive -p
@@ -542,10 +533,11 @@ __device__ void recip01(const TP<T, 4>& P4, const TP<T, 4>& Q4, int sp, T& lo, T
       ql = -qh;
       qh = -t;
     }
-    if (!(pl > tiny_pos<T>())) return;
+    if (!(pl > tiny_pos<T>())) bad = true;
     mn = fmin(mn, F::div_rd(ql, ql >= T(0) ? ph : pl));
     mx = fmax(mx, F::div_ru(qh, qh >= T(0) ? pl : ph));
-  }
+  });
+  if (bad) return;  // universal set
   // r = q/p in [mn, mx]; p/q = 1/r
   T L = T(1), H = T(0);
   auto add = [&](T a, T b) {
@@ -567,8 +559,12 @@ __device__ void recip01(const TP<T, 4>& P4, const TP<T, 4>& Q4, int sp, T& lo, T
 }
 
 // ------------------------------------------------------------------ one cell
+static __device__ __noinline__ void process_cell_fp64(const BoundParams& P, int e, int t, uint32_t id, int depth,
+                                                      int64_t slot);
+
 template <typename T>
-__device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t, uint32_t id, int depth, int64_t slot) {
+__device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t, uint32_t id, int depth, int64_t slot,
+                                             uint32_t extra_flags = 0) {
   using F = FP<T>;
   float pf[3][3], nf[3][3];
   load_tri(P.tri, t, pf, nf);
@@ -587,7 +583,7 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     e2[a] = (T)P.re2[a];
     rp0[a] = (T)P.rp0[a];
   }
-  const uint32_t dflag = (uint32_t)depth << BNB_CELL_DEPTH_SHIFT;
+  const uint32_t dflag = ((uint32_t)depth << BNB_CELL_DEPTH_SHIFT) | extra_flags;
   T cu[3], cv[3];
   cell_corners<T>(id, depth, cu, cv);
 
@@ -630,18 +626,20 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
   TP<T, 3> Q = q_of<T>(D, e1, e2);
   renorm(Q);
   uint32_t flags = dflag;
-  int sq = cert_sign(Q);
-  if (sq == 0) {
-    if constexpr (sizeof(T) == 4) {
-      sq = q_sign_fp64(pf, nf, x0f, P.re1, P.re2, id, depth);
-      flags |= BNB_CELL_QSIGN_FP64;
+  const int sq = cert_sign(Q);
+  if constexpr (sizeof(T) == 4) {
+    // The float32 intervals cannot decide the denominator's sign: the split decision, the
+    // reciprocal rule and the bounds of this cell are taken in float64 (flag QSIGN_FP64).
+    if (sq == 0) {
+      process_cell_fp64(P, e, t, id, depth, slot);
+      return;
     }
   }
   // Receiver-side linear terms: W = x1 - p', h_u = e2 x W, h_v = W x e1 and their derivatives.
   TP<T, 1> hu[3], hv[3];
   TP<T, 0> Dhu[2][3], Dhv[2][3];
   auto build_h = [&](T ou, T ov) {
-    const T g2e = gam<T>(2), uu = (T)FP<T>::u;
+    constexpr T g2e = GAM<T, 2>, uu = (T)FP<T>::u;
     TP<T, 1> W[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -778,14 +776,14 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     TP<T, 4> Q4;
     elevate(Q4, Q);
     T umn = F::inf(), umx = -F::inf(), vmn = F::inf(), vmx = -F::inf();
-#pragma unroll
-    for (int i = 0; i < nc(4); ++i) {
+    static_for<nc(4)>([&](auto I) {
+      constexpr int i = decltype(I)::value;
       T ql, qh, al, ah, bl, bh;
-      coef_iv(Q4, i, ql, qh);
-      coef_iv(A, i, al, ah);
-      coef_iv(B, i, bl, bh);
-      // Q > 0 is certified (float32 or float64); a float32 interval reaching down to 0 makes
-      // the ratio unbounded on the side of the numerator's sign only.
+      coef_iv<i>(Q4, ql, qh);
+      coef_iv<i>(A, al, ah);
+      coef_iv<i>(B, bl, bh);
+      // Q > 0 is certified; a float32 interval reaching down to 0 makes the ratio unbounded
+      // on the side of the numerator's sign only.
       const bool open = !(ql > tiny_pos<T>());
       const T rl = open ? F::inf() : F::rcp_rn(ql), rh = F::rcp_rn(qh);
       ratio_acc(al, ah, rl, rh, umn, umx);
@@ -796,7 +794,7 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
         if (bl == T(0)) vmn = fmin(vmn, T(0));
         if (bh == T(0)) vmx = fmax(vmx, T(0));
       }
-    }
+    });
     ul = F::add_rd(uc, widen_lo(umn));
     uh = F::add_ru(uc, widen_hi(umx));
     vl = F::add_rd(vc, widen_lo(vmn));
@@ -856,12 +854,12 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
   for (int c = 0; c < 3; ++c) mac(S, L.D0[c], L.D0[c]);
   renorm(S);
   T sl = F::inf(), sh = T(0);
-#pragma unroll
-  for (int i = 0; i < nc(2); ++i) {
-    const T cl = S.c[i] / (T)mult_c(2, i);  // exact: C in {1, 2}
+  static_for<nc(2)>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const T cl = S.c[i] * (T)(1.0 / mult_c(2, i));  // exact: C in {1, 2}
     sl = fmin(sl, F::add_rd(cl, -S.E));
     sh = fmax(sh, F::add_ru(cl, S.E));
-  }
+  });
   if (!(sl > tiny_pos<T>())) {
     put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_FOLD);
     return;
@@ -874,17 +872,17 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
   {
     const T c0 = cb + dlo, c1 = cb + dhi;
     const T uu = (T)FP<T>::u;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      const T one = (T)mult_c(2, i);
+    static_for<6>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr T one = MULT<T, 2, i>;
       F0[i] = F::fma_rn(ca, S.c[i], c0 * one);
       F1[i] = F::fma_rn(ca, S.c[i], c1 * one);
-    }
+    });
     const T as = F::mul_ru(fabs(ca), F::add_ru(S.B, S.E));
     FB = F::add_ru(F::mul_ru(fabs(ca), S.B), F::mul_ru(fmax(fabs(c0), fabs(c1)), (T)(1.0 + 2.0 * FP<T>::u)));
     const T base = F::mul_ru(fabs(ca), S.E);
-    FE0 = F::add_ru(F::add_ru(base, F::mul_ru(uu, fabs(c0))), F::mul_ru(gam<T>(2), F::add_ru(as, fabs(c0))));
-    FE1 = F::add_ru(F::add_ru(base, F::mul_ru(uu, fabs(c1))), F::mul_ru(gam<T>(2), F::add_ru(as, fabs(c1))));
+    FE0 = F::add_ru(F::add_ru(base, F::mul_ru(uu, fabs(c0))), F::mul_ru(GAM<T, 2>, F::add_ru(as, fabs(c0))));
+    FE1 = F::add_ru(F::add_ru(base, F::mul_ru(uu, fabs(c1))), F::mul_ru(GAM<T, 2>, F::add_ru(as, fabs(c1))));
   }
   // Q^3 (Q > 0 after normalization).
   TP<T, 9> Q3;
@@ -904,15 +902,15 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
   acc.unbounded = false;
   {
     T rB = T(0), rE = T(0);
-    track_mac<T>(rB, rE, Q3.B, Q3.E, FB, FE0, 6);
+    track_mac<6>(rB, rE, Q3.B, Q3.E, FB, FE0);
     acc.EN0 = rE;
     rB = T(0);
     rE = T(0);
-    track_mac<T>(rB, rE, Q3.B, Q3.E, FB, FE1, 6);
+    track_mac<6>(rB, rE, Q3.B, Q3.E, FB, FE1);
     acc.EN1 = rE;
     rB = T(0);
     rE = T(0);
-    track_mac<T>(rB, rE, M.B, M.E, T(1), T(0), 6);
+    track_mac<6>(rB, rE, M.B, M.E, T(1), T(0));
     acc.EM = rE;
   }
   irr_all<T>(Q3, F0, F1, M, acc, std::make_integer_sequence<int, nc(11)>{});
@@ -939,14 +937,14 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
       const int i = (c + 1) % 3, j = (c + 2) % 3;
       mag = F::fma_ru(fabs(r[c]), F::fma_ru(fabs(a[i]), fabs(b[j]), F::mul_ru(fabs(a[j]), fabs(b[i]))), mag);
     }
-    const T cerr = F::mul_ru(gam<T>(10), mag);
+    const T cerr = F::mul_ru(GAM<T, 10>, mag);
     const T C1hi = F::add_ru(fabs(C1), cerr), C1lo = fmax(F::add_rd(fabs(C1), -cerr), T(0));
     T nkl2 = T(0), nkh2 = T(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int i = (c + 1) % 3, j = (c + 2) % 3;
       const T v = e1[i] * e2[j] - e1[j] * e2[i];
-      const T err = F::mul_ru(gam<T>(2), F::fma_ru(fabs(e1[i]), fabs(e2[j]), F::mul_ru(fabs(e1[j]), fabs(e2[i]))));
+      const T err = F::mul_ru(GAM<T, 2>, F::fma_ru(fabs(e1[i]), fabs(e2[j]), F::mul_ru(fabs(e1[j]), fabs(e2[i]))));
       const T lo = fmax(F::add_rd(fabs(v), -err), T(0)), hi = F::add_ru(fabs(v), err);
       nkl2 = F::fma_rd(lo, lo, nkl2);
       nkh2 = F::fma_ru(hi, hi, nkh2);
@@ -965,6 +963,11 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
   T ehm = fmax(F::mul_rd(Klo, widen_lo(acc.eh_in)), T(0));
   if (!(ehm <= eh)) ehm = T(0);
   put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), f_dn(el), f_up(eh), e, t, id, flags, f_dn(ehm));
+}
+
+static __device__ __noinline__ void process_cell_fp64(const BoundParams& P, int e, int t, uint32_t id, int depth,
+                                                      int64_t slot) {
+  process_cell<double>(P, e, t, id, depth, slot, BNB_CELL_QSIGN_FP64);
 }
 
 // ------------------------------------------------------------------ kernels

@@ -56,6 +56,17 @@ __host__ __device__ constexpr double mult_c(int n, int i) {  // C(n; g) for coef
 // Number of (a, b) pairs that meet in one output coefficient of a degree-M x degree-N product.
 __host__ __device__ constexpr int kterms(int M, int N) { return nc(M < N ? M : N); }
 
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0..N-1, so that every index and
+// every table value derived from it (multinomials, gamma_k) is a constant expression.
+template <class F, int... I>
+__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
 // ---------------------------------------------------------------- arithmetic traits
 template <typename T>
 struct FP;
@@ -119,13 +130,13 @@ __device__ __forceinline__ void tp_zero(TP<T, N>& r) {
 }
 
 // Error/bound update for r <- r + sign * p * q computed as a k-term FMA chain per coefficient.
-template <typename T>
-__device__ __forceinline__ void track_mac(T& rB, T& rE, T pB, T pE, T qB, T qE, int k) {
+template <int K, typename T>
+__device__ __forceinline__ void track_mac(T& rB, T& rE, T pB, T pE, T qB, T qE) {
   using F = FP<T>;
   T p1 = F::add_ru(pB, pE), q1 = F::add_ru(qB, qE);
   T inh = F::fma_ru(pE, q1, F::mul_ru(pB, qE));
   T mag = F::fma_ru(p1, q1, F::add_ru(rB, rE));
-  T g = gam<T>(k);  // k FMAs per output coefficient, one rounding each
+  constexpr T g = gam<T>(K);  // K FMAs per output coefficient, one rounding each
   rE = F::add_ru(F::add_ru(rE, inh), F::mul_ru(g, mag));
   rB = F::fma_ru(pB, qB, rB);
 }
@@ -152,7 +163,7 @@ __device__ __forceinline__ void conv_acc(T* __restrict__ r, const T* __restrict_
 template <bool NEG = false, typename T, int M, int N>
 __device__ __forceinline__ void mac(TP<T, M + N>& r, const TP<T, M>& p, const TP<T, N>& q) {
   conv_acc<T, M, N, NEG>(r.c, p.c, q.c, std::make_integer_sequence<int, nc(M) * nc(N)>{});
-  track_mac<T>(r.B, r.E, p.B, p.E, q.B, q.E, kterms(M, N));
+  track_mac<kterms(M, N)>(r.B, r.E, p.B, p.E, q.B, q.E);
 }
 
 // r += s * p for an exact scalar s (a float input such as a receiver edge component).
@@ -161,26 +172,25 @@ __device__ __forceinline__ void mac_s(TP<T, N>& r, T s, const TP<T, N>& p) {
   T ss = NEG ? -s : s;
 #pragma unroll
   for (int i = 0; i < nc(N); ++i) r.c[i] = FP<T>::fma_rn(ss, p.c[i], r.c[i]);
-  track_mac<T>(r.B, r.E, fabs(s), T(0), p.B, p.E, 1);
+  track_mac<1>(r.B, r.E, fabs(s), T(0), p.B, p.E);
 }
 
 // Degree elevation by one (scaled form: sum of the up-to-three lower neighbours).
 template <typename T, int N>
 __device__ __forceinline__ void elevate(TP<T, N + 1>& r, const TP<T, N>& p) {
-#pragma unroll
-  for (int i = 0; i < nc(N + 1); ++i) {
-    constexpr int dummy = 0;
-    (void)dummy;
-    const int g1 = g1_of(N + 1, i), g2 = g2_of(N + 1, i), g0 = N + 1 - g1 - g2;
+  static_for<nc(N + 1)>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int g1 = g1_of(N + 1, i), g2 = g2_of(N + 1, i), g0 = N + 1 - g1 - g2;
     T s = T(0);
-    if (g0 >= 1) s = s + p.c[idx_of(N, g1, g2)];
-    if (g1 >= 1) s = s + p.c[idx_of(N, g1 - 1, g2)];
-    if (g2 >= 1) s = s + p.c[idx_of(N, g1, g2 - 1)];
+    if constexpr (g0 >= 1) s = s + p.c[idx_of(N, g1, g2)];
+    if constexpr (g1 >= 1) s = s + p.c[idx_of(N, g1 - 1, g2)];
+    if constexpr (g2 >= 1) s = s + p.c[idx_of(N, g1, g2 - 1)];
     r.c[i] = s;
-  }
+  });
   using F = FP<T>;
+  constexpr T g2 = gam<T>(2);
   r.B = p.B;
-  r.E = F::add_ru(p.E, F::mul_ru(gam<T>(2), F::add_ru(p.B, p.E)));
+  r.E = F::add_ru(p.E, F::mul_ru(g2, F::add_ru(p.B, p.E)));
 }
 
 // Re-derive B from the computed coefficients: max_g |c_g| / C(n;g) + E.  Tightens B after
@@ -189,12 +199,12 @@ template <typename T, int N>
 __device__ __forceinline__ void renorm(TP<T, N>& p) {
   using F = FP<T>;
   T m = T(0);
-#pragma unroll
-  for (int i = 0; i < nc(N); ++i) {
+  static_for<nc(N)>([&](auto I) {
+    constexpr int i = decltype(I)::value;
     // 1/C rounded up, then |c| * (1/C) rounded up, is >= |c| / C.
-    const T inv = (T)(1.0 / mult_c(N, i) * (1.0 + 4.0 * FP<T>::u));
+    constexpr T inv = (T)(1.0 / mult_c(N, i) * (1.0 + 4.0 * FP<T>::u));
     m = fmax(m, F::mul_ru(fabs(p.c[i]), inv));
-  }
+  });
   T nb = F::add_ru(m, p.E);
   p.B = fmin(p.B, nb);
 }
@@ -204,14 +214,14 @@ template <typename T, int N>
 __device__ __forceinline__ int cert_sign(const TP<T, N>& p) {
   using F = FP<T>;
   bool pos = true, neg = true;
-#pragma unroll
-  for (int i = 0; i < nc(N); ++i) {
-    const T C = (T)mult_c(N, i);
-    T lo = F::fma_rd(-p.E, C, p.c[i]);
-    T hi = F::fma_ru(p.E, C, p.c[i]);
+  static_for<nc(N)>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr T C = (T)(mult_c(N, i) * (1.0 + 4.0 * FP<T>::u));
+    const T lo = F::fma_rd(-p.E, C, p.c[i]);
+    const T hi = F::fma_ru(p.E, C, p.c[i]);
     pos = pos && (lo > T(0));
     neg = neg && (hi < T(0));
-  }
+  });
   return pos ? 1 : (neg ? -1 : 0);
 }
 

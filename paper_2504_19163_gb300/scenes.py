@@ -139,15 +139,39 @@ def _to_surface(P: np.ndarray, N: np.ndarray, tris: np.ndarray, kind: int, eta: 
                    i2=tris[:, 2].astype(np.int32), kind=kind, eta=float(eta))
 
 
+def _value_noise(X: np.ndarray, Y: np.ndarray, extent: float, lattice: int, amp: float,
+                 rng: np.random.Generator) -> np.ndarray:
+    """Smooth value noise: U[-amp, amp] on a (lattice+3)^2 grid over [-extent, extent]^2,
+    Catmull-Rom interpolated (C1) at the points."""
+    V = rng.uniform(-amp, amp, (lattice + 3, lattice + 3))
+    gx = (X + extent) / (2 * extent) * lattice + 1.0
+    gy = (Y + extent) / (2 * extent) * lattice + 1.0
+    ix = np.clip(np.floor(gx).astype(np.int64), 1, lattice)
+    iy = np.clip(np.floor(gy).astype(np.int64), 1, lattice)
+    tx, ty = gx - ix, gy - iy
+
+    def w(t):
+        return np.stack([(-t ** 3 + 2 * t ** 2 - t) / 2, (3 * t ** 3 - 5 * t ** 2 + 2) / 2,
+                         (-3 * t ** 3 + 4 * t ** 2 + t) / 2, (t ** 3 - t ** 2) / 2], axis=0)
+    wx, wy = w(tx), w(ty)
+    out = np.zeros_like(X)
+    for a in range(4):
+        for b in range(4):
+            out += wx[a] * wy[b] * V[ix - 1 + a, iy - 1 + b]
+    return out
+
+
 def heightfield(n: int, seed: int, n_waves: int = 4, amp_total: float = 0.05,
                 noise: float = 0.0, normals: str = "analytic", extent: float = 1.0,
                 z0: float = 0.0, kind: int = SURFACE_REFLECT, eta: float = 1.0,
-                flip_normals: bool = False) -> Surface:
-    """Heightfield z = z0 + sum_i A sin(k_i . (x,y) + phi_i) (+ U[-noise,noise]) on [-extent,extent]^2.
+                flip_normals: bool = False, noise_lattice: int = 0) -> Surface:
+    """Heightfield z = z0 + sum_i A sin(k_i . (x,y) + phi_i) + noise on [-extent,extent]^2.
 
-    ``normals='analytic'`` uses the normalized gradient normal of the smooth
-    sinusoid sum; ``'face'`` uses the normalized area-weighted average of the
-    face normals (needed once per-vertex noise is added).
+    Noise of amplitude ``noise``: with ``noise_lattice = 0`` independent U[-noise, noise] per
+    vertex; otherwise smooth value noise on a ``noise_lattice``^2 lattice.
+    ``normals='analytic'`` uses the normalized gradient normal of the sinusoid sum;
+    ``'face'`` uses the normalized area-weighted average of the face normals (needed once
+    noise is added).
     """
     rng = np.random.default_rng(seed)
     kx, ky, ph, amp = _sinusoids(rng, n_waves, amp_total)
@@ -157,8 +181,10 @@ def heightfield(n: int, seed: int, n_waves: int = 4, amp_total: float = 0.05,
     Y = Y.reshape(-1)
     arg = np.outer(X, kx) + np.outer(Y, ky) + ph
     Z = z0 + (np.sin(arg) * amp).sum(axis=1)
-    if noise > 0.0:
+    if noise > 0.0 and noise_lattice == 0:
         Z = Z + rng.uniform(-noise, noise, Z.shape[0])
+    elif noise > 0.0:
+        Z = Z + _value_noise(X, Y, extent, noise_lattice, noise, rng)
     P = np.stack([X, Y, Z], axis=1)
     tris = _grid_triangles(n)
     if normals == "analytic":
@@ -252,8 +278,10 @@ def shading_points(nx: int, ny: int, seed: int, jitter: float = 0.25):
 # ---------------------------------------------------------------------------
 # Workloads.  Sizes follow the paper-shaped configurations:
 #   mirror32   : 32^2 mirror (2048 tris), light (0,0,2), 64^2 points, depth 2
-#   mirror256  : 256^2 mirror (131,072 tris), 0.2x0.2 area light with 4x4
-#                strata at z=2, 1024^2 points, depth 3
+#   mirror256  : 256^2 mirror (131,072 tris), 6 sinusoids + smooth noise of
+#                amplitude 0.01, 0.2x0.2 area light with 4x4 strata at z=2,
+#                1024^2 points, depth 3
+#   mirror256_rough : the same with independent per-vertex noise (bound tests only)
 #   water420   : 420^2 Gerstner water (352,800 tris), 4 lights, floor 1 below,
 #                1920x1080 points, depth 3
 #   slab48     : glass slab with two 48^2 faces, light (0,0,2), 512^2 points, depth 2
@@ -262,8 +290,9 @@ def shading_points(nx: int, ny: int, seed: int, jitter: float = 0.25):
 
 def mirror(n: int, seed: int, n_waves: int, noise: float, normals: str, emitters: Emitters,
            points: int, depth: int, name: str, receiver_z: float = 1.0, point_seed: Optional[int] = None,
-           points_y: Optional[int] = None) -> Scene:
-    s1 = heightfield(n, seed, n_waves=n_waves, amp_total=0.05, noise=noise, normals=normals)
+           points_y: Optional[int] = None, noise_lattice: int = 0) -> Scene:
+    s1 = heightfield(n, seed, n_waves=n_waves, amp_total=0.05, noise=noise, normals=normals,
+                     noise_lattice=noise_lattice)
     rec = receiver_square(receiver_z, 1.5)
     py = points if points_y is None else points_y
     su, sv = shading_points(points, py, seed + 1000 if point_seed is None else point_seed)
@@ -277,6 +306,13 @@ def config(name: str, **kw) -> Scene:
         return mirror(32, 1, 4, 0.0, "analytic", em, kw.get("points", 64), kw.get("depth", 2), name,
                       receiver_z=kw.get("receiver_z", 1.0))
     if name == "mirror256":
+        # smooth value noise of amplitude 0.01 on a 16^2 lattice (see the module docstring)
+        em = area_quad_emitters((0.0, 0.0, 2.0), 0.2, 4, seed=2)
+        return mirror(256, 2, 6, 0.01, "face", em, kw.get("points", 1024), kw.get("depth", 3), name,
+                      noise_lattice=kw.get("noise_lattice", 16))
+    if name == "mirror256_rough":
+        # per-vertex U[-0.01, 0.01] noise (slopes up to ~2.5): every cell's image spreads over
+        # hundreds of grid cells; kept for the bound-pass tests only
         em = area_quad_emitters((0.0, 0.0, 2.0), 0.2, 4, seed=2)
         return mirror(256, 2, 6, 0.01, "face", em, kw.get("points", 1024), kw.get("depth", 3), name)
     if name == "tiny":

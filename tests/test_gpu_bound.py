@@ -96,10 +96,11 @@ def test_no_emitters_is_empty(B):
     assert int(cb.status.item()) == 0
 
 
-def test_full_size_area_light_sampled(B, orc):
+@pytest.mark.parametrize("name", ["mirror256", "mirror256_rough"])
+def test_full_size_area_light_sampled(B, orc, name):
     """256^2 noisy mirror, 16 area-light samples, depth 3 (134M cells) in one launch; 20000
     seeded base cells compared with the oracle slot by slot."""
-    sc = S.config("mirror256")
+    sc = S.config(name)
     ds = B.DeviceScene(sc)
     cb = B.bound_tuples(ds, sc.depth, with_e_hi_min=True)
     torch.cuda.synchronize()

@@ -83,20 +83,31 @@ def test_index_multiplier_m(B, orc):
 
 
 def test_index_capacity_reported_then_exact(B, orc):
-    """A too-small output reports BNB_ERR_CAPACITY and the needed size; re-calling with it is exact."""
+    """A too-small output reports BNB_ERR_CAPACITY and the needed size; re-calling with it is exact.
+    A too-small pre-merge workspace reports the pre-merge entries it needed."""
     rec = S.synthetic_cell_records(1000, 2, n_tris=5000, n_emitters=2, n_overflow=50, seed=8)
     cb = upload_records(B, rec)
+    o = oracle_index(orc, rec, 512)
     small = B.Index(512, 100, torch.device("cuda"))
-    idx = B.build_index(cb, grid_res=512, capacity=100, out=small, sync_check=False)
+    idx = B.build_index(cb, grid_res=512, pre_capacity=4 * o[1].shape[0], capacity=100, out=small,
+                        sync_check=False)
     torch.cuda.synchronize()
     assert int(idx.status.item()) == B.BNB_ERR_CAPACITY
     need = int(idx.count[0].item())
-    o = oracle_index(orc, rec, 512)
     assert need == o[1].shape[0]
     idx2 = B.build_index(cb, grid_res=512, capacity=need)
     torch.cuda.synchronize()
     assert int(idx2.status.item()) == 0
     assert_same_index(idx2.to_numpy(), o)
+    # pre-merge workspace too small: status and the pre-merge count that is needed
+    idx3 = B.build_index(cb, grid_res=512, pre_capacity=64, capacity=need, sync_check=False)
+    torch.cuda.synchronize()
+    assert int(idx3.status.item()) == B.BNB_ERR_CAPACITY
+    pre_need = int(idx3.count[1].item())
+    assert pre_need >= need
+    idx4 = B.build_index(cb, grid_res=512, pre_capacity=pre_need, capacity=need)
+    torch.cuda.synchronize()
+    assert_same_index(idx4.to_numpy(), o)
 
 
 def test_index_of_nothing(B):

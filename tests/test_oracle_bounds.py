@@ -143,9 +143,11 @@ def test_dense_sweep_containment_heightfield(orc):
     assert viol == 0
 
 
-def test_dense_sweep_containment_noisy_area_light(orc):
-    """Same on the 256^2 noisy mirror with face-averaged normals and 16 area-light samples."""
-    sc = S.config("mirror256")
+@pytest.mark.parametrize("name", ["mirror256", "mirror256_rough"])
+def test_dense_sweep_containment_noisy_area_light(orc, name):
+    """Same on the 256^2 noisy mirrors (smooth and per-vertex noise) with face-averaged normals
+    and 16 area-light samples."""
+    sc = S.config(name)
     rng = np.random.default_rng(12)
     n_base = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
     work = np.sort(rng.choice(n_base, 1500, replace=False))
