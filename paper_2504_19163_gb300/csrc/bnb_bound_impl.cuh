@@ -971,18 +971,28 @@ static __device__ __noinline__ void process_cell_fp64(const BoundParams& P, int 
 }
 
 // ------------------------------------------------------------------ kernels
+// One 256-thread block per SM, persistent.  Every round starts with a block barrier so the
+// eight warps walk the (long, straight-line) cell program together and share instruction
+// fetches; the round count is uniform across the block, so every thread reaches every barrier.
+constexpr int kBoundThreads = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(128) bound_base_k(BoundParams P) {
+__global__ void __launch_bounds__(kBoundThreads, 1) bound_base_k(BoundParams P) {
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)P.count, (unsigned long long)P.n_base);
   const int64_t per_tuple = (int64_t)1 << (2 * P.depth);
   const int64_t per_em = per_tuple * P.n_tris;
-  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < P.n_base;
-       w += (int64_t)gridDim.x * blockDim.x) {
-    const int e = (int)(w / per_em);
-    const int64_t r = w - (int64_t)e * per_em;
-    const int t = (int)(r / per_tuple);
-    const uint32_t c = (uint32_t)(r - (int64_t)t * per_tuple);
-    process_cell<T>(P, e, t, c, P.depth, w);
+  const int64_t stride = (int64_t)gridDim.x * kBoundThreads;
+  const int64_t rounds = (P.n_base + stride - 1) / stride;
+  for (int64_t r = 0; r < rounds; ++r) {
+    __syncthreads();
+    const int64_t w = r * stride + (int64_t)blockIdx.x * kBoundThreads + threadIdx.x;
+    if (w < P.n_base) {
+      const int e = (int)(w / per_em);
+      const int64_t rr = w - (int64_t)e * per_em;
+      const int t = (int)(rr / per_tuple);
+      const uint32_t c = (uint32_t)(rr - (int64_t)t * per_tuple);
+      process_cell<T>(P, e, t, c, P.depth, w);
+    }
   }
 }
 
@@ -1002,13 +1012,13 @@ int grid_for_T(int64_t n, int block) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = (n + block - 1) / block;
-  const int64_t cap = (int64_t)sms * 16;
+  const int64_t cap = (int64_t)sms;  // one resident block per SM (255 registers x 256 threads)
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
 }
 
 template <typename T>
 cudaError_t launch_bound_base_T(const BoundParams& p, cudaStream_t st) {
-  bound_base_k<T><<<grid_for_T<T>(p.n_base, 128), 128, 0, st>>>(p);
+  bound_base_k<T><<<grid_for_T<T>(p.n_base, kBoundThreads), kBoundThreads, 0, st>>>(p);
   return cudaGetLastError();
 }
 
