@@ -163,6 +163,24 @@ int32_t bnb_bound_tuples(const bnb_surface *s1, const bnb_surface *s2, const bnb
 size_t bnb_bound_tuples_ws(const bnb_surface *s1, const bnb_surface *s2, const bnb_emitters *em,
                            const bnb_bound_cfg *cfg);
 
+/* Bound pass for callers that cannot allocate device memory.  The paper has no counterpart: this
+ * is an interface for callers with no device allocator of their own (a plug-in or callback inside
+ * an application whose device memory is owned by another runtime, or a program that forbids
+ * allocation after start-up).  Same inputs, outputs and results as bnb_bound_tuples, but the
+ * scratch comes from a fixed 8 MiB array inside the library (each GPU that loads the library holds
+ * it until the process exits) instead of a caller workspace.
+ *   - Returns BNB_ERR_CAPACITY, launching nothing, when bnb_bound_tuples_ws() for these arguments
+ *     exceeds 8 MiB (e.g. up to ~50k triangles with ~2M base cells).
+ *   - The first call on a device, with that device current, looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture on that device.
+ *   - All calls share the one array, which keeps the last call's contents; each call clears what
+ *     must start at zero on its stream.  Calls whose kernels overlap on the GPU (on different
+ *     streams, or from different threads) race on the array: serialize them.
+ *   - Calls no allocating function (no cudaMalloc/cudaFree, no library allocator). */
+int32_t bnb_bound_tuples_noalloc(const bnb_surface *s1, const bnb_surface *s2, const bnb_receiver *rec,
+                                 const bnb_emitters *em, const bnb_bound_cfg *cfg, bnb_cell_bounds *out,
+                                 void *stream);
+
 /* Bound storage (Sec. 6.1) over the records of one bnb_bound_tuples call (its
  * host fields must be set).  m multiplies the bound (Eq. eq_pertuple_b; the
  * paper uses m = 1).  pre_capacity: pre-merge (grid cell, tuple) entries the

@@ -71,8 +71,9 @@ class bnb_sample_stats(C.Structure):
 
 
 _lib = None
-EXPORTS = ["bnb_bound_tuples", "bnb_bound_tuples_ws", "bnb_build_index", "bnb_build_index_ws",
-           "bnb_sample_and_solve", "bnb_sample_and_solve_ws", "bnb_status_string", "bnb_abi_version"]
+EXPORTS = ["bnb_bound_tuples", "bnb_bound_tuples_ws", "bnb_bound_tuples_noalloc", "bnb_build_index",
+           "bnb_build_index_ws", "bnb_sample_and_solve", "bnb_sample_and_solve_ws", "bnb_status_string",
+           "bnb_abi_version"]
 
 
 def lib():
@@ -88,6 +89,9 @@ def lib():
                                        P(bnb_bound_cfg), P(bnb_cell_bounds), vp, sz, vp]
         L.bnb_bound_tuples_ws.restype = sz
         L.bnb_bound_tuples_ws.argtypes = [P(bnb_surface), P(bnb_surface), P(bnb_emitters), P(bnb_bound_cfg)]
+        L.bnb_bound_tuples_noalloc.restype = i32
+        L.bnb_bound_tuples_noalloc.argtypes = [P(bnb_surface), P(bnb_surface), P(bnb_receiver), P(bnb_emitters),
+                                               P(bnb_bound_cfg), P(bnb_cell_bounds), vp]
         L.bnb_build_index.restype = i32
         L.bnb_build_index.argtypes = [P(bnb_cell_bounds), f32, i64, P(bnb_index), vp, sz, vp]
         L.bnb_build_index_ws.restype = sz
@@ -112,6 +116,10 @@ def bnb_bound_tuples(*a):
 
 def bnb_bound_tuples_ws(*a):
     return lib().bnb_bound_tuples_ws(*a)
+
+
+def bnb_bound_tuples_noalloc(*a):
+    return lib().bnb_bound_tuples_noalloc(*a)
 
 
 def bnb_build_index(*a):
