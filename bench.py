@@ -220,7 +220,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
 
     # Buffers sized once (first call discovers the capacities), then reused every step.
-    cb = bnb.bound_tuples(ds, sc.depth)
+    cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False)  # the index needs E_hi only
     idx = bnb.build_index(cb, grid_res=sc.grid_res)
     # gamma: expected |S| of about 4 per shading point (paper's Plane scene: |S| = 3.4)
     gamma = calibrate_gamma(bnb, ds, idx, target=4.0)

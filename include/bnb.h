@@ -111,7 +111,8 @@ typedef struct bnb_cell_bounds {
   int64_t capacity;
   int64_t *count;  /* device int64: records produced (n_base + children); may exceed capacity */
   int32_t *status; /* device int32: BNB_OK or BNB_ERR_CAPACITY */
-  float *u_lo, *u_hi, *v_lo, *v_hi, *e_lo, *e_hi;
+  float *u_lo, *u_hi, *v_lo, *v_hi, *e_hi;
+  float *e_lo;                    /* optional (NULL: the lower irradiance bound is neither computed nor written) */
   int32_t *emitter, *tri0, *tri1; /* tri1 = -1 for single scattering */
   uint32_t *cell;                 /* base-4 digits of the cell path, most significant first */
   uint32_t *flags;                /* BNB_CELL_* | depth << BNB_CELL_DEPTH_SHIFT */

@@ -51,7 +51,7 @@ class bnb_bound_cfg(C.Structure):
 
 class bnb_cell_bounds(C.Structure):
     _fields_ = [("capacity", i64), ("count", vp), ("status", vp), ("u_lo", vp), ("u_hi", vp), ("v_lo", vp),
-                ("v_hi", vp), ("e_lo", vp), ("e_hi", vp), ("emitter", vp), ("tri0", vp), ("tri1", vp),
+                ("v_hi", vp), ("e_hi", vp), ("e_lo", vp), ("emitter", vp), ("tri0", vp), ("tri1", vp),
                 ("cell", vp), ("flags", vp), ("e_hi_min", vp), ("n_base", i64), ("depth", i32), ("n_emitters", i32),
                 ("n_tris", i32)]
 
@@ -201,19 +201,20 @@ class DeviceScene:
 class CellBounds:
     """Cell records (SoA device tensors) plus their bnb_cell_bounds view."""
 
-    def __init__(self, capacity: int, device, with_e_hi_min: bool = False):
+    def __init__(self, capacity: int, device, with_e_hi_min: bool = False, with_e_lo: bool = True):
         d = device
         self.capacity = int(capacity)
         f = lambda dt: torch.empty(self.capacity, dtype=dt, device=d)
         self.count = torch.zeros(1, dtype=torch.int64, device=d)
         self.status = torch.zeros(1, dtype=torch.int32, device=d)
         self.u_lo, self.u_hi, self.v_lo, self.v_hi = f(torch.float32), f(torch.float32), f(torch.float32), f(torch.float32)
-        self.e_lo, self.e_hi = f(torch.float32), f(torch.float32)
+        self.e_hi = f(torch.float32)
+        self.e_lo = f(torch.float32) if with_e_lo else None
         self.emitter, self.tri0, self.tri1 = f(torch.int32), f(torch.int32), f(torch.int32)
         self.cell, self.flags = f(torch.int32), f(torch.int32)
         self.e_hi_min = f(torch.float32) if with_e_hi_min else None
         self.c = bnb_cell_bounds(self.capacity, _ptr(self.count), _ptr(self.status), _ptr(self.u_lo),
-                                 _ptr(self.u_hi), _ptr(self.v_lo), _ptr(self.v_hi), _ptr(self.e_lo), _ptr(self.e_hi),
+                                 _ptr(self.u_hi), _ptr(self.v_lo), _ptr(self.v_hi), _ptr(self.e_hi), _ptr(self.e_lo),
                                  _ptr(self.emitter), _ptr(self.tri0), _ptr(self.tri1), _ptr(self.cell),
                                  _ptr(self.flags), _ptr(self.e_hi_min), 0, 0, 0, 0)
 
@@ -227,8 +228,8 @@ class CellBounds:
     def to_numpy(self) -> dict:
         n = self.n_records()
         g = lambda t: t[:n].cpu().numpy()
-        out = dict(u_lo=g(self.u_lo), u_hi=g(self.u_hi), v_lo=g(self.v_lo), v_hi=g(self.v_hi), e_lo=g(self.e_lo),
-                   e_hi=g(self.e_hi), emitter=g(self.emitter), tri0=g(self.tri0), tri1=g(self.tri1),
+        out = dict(u_lo=g(self.u_lo), u_hi=g(self.u_hi), v_lo=g(self.v_lo), v_hi=g(self.v_hi),
+                   e_lo=g(self.e_lo) if self.e_lo is not None else np.zeros(n, np.float32), e_hi=g(self.e_hi), emitter=g(self.emitter), tri0=g(self.tri0), tri1=g(self.tri1),
                    cell=g(self.cell).view(np.uint32), flags=g(self.flags).view(np.uint32))
         if self.e_hi_min is not None:
             out["e_hi_min"] = g(self.e_hi_min)
@@ -262,11 +263,12 @@ class Index:
 def bound_tuples(ds: DeviceScene, depth: int, max_extra_split: int = 4, irradiance: bool = True,
                  fp64: bool = False, capacity: Optional[int] = None, out: Optional[CellBounds] = None,
                  ws: Optional[torch.Tensor] = None, stream=None, sync_check: bool = True,
-                 with_e_hi_min: bool = False) -> CellBounds:
+                 with_e_hi_min: bool = False, with_e_lo: bool = True) -> CellBounds:
     cfg = bnb_bound_cfg(depth, max_extra_split, int(irradiance), int(fp64))
     n_base = ds.scene.emitters.n * ds.s1.n_tris * 4 ** depth
     if out is None:
-        out = CellBounds(capacity if capacity is not None else n_base + n_base // 8 + 1024, ds.device, with_e_hi_min)
+        out = CellBounds(capacity if capacity is not None else n_base + n_base // 8 + 1024, ds.device, with_e_hi_min,
+                         with_e_lo)
     need = bnb_bound_tuples_ws(C.byref(ds.s1), None, C.byref(ds.em), C.byref(cfg))
     if ws is None or ws.numel() < need + 256:
         ws = _ws(need, ds.device)
@@ -279,7 +281,7 @@ def bound_tuples(ds: DeviceScene, depth: int, max_extra_split: int = 4, irradian
             return out
         if int(out.status.item()) == BNB_OK:
             return out
-        out = CellBounds(int(out.count.item()) + 1024, ds.device, with_e_hi_min)
+        out = CellBounds(int(out.count.item()) + 1024, ds.device, with_e_hi_min, with_e_lo)
     raise BnbError("bnb_bound_tuples: capacity exceeded twice")
 
 

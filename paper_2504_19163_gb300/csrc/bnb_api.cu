@@ -108,7 +108,7 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
   const int64_t nb = n_base_of(s1, em, cfg->depth);
   if (!out->count || !out->status) return BNB_ERR_INVALID;
   if (out->capacity < nb) return BNB_ERR_INVALID;
-  if (out->capacity > 0 && (!out->u_lo || !out->u_hi || !out->v_lo || !out->v_hi || !out->e_lo || !out->e_hi ||
+  if (out->capacity > 0 && (!out->u_lo || !out->u_hi || !out->v_lo || !out->v_hi || !out->e_hi ||
                             !out->emitter || !out->tri0 || !out->tri1 || !out->cell || !out->flags))
     return BNB_ERR_INVALID;
   const int64_t qcap = split_queue_cap(nb);

@@ -386,14 +386,14 @@ struct Term2 {
   static constexpr double c2 = mult_c(2, Bi);
 };
 
-template <typename T, int M, int G, int... Bi>
+template <bool LO, typename T, int M, int G, int... Bi>
 __device__ __forceinline__ void coef3(const T* __restrict__ p, const T* __restrict__ f0, const T* __restrict__ f1,
                                       const T* __restrict__ m, T& n0, T& n1, T& mm, std::integer_sequence<int, Bi...>) {
-  // n0 = sum f0[b] p[G-b], n1 = sum f1[b] p[G-b], mm = sum C(2;b) m[G-b]
+  // n0 = sum f0[b] p[G-b] (only when LO), n1 = sum f1[b] p[G-b], mm = sum C(2;b) m[G-b]
   n0 = T(0);
   n1 = T(0);
   mm = T(0);
-  ((Term2<M, G, Bi>::valid ? (n0 = FP<T>::fma_rn(f0[Bi], p[Term2<M, G, Bi>::a], n0),
+  ((Term2<M, G, Bi>::valid ? (n0 = LO ? FP<T>::fma_rn(f0[Bi], p[Term2<M, G, Bi>::a], n0) : n0,
                               n1 = FP<T>::fma_rn(f1[Bi], p[Term2<M, G, Bi>::a], n1),
                               mm = FP<T>::fma_rn((T)Term2<M, G, Bi>::c2, m[Term2<M, G, Bi>::a], mm), 0)
                            : 0),
@@ -408,27 +408,31 @@ struct IrrAcc {
   T EN0, EN1, EM;  // coefficient error bounds (classical)
 };
 
-template <typename T, int G>
+// LO: also the lower irradiance bound (xi = 0 side) and the inner end of the enclosure of the
+// exact upper bound; both are skipped when the caller does not ask for e_lo / e_hi_min.
+template <bool LO, typename T, int G>
 __device__ __forceinline__ void irr_step(const TP<T, 9>& Q3, const T (&F0)[6], const T (&F1)[6], const TP<T, 9>& M,
                                          IrrAcc<T>& acc) {
   T n0, n1, mm;
-  coef3<T, 9, G>(Q3.c, F0, F1, M.c, n0, n1, mm, std::make_integer_sequence<int, 6>{});
+  coef3<LO, T, 9, G>(Q3.c, F0, F1, M.c, n0, n1, mm, std::make_integer_sequence<int, 6>{});
   constexpr T C = MULTUP<T, 11, G>;
   const T ml = FP<T>::fma_rd(-acc.EM, C, mm), mh = FP<T>::fma_ru(acc.EM, C, mm);
   if (!(ml > tiny_pos<T>())) acc.unbounded = true;
   const T rl = FP<T>::rcp_rn(ml), rh = FP<T>::rcp_rn(mh);
   const T n1h = FP<T>::fma_ru(acc.EN1, C, n1);
-  const T n0l = FP<T>::fma_rd(-acc.EN0, C, n0);
   acc.eh_mx = fmax(acc.eh_mx, n1h * (n1h >= T(0) ? rl : rh));
-  acc.el_mn = fmin(acc.el_mn, n0l * (n0l >= T(0) ? rh : rl));
-  const T n1l = FP<T>::fma_rd(-acc.EN1, C, n1);
-  acc.eh_in = fmax(acc.eh_in, n1l * (n1l >= T(0) ? rh : rl));
+  if constexpr (LO) {
+    const T n0l = FP<T>::fma_rd(-acc.EN0, C, n0);
+    acc.el_mn = fmin(acc.el_mn, n0l * (n0l >= T(0) ? rh : rl));
+    const T n1l = FP<T>::fma_rd(-acc.EN1, C, n1);
+    acc.eh_in = fmax(acc.eh_in, n1l * (n1l >= T(0) ? rh : rl));
+  }
 }
 
-template <typename T, int... G>
+template <bool LO, typename T, int... G>
 __device__ __forceinline__ void irr_all(const TP<T, 9>& Q3, const T (&F0)[6], const T (&F1)[6], const TP<T, 9>& M,
                                         IrrAcc<T>& acc, std::integer_sequence<int, G...>) {
-  (irr_step<T, G>(Q3, F0, F1, M, acc), ...);
+  (irr_step<LO, T, G>(Q3, F0, F1, M, acc), ...);
 }
 
 // Chord of f(s) = s^(-3/2) on [sl, sh] with rigorous remainder bounds dlo <= f - (a s + b) <= dhi.
@@ -500,7 +504,7 @@ __device__ __forceinline__ void put_rec(const BoundParams& P, int64_t slot, floa
   P.u_hi[slot] = uh;
   P.v_lo[slot] = vl;
   P.v_hi[slot] = vh;
-  P.e_lo[slot] = el;
+  if (P.e_lo) P.e_lo[slot] = el;
   P.e_hi[slot] = eh;
   P.emitter[slot] = e;
   P.tri0[slot] = t;
@@ -913,7 +917,11 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     track_mac<6>(rB, rE, M.B, M.E, T(1), T(0));
     acc.EM = rE;
   }
-  irr_all<T>(Q3, F0, F1, M, acc, std::make_integer_sequence<int, nc(11)>{});
+  const bool want_lo = P.e_lo != nullptr || P.e_hi_min != nullptr;  // uniform across the launch
+  if (want_lo)
+    irr_all<true, T>(Q3, F0, F1, M, acc, std::make_integer_sequence<int, nc(11)>{});
+  else
+    irr_all<false, T>(Q3, F0, F1, M, acc, std::make_integer_sequence<int, nc(11)>{});
   if (acc.unbounded) {
     put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_FOLD);
     return;
@@ -958,7 +966,7 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     (void)uu;
   }
   T eh = F::mul_ru(Khi, widen_hi(acc.eh_mx));
-  T el = fmax(F::mul_rd(Klo, widen_lo(acc.el_mn)), T(0));
+  T el = want_lo ? fmax(F::mul_rd(Klo, widen_lo(acc.el_mn)), T(0)) : T(0);
   if (!(eh >= T(0))) eh = F::inf();  // NaN guard: never report a finite bound by accident
   T ehm = fmax(F::mul_rd(Klo, widen_lo(acc.eh_in)), T(0));
   if (!(ehm <= eh)) ehm = T(0);

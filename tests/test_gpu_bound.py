@@ -124,3 +124,15 @@ def test_full_size_area_light_sampled(B, orc, name):
     rep = parity.compare_bounds(g, o_base)
     print(rep)
     parity.assert_bounds_parity(rep)
+
+
+def test_upper_bound_identical_without_optional_outputs(B):
+    """Skipping e_lo and e_hi_min (the index needs e_hi only) leaves every other field bit-identical."""
+    sc = S.config("mirror32")
+    ds = B.DeviceScene(sc)
+    full = B.bound_tuples(ds, sc.depth, with_e_hi_min=True)
+    lean = B.bound_tuples(ds, sc.depth, with_e_lo=False)
+    torch.cuda.synchronize()
+    a, b = full.to_numpy(), lean.to_numpy()
+    for k in ("u_lo", "u_hi", "v_lo", "v_hi", "e_hi", "emitter", "tri0", "cell", "flags"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
