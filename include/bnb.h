@@ -201,11 +201,72 @@ int32_t bnb_sample_and_solve(const bnb_surface *s1, const bnb_surface *s2, const
                              bnb_sample_stats *stats, void *ws, size_t ws_bytes, void *stream);
 size_t bnb_sample_and_solve_ws(const bnb_surface *s1, int64_t n_points, int64_t worklist_capacity);
 
+/* ---- Batched rendering pass ------------------------------------------------
+ * The paper renders one frame at a time; these calls serve many rendering
+ * requests at once.  A job is one request's shading points against one scene
+ * whose bound pass and index are already resident on the device.  The job
+ * table and the job count are DEVICE memory and every launch is sized from the
+ * capacities in bnb_batch_cfg only, so one launch sequence can be captured in a
+ * CUDA graph and replayed with a rewritten job table.  The Philox counter is
+ * the point's index within its job, so a job's estimate does not depend on
+ * which other jobs share the batch; with emitter_on NULL it is bit-identical
+ * to bnb_sample_and_solve on that job's points with the job's gamma and seed. */
+
+/* Triangles of s in the packed layout the batched pass reads (80 bytes per
+ * triangle: p0, p1, p2, n0, n1, n2 as 18 floats in five 16-byte words).
+ * `packed` is a device buffer of bnb_pack_surface_bytes(s) bytes, 16-byte
+ * aligned, owned by the caller; it stays valid while the caller keeps it. */
+size_t bnb_pack_surface_bytes(const bnb_surface *s);
+int32_t bnb_pack_surface(const bnb_surface *s, void *packed, size_t packed_bytes, void *stream);
+
+/* One job of a batch (the table is a device array of these, 8-byte aligned).
+ * All pointers are device pointers that stay valid until the batch is done. */
+typedef struct bnb_job {
+  const void *packed_tris;         /* bnb_pack_surface output of the scene's specular surface */
+  int32_t n_tris, n_emitters;
+  const float *ex, *ey, *ez, *ei;  /* the scene's emitters (as passed to bnb_bound_tuples) */
+  const uint8_t *emitter_on;       /* optional, n_emitters bytes: the job renders the emitters whose byte
+                                      is nonzero; the other emitters' tuples are skipped (NULL: all) */
+  float rp0[3], re1[3], re2[3];    /* the scene's receiver */
+  int32_t grid_res;                /* index of the scene (bnb_build_index output) */
+  const int64_t *offsets;
+  const uint64_t *key;
+  const float *etilde;
+  int64_t index_capacity;
+  const float *su, *sv;            /* the request's shading points, n_points each */
+  int64_t n_points;
+  float gamma;                     /* as bnb_sample_cfg */
+  uint32_t reserved;                /* 0 */
+  uint64_t seed;
+  float *E_out;                    /* n_points estimates */
+} bnb_job;
+
+typedef struct bnb_batch_cfg {
+  int32_t max_jobs;          /* capacity of the job table (1..65536) */
+  int32_t newton_iters;      /* as bnb_sample_cfg */
+  int64_t max_points;        /* capacity: sum of the jobs' n_points */
+  int64_t worklist_capacity; /* capacity: selected (point, tuple) pairs of the whole batch */
+  int32_t polish_iters;
+  float tol;
+  int32_t block_threads;     /* launch shape of the per-point and per-tuple kernels: 0 = 256, else 64..512, multiple of 32 */
+  int32_t blocks_per_sm;     /* resident-grid factor: grids hold at most #SMs x this many blocks (0 = 8; 1..64) */
+} bnb_batch_cfg;
+
+/* Runs every job of jobs[0 .. *n_jobs) (device int32, read on the device).
+ * Device-side overflows (sum of n_points > max_points, *n_jobs > max_jobs,
+ * more selections than worklist_capacity) set *stats->status =
+ * BNB_ERR_CAPACITY; stats->counters as bnb_sample_and_solve, summed over the
+ * batch; stats->sel_count is not written.  The caller zeroes status and
+ * counters before each batch.  ws: bnb_sample_and_solve_batched_ws(cfg) bytes. */
+int32_t bnb_sample_and_solve_batched(const bnb_job *jobs, const int32_t *n_jobs, const bnb_batch_cfg *cfg,
+                                     bnb_sample_stats *stats, void *ws, size_t ws_bytes, void *stream);
+size_t bnb_sample_and_solve_batched_ws(const bnb_batch_cfg *cfg);
+
 /* Human-readable name of a status code (static string). */
 const char *bnb_status_string(int32_t status);
 
 /* ABI version of this header (increments on any struct or signature change). */
-int32_t bnb_abi_version(void);  /* 2 */
+int32_t bnb_abi_version(void);  /* 3 */
 
 #ifdef __cplusplus
 }

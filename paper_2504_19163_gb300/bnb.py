@@ -70,10 +70,24 @@ class bnb_sample_stats(C.Structure):
     _fields_ = [("counters", vp), ("status", vp), ("sel_count", vp)]
 
 
+class bnb_job(C.Structure):
+    _fields_ = [("packed_tris", vp), ("n_tris", i32), ("n_emitters", i32), ("ex", vp), ("ey", vp), ("ez", vp),
+                ("ei", vp), ("emitter_on", vp), ("rp0", f32 * 3), ("re1", f32 * 3), ("re2", f32 * 3),
+                ("grid_res", i32), ("offsets", vp), ("key", vp), ("etilde", vp), ("index_capacity", i64),
+                ("su", vp), ("sv", vp), ("n_points", i64), ("gamma", f32), ("reserved", C.c_uint32), ("seed", u64),
+                ("E_out", vp)]
+
+
+class bnb_batch_cfg(C.Structure):
+    _fields_ = [("max_jobs", i32), ("newton_iters", i32), ("max_points", i64), ("worklist_capacity", i64),
+                ("polish_iters", i32), ("tol", f32), ("block_threads", i32), ("blocks_per_sm", i32)]
+
+
 _lib = None
 EXPORTS = ["bnb_bound_tuples", "bnb_bound_tuples_ws", "bnb_bound_tuples_noalloc", "bnb_build_index",
            "bnb_build_index_ws", "bnb_sample_and_solve", "bnb_sample_and_solve_ws", "bnb_status_string",
-           "bnb_abi_version"]
+           "bnb_abi_version", "bnb_pack_surface", "bnb_pack_surface_bytes", "bnb_sample_and_solve_batched",
+           "bnb_sample_and_solve_batched_ws"]
 
 
 def lib():
@@ -105,6 +119,14 @@ def lib():
         L.bnb_status_string.restype = C.c_char_p
         L.bnb_status_string.argtypes = [i32]
         L.bnb_abi_version.restype = i32
+        L.bnb_pack_surface_bytes.restype = sz
+        L.bnb_pack_surface_bytes.argtypes = [P(bnb_surface)]
+        L.bnb_pack_surface.restype = i32
+        L.bnb_pack_surface.argtypes = [P(bnb_surface), vp, sz, vp]
+        L.bnb_sample_and_solve_batched.restype = i32
+        L.bnb_sample_and_solve_batched.argtypes = [vp, vp, P(bnb_batch_cfg), P(bnb_sample_stats), vp, sz, vp]
+        L.bnb_sample_and_solve_batched_ws.restype = sz
+        L.bnb_sample_and_solve_batched_ws.argtypes = [P(bnb_batch_cfg)]
         _lib = L
     return _lib
 
@@ -136,6 +158,22 @@ def bnb_sample_and_solve(*a):
 
 def bnb_sample_and_solve_ws(*a):
     return lib().bnb_sample_and_solve_ws(*a)
+
+
+def bnb_pack_surface(*a):
+    return lib().bnb_pack_surface(*a)
+
+
+def bnb_pack_surface_bytes(*a):
+    return lib().bnb_pack_surface_bytes(*a)
+
+
+def bnb_sample_and_solve_batched(*a):
+    return lib().bnb_sample_and_solve_batched(*a)
+
+
+def bnb_sample_and_solve_batched_ws(*a):
+    return lib().bnb_sample_and_solve_batched_ws(*a)
 
 
 def bnb_status_string(s: int) -> str:
@@ -195,6 +233,25 @@ class DeviceScene:
     @property
     def n_points(self) -> int:
         return int(self.t["su"].shape[0])
+
+    def with_emitters(self, which) -> "DeviceScene":
+        """The same resident mesh, receiver and points lit by the emitters `which` (indices into
+        this scene's emitters, gathered into new device arrays)."""
+        out = object.__new__(DeviceScene)
+        out.device = self.device
+        sel = np.asarray(which, dtype=np.int64)
+        e = self.scene.emitters
+        out.scene = dataclasses.replace(self.scene, emitters=dataclasses.replace(
+            e, x=e.x[sel], y=e.y[sel], z=e.z[sel], intensity=e.intensity[sel]))
+        idx = torch.as_tensor(sel, device=self.device)
+        out.t = dict(self.t)
+        for k in ("ex", "ey", "ez", "ei"):
+            out.t[k] = self.t[k].index_select(0, idx)
+        out.s1 = self.s1
+        out.rec = self.rec
+        T = out.t
+        out.em = bnb_emitters(int(sel.shape[0]), _ptr(T["ex"]), _ptr(T["ey"]), _ptr(T["ez"]), _ptr(T["ei"]))
+        return out
 
 
 # ----------------------------------------------------------------------------- outputs

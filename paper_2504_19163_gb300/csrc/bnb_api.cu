@@ -16,6 +16,9 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_receiver* r
                                     const bnb_index* idx, const float* su, const float* sv, int64_t n_points,
                                     const bnb_sample_cfg* cfg, float* E_out, bnb_sample_stats* stats, void* ws,
                                     cudaStream_t st);
+size_t batch_ws_bytes(const bnb_batch_cfg* c);
+cudaError_t launch_sample_and_solve_batched(const bnb_job* jobs, const int32_t* n_jobs, const bnb_batch_cfg* c,
+                                            bnb_sample_stats* stats, void* ws, cudaStream_t st);
 }  // namespace bnb
 
 using namespace bnb;
@@ -74,7 +77,7 @@ BoundWs carve_bound_ws(void* base, int64_t n_tris, int64_t qcap) {
 
 extern "C" {
 
-int32_t bnb_abi_version(void) { return 2; }
+int32_t bnb_abi_version(void) { return 3; }
 
 const char* bnb_status_string(int32_t s) {
   switch (s) {
@@ -214,6 +217,46 @@ int32_t bnb_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2, const
   if (ws_bytes < need || !ws || !aligned256(ws)) return BNB_ERR_INVALID;
   return launch_sample_and_solve(s1, rec, em, index, su, sv, n_points, cfg, E_out, stats, ws,
                                  (cudaStream_t)stream) == cudaSuccess
+             ? BNB_OK
+             : BNB_ERR_CUDA;
+}
+
+size_t bnb_pack_surface_bytes(const bnb_surface* s) {
+  if (!surface_ok(s)) return 0;
+  return (size_t)s->n_tris * kTriF4 * sizeof(float4);
+}
+
+int32_t bnb_pack_surface(const bnb_surface* s, void* packed, size_t packed_bytes, void* stream) {
+  if (!surface_ok(s)) return BNB_ERR_INVALID;
+  const size_t need = (size_t)s->n_tris * kTriF4 * sizeof(float4);
+  if (packed_bytes < need || (need > 0 && (!packed || ((uintptr_t)packed & 15u) != 0))) return BNB_ERR_INVALID;
+  if (need == 0) return BNB_OK;
+  return launch_pack_tris(s, (float4*)packed, (cudaStream_t)stream) == cudaSuccess ? BNB_OK : BNB_ERR_CUDA;
+}
+
+static bool batch_cfg_ok(const bnb_batch_cfg* c) {
+  if (!c) return false;
+  if (c->max_jobs < 1 || c->max_jobs > 65536 || c->max_points < 0 || c->worklist_capacity < 0) return false;
+  if (c->newton_iters < 0 || c->newton_iters > 64 || c->polish_iters < 0 || c->polish_iters > 8) return false;
+  if (!(c->tol > 0.0f)) return false;
+  if (c->block_threads != 0 && (c->block_threads < 64 || c->block_threads > 512 || c->block_threads % 32 != 0))
+    return false;
+  if (c->blocks_per_sm < 0 || c->blocks_per_sm > 64) return false;
+  return true;
+}
+
+size_t bnb_sample_and_solve_batched_ws(const bnb_batch_cfg* cfg) {
+  if (!batch_cfg_ok(cfg)) return 0;
+  return batch_ws_bytes(cfg);
+}
+
+int32_t bnb_sample_and_solve_batched(const bnb_job* jobs, const int32_t* n_jobs, const bnb_batch_cfg* cfg,
+                                     bnb_sample_stats* stats, void* ws, size_t ws_bytes, void* stream) {
+  if (!jobs || !n_jobs || !batch_cfg_ok(cfg) || !stats || !stats->counters || !stats->status) return BNB_ERR_INVALID;
+  if (((uintptr_t)jobs & 7u) != 0) return BNB_ERR_INVALID;
+  const size_t need = batch_ws_bytes(cfg);
+  if (ws_bytes < need || !ws || !aligned256(ws)) return BNB_ERR_INVALID;
+  return launch_sample_and_solve_batched(jobs, n_jobs, cfg, stats, ws, (cudaStream_t)stream) == cudaSuccess
              ? BNB_OK
              : BNB_ERR_CUDA;
 }

@@ -333,6 +333,48 @@ def config(name: str, **kw) -> Scene:
     raise KeyError(name)
 
 
+def emitter_pool(center, half: float, n: int, seed: int) -> Emitters:
+    """n point lights drawn uniformly (seeded) over a horizontal square of half-size `half`
+    centred at `center`, each of intensity 1/n."""
+    rng = np.random.default_rng(seed)
+    c = np.asarray(center, dtype=np.float64)
+    xy = rng.uniform(-half, half, (n, 2))
+    pts = np.stack([c[0] + xy[:, 0], c[1] + xy[:, 1], np.full(n, c[2])], axis=1)
+    return point_emitters(pts, 1.0 / n)
+
+
+# Serving catalogue: the three single-specular-vertex mesh sizes of the rendering workloads, each
+# with a fixed pool of 8 point lights; a request renders a subset of a scene's pool.
+SERVING_SCENES = ("serve32", "serve256", "serve420")
+SERVING_POOL = 8
+
+
+def serving_scene(name: str) -> Scene:
+    """A scene of the serving catalogue (mesh, receiver, emitter pool, bound depth).
+
+    serve32  : the 32^2 mirror heightfield (2048 tris), depth 2
+    serve256 : the 256^2 mirror heightfield with smooth noise (131,072 tris), depth 3
+    serve420 : the 420^2 Gerstner water surface (352,800 tris) as a mirror, receiver 1 above
+               over [-2,2]^2, depth 3 (single reflection: the refracting variant of this mesh is
+               not part of the rendering pass)
+    Shading points are per request; the scene's own point set is a small placeholder."""
+    su, sv = shading_points(8, 8, 0)
+    if name == "serve32":
+        s1 = heightfield(32, 1, n_waves=4, amp_total=0.05, normals="analytic")
+        em = emitter_pool((0.0, 0.0, 2.0), 0.3, SERVING_POOL, seed=51)
+        return Scene(name, s1, None, receiver_square(1.0, 1.5), em, 2, su, sv)
+    if name == "serve256":
+        s1 = heightfield(256, 2, n_waves=6, amp_total=0.05, noise=0.01, normals="face", noise_lattice=16)
+        em = emitter_pool((0.0, 0.0, 2.0), 0.3, SERVING_POOL, seed=52)
+        return Scene(name, s1, None, receiver_square(1.0, 1.5), em, 3, su, sv)
+    if name == "serve420":
+        s1 = gerstner(420, 3)
+        s1 = dataclasses.replace(s1, kind=SURFACE_REFLECT, eta=1.0)
+        em = emitter_pool((0.0, 0.0, 2.0), 0.5, SERVING_POOL, seed=53)
+        return Scene(name, s1, None, receiver_square(1.0, 2.0), em, 3, su, sv)
+    raise KeyError(name)
+
+
 def synthetic_cell_records(n_tuples: int, depth: int, n_tris: int, n_emitters: int, n_overflow: int, seed: int,
                            grid_res: int = 512):
     """Seeded synthetic bound records (float32 SoA) in the record layout of the bound pass:

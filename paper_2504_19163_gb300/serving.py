@@ -1,0 +1,588 @@
+"""Serving loop: continuous batching of caustic render requests over device-resident scenes.
+
+A request asks for the caustic irradiance of one catalogue scene, lit by a subset of the scene's
+emitter pool, at an n x n grid of jittered shading points.  The server
+
+* keeps each scene's precomputation resident (``SceneCache``): the bound pass over the scene's
+  whole emitter pool, its index and the sampling rate gamma.  A request's emitter subset becomes
+  the job's ``emitter_on`` mask, so every subset of a scene shares one resident index.  Scenes
+  are built on first use by a worker thread on its own CUDA stream, overlapping the rendering of
+  other scenes' requests, and evicted least-recently-used (when idle) to stay inside the HBM
+  budget;
+* admits arrived requests into batches as rendering slots and HBM free up: a batch holds at most
+  ``max_jobs`` requests and ``max_points`` shading points, and the shading points and outputs of
+  all requests in flight stay inside the HBM budget;
+* runs every batch through a ``BatchRunner`` whose launch sequence is captured once in a CUDA
+  graph; two runners on two streams alternate, so the host prepares and enqueues the next batch
+  while the previous one is still on the device, and batches overlap on the GPU.
+
+A request's result depends only on the request (its scene, emitter subset, points and seed),
+not on the batch it joins: the Philox counter of a shading point is its index within the request.
+
+``plain_per_request`` is the baseline path: requests one at a time, each running the three
+calls of the rendering pipeline (bound pass over the request's emitters, index, sample and
+solve) and waiting for the result before the next.  ``plain_cached`` serves one request at a
+time from the resident scenes (no batching, no graph, no overlap).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import queue
+import threading
+import time
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import bnb
+from . import scenes as S
+from .batch import BatchRunner, Job, ResidentScene, gamma_for_target
+
+SIDES = (64, 128, 256, 512, 1024)
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    scene: str
+    emitters: tuple
+    n_side: int
+    seed: int
+    arrival: float = 0.0  # seconds after the start of the run
+    # results
+    t_start: float = math.nan
+    t_done: float = math.nan
+    E: Optional[np.ndarray] = None
+    status: int = 0
+    batch: int = -1
+    entry: object = dataclasses.field(default=None, repr=False)
+
+    @property
+    def n_points(self) -> int:
+        return self.n_side * self.n_side
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+    def points(self):
+        """The request's shading points (receiver texture coordinates) as numpy float32 arrays:
+        the jittered n_side x n_side pixel grid of the client's view."""
+        return S.shading_points(self.n_side, self.n_side, 10_000 + self.n_side)
+
+    def host_points(self):
+        """The shading points as pinned host tensors (the request payload as it arrives)."""
+        hit = _PINNED_POINTS.get(self.n_side)
+        if hit is None:
+            su, sv = self.points()
+            hit = (torch.from_numpy(su).pin_memory(), torch.from_numpy(sv).pin_memory())
+            _PINNED_POINTS[self.n_side] = hit
+        return hit
+
+
+_PINNED_POINTS: Dict[int, tuple] = {}
+
+
+def make_requests(n: int, seed: int, scene_names: Sequence[str] = S.SERVING_SCENES, sides: Sequence[int] = SIDES,
+                  pool: int = S.SERVING_POOL) -> List[Request]:
+    """n requests: scene uniform over the catalogue, points n_side^2 with n_side uniform over
+    `sides`, emitters a uniform-size (1..pool) uniform subset of the pool; arrivals unset."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        sc = scene_names[int(rng.integers(len(scene_names)))]
+        k = int(rng.integers(1, pool + 1))
+        em = tuple(sorted(int(e) for e in rng.choice(pool, k, replace=False)))
+        side = int(sides[int(rng.integers(len(sides)))])
+        out.append(Request(i, sc, em, side, int(rng.integers(1 << 62))))
+    return out
+
+
+def poisson_arrivals(reqs: List[Request], rate: float, seed: int):
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    for r in reqs:
+        t += float(rng.exponential(1.0 / rate))
+        r.arrival = t
+
+
+def reset(reqs: List[Request]):
+    for r in reqs:
+        r.t_start = r.t_done = math.nan
+        r.E = None
+        r.status = 0
+        r.batch = -1
+        r.entry = None
+
+
+def _cuda_device(device) -> torch.device:
+    d = torch.device(device)
+    if d.type != "cuda":
+        raise ValueError(f"the serving loop runs on a CUDA device, not {d}")
+    return d if d.index is not None else torch.device("cuda", torch.cuda.current_device())
+
+
+# ----------------------------------------------------------------------------- scene cache
+class SceneEntry:
+    def __init__(self, name: str):
+        self.name = name
+        self.ready = threading.Event()
+        self.resident: Optional[ResidentScene] = None
+        self.error: Optional[BaseException] = None
+        self.in_flight = 0
+        self.last_use = 0.0
+        self.build_s = 0.0
+
+
+class SceneCache:
+    """Resident scenes keyed by catalogue name, built by a worker thread on its own stream."""
+
+    def __init__(self, catalogue: Callable[[str], S.Scene], device="cuda", budget_bytes: Optional[int] = None,
+                 grid_res: int = 512, target_sel: float = 4.0, max_extra_split: int = 4):
+        self.catalogue = catalogue
+        self.device = _cuda_device(device)
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            budget_bytes = int(free * 0.5)
+        self.budget = int(budget_bytes)
+        self.grid_res = grid_res
+        self.target_sel = target_sel
+        self.max_extra_split = max_extra_split
+        self.entries: Dict[str, SceneEntry] = {}
+        self.lock = threading.Lock()
+        self.q: "queue.Queue[Optional[str]]" = queue.Queue()
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.worker = threading.Thread(target=self._work, daemon=True)
+        self.worker.start()
+
+    def close(self):
+        self.q.put(None)
+        self.worker.join()
+
+    def resident_bytes(self) -> int:
+        with self.lock:
+            return sum(e.resident.device_bytes() for e in self.entries.values() if e.resident is not None)
+
+    def request(self, name: str) -> SceneEntry:
+        """The entry of `name`, queueing its build when it is not resident."""
+        with self.lock:
+            e = self.entries.get(name)
+            if e is None:
+                e = SceneEntry(name)
+                self.entries[name] = e
+                self.q.put(name)
+            e.last_use = time.perf_counter()
+            return e
+
+    def _evict_for(self, need: int):
+        with self.lock:
+            used = sum(e.resident.device_bytes() for e in self.entries.values() if e.resident is not None)
+            idle = sorted((e for e in self.entries.values() if e.resident is not None and e.in_flight == 0),
+                          key=lambda e: e.last_use)
+            for e in idle:
+                if used + need <= self.budget:
+                    break
+                used -= e.resident.device_bytes()
+                del self.entries[e.name]
+
+    def build(self, name: str) -> ResidentScene:
+        sc = self.catalogue(name)
+        with torch.cuda.stream(self.stream):
+            ds = bnb.DeviceScene(sc, self.device)
+            cells = bnb.bound_tuples(ds, sc.depth, max_extra_split=self.max_extra_split, stream=self.stream,
+                                     with_e_lo=False)
+            idx = bnb.build_index(cells, grid_res=self.grid_res, stream=self.stream)
+            del cells
+            gamma = gamma_for_target(idx, self.target_sel)
+            rs = ResidentScene(ds, idx, gamma, stream=self.stream)
+        self.stream.synchronize()
+        return rs
+
+    def _work(self):
+        setup_error: Optional[BaseException] = None
+        try:
+            torch.cuda.set_device(self.device)
+        except BaseException as ex:  # every build then fails with this error
+            setup_error = ex
+        while True:
+            name = self.q.get()
+            if name is None:
+                return
+            with self.lock:
+                e = self.entries.get(name)
+            if e is None:
+                continue
+            t = time.perf_counter()
+            try:
+                if setup_error is not None:
+                    raise setup_error
+                rs = self.build(name)
+                self._evict_for(rs.device_bytes())
+                e.resident = rs
+            except BaseException as ex:  # reported to the requests of this scene
+                e.error = ex
+            finally:
+                e.build_s = time.perf_counter() - t
+                e.ready.set()
+
+
+# ----------------------------------------------------------------------------- server
+class _Slot:
+    def __init__(self, runner: BatchRunner):
+        self.runner = runner
+        self.reqs: List[Request] = []
+        self.bufs: List[tuple] = []
+        self.fin: Optional[torch.cuda.Event] = None
+        self.bytes = 0
+
+    @property
+    def busy(self) -> bool:
+        return self.fin is not None
+
+
+class Server:
+    """Continuous-batching server over a SceneCache (see the module docstring)."""
+
+    def __init__(self, cache: SceneCache, max_jobs: int = 64, max_points: int = 1 << 22,
+                 worklist_per_point: float = 8.0, n_slots: int = 2, hbm_budget_bytes: Optional[int] = None,
+                 block_threads: int = 0, blocks_per_sm: int = 0, use_graph: bool = True):
+        self.cache = cache
+        d = cache.device
+        self.device = d
+        self.max_jobs = max_jobs
+        self.max_points = max_points
+        self.wl = int(worklist_per_point * max_points) + (1 << 16)
+        self.launch = (block_threads, blocks_per_sm)
+        self.use_graph = use_graph
+        self.slots = [_Slot(self._runner()) for _ in range(n_slots)]
+        if hbm_budget_bytes is None:
+            hbm_budget_bytes = 8 << 30
+        self.hbm_budget = hbm_budget_bytes  # shading points and outputs of the requests in flight
+        self.in_flight_bytes = 0
+        self.n_batches = 0
+        self.batch_sizes: List[int] = []
+        self.retries = 0
+        self.max_retries = 4
+
+    def _runner(self, wl: Optional[int] = None) -> BatchRunner:
+        return BatchRunner(self.max_jobs, self.max_points, wl or self.wl, block_threads=self.launch[0],
+                           blocks_per_sm=self.launch[1], device=self.device, use_graph=self.use_graph)
+
+    @staticmethod
+    def request_bytes(r: Request) -> int:
+        return r.n_points * 12 * 2  # su, sv, E on the device and pinned on the host
+
+    def warm_up(self):
+        """Capture every slot's graph (on an empty batch) before serving starts."""
+        for s in self.slots:
+            s.runner.submit([])
+            s.runner.result()
+
+    def _launch(self, slot: _Slot, reqs: List[Request], t0: float):
+        runner = slot.runner
+        jobs, bufs = [], []
+        with torch.cuda.stream(runner.stream):
+            for r in reqs:
+                su_p, sv_p = r.host_points()
+                su = su_p.to(self.device, non_blocking=True)
+                sv = sv_p.to(self.device, non_blocking=True)
+                E = torch.empty(r.n_points, dtype=torch.float32, device=self.device)
+                E_h = torch.empty(r.n_points, dtype=torch.float32).pin_memory()
+                e = r.entry
+                on = torch.zeros(e.resident.n_emitters, dtype=torch.uint8)
+                on[list(r.emitters)] = 1
+                on_d = on.pin_memory().to(self.device, non_blocking=True)
+                jobs.append(Job(e.resident, su, sv, E, r.seed, on_d))
+                bufs.append((su_p, sv_p, su, sv, E, E_h, on_d))
+                r.t_start = time.perf_counter() - t0
+        runner.submit(jobs)
+        with torch.cuda.stream(runner.stream):
+            for b in bufs:
+                b[5].copy_(b[4], non_blocking=True)
+            fin = torch.cuda.Event()
+            fin.record(runner.stream)
+        slot.reqs, slot.bufs, slot.fin = reqs, bufs, fin
+        slot.bytes = sum(self.request_bytes(r) for r in reqs)
+        self.in_flight_bytes += slot.bytes
+        for r in reqs:
+            r.batch = self.n_batches
+        self.n_batches += 1
+        self.batch_sizes.append(len(reqs))
+
+    def _complete(self, slot: _Slot, t0: float, pending: collections.deque) -> List[Request]:
+        status, _ = slot.runner.result()
+        now = time.perf_counter() - t0
+        done = []
+        if status != bnb.BNB_OK and self.retries < self.max_retries:
+            # worklist overflow: grow the runner (a new graph) and run the batch again
+            self.retries += 1
+            self.wl *= 2
+            slot.runner = self._runner()
+            for r in reversed(slot.reqs):
+                pending.appendleft(r)
+        elif status != bnb.BNB_OK:
+            for r in slot.reqs:
+                r.status = status
+                r.t_done = now
+                done.append(r)
+        else:
+            for r, b in zip(slot.reqs, slot.bufs):
+                r.E = b[5].numpy().copy()
+                r.t_done = now
+                done.append(r)
+        with self.cache.lock:
+            for r in slot.reqs:
+                r.entry.in_flight -= 1
+        self.in_flight_bytes -= slot.bytes
+        slot.reqs, slot.bufs, slot.fin, slot.bytes = [], [], None, 0
+        return done
+
+    def _form_batch(self, pending: collections.deque, t0: float):
+        """(batch, failed): arrived requests whose scene is resident, in arrival order, while the
+        batch and the HBM budget have room; requests whose scene failed to build."""
+        batch, failed, pts, byts = [], [], 0, self.in_flight_bytes
+        keep = collections.deque()
+        while pending and len(batch) < self.max_jobs:
+            r = pending.popleft()
+            e = self.cache.request(r.scene)
+            if not e.ready.is_set():
+                keep.append(r)
+                continue
+            if e.error is not None:
+                r.status = bnb.BNB_ERR_CUDA
+                r.t_done = time.perf_counter() - t0
+                failed.append(r)
+                continue
+            if r.n_points > self.max_points or self.request_bytes(r) > self.hbm_budget:
+                r.status = bnb.BNB_ERR_CAPACITY  # can never be admitted
+                r.t_done = time.perf_counter() - t0
+                failed.append(r)
+                continue
+            if pts + r.n_points > self.max_points or byts + self.request_bytes(r) > self.hbm_budget:
+                keep.append(r)
+                break
+            with self.cache.lock:
+                e.in_flight += 1
+            r.entry = e
+            batch.append(r)
+            pts += r.n_points
+            byts += self.request_bytes(r)
+        while keep:
+            pending.appendleft(keep.pop())
+        return batch, failed
+
+    def serve(self, reqs: List[Request], timeout_s: float = 600.0) -> List[Request]:
+        """Serve `reqs` (arrival times set) as they arrive; returns them with results and times.
+        Raises TimeoutError when the requests are not all finished `timeout_s` after the start."""
+        order = sorted(reqs, key=lambda r: r.arrival)
+        pending: collections.deque = collections.deque()
+        nxt = 0
+        finished = 0
+        t0 = time.perf_counter()
+        while finished < len(order):
+            now = time.perf_counter() - t0
+            if now > timeout_s:
+                raise TimeoutError(f"serve: {len(order) - finished} of {len(order)} requests unfinished "
+                                   f"after {timeout_s} s")
+            while nxt < len(order) and order[nxt].arrival <= now:
+                r = order[nxt]
+                self.cache.request(r.scene)
+                pending.append(r)
+                nxt += 1
+            progressed = False
+            for s in self.slots:
+                if s.busy and s.fin.query():
+                    finished += len(self._complete(s, t0, pending))
+                    progressed = True
+            for s in self.slots:
+                if not s.busy and pending:
+                    batch, failed = self._form_batch(pending, t0)
+                    finished += len(failed)
+                    if batch:
+                        self._launch(s, batch, t0)
+                        progressed = True
+            if not progressed:
+                nxt_t = order[nxt].arrival if nxt < len(order) else math.inf
+                wait = min(nxt_t - (time.perf_counter() - t0), 2e-4)
+                if wait > 0:
+                    time.sleep(wait)
+        return reqs
+
+
+# ----------------------------------------------------------------------------- baselines
+def _wait_until(t0: float, t: float):
+    while True:
+        d = t - (time.perf_counter() - t0)
+        if d <= 0:
+            return
+        time.sleep(min(d, 1e-3))
+
+
+def plain_per_request(reqs: List[Request], catalogue: Callable[[str], S.Scene], gammas: Dict[str, float],
+                      device="cuda", honour_arrivals: bool = True, grid_res: int = 512,
+                      max_extra_split: int = 4) -> List[Request]:
+    """Each request alone through bnb_bound_tuples (the request's emitters), bnb_build_index and
+    bnb_sample_and_solve, its result read back before the next request starts.  Scene meshes are
+    uploaded once and reused; the precomputation is not."""
+    dev = _cuda_device(device)
+    scenes: Dict[str, bnb.DeviceScene] = {}
+    t0 = time.perf_counter()
+    for r in sorted(reqs, key=lambda r: r.arrival):
+        if honour_arrivals:
+            _wait_until(t0, r.arrival)
+        r.t_start = time.perf_counter() - t0
+        if r.scene not in scenes:
+            scenes[r.scene] = bnb.DeviceScene(catalogue(r.scene), dev)
+        ds = scenes[r.scene].with_emitters(list(r.emitters))
+        sc = ds.scene
+        su_p, sv_p = r.host_points()
+        su = su_p.to(dev, non_blocking=True)
+        sv = sv_p.to(dev, non_blocking=True)
+        cells = bnb.bound_tuples(ds, sc.depth, max_extra_split=max_extra_split, with_e_lo=False)
+        idx = bnb.build_index(cells, grid_res=grid_res)
+        del cells
+        res = bnb.sample_and_solve(ds, idx, gammas[r.scene], r.seed, su=su, sv=sv,
+                                   worklist_capacity=8 * r.n_points + 65536)
+        r.E = res.E.cpu().numpy()
+        r.status = int(res.status.item())
+        r.t_done = time.perf_counter() - t0
+    return reqs
+
+
+def plain_cached(reqs: List[Request], cache: SceneCache, honour_arrivals: bool = True) -> List[Request]:
+    """Each request alone (one job, no graph) on the resident scenes, read back before the next."""
+    dev = cache.device
+    runners: Dict[int, BatchRunner] = {}
+    t0 = time.perf_counter()
+    for r in sorted(reqs, key=lambda r: r.arrival):
+        if honour_arrivals:
+            _wait_until(t0, r.arrival)
+        r.t_start = time.perf_counter() - t0
+        e = cache.request(r.scene)
+        if not e.ready.wait(timeout=600.0) or e.error is not None:
+            raise RuntimeError(f"scene {r.scene} is not resident: {e.error}")
+        runner = runners.get(r.n_points)
+        if runner is None:
+            runner = BatchRunner(1, r.n_points, 8 * r.n_points + 65536, device=dev, use_graph=False)
+            runners[r.n_points] = runner
+        su_p, sv_p = r.host_points()
+        with torch.cuda.stream(runner.stream):
+            su = su_p.to(dev, non_blocking=True)
+            sv = sv_p.to(dev, non_blocking=True)
+            on = torch.zeros(e.resident.n_emitters, dtype=torch.uint8)
+            on[list(r.emitters)] = 1
+            on_d = on.pin_memory().to(dev, non_blocking=True)
+            E = torch.empty(r.n_points, dtype=torch.float32, device=dev)
+        runner.submit([Job(e.resident, su, sv, E, r.seed, on_d)])
+        with torch.cuda.stream(runner.stream):
+            E_h = E.to("cpu", non_blocking=True)
+        r.status, _ = runner.result()
+        runner.stream.synchronize()
+        r.E = E_h.numpy()
+        r.t_done = time.perf_counter() - t0
+    return reqs
+
+
+def summarize(reqs: List[Request]) -> dict:
+    ok = [r for r in reqs if r.E is not None and r.status == 0]
+    lat = np.array([r.latency for r in ok]) if ok else np.zeros(1)
+    t_first = min(r.arrival for r in reqs)
+    t_last = max(r.t_done for r in ok) if ok else t_first
+    pts = sum(r.n_points for r in ok)
+    span = max(t_last - t_first, 1e-9)
+    return {"requests": len(reqs), "completed": len(ok), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "samples_per_s": pts / span, "requests_per_s": len(ok) / span, "span_s": span}
+
+
+def run_workload(n_requests: int = 256, seed: int = 5, load: float = 0.7, device="cuda", max_jobs: int = 64,
+                 max_points: int = 1 << 22, autotune_launch: bool = True, log=print) -> dict:
+    """The serving workload: `n_requests` requests over the catalogue (scene uniform, 64^2..1024^2
+    points, 1..8 lights of the scene's pool) with Poisson arrivals at `load` x the measured
+    capacity of the plain per-request path; the same trace served three ways (plain per request,
+    plain on resident scenes, continuous batching).  Returns the summaries."""
+    from . import batch as BA
+    cache = SceneCache(S.serving_scene, device=device)
+    out = {"workload": f"{n_requests} requests, Poisson arrivals at {load} x plain capacity, scenes "
+                       f"{'/'.join(S.SERVING_SCENES)}, {SIDES[0]}^2..{SIDES[-1]}^2 points, 1..{S.SERVING_POOL} "
+                       f"lights of a pool of {S.SERVING_POOL}"}
+    try:
+        t = time.perf_counter()
+        entries = [cache.request(n) for n in S.SERVING_SCENES]
+        for e in entries:
+            if not e.ready.wait(timeout=900.0):
+                raise TimeoutError(f"scene {e.name} not built within 900 s")
+            if e.error is not None:
+                raise e.error
+        out["scene_build_s"] = {e.name: round(e.build_s, 4) for e in entries}
+        out["resident_bytes"] = cache.resident_bytes()
+        log(f"scenes resident in {time.perf_counter() - t:.2f} s: {out['scene_build_s']}")
+        gammas = {e.name: e.resident.gamma for e in entries}
+        reqs = make_requests(n_requests, seed)
+        for r in reqs:
+            r.host_points()  # the request payloads exist on the host before the run starts
+        # plain per-request capacity: back to back, no arrivals
+        plain_per_request(reqs[:4], S.serving_scene, gammas, device, honour_arrivals=False)  # warm-up
+        reset(reqs)
+        t = time.perf_counter()
+        plain_per_request(reqs, S.serving_scene, gammas, device, honour_arrivals=False)
+        sat = time.perf_counter() - t
+        cap = n_requests / sat
+        out["plain_capacity_req_per_s"] = cap
+        rate = load * cap
+        out["arrival_rate_req_per_s"] = rate
+        log(f"plain per-request capacity {cap:.2f} req/s; arrivals at {rate:.2f} req/s")
+        poisson_arrivals(reqs, rate, seed + 1)
+        reset(reqs)
+        plain_per_request(reqs, S.serving_scene, gammas, device)
+        out["plain"] = summarize(reqs)
+        log(f"plain        {out['plain']}")
+        reset(reqs)
+        plain_cached(reqs, cache)
+        out["plain_cached"] = summarize(reqs)
+        alone = {r.rid: r.E for r in reqs}
+        log(f"plain_cached {out['plain_cached']}")
+        launch = (0, 0)
+        if autotune_launch:
+            rs = entries[-1].resident
+            pts = [torch.as_tensor(a).to(device) for a in S.shading_points(1024, 1024, 1)]
+            E = torch.empty(1024 * 1024, device=device)
+            jobs = [BA.Job(rs, pts[0], pts[1], E, 1)]
+            tune = BA.autotune(jobs, 8 * 1024 * 1024 + (1 << 16))
+            launch = (tune["block_threads"], tune["blocks_per_sm"])
+            out["autotuned_launch"] = {"block_threads": launch[0], "blocks_per_sm": launch[1], "ms": tune["ms"]}
+        srv = Server(cache, max_jobs=max_jobs, max_points=max_points, block_threads=launch[0],
+                     blocks_per_sm=launch[1])
+        srv.warm_up()
+        reset(reqs)
+        srv.serve(reqs)
+        out["served"] = summarize(reqs)
+        out["served"]["batches"] = srv.n_batches
+        out["served"]["mean_batch"] = float(np.mean(srv.batch_sizes)) if srv.batch_sizes else 0.0
+        out["served"]["retries"] = srv.retries
+        out["served_equals_alone"] = all(r.E is not None and np.array_equal(r.E.view(np.uint32),
+                                                                            alone[r.rid].view(np.uint32))
+                                         for r in reqs)
+        log(f"served       {out['served']}  identical to alone: {out['served_equals_alone']}")
+    finally:
+        cache.close()
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="Serving workload: plain per-request vs continuous batching")
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--load", type=float, default=0.7)
+    ap.add_argument("--no-autotune", action="store_true")
+    a = ap.parse_args()
+    from . import build as _build
+    _build.build()
+    res = run_workload(a.requests, a.seed, a.load, autotune_launch=not a.no_autotune)
+    print(json.dumps(res))

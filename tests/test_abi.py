@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(bnb):
 def test_status_strings_and_version(bnb):
     assert bnb.bnb_status_string(0) == "ok"
     assert "capacity" in bnb.bnb_status_string(-2)
-    assert bnb.lib().bnb_abi_version() == 2
+    assert bnb.lib().bnb_abi_version() == 3
 
 
 def test_workspace_queries_are_host_only(bnb):
@@ -92,3 +92,58 @@ def test_no_oracle_import_in_library_path():
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             src = open(f).read()
             assert "import oracle" not in src and "from oracle" not in src and "liboracle" not in src, f
+
+
+def test_ctypes_structs_match_the_header(bnb, tmp_path):
+    """Field offsets and sizes of the Python mirrors equal the C compiler's for every struct."""
+    structs = {n: getattr(bnb, n) for n in ("bnb_surface", "bnb_receiver", "bnb_emitters", "bnb_bound_cfg",
+                                              "bnb_cell_bounds", "bnb_index", "bnb_sample_cfg", "bnb_sample_stats",
+                                              "bnb_job", "bnb_batch_cfg")}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "bnb.h")}"',
+             "int main(void) {"]
+    for n, cls in structs.items():
+        lines.append(f'  printf("{n} sizeof %zu\\n", sizeof({n}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        n, f, v = ln.split()
+        got[(n, f)] = int(v)
+    for n, cls in structs.items():
+        assert got[(n, "sizeof")] == C.sizeof(cls), n
+        for f, _ in cls._fields_:
+            assert got[(n, f)] == getattr(cls, f).offset, (n, f)
+
+
+def test_batched_queries_and_rejections_are_host_only(bnb):
+    s = bnb.bnb_surface()
+    s.n_tris = 100
+    s.n_verts = 121
+    for f in ("px", "py", "pz", "nx", "ny", "nz", "i0", "i1", "i2"):
+        setattr(s, f, 4096)
+    assert bnb.bnb_pack_surface_bytes(C.byref(s)) == 100 * 80
+    assert bnb.bnb_pack_surface(C.byref(s), 4096, 100, None) == bnb.BNB_ERR_INVALID  # too small
+    assert bnb.bnb_pack_surface(C.byref(s), 4100, 8000, None) == bnb.BNB_ERR_INVALID  # misaligned
+    cfg = bnb.bnb_batch_cfg(16, 16, 1 << 20, 1 << 22, 2, 1e-5, 0, 0)
+    ws = bnb.bnb_sample_and_solve_batched_ws(C.byref(cfg))
+    assert ws >= (1 << 20) * 16 + (1 << 22) * 24
+    for bad in (bnb.bnb_batch_cfg(0, 16, 1, 1, 2, 1e-5, 0, 0),         # no job slot
+                bnb.bnb_batch_cfg(16, 65, 1, 1, 2, 1e-5, 0, 0),        # newton_iters > 64
+                bnb.bnb_batch_cfg(16, 16, 1, 1, 2, 0.0, 0, 0),         # tol <= 0
+                bnb.bnb_batch_cfg(16, 16, 1, 1, 2, 1e-5, 96 + 1, 0),   # not a multiple of 32
+                bnb.bnb_batch_cfg(16, 16, 1, 1, 2, 1e-5, 1024, 0),     # above 512 threads
+                bnb.bnb_batch_cfg(16, 16, 1, 1, 2, 1e-5, 0, 65)):      # blocks_per_sm > 64
+        assert bnb.bnb_sample_and_solve_batched_ws(C.byref(bad)) == 0
+    stats = bnb.bnb_sample_stats(4096, 4096, None)
+    assert bnb.bnb_sample_and_solve_batched(4096, 4096, C.byref(cfg), C.byref(stats), 4096, 100, None) == \
+        bnb.BNB_ERR_INVALID  # workspace too small
+    assert bnb.bnb_sample_and_solve_batched(None, 4096, C.byref(cfg), C.byref(stats), 4096, ws, None) == \
+        bnb.BNB_ERR_INVALID
+    assert bnb.bnb_sample_and_solve_batched(4100, 4096, C.byref(cfg), C.byref(stats), 4096, ws, None) == \
+        bnb.BNB_ERR_INVALID  # job table not 8-byte aligned
