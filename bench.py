@@ -345,6 +345,10 @@ def run_gpu(args):
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches_per_step(n_points, sc.grid_res) * args.steps,
             "clocks": clk.summary()}
+    if args.serving_requests > 0 and rank == 0 and world == 1 and not args.emitters:
+        del cb, idx, cb_ws, ix_ws, sm_ws, flush
+        torch.cuda.empty_cache()
+        line["serving"] = serving_summary(args.serving_requests, dev)
     if not args.no_cpu_baseline and rank == 0 and world == 1 and not args.emitters:
         line["cpu_baseline"] = cpu_baseline(counters[0] / n_points, counters[1] / n_points)
     if rank == 0:
@@ -364,7 +368,7 @@ def scan_launches(n: int) -> int:
 def launches_per_step(n_points: int, G: int) -> int:
     bound = 1 + 1 + 4                                # pack, base, 4 split levels
     index = 2 + scan_launches(G * G) + 3 + scan_launches(G * G) + 2
-    sample = 1 + 1 + scan_launches(n_points) + 1 + 1 + 1
+    sample = 1 + 1 + scan_launches(n_points) + 1 + 2 + 1  # pack, count, scan, fill, solve32 + polish, reduce
     return bound + index + sample
 
 
@@ -394,6 +398,27 @@ def calibrate_gamma(bnb, ds, idx, target: float) -> float:
         else:
             hi = mid
     return float(2.0 ** hi)
+
+
+def serving_summary(n_requests: int, dev) -> dict:
+    """The request workload served by the continuous-batching loop next to the plain per-request
+    paths (p50/p99 latency, shading samples/s); outside the timed region of the bound benchmark."""
+    from paper_2504_19163_gb300 import serving as SV
+    try:
+        res = SV.run_workload(n_requests, device=dev, log=lambda *a: None)
+    except Exception as ex:  # reported in the line; the bound benchmark above stands
+        return {"error": f"{type(ex).__name__}: {ex}"}
+    keep = ("p50_ms", "p99_ms", "samples_per_s", "requests_per_s", "mean_batch")
+    out = {"workload": res["workload"], "capacity_req_per_s": res["capacity_req_per_s"],
+           "served_equals_alone": res["served_equals_alone"], "autotuned_launch": res.get("autotuned_launch"),
+           "scene_build_s": res["scene_build_s"]}
+    for tag in ("load_plain", "load_cached", "burst"):
+        b = res[tag]
+        out[tag] = {"arrival_rate_req_per_s": b["arrival_rate_req_per_s"]}
+        for m in ("plain", "plain_cached", "served"):
+            if m in b:
+                out[tag][m] = {k: b[m][k] for k in keep if k in b[m]}
+    return out
 
 
 def cpu_baseline(u_per_point: float, s_per_point: float) -> dict:
@@ -426,6 +451,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--emitters", type=int, default=0, help="use only the first N area-light samples (profiling case)")
+    ap.add_argument("--serving-requests", type=int, default=256,
+                    help="requests of the serving workload reported under 'serving' (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -25,6 +25,9 @@ struct BatchWs {
   uint64_t* wl_key;
   float* wl_p;
   float* contrib;
+  int64_t* pl_count;  // float32 survivors handed to the float64 polish
+  int64_t* pl_idx;
+  float *pl_u, *pl_v;
   void* scan;
   size_t bytes;
 };
@@ -44,6 +47,10 @@ static BatchWs carve_batch_ws(void* base, const bnb_batch_cfg* c) {
   w.wl_key = (uint64_t*)take((size_t)c->worklist_capacity * 8);
   w.wl_p = (float*)take((size_t)c->worklist_capacity * 4);
   w.contrib = (float*)take((size_t)c->worklist_capacity * 4);
+  w.pl_count = (int64_t*)take(8);
+  w.pl_idx = (int64_t*)take((size_t)c->worklist_capacity * 8);
+  w.pl_u = (float*)take((size_t)c->worklist_capacity * 4);
+  w.pl_v = (float*)take((size_t)c->worklist_capacity * 4);
   w.scan = take(scan_ws_bytes(c->max_points));
   w.bytes = o;
   return w;
@@ -120,6 +127,9 @@ struct BatchParams {
   uint64_t* wl_key;
   float* wl_p;
   float* contrib;
+  int64_t* pl_count;
+  int64_t* pl_idx;
+  float *pl_u, *pl_v;
   int64_t* counters;
   int32_t* status;
   int32_t newton_iters, polish_iters;
@@ -187,10 +197,10 @@ __global__ void __launch_bounds__(512) sample_b_k(BatchParams B) {
   }
 }
 
-__global__ void __launch_bounds__(512) solve_b_k(BatchParams B) {
+// float32 Newton phase over every selection of the batch (see newton32); survivors are listed.
+__global__ void __launch_bounds__(512) solve32_b_k(BatchParams B) {
   const int nj = max(0, min(*B.n_jobs, B.max_jobs));
   const int64_t n = min(B.woff[B.max_points], B.wl_cap);
-  long long roots = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = B.wl_point[i];
     const int j = job_of(B.job_off, nj, p);
@@ -198,17 +208,46 @@ __global__ void __launch_bounds__(512) solve_b_k(BatchParams B) {
     const int64_t lp = p - B.job_off[j];
     const uint64_t k = B.wl_key[i];
     const int e = (int)(k >> 48), t = (int)(k & 0xFFFFFFull);
-    float c = 0.0f;
+    bool need = false;
+    float u = 0.0f, v = 0.0f;
     if (t < J.n_tris && e < J.n_emitters) {
       float pf[3][3], nf[3][3];
       load_tri_s((const float4*)J.packed_tris, t, pf, nf);
       const float x0[3] = {__ldg(J.ex + e), __ldg(J.ey + e), __ldg(J.ez + e)};
-      const double E = solve_tuple(pf, nf, x0, __ldg(J.ei + e), J.rp0, J.re1, J.re2, J.su[lp], J.sv[lp],
-                                   B.newton_iters, B.polish_iters, B.tol);
-      if (E >= 0.0) {
-        c = (float)(E / (double)B.wl_p[i]);
-        ++roots;
-      }
+      need = newton32(pf, nf, x0, __ldg(J.ei + e), J.rp0, J.re1, J.re2, J.su[lp], J.sv[lp], B.newton_iters, u, v);
+    }
+    if (!need) B.contrib[i] = 0.0f;
+    const int64_t q = warp_append(need, B.pl_count);
+    if (need) {
+      B.pl_idx[q] = i;
+      B.pl_u[q] = u;
+      B.pl_v[q] = v;
+    }
+  }
+}
+
+// float64 polish of the listed selections, acceptance tests, contribution E(root) / P.
+__global__ void __launch_bounds__(512) polish_b_k(BatchParams B) {
+  const int nj = max(0, min(*B.n_jobs, B.max_jobs));
+  const int64_t n = *B.pl_count;
+  long long roots = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = B.pl_idx[q];
+    const int64_t p = B.wl_point[i];
+    const int j = job_of(B.job_off, nj, p);
+    const bnb_job& J = B.jobs[j];
+    const int64_t lp = p - B.job_off[j];
+    const uint64_t k = B.wl_key[i];
+    const int e = (int)(k >> 48), t = (int)(k & 0xFFFFFFull);
+    float pf[3][3], nf[3][3];
+    load_tri_s((const float4*)J.packed_tris, t, pf, nf);
+    const float x0[3] = {__ldg(J.ex + e), __ldg(J.ey + e), __ldg(J.ez + e)};
+    const double E = polish64(pf, nf, x0, __ldg(J.ei + e), J.rp0, J.re1, J.re2, J.su[lp], J.sv[lp],
+                              B.polish_iters, B.tol, B.pl_u[q], B.pl_v[q]);
+    float c = 0.0f;
+    if (E >= 0.0) {
+      c = (float)(E / (double)B.wl_p[i]);
+      ++roots;
     }
     B.contrib[i] = c;
   }
@@ -250,6 +289,10 @@ cudaError_t launch_sample_and_solve_batched(const bnb_job* jobs, const int32_t* 
   B.wl_key = w.wl_key;
   B.wl_p = w.wl_p;
   B.contrib = w.contrib;
+  B.pl_count = w.pl_count;
+  B.pl_idx = w.pl_idx;
+  B.pl_u = w.pl_u;
+  B.pl_v = w.pl_v;
   B.counters = stats->counters;
   B.status = stats->status;
   B.newton_iters = c->newton_iters;
@@ -262,7 +305,9 @@ cudaError_t launch_sample_and_solve_batched(const bnb_job* jobs, const int32_t* 
   cudaError_t e = launch_exclusive_scan(w.n_sel, w.woff, c->max_points, w.scan, st);
   if (e != cudaSuccess) return e;
   sample_b_k<true><<<(unsigned)pblocks, threads, 0, st>>>(B);
-  solve_b_k<<<sms * per_sm, threads, 0, st>>>(B);
+  if ((e = cudaMemsetAsync(w.pl_count, 0, sizeof(int64_t), st)) != cudaSuccess) return e;
+  solve32_b_k<<<sms * per_sm, threads, 0, st>>>(B);
+  polish_b_k<<<sms * per_sm, threads, 0, st>>>(B);
   reduce_b_k<<<(unsigned)pblocks, threads, 0, st>>>(B);
   return cudaGetLastError();
 }

@@ -352,20 +352,37 @@ __device__ __forceinline__ TP<T, 3> q_of(const Dir<T>& D, const T (&e1)[3], cons
 
 // ------------------------------------------------------------------ ratio helpers
 // Track min/max of p/q over a coefficient with intervals [pl,ph] / [ql,qh], ql > 0, given
-// rl = rcp(ql), rh = rcp(qh) (round-to-nearest).  Each product carries at most two roundings;
-// the caller widens the final min/max by the relative factor kRelDiv.
+// Reciprocals of positive interval ends for the ratio bounds, each within the relative error
+// FP<T>::rcp_rel of the exact value.  rcp_hi(x) stands for 1/x where an upper-side value is needed
+// (x is clamped to rcp_big, which can only enlarge the result); rcp_lo(x) where a lower-side value
+// is needed (0 above rcp_big).
+template <typename T>
+__device__ __forceinline__ T rcp_hi(T x) {
+  return FP<T>::rcp_fast(fmin(x, (T)FP<T>::rcp_big));
+}
+template <typename T>
+__device__ __forceinline__ T rcp_lo(T x) {
+  return x > (T)FP<T>::rcp_big ? T(0) : FP<T>::rcp_fast(x);
+}
+// rl = rcp_hi(ql), rh = rcp_lo(qh).  Each ratio carries the reciprocal's error and one product
+// rounding; the caller widens the final min/max by the relative factor of widen_lo / widen_hi.
 template <typename T>
 __device__ __forceinline__ void ratio_acc(T pl, T ph, T rl, T rh, T& mn, T& mx) {
   mn = fmin(mn, pl * (pl >= T(0) ? rh : rl));
   mx = fmax(mx, ph * (ph >= T(0) ? rl : rh));
 }
+// A ratio p = fl(n * r) with r = (1/d)(1 + d1), |d1| <= rcp_rel, satisfies
+// n/d = p / ((1 + d1)(1 + d2)), |d2| <= u: the exact ratio lies within the relative distance
+// rcp_rel + u + (rcp_rel + u)^2 < rcp_rel + 1.5 u of p.
+template <typename T>
+constexpr T kWiden = (T)(FP<T>::rcp_rel + 1.5 * FP<T>::u);
 template <typename T>
 __device__ __forceinline__ T widen_lo(T x) {
-  return FP<T>::fma_rd(-fabs(x), (T)(2.5 * FP<T>::u), x);
+  return FP<T>::fma_rd(-fabs(x), kWiden<T>, x);
 }
 template <typename T>
 __device__ __forceinline__ T widen_hi(T x) {
-  return FP<T>::fma_ru(fabs(x), (T)(2.5 * FP<T>::u), x);
+  return FP<T>::fma_ru(fabs(x), kWiden<T>, x);
 }
 
 // Interval of coefficient i of a tracked polynomial (scaled form).
@@ -418,14 +435,20 @@ __device__ __forceinline__ void irr_step(const TP<T, 9>& Q3, const T (&F0)[6], c
   constexpr T C = MULTUP<T, 11, G>;
   const T ml = FP<T>::fma_rd(-acc.EM, C, mm), mh = FP<T>::fma_ru(acc.EM, C, mm);
   if (!(ml > tiny_pos<T>())) acc.unbounded = true;
-  const T rl = FP<T>::rcp_rn(ml), rh = FP<T>::rcp_rn(mh);
   const T n1h = FP<T>::fma_ru(acc.EN1, C, n1);
-  acc.eh_mx = fmax(acc.eh_mx, n1h * (n1h >= T(0) ? rl : rh));
   if constexpr (LO) {
+    const T rl = rcp_hi(ml), rh = rcp_lo(mh);
+    acc.eh_mx = fmax(acc.eh_mx, n1h * (n1h >= T(0) ? rl : rh));
     const T n0l = FP<T>::fma_rd(-acc.EN0, C, n0);
     acc.el_mn = fmin(acc.el_mn, n0l * (n0l >= T(0) ? rh : rl));
     const T n1l = FP<T>::fma_rd(-acc.EN1, C, n1);
     acc.eh_in = fmax(acc.eh_in, n1l * (n1l >= T(0) ? rh : rl));
+  } else {
+    // only the reciprocal the numerator's sign selects: rcp_hi(ml) for n1h >= 0, rcp_lo(mh) below
+    const bool pos = n1h >= T(0);
+    T r = FP<T>::rcp_fast(fmin(pos ? ml : mh, (T)FP<T>::rcp_big));
+    if (!pos && mh > (T)FP<T>::rcp_big) r = T(0);
+    acc.eh_mx = fmax(acc.eh_mx, n1h * r);
   }
 }
 
@@ -789,7 +812,7 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
       // Q > 0 is certified; a float32 interval reaching down to 0 makes the ratio unbounded
       // on the side of the numerator's sign only.
       const bool open = !(ql > tiny_pos<T>());
-      const T rl = open ? F::inf() : F::rcp_rn(ql), rh = F::rcp_rn(qh);
+      const T rl = open ? F::inf() : rcp_hi(ql), rh = rcp_lo(qh);
       ratio_acc(al, ah, rl, rh, umn, umx);
       ratio_acc(bl, bh, rl, rh, vmn, vmx);
       if (open) {  // 0 * inf: a zero numerator end stays 0

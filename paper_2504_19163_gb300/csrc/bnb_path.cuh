@@ -151,26 +151,42 @@ __device__ __forceinline__ bool newton_step(const Path<T>& P, T tu, T tv, bool d
   return isfinite(u) && isfinite(v);
 }
 
-// One tuple's Newton solve at a receiver point (Sec. 6.1 "Root-finding", deterministic init):
-// float32 damped steps from the centroid, float64 polish, acceptance tests.  Returns the path
-// irradiance E (float64) or a negative value when no admissible root is found.
-__device__ __forceinline__ double solve_tuple(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0)[3],
-                                              float I0, const float (&rp0)[3], const float (&re1)[3],
-                                              const float (&re2)[3], float tuf, float tvf, int newton_iters,
-                                              int polish_iters, float tol) {
-  float u = 1.0f / 3.0f, v = 1.0f / 3.0f;
-  bool good = true;
+// One tuple's Newton solve at a receiver point (Sec. 6.1 "Root-finding", deterministic init) in
+// two phases, so that the float64 work runs only for the tuples that need it:
+//
+//   newton32  float32 damped steps from the centroid.  Returns false when the tuple has no
+//             admissible root: a step failed (non-finite or singular), or the iteration converged
+//             (last step below 1e-6, so the root is known to about 1e-6) more than kOutside = 1e-3
+//             outside the triangle, a distance the float64 polish, whose steps from there are of
+//             the size of the float32 root error, cannot cover.  Otherwise (u, v) is the start of
+//             the polish.
+//   polish64  float64 polish steps and the acceptance tests.  Returns the path irradiance E
+//             (float64), or a negative value when no admissible root is found.
+__device__ __forceinline__ bool newton32(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0)[3],
+                                         float I0, const float (&rp0)[3], const float (&re1)[3], const float (&re2)[3],
+                                         float tuf, float tvf, int newton_iters, float& u, float& v) {
+  u = 1.0f / 3.0f;
+  v = 1.0f / 3.0f;
+  bool converged = false;
   for (int it = 0; it < newton_iters; ++it) {
     const Path<float> P = eval_path<float>(pf, nf, x0, I0, rp0, re1, re2, u, v);
     float step;
-    if (!newton_step<float>(P, tuf, tvf, true, u, v, step)) {
-      good = false;
+    if (!newton_step<float>(P, tuf, tvf, true, u, v, step)) return false;
+    if (step < 1e-6f) {
+      converged = true;
       break;
     }
-    if (step < 1e-6f) break;
   }
-  if (!good) return -1.0;
+  constexpr float kOutside = 1e-3f;
+  return !(converged && fminf(fminf(u, v), 1.0f - u - v) < -kOutside);
+}
+
+__device__ __forceinline__ double polish64(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0)[3],
+                                           float I0, const float (&rp0)[3], const float (&re1)[3],
+                                           const float (&re2)[3], float tuf, float tvf, int polish_iters, float tol,
+                                           float u, float v) {
   double ud = u, vd = v;
+  bool good = true;
   for (int it = 0; it < polish_iters && good; ++it) {
     const Path<double> P = eval_path<double>(pf, nf, x0, I0, rp0, re1, re2, ud, vd);
     double step;
@@ -184,6 +200,20 @@ __device__ __forceinline__ double solve_tuple(const float (&pf)[3][3], const flo
   const bool inside = ud >= 0.0 && vd >= 0.0 && ud + vd <= 1.0;
   if (P.ok && res < (double)tol && inside && P.t > 0.0 && isfinite(P.E)) return P.E;
   return -1.0;
+}
+
+// Appends the calling lane to a device list when `need` is set (one atomic per warp); returns the
+// lane's list position, or -1.  Every lane active at the call must make it.
+__device__ __forceinline__ int64_t warp_append(bool need, int64_t* count) {
+  const unsigned active = __activemask();
+  const unsigned m = __ballot_sync(active, need);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(active) - 1;
+  unsigned long long base = 0;
+  if (lane == leader && m != 0u) base = atomicAdd((unsigned long long*)count, (unsigned long long)__popc(m));
+  base = __shfl_sync(active, base, leader);
+  if (!need) return -1;
+  return (int64_t)base + __popc(m & ((1u << lane) - 1u));
 }
 
 }  // namespace bnb

@@ -86,6 +86,16 @@ struct FP<float> {
   __device__ static __forceinline__ float sqrt_ru(float a) { return __fsqrt_ru(a); }
   __device__ static __forceinline__ float sqrt_rd(float a) { return __fsqrt_rd(a); }
   __device__ static __forceinline__ float rcp_rn(float a) { return __frcp_rn(a); }
+  // Hardware reciprocal approximation (rcp.approx.ftz.f32, one MUFU operation): relative error at
+  // most rcp_rel = 2^-23 (1 ulp) for normal inputs up to rcp_big, checked exhaustively over that
+  // range by the test suite.  Inputs above rcp_big would give flushed subnormal results.
+  static constexpr double rcp_rel = 1.1920928955078125e-07;  // 2^-23
+  static constexpr float rcp_big = 1.329227995784916e36f;    // 2^120
+  __device__ static __forceinline__ float rcp_fast(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+  }
   __device__ static __forceinline__ float inf() { return __int_as_float(0x7f800000); }
 };
 
@@ -104,6 +114,10 @@ struct FP<double> {
   __device__ static __forceinline__ double sqrt_ru(double a) { return __dsqrt_ru(a); }
   __device__ static __forceinline__ double sqrt_rd(double a) { return __dsqrt_rd(a); }
   __device__ static __forceinline__ double rcp_rn(double a) { return __drcp_rn(a); }
+  // float64: the correctly rounded reciprocal (relative error at most u).
+  static constexpr double rcp_rel = 1.1102230246251565e-16;  // 2^-53
+  static constexpr double rcp_big = 1e300;
+  __device__ static __forceinline__ double rcp_fast(double a) { return __drcp_rn(a); }
   __device__ static __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
 };
 

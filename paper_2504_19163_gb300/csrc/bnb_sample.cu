@@ -8,9 +8,10 @@
 //                     the tuple is selected when r < P.  Counts per point.
 //   scan              -> worklist offsets (point order, then key order).
 //   sample_k (fill)   the same draws, writing (point, key, P).
-//   solve_k           per selected tuple: Newton's method in T1's barycentric
+//   solve32_k         per selected tuple: Newton's method in T1's barycentric
 //                     coordinates from the centroid (deterministic init), float32
-//                     damped steps then float64 polish steps, acceptance tests,
+//                     damped steps; tuples left with a possible root are listed.
+//   polish_k          per listed tuple: float64 polish steps, acceptance tests,
 //                     contribution E(root) / P.
 //   reduce_k          per point, contributions summed in worklist order.
 #include <stdint.h>
@@ -106,25 +107,52 @@ struct SolveParams {
   float tol;
   float* contrib;
   int64_t* counters;
+  // tuples handed from the float32 phase to the float64 polish
+  int64_t* pl_count;
+  int64_t* pl_idx;
+  float *pl_u, *pl_v;
 };
 
-__global__ void __launch_bounds__(256) solve_k(SolveParams S) {
+// float32 Newton phase over every selection: contributions of the tuples without an admissible
+// root are 0 now; the others go to the polish list with their float32 root.
+__global__ void __launch_bounds__(256) solve32_k(SolveParams S) {
   const int64_t n = min(*S.n_wl, S.wl_cap);
-  long long roots = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t k = S.wl_key[i];
     const int e = (int)(k >> 48), t = (int)(k & 0xFFFFFFull);
-    if (t >= S.n_tris || e >= S.n_emitters) {  // key from another scene: no path, no read
-      S.contrib[i] = 0.0f;
-      continue;
+    bool need = false;
+    float u = 0.0f, v = 0.0f;
+    if (t < S.n_tris && e < S.n_emitters) {  // a key from another scene has no path and reads nothing
+      float pf[3][3], nf[3][3];
+      load_tri_s(S.tri, t, pf, nf);
+      const float x0[3] = {__ldg(S.ex + e), __ldg(S.ey + e), __ldg(S.ez + e)};
+      const int64_t pt = S.wl_point[i];
+      need = newton32(pf, nf, x0, __ldg(S.ei + e), S.rp0, S.re1, S.re2, S.su[pt], S.sv[pt], S.newton_iters, u, v);
     }
+    if (!need) S.contrib[i] = 0.0f;
+    const int64_t j = warp_append(need, S.pl_count);
+    if (need) {
+      S.pl_idx[j] = i;
+      S.pl_u[j] = u;
+      S.pl_v[j] = v;
+    }
+  }
+}
+
+// float64 polish of the listed tuples, acceptance tests, contribution E(root) / P.
+__global__ void __launch_bounds__(256) polish_k(SolveParams S) {
+  const int64_t n = *S.pl_count;
+  long long roots = 0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = S.pl_idx[j];
+    const uint64_t k = S.wl_key[i];
+    const int e = (int)(k >> 48), t = (int)(k & 0xFFFFFFull);
     float pf[3][3], nf[3][3];
     load_tri_s(S.tri, t, pf, nf);
     const float x0[3] = {__ldg(S.ex + e), __ldg(S.ey + e), __ldg(S.ez + e)};
-    const float I0 = __ldg(S.ei + e);
     const int64_t pt = S.wl_point[i];
-    const double E = solve_tuple(pf, nf, x0, I0, S.rp0, S.re1, S.re2, S.su[pt], S.sv[pt], S.newton_iters,
-                                 S.polish_iters, S.tol);
+    const double E = polish64(pf, nf, x0, __ldg(S.ei + e), S.rp0, S.re1, S.re2, S.su[pt], S.sv[pt],
+                              S.polish_iters, S.tol, S.pl_u[j], S.pl_v[j]);
     float c = 0.0f;
     if (E >= 0.0) {
       c = (float)(E / (double)S.wl_p[i]);
@@ -156,6 +184,9 @@ struct SampleWs {
   uint64_t* wl_key;
   float* wl_p;
   float* contrib;
+  int64_t* pl_count;
+  int64_t* pl_idx;
+  float *pl_u, *pl_v;
   void* scan;
   size_t bytes;
 };
@@ -175,6 +206,10 @@ static SampleWs carve_sample_ws(void* base, int64_t n_tris, int64_t n_points, in
   w.wl_key = (uint64_t*)take((size_t)wl_cap * 8);
   w.wl_p = (float*)take((size_t)wl_cap * 4);
   w.contrib = (float*)take((size_t)wl_cap * 4);
+  w.pl_count = (int64_t*)take(8);
+  w.pl_idx = (int64_t*)take((size_t)wl_cap * 8);
+  w.pl_u = (float*)take((size_t)wl_cap * 4);
+  w.pl_v = (float*)take((size_t)wl_cap * 4);
   w.scan = take(scan_ws_bytes(n_points));
   w.bytes = o;
   return w;
@@ -244,7 +279,13 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_receiver* r
   S.tol = cfg->tol;
   S.contrib = w.contrib;
   S.counters = stats->counters;
-  solve_k<<<sms * 16, 256, 0, st>>>(S);
+  S.pl_count = w.pl_count;
+  S.pl_idx = w.pl_idx;
+  S.pl_u = w.pl_u;
+  S.pl_v = w.pl_v;
+  if ((e = cudaMemsetAsync(w.pl_count, 0, sizeof(int64_t), st)) != cudaSuccess) return e;
+  solve32_k<<<sms * 16, 256, 0, st>>>(S);
+  polish_k<<<sms * 16, 256, 0, st>>>(S);
   reduce_k<<<(unsigned)pblocks, 256, 0, st>>>(w.woff, w.contrib, n_points, cfg->worklist_capacity, E_out);
   return cudaGetLastError();
 }

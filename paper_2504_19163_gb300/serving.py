@@ -452,10 +452,12 @@ def plain_per_request(reqs: List[Request], catalogue: Callable[[str], S.Scene], 
     return reqs
 
 
-def plain_cached(reqs: List[Request], cache: SceneCache, honour_arrivals: bool = True) -> List[Request]:
-    """Each request alone (one job, no graph) on the resident scenes, read back before the next."""
+def plain_cached(reqs: List[Request], cache: SceneCache, honour_arrivals: bool = True,
+                 runners: Optional[Dict[int, BatchRunner]] = None) -> List[Request]:
+    """Each request alone (one job, no graph) on the resident scenes, read back before the next.
+    `runners` (one per request size, created on first use) may be kept across calls."""
     dev = cache.device
-    runners: Dict[int, BatchRunner] = {}
+    runners = {} if runners is None else runners
     t0 = time.perf_counter()
     for r in sorted(reqs, key=lambda r: r.arrival):
         if honour_arrivals:
@@ -501,14 +503,20 @@ def summarize(reqs: List[Request]) -> dict:
 def run_workload(n_requests: int = 256, seed: int = 5, load: float = 0.7, device="cuda", max_jobs: int = 64,
                  max_points: int = 1 << 22, autotune_launch: bool = True, log=print) -> dict:
     """The serving workload: `n_requests` requests over the catalogue (scene uniform, 64^2..1024^2
-    points, 1..8 lights of the scene's pool) with Poisson arrivals at `load` x the measured
-    capacity of the plain per-request path; the same trace served three ways (plain per request,
-    plain on resident scenes, continuous batching).  Returns the summaries."""
+    points, 1..8 lights of the scene's pool), served three ways (plain per request, plain on
+    resident scenes, continuous batching) on three arrival traces:
+
+    * load_plain : Poisson arrivals at `load` x the measured capacity of the plain per-request
+                   path (bound pass, index, sample and solve per request);
+    * load_cached: Poisson arrivals at `load` x the measured capacity of the plain path on
+                   resident scenes (one request at a time, no batching);
+    * burst      : every request arrives at once (throughput).
+    Every served estimate is checked bit for bit against the same request served alone."""
     from . import batch as BA
     cache = SceneCache(S.serving_scene, device=device)
-    out = {"workload": f"{n_requests} requests, Poisson arrivals at {load} x plain capacity, scenes "
-                       f"{'/'.join(S.SERVING_SCENES)}, {SIDES[0]}^2..{SIDES[-1]}^2 points, 1..{S.SERVING_POOL} "
-                       f"lights of a pool of {S.SERVING_POOL}"}
+    out = {"workload": f"{n_requests} requests, scenes {'/'.join(S.SERVING_SCENES)}, {SIDES[0]}^2..{SIDES[-1]}^2 "
+                       f"points, 1..{S.SERVING_POOL} lights of a pool of {S.SERVING_POOL}; Poisson arrivals at "
+                       f"{load} x the capacity of each plain path, and a burst"}
     try:
         t = time.perf_counter()
         entries = [cache.request(n) for n in S.SERVING_SCENES]
@@ -524,49 +532,76 @@ def run_workload(n_requests: int = 256, seed: int = 5, load: float = 0.7, device
         reqs = make_requests(n_requests, seed)
         for r in reqs:
             r.host_points()  # the request payloads exist on the host before the run starts
-        # plain per-request capacity: back to back, no arrivals
-        plain_per_request(reqs[:4], S.serving_scene, gammas, device, honour_arrivals=False)  # warm-up
-        reset(reqs)
-        t = time.perf_counter()
-        plain_per_request(reqs, S.serving_scene, gammas, device, honour_arrivals=False)
-        sat = time.perf_counter() - t
-        cap = n_requests / sat
-        out["plain_capacity_req_per_s"] = cap
-        rate = load * cap
-        out["arrival_rate_req_per_s"] = rate
-        log(f"plain per-request capacity {cap:.2f} req/s; arrivals at {rate:.2f} req/s")
-        poisson_arrivals(reqs, rate, seed + 1)
-        reset(reqs)
-        plain_per_request(reqs, S.serving_scene, gammas, device)
-        out["plain"] = summarize(reqs)
-        log(f"plain        {out['plain']}")
-        reset(reqs)
-        plain_cached(reqs, cache)
-        out["plain_cached"] = summarize(reqs)
-        alone = {r.rid: r.E for r in reqs}
-        log(f"plain_cached {out['plain_cached']}")
         launch = (0, 0)
         if autotune_launch:
             rs = entries[-1].resident
-            pts = [torch.as_tensor(a).to(device) for a in S.shading_points(1024, 1024, 1)]
-            E = torch.empty(1024 * 1024, device=device)
-            jobs = [BA.Job(rs, pts[0], pts[1], E, 1)]
+            su, sv = reqs[0].host_points() if reqs[0].n_side == 1024 else Request(0, "", (), 1024, 0).host_points()
+            jobs = [BA.Job(rs, su.to(device), sv.to(device), torch.empty(1024 * 1024, device=device), 1)]
             tune = BA.autotune(jobs, 8 * 1024 * 1024 + (1 << 16))
             launch = (tune["block_threads"], tune["blocks_per_sm"])
             out["autotuned_launch"] = {"block_threads": launch[0], "blocks_per_sm": launch[1], "ms": tune["ms"]}
         srv = Server(cache, max_jobs=max_jobs, max_points=max_points, block_threads=launch[0],
                      blocks_per_sm=launch[1])
         srv.warm_up()
+
+        # every request alone (the reference for the identity check) and the cached capacity
+        runners: Dict[int, BatchRunner] = {}
+        for side in SIDES:  # one runner per request size, created before any timing
+            plain_cached([Request(0, S.SERVING_SCENES[0], (0,), side, 0)], cache, False, runners)
         reset(reqs)
-        srv.serve(reqs)
-        out["served"] = summarize(reqs)
-        out["served"]["batches"] = srv.n_batches
-        out["served"]["mean_batch"] = float(np.mean(srv.batch_sizes)) if srv.batch_sizes else 0.0
-        out["served"]["retries"] = srv.retries
-        out["served_equals_alone"] = all(r.E is not None and np.array_equal(r.E.view(np.uint32),
-                                                                            alone[r.rid].view(np.uint32))
-                                         for r in reqs)
-        log(f"served       {out['served']}  identical to alone: {out['served_equals_alone']}")
+        t = time.perf_counter()
+        plain_cached(reqs, cache, honour_arrivals=False, runners=runners)
+        cap_cached = n_requests / (time.perf_counter() - t)
+        alone = {r.rid: r.E for r in reqs}
+        # plain per-request capacity
+        plain_per_request(reqs[:4], S.serving_scene, gammas, device, honour_arrivals=False)  # warm-up
+        reset(reqs)
+        t = time.perf_counter()
+        plain_per_request(reqs, S.serving_scene, gammas, device, honour_arrivals=False)
+        cap_plain = n_requests / (time.perf_counter() - t)
+        out["capacity_req_per_s"] = {"plain": cap_plain, "plain_cached": cap_cached}
+        log(f"capacity: plain {cap_plain:.2f} req/s, plain_cached {cap_cached:.2f} req/s")
+
+        identical = True
+
+        def serve_trace(tag):
+            nonlocal identical
+            b0, s0, r0 = srv.n_batches, len(srv.batch_sizes), srv.retries
+            reset(reqs)
+            srv.serve(reqs)
+            res = summarize(reqs)
+            sizes = srv.batch_sizes[s0:]
+            res.update(batches=srv.n_batches - b0, mean_batch=float(np.mean(sizes)) if sizes else 0.0,
+                       max_batch=int(max(sizes)) if sizes else 0, retries=srv.retries - r0)
+            same = all(r.E is not None and np.array_equal(r.E.view(np.uint32), alone[r.rid].view(np.uint32))
+                       for r in reqs)
+            identical = identical and same
+            log(f"{tag:12s} served       {res}")
+            return res
+
+        for tag, rate, modes in (("load_plain", load * cap_plain, ("plain", "plain_cached", "served")),
+                                 ("load_cached", load * cap_cached, ("plain_cached", "served")),
+                                 ("burst", math.inf, ("plain_cached", "served"))):
+            if math.isinf(rate):
+                for r in reqs:
+                    r.arrival = 0.0
+            else:
+                poisson_arrivals(reqs, rate, seed + 1)
+            block = {"arrival_rate_req_per_s": None if math.isinf(rate) else rate}
+            for m in modes:
+                if m == "served":
+                    block[m] = serve_trace(tag)
+                    continue
+                reset(reqs)
+                if m == "plain":
+                    plain_per_request(reqs, S.serving_scene, gammas, device)
+                else:
+                    plain_cached(reqs, cache, runners=runners)
+                block[m] = summarize(reqs)
+                log(f"{tag:12s} {m:12s} {block[m]}")
+            out[tag] = block
+        out["served_equals_alone"] = identical
+        log(f"every served estimate identical to the request served alone: {identical}")
     finally:
         cache.close()
     return out
