@@ -232,6 +232,8 @@ PV pv_subc(const PV& a, V3 c) {
   for (auto& v : r.z.c) v -= c.z;
   return r;
 }
+PV pv_scale(const PV& a, double s) { return {pscale(a.x, s), pscale(a.y, s), pscale(a.z, s)}; }
+PV pv_elev(const PV& a, int n) { return {pelevate_to(a.x, n), pelevate_to(a.y, n), pelevate_to(a.z, n)}; }
 PV pv_crossc(const PV& a, V3 b) {  // a x b, b constant
   return {padd(pscale(a.y, b.z), pscale(a.z, b.y), -1.0), padd(pscale(a.z, b.x), pscale(a.x, b.z), -1.0),
           padd(pscale(a.x, b.y), pscale(a.y, b.x), -1.0)};
@@ -347,6 +349,27 @@ void chord_inv32(double s_lo, double s_hi, double* a, double* b, double* dlo, do
   ss = std::min(std::max(ss, s_lo), s_hi);
   *dlo = std::min(0.0, f(ss) - (*a * ss + *b));
   *dhi = 0.0;
+}
+
+// Chord r(beta) = a beta + b of g(beta) = sqrt(beta) on [lo, hi] (lo >= 0) and the range
+// [dlo, dhi] of g - r (Sec. 4.3, "Remainder variables", linear r built from the range of beta
+// on the current cell).  g is concave: the chord lies below g, so g - r >= 0, zero at both
+// ends and largest where g'(b*) = a, i.e. b* = 1 / (4 a^2).  A degenerate interval gives
+// a = 0, b = g(lo), d = 0.
+void chord_sqrt(double lo, double hi, double* a, double* b, double* dlo, double* dhi) {
+  if (!(hi > lo)) {
+    *a = 0.0;
+    *b = std::sqrt(lo);
+    *dlo = 0.0;
+    *dhi = 0.0;
+    return;
+  }
+  *a = (std::sqrt(hi) - std::sqrt(lo)) / (hi - lo);
+  *b = std::sqrt(lo) - *a * lo;
+  double bs = 1.0 / (4.0 * *a * *a);
+  bs = std::min(std::max(bs, lo), hi);
+  *dlo = 0.0;
+  *dhi = std::max(0.0, std::sqrt(bs) - (*a * bs + *b));
 }
 
 // Ratio bound [min, max] of b(p)/b(q) (same degree; q must have uniform sign).
@@ -552,6 +575,117 @@ void bound_cell_reflect(const Ctx& cx, int e, int t, uint32_t id, int depth, std
   out.push_back(r);
 }
 
+// Bound one cell of one (emitter, triangle) tuple for single refraction (Eq. eq_refr_rational,
+// refraction; Sec. 4.3 "Remainder variables").  sqrt(beta) is replaced by
+//   r~(beta, xi) = a beta + b + (1 - xi) dlo + xi dhi,   xi in [0, 1],
+// with the chord of sqrt on the cell's range of beta; every quantity below is affine in r~,
+// so it is a degree-(n, 1) Bernstein form on the product of the cell and [0, 1] (xi), stored
+// as its two faces xi = 0 and xi = 1, and the ratio bound runs over the coefficients of both
+// faces.  Readings: the normals face the incident side (d0.n < 0 on real paths); a cell where
+// beta < 0 everywhere has no refracted path (total internal reflection: flag TIR); beta < 0
+// elsewhere is clipped from the chord's range (no path exists there); a mixed-sign denominator
+// is split up to the extra-split limit and then kept with the universal box [0,1]^2; the
+// irradiance bound of refraction is not built: E_hi = +inf.
+void bound_cell_refract(const Ctx& cx, int e, int t, uint32_t id, int depth, std::vector<orc_record>& out) {
+  UV C[3];
+  cell_corners(id, depth, C);
+  Tri T = get_tri(cx.s1, t);
+  V3 x0 = {cx.em->x[e], cx.em->y[e], cx.em->z[e]};
+  V3 e11 = T.p[1] - T.p[0], e12 = T.p[2] - T.p[0];
+  V3 n1d = T.n[1] - T.n[0], n2d = T.n[2] - T.n[0];
+  V3 xc[3], nc[3];
+  for (int k = 0; k < 3; ++k) {
+    xc[k] = T.p[0] + C[k].u * e11 + C[k].v * e12;  // Eq. eq_xi
+    nc[k] = T.n[0] + C[k].u * n1d + C[k].v * n2d;  // Eq. eq_ni
+  }
+  PV x1 = pv_affine(xc[0], xc[1], xc[2]);
+  PV n1 = pv_affine(nc[0], nc[1], nc[2]);
+  PV d0 = pv_subc(x1, x0);
+  const double eta = cx.s1->eta;
+  Poly nn = pv_dot(n1, n1), dn = pv_dot(d0, n1), ss = pv_dot(d0, d0);
+  // beta = (1 - eta'^2) (n.n)(d0.d0) + eta'^2 (d0.n)^2   (degree 4)
+  Poly beta = padd(pscale(pmul(nn, ss), 1.0 - eta * eta), pscale(pmul(dn, dn), eta * eta));
+  const Rec& R = cx.rec;
+  PV w = pv_subc(x1, R.p0);
+  Poly Tn = pv_dotc(pv_crossc(w, R.e1), R.e2);  // t = Tn / Q (forward distance)
+
+  orc_record r;
+  std::memset(&r, 0, sizeof(r));
+  r.emitter = e;
+  r.tri0 = t;
+  r.tri1 = -1;
+  r.cell = id;
+  r.flags = (uint32_t)depth << 24;
+
+  const double blo = pmin(beta), bhi = pmax(beta);
+  if (!(bhi > 0.0)) {
+    r.flags |= F_TIR;
+    out.push_back(r);
+    return;
+  }
+  double a, b, dlo, dhi;
+  chord_sqrt(std::max(blo, 0.0), bhi, &a, &b, &dlo, &dhi);
+  // tangential part eta' ((n.n) d0 - (d0.n) n), degree 3, elevated to 5
+  PV tang = pv_elev(pv_scale(pv_sub(pv_mul(nn, d0), pv_mul(dn, n1)), eta), 5);
+  Poly Qf[2], Puf[2], Pvf[2];
+  for (int j = 0; j < 2; ++j) {
+    Poly W = padd(pscale(beta, a), pconst(2, 4, b + (j == 0 ? dlo : dhi)));  // r~ at xi = j
+    PV dt = pv_sub(tang, pv_mul(W, n1));                                    // degree 5
+    PV dxe2 = pv_crossc(dt, R.e2);
+    Qf[j] = pv_dotc(dxe2, R.e1);                // Eq. eq_rct
+    Puf[j] = pv_dot(dxe2, w);
+    Pvf[j] = pv_dot(pv_crossc(w, R.e1), dt);
+  }
+  r.q_cond = std::min(cond_of(Qf[0]), cond_of(Qf[1]));
+  const int s0 = psign(Qf[0]), s1 = psign(Qf[1]);
+  const int sq = s0 == s1 ? s0 : 0;
+  if (sq == 0) {
+    if (depth < cx.max_total_depth) {
+      r.flags |= F_SPLIT;
+      out.push_back(r);
+      for (int k = 0; k < 4; ++k) bound_cell_refract(cx, e, t, id * 4u + (uint32_t)k, depth + 1, out);
+      return;
+    }
+    r.u_lo = r.v_lo = 0.0;
+    r.u_hi = r.v_hi = 1.0;
+    r.e_hi = std::numeric_limits<double>::infinity();
+    r.flags |= F_LIVE | F_POS_UNBOUNDED;
+    out.push_back(r);
+    return;
+  }
+  int st = psign(Tn);
+  if (st != 0 && st != sq) {
+    r.flags |= F_CULL_BEHIND;
+    out.push_back(r);
+    return;
+  }
+  double ul = std::numeric_limits<double>::infinity(), uh = -ul, vl = ul, vh = -ul;
+  for (int j = 0; j < 2; ++j) {
+    Poly Q6 = pelevate(Qf[j]);
+    double l, h;
+    ratio_bound(Puf[j], Q6, &l, &h);
+    ul = std::min(ul, l);
+    uh = std::max(uh, h);
+    ratio_bound(Pvf[j], Q6, &l, &h);
+    vl = std::min(vl, l);
+    vh = std::max(vh, h);
+  }
+  r.u_lo = std::max(ul, 0.0);
+  r.u_hi = std::min(uh, 1.0);
+  r.v_lo = std::max(vl, 0.0);
+  r.v_hi = std::min(vh, 1.0);
+  if (r.u_lo > r.u_hi || r.v_lo > r.v_hi) {
+    r.u_lo = r.u_hi = r.v_lo = r.v_hi = 0.0;
+    r.flags |= F_CULL_EMPTY;
+    out.push_back(r);
+    return;
+  }
+  r.flags |= F_LIVE;
+  r.e_lo = 0.0;
+  r.e_hi = std::numeric_limits<double>::infinity();
+  out.push_back(r);
+}
+
 void decode_work(int64_t i, int n_tris, int depth, int* e, int* t, uint32_t* c) {
   int64_t per = (int64_t)1 << (2 * depth);
   *c = (uint32_t)(i % per);
@@ -626,7 +760,9 @@ struct PathEval {
   bool ok;
 };
 
-PathEval eval_reflect(const Tri& T, V3 x0, double I0, const Rec& R, double u, double v) {
+// kind 0: reflection, 1: refraction with eta' = eta (Eq. eq_refr_rational).  For refraction the
+// derivative of sqrt(beta) is d beta / (2 sqrt(beta)); ok is false where beta <= 0 (no path).
+PathEval eval_path(const Tri& T, V3 x0, double I0, const Rec& R, double u, double v, int kind, double eta) {
   PathEval P;
   V3 e1 = T.p[1] - T.p[0], e2 = T.p[2] - T.p[0];
   V3 dn1 = T.n[1] - T.n[0], dn2 = T.n[2] - T.n[0];
@@ -634,8 +770,21 @@ PathEval eval_reflect(const Tri& T, V3 x0, double I0, const Rec& R, double u, do
   V3 n = T.n[0] + u * dn1 + v * dn2;
   V3 d0 = x - x0;
   V3 dx[2] = {e1, e2}, dnn[2] = {dn1, dn2};
-  double nn = dot(n, n), dn = dot(d0, n);
-  V3 dt = nn * d0 - 2.0 * dn * n;
+  double nn = dot(n, n), dn = dot(d0, n), ss = dot(d0, d0);
+  double W = 0.0;
+  V3 dt;
+  if (kind == 0) {
+    dt = nn * d0 - 2.0 * dn * n;
+  } else {
+    const double beta = (1.0 - eta * eta) * nn * ss + eta * eta * dn * dn;
+    if (!(beta > 0.0)) {
+      P = PathEval{};
+      P.ok = false;
+      return P;
+    }
+    W = std::sqrt(beta);
+    dt = eta * (nn * d0 - dn * n) - W * n;
+  }
   V3 w = x - R.p0;
   V3 g = cross(R.e2, R.e1);
   double Q = dot(dt, g);
@@ -645,7 +794,15 @@ PathEval eval_reflect(const Tri& T, V3 x0, double I0, const Rec& R, double u, do
   for (int j = 0; j < 2; ++j) {
     double dnn_j = 2.0 * dot(n, dnn[j]);
     double ddn_j = dot(dx[j], n) + dot(d0, dnn[j]);
-    V3 ddt = dnn_j * d0 + nn * dx[j] - 2.0 * (ddn_j * n + dn * dnn[j]);
+    V3 ddt;
+    if (kind == 0) {
+      ddt = dnn_j * d0 + nn * dx[j] - 2.0 * (ddn_j * n + dn * dnn[j]);
+    } else {
+      const double dss_j = 2.0 * dot(d0, dx[j]);
+      const double dbeta_j = (1.0 - eta * eta) * (dnn_j * ss + nn * dss_j) + eta * eta * 2.0 * dn * ddn_j;
+      const double dW_j = dbeta_j / (2.0 * W);
+      ddt = eta * (dnn_j * d0 + nn * dx[j] - ddn_j * n - dn * dnn[j]) - dW_j * n - W * dnn[j];
+    }
     dQ[j] = dot(ddt, g);
     dA[j] = dot(ddt, he2w) + dot(dt, cross(R.e2, dx[j]));
     dB[j] = dot(cross(dx[j], R.e1), dt) + dot(hwe1, ddt);
@@ -661,7 +818,7 @@ PathEval eval_reflect(const Tri& T, V3 x0, double I0, const Rec& R, double u, do
   double detJ = P.J[0][0] * P.J[1][1] - P.J[0][1] * P.J[1][0];
   V3 N1 = cross(e1, e2);
   double C1 = dot(T.p[0] - x0, N1);
-  double s = dot(d0, d0);
+  double s = ss;
   P.E = I0 * std::fabs(C1) / (s * std::sqrt(s) * norm(cross(R.e1, R.e2)) * std::fabs(detJ));
   P.ok = std::isfinite(P.uk) && std::isfinite(P.vk) && std::isfinite(detJ) && Q != 0.0;
   return P;
@@ -728,6 +885,46 @@ bool eval_direct_reflect(const Tri& T, V3 x0, double I0, const Rec& R, double u,
   return std::isfinite(Uk.v) && std::isfinite(Vk.v);
 }
 
+// Direct geometry for refraction: unit normal and unit incident direction, the textbook vector
+// form of Snell's law t = eta i + (eta c1 - sqrt(1 - eta^2 (1 - c1^2))) n with c1 = -i.n (the
+// normal faces the incident side), ray/plane hit, Jacobian by duals.  Returns false under total
+// internal reflection.
+bool eval_direct_refract(const Tri& T, V3 x0, double I0, const Rec& R, double eta, double u, double v, double* uk,
+                         double* vk, double* E, double* tt) {
+  Dual U = dmk(u, 1, 0), W = dmk(v, 0, 1);
+  DV3 p0 = dconst(T.p[0]), e1 = dconst(T.p[1] - T.p[0]), e2 = dconst(T.p[2] - T.p[0]);
+  DV3 x = p0 + U * e1 + W * e2;
+  DV3 n = dconst(T.n[0]) + U * dconst(T.n[1] - T.n[0]) + W * dconst(T.n[2] - T.n[0]);
+  Dual ln = dsqrt(ddot(n, n));
+  DV3 nh = {n.x / ln, n.y / ln, n.z / ln};
+  DV3 d = x - dconst(x0);
+  Dual ld = dsqrt(ddot(d, d));
+  DV3 ih = {d.x / ld, d.y / ld, d.z / ld};
+  Dual c1 = dc(0.0) - ddot(ih, nh);
+  Dual k = dc(1.0) - dc(eta * eta) * (dc(1.0) - c1 * c1);
+  if (!(k.v > 0.0)) return false;
+  DV3 tdir = dc(eta) * ih + (dc(eta) * c1 - dsqrt(k)) * nh;
+  V3 Nk = cross(R.e1, R.e2);
+  DV3 Nkd = dconst(Nk);
+  Dual t = ddot(dconst(R.p0) - x, Nkd) / ddot(tdir, Nkd);
+  DV3 X = x + t * tdir;
+  double g11 = dot(R.e1, R.e1), g12 = dot(R.e1, R.e2), g22 = dot(R.e2, R.e2);
+  double det = g11 * g22 - g12 * g12;
+  DV3 rel = X - dconst(R.p0);
+  Dual a = ddot(rel, dconst(R.e1)), b = ddot(rel, dconst(R.e2));
+  Dual Uk = (dc(g22) * a - dc(g12) * b) / dc(det);
+  Dual Vk = (dc(g11) * b - dc(g12) * a) / dc(det);
+  double detJ = Uk.d[0] * Vk.d[1] - Uk.d[1] * Vk.d[0];
+  V3 N1 = cross(T.p[1] - T.p[0], T.p[2] - T.p[0]);
+  V3 dd = {d.x.v, d.y.v, d.z.v};
+  double s = dot(dd, dd);
+  *E = I0 * std::fabs(dot(dd, N1)) / (s * std::sqrt(s)) / (std::fabs(detJ) * norm(Nk));
+  *uk = Uk.v;
+  *vk = Vk.v;
+  *tt = t.v;
+  return std::isfinite(Uk.v) && std::isfinite(Vk.v);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -757,6 +954,7 @@ double orc_bb_eval(int dim, int n, const double* p, double m1, double m2) {
   Poly P{dim, n, std::vector<double>(p, p + psize(dim, n))};
   return peval(P, m1, m2);
 }
+void orc_chord_sqrt(double lo, double hi, double* out4) { chord_sqrt(lo, hi, &out4[0], &out4[1], &out4[2], &out4[3]); }
 void orc_chord_inv32(double s_lo, double s_hi, double* out4) {
   chord_inv32(s_lo, s_hi, &out4[0], &out4[1], &out4[2], &out4[3]);
 }
@@ -777,7 +975,7 @@ void orc_cell_corners(uint32_t id, int depth, double* out6) {
 int orc_bound(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, int32_t depth,
               int32_t max_extra_split, int32_t irradiance, const int64_t* work, int64_t n_work,
               orc_record* out, int64_t cap, int64_t* n_out, int32_t n_threads) {
-  if (s1->kind != 0) return -4;
+  if (s1->kind != 0 && s1->kind != 1) return -4;
   Ctx cx{s1, get_rec(rec), em, irradiance, depth + max_extra_split};
   int64_t total = work ? n_work : (int64_t)em->n * s1->n_tris * ((int64_t)1 << (2 * depth));
   int nt = std::max(1, (int)n_threads);
@@ -788,7 +986,10 @@ int orc_bound(const orc_surface* s1, const orc_receiver* rec, const orc_emitters
       int e, t;
       uint32_t c;
       decode_work(work ? work[i] : i, s1->n_tris, depth, &e, &t, &c);
-      bound_cell_reflect(cx, e, t, c, depth, v);
+      if (s1->kind == 0)
+        bound_cell_reflect(cx, e, t, c, depth, v);
+      else
+        bound_cell_refract(cx, e, t, c, depth, v);
     }
   });
   int64_t n = 0;
@@ -903,7 +1104,7 @@ int orc_solve(const orc_surface* s1, const orc_receiver* rec, const orc_emitters
       double u = 1.0 / 3.0, v = 1.0 / 3.0;
       bool bad = false;
       for (int it = 0; it < newton_iters + polish_iters; ++it) {
-        PathEval P = eval_reflect(T, x0, I0, R, u, v);
+        PathEval P = eval_path(T, x0, I0, R, u, v, s1->kind, s1->eta);
         double det = P.J[0][0] * P.J[1][1] - P.J[0][1] * P.J[1][0];
         if (!P.ok || !(det != 0.0) || !std::isfinite(det)) {
           bad = true;
@@ -931,7 +1132,7 @@ int orc_solve(const orc_surface* s1, const orc_receiver* rec, const orc_emitters
       root_u[i] = u;
       root_v[i] = v;
       if (bad) continue;
-      PathEval P = eval_reflect(T, x0, I0, R, u, v);
+      PathEval P = eval_path(T, x0, I0, R, u, v, s1->kind, s1->eta);
       if (!P.ok) continue;
       double fu = P.uk - tu, fv = P.vk - tv;
       V3 res = fu * R.e1 + fv * R.e2;
@@ -952,11 +1153,12 @@ int orc_eval_path(const orc_surface* s1, const orc_receiver* rec, const orc_emit
   Tri T = get_tri(s1, t);
   V3 x0 = {em->x[e], em->y[e], em->z[e]};
   for (int64_t i = 0; i < n; ++i) {
-    PathEval P = eval_reflect(T, x0, em->intensity[e], R, u[i], v[i]);
-    uk[i] = P.uk;
-    vk[i] = P.vk;
-    E[i] = P.E;
-    tt[i] = P.t;
+    PathEval P = eval_path(T, x0, em->intensity[e], R, u[i], v[i], s1->kind, s1->eta);
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    uk[i] = P.ok ? P.uk : nan;
+    vk[i] = P.ok ? P.vk : nan;
+    E[i] = P.ok ? P.E : nan;
+    tt[i] = P.ok ? P.t : nan;
   }
   return 0;
 }
@@ -967,8 +1169,14 @@ int orc_eval_direct(const orc_surface* s1, const orc_receiver* rec, const orc_em
   Rec R = get_rec(rec);
   Tri T = get_tri(s1, t);
   V3 x0 = {em->x[e], em->y[e], em->z[e]};
-  for (int64_t i = 0; i < n; ++i)
-    eval_direct_reflect(T, x0, em->intensity[e], R, u[i], v[i], &uk[i], &vk[i], &E[i], &tt[i]);
+  for (int64_t i = 0; i < n; ++i) {
+    bool ok;
+    if (s1->kind == 0)
+      ok = eval_direct_reflect(T, x0, em->intensity[e], R, u[i], v[i], &uk[i], &vk[i], &E[i], &tt[i]);
+    else
+      ok = eval_direct_refract(T, x0, em->intensity[e], R, s1->eta, u[i], v[i], &uk[i], &vk[i], &E[i], &tt[i]);
+    if (!ok) uk[i] = vk[i] = E[i] = tt[i] = std::numeric_limits<double>::quiet_NaN();
+  }
   return 0;
 }
 

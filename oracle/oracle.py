@@ -88,6 +88,7 @@ def lib():
             L.orc_bb_deriv.argtypes = [C.c_int, vp, C.c_int, vp]
             L.orc_bb_eval.argtypes = [C.c_int, C.c_int, vp, f64, f64]
             L.orc_chord_inv32.argtypes = [f64, f64, vp]
+            L.orc_chord_sqrt.argtypes = [f64, f64, vp]
             L.orc_philox4x32_10.argtypes = [vp, vp, vp]
             L.orc_cell_corners.argtypes = [C.c_uint32, C.c_int, vp]
             _lib = L
@@ -163,6 +164,13 @@ def bb_index(n: int):
 def chord_inv32(s_lo: float, s_hi: float):
     out = np.zeros(4)
     lib().orc_chord_inv32(s_lo, s_hi, _p(out))
+    return tuple(out)
+
+
+def chord_sqrt(lo: float, hi: float):
+    """Chord a*beta + b of sqrt on [lo, hi] and the range [dlo, dhi] of sqrt - chord."""
+    out = np.zeros(4)
+    lib().orc_chord_sqrt(lo, hi, _p(out))
     return tuple(out)
 
 

@@ -315,6 +315,25 @@ def config(name: str, **kw) -> Scene:
         # hundreds of grid cells; kept for the bound-pass tests only
         em = area_quad_emitters((0.0, 0.0, 2.0), 0.2, 4, seed=2)
         return mirror(256, 2, 6, 0.01, "face", em, kw.get("points", 1024), kw.get("depth", 3), name)
+    if name == "water420":
+        # 420^2 Gerstner water on [-2,2]^2 (352,800 tris), eta' = 1/1.33, pool floor 1 below over
+        # [-2,2] x [-1.125,1.125], lights at (+-0.5, +-0.5, 2), 1920x1080 points, depth 3
+        s1 = gerstner(420, 3)
+        em = point_emitters([(-0.5, -0.5, 2.0), (0.5, -0.5, 2.0), (-0.5, 0.5, 2.0), (0.5, 0.5, 2.0)], 1.0)
+        rec = receiver_square(-1.0, 2.0, half_y=1.125)
+        su, sv = shading_points(kw.get("points_x", 1920), kw.get("points_y", 1080), 1003)
+        return Scene(name, s1, None, rec, em, kw.get("depth", 3), su, sv)
+    if name == "water":
+        # small refraction case: n^2 Gerstner water on [-ext,ext]^2, floor 1 below
+        n = kw.get("n", 8)
+        ext = kw.get("extent", 0.5)
+        s1 = gerstner(n, kw.get("seed", 3), n_waves=kw.get("waves", 16), extent=ext, steep=kw.get("steep", 0.02),
+                      lam_lo=kw.get("lam_lo", 0.2), lam_hi=kw.get("lam_hi", 1.0))
+        em = point_emitters(kw.get("lights", [(0.1, -0.05, 2.0)]), 1.0)
+        rec = receiver_square(-1.0, kw.get("rec_half", 0.8))
+        p = kw.get("points", 32)
+        su, sv = shading_points(p, p, 1004)
+        return Scene(name, s1, None, rec, em, kw.get("depth", 1), su, sv)
     if name == "tiny":
         # A few triangles: exhaustive enumeration fits in milliseconds.
         n = kw.get("n", 4)
