@@ -229,6 +229,9 @@ typedef struct bnb_job {
                                       is nonzero; the other emitters' tuples are skipped (NULL: all) */
   float rp0[3], re1[3], re2[3];    /* the scene's receiver */
   int32_t grid_res;                /* index of the scene (bnb_build_index output) */
+  int32_t kind;                    /* the surface's BNB_REFLECT or BNB_REFRACT */
+  float eta;                       /* refraction: the surface's eta */
+  int32_t reserved0;               /* 0 */
   const int64_t *offsets;
   const uint64_t *key;
   const float *etilde;
@@ -266,7 +269,7 @@ size_t bnb_sample_and_solve_batched_ws(const bnb_batch_cfg *cfg);
 const char *bnb_status_string(int32_t status);
 
 /* ABI version of this header (increments on any struct or signature change). */
-int32_t bnb_abi_version(void);  /* 3 */
+int32_t bnb_abi_version(void);  /* 4 */
 
 #ifdef __cplusplus
 }

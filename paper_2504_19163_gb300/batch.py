@@ -105,6 +105,9 @@ class ResidentScene:
             job.rp0[c], job.re1[c], job.re2[c] = r.p0[c], r.e1[c], r.e2[c]
         ix = self.index
         job.grid_res = ix.grid_res
+        job.kind = self.ds.s1.kind
+        job.eta = self.ds.s1.eta
+        job.reserved0 = 0
         job.offsets, job.key, job.etilde = ix.offsets.data_ptr(), ix.key.data_ptr(), ix.etilde.data_ptr()
         job.index_capacity = ix.capacity
         job.su, job.sv = su.data_ptr(), sv.data_ptr()

@@ -73,7 +73,7 @@ class bnb_sample_stats(C.Structure):
 class bnb_job(C.Structure):
     _fields_ = [("packed_tris", vp), ("n_tris", i32), ("n_emitters", i32), ("ex", vp), ("ey", vp), ("ez", vp),
                 ("ei", vp), ("emitter_on", vp), ("rp0", f32 * 3), ("re1", f32 * 3), ("re2", f32 * 3),
-                ("grid_res", i32), ("offsets", vp), ("key", vp), ("etilde", vp), ("index_capacity", i64),
+                ("grid_res", i32), ("kind", i32), ("eta", f32), ("reserved0", i32), ("offsets", vp), ("key", vp), ("etilde", vp), ("index_capacity", i64),
                 ("su", vp), ("sv", vp), ("n_points", i64), ("gamma", f32), ("reserved", C.c_uint32), ("seed", u64),
                 ("E_out", vp)]
 

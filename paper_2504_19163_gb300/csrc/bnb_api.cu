@@ -77,7 +77,7 @@ BoundWs carve_bound_ws(void* base, int64_t n_tris, int64_t qcap) {
 
 extern "C" {
 
-int32_t bnb_abi_version(void) { return 3; }
+int32_t bnb_abi_version(void) { return 4; }
 
 const char* bnb_status_string(int32_t s) {
   switch (s) {
@@ -104,7 +104,8 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
                          size_t ws_bytes, void* stream) {
   if (!surface_ok(s1) || !emitters_ok(em) || !rec || !cfg || !out) return BNB_ERR_INVALID;
   if (s2 != nullptr) return BNB_ERR_UNSUPPORTED;
-  if (s1->kind != BNB_REFLECT) return BNB_ERR_UNSUPPORTED;
+  if (s1->kind != BNB_REFLECT && s1->kind != BNB_REFRACT) return BNB_ERR_INVALID;
+  if (s1->kind == BNB_REFRACT && !(s1->eta > 0.0f && s1->eta < 1e6f)) return BNB_ERR_INVALID;
   if (cfg->depth < 0 || cfg->depth > kMaxBaseDepth || cfg->max_extra_split < 0 || cfg->max_extra_split > kMaxExtra ||
       cfg->depth + cfg->max_extra_split > kMaxDepth)
     return BNB_ERR_INVALID;
@@ -142,6 +143,8 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
   P.depth = cfg->depth;
   P.max_depth = cfg->depth + cfg->max_extra_split;
   P.irradiance = cfg->irradiance ? 1 : 0;
+  P.kind = s1->kind;
+  P.eta = s1->eta;
   P.n_base = nb;
   P.capacity = out->capacity;
   P.count = out->count;
@@ -206,7 +209,9 @@ int32_t bnb_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2, const
                              int64_t n_points, const bnb_sample_cfg* cfg, float* E_out, bnb_sample_stats* stats,
                              void* ws, size_t ws_bytes, void* stream) {
   if (!surface_ok(s1) || !emitters_ok(em) || !rec || !index || !cfg || !stats) return BNB_ERR_INVALID;
-  if (s2 != nullptr || s1->kind != BNB_REFLECT) return BNB_ERR_UNSUPPORTED;
+  if (s2 != nullptr) return BNB_ERR_UNSUPPORTED;
+  if (s1->kind != BNB_REFLECT && s1->kind != BNB_REFRACT) return BNB_ERR_INVALID;
+  if (s1->kind == BNB_REFRACT && !(s1->eta > 0.0f && s1->eta < 1e6f)) return BNB_ERR_INVALID;
   if (n_points < 0 || (n_points > 0 && (!su || !sv || !E_out))) return BNB_ERR_INVALID;
   if (!stats->counters || !stats->status || !index->offsets) return BNB_ERR_INVALID;
   if (index->grid_res < 1 || index->grid_res > 4096) return BNB_ERR_INVALID;

@@ -214,7 +214,12 @@ __global__ void __launch_bounds__(512) solve32_b_k(BatchParams B) {
       float pf[3][3], nf[3][3];
       load_tri_s((const float4*)J.packed_tris, t, pf, nf);
       const float x0[3] = {__ldg(J.ex + e), __ldg(J.ey + e), __ldg(J.ez + e)};
-      need = newton32(pf, nf, x0, __ldg(J.ei + e), J.rp0, J.re1, J.re2, J.su[lp], J.sv[lp], B.newton_iters, u, v);
+      if (J.kind == BNB_REFRACT)
+        need = newton32<true>(pf, nf, x0, __ldg(J.ei + e), J.rp0, J.re1, J.re2, J.su[lp], J.sv[lp], B.newton_iters,
+                              J.eta, u, v);
+      else
+        need = newton32<false>(pf, nf, x0, __ldg(J.ei + e), J.rp0, J.re1, J.re2, J.su[lp], J.sv[lp], B.newton_iters,
+                               J.eta, u, v);
     }
     if (!need) B.contrib[i] = 0.0f;
     const int64_t q = warp_append(need, B.pl_count);
@@ -242,8 +247,12 @@ __global__ void __launch_bounds__(512) polish_b_k(BatchParams B) {
     float pf[3][3], nf[3][3];
     load_tri_s((const float4*)J.packed_tris, t, pf, nf);
     const float x0[3] = {__ldg(J.ex + e), __ldg(J.ey + e), __ldg(J.ez + e)};
-    const double E = polish64(pf, nf, x0, __ldg(J.ei + e), J.rp0, J.re1, J.re2, J.su[lp], J.sv[lp],
-                              B.polish_iters, B.tol, B.pl_u[q], B.pl_v[q]);
+    const double E =
+        J.kind == BNB_REFRACT
+            ? polish64<true>(pf, nf, x0, __ldg(J.ei + e), J.rp0, J.re1, J.re2, J.su[lp], J.sv[lp], B.polish_iters,
+                             B.tol, J.eta, B.pl_u[q], B.pl_v[q])
+            : polish64<false>(pf, nf, x0, __ldg(J.ei + e), J.rp0, J.re1, J.re2, J.su[lp], J.sv[lp], B.polish_iters,
+                              B.tol, J.eta, B.pl_u[q], B.pl_v[q]);
     float c = 0.0f;
     if (E >= 0.0) {
       c = (float)(E / (double)B.wl_p[i]);

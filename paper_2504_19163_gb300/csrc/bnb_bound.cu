@@ -4,11 +4,19 @@
 
 namespace bnb {
 
-template cudaError_t launch_bound_base_T<float>(const BoundParams&, cudaStream_t);
-template cudaError_t launch_bound_split_T<float>(const BoundParams&, const SplitItem*, const int64_t*, cudaStream_t);
-extern template cudaError_t launch_bound_base_T<double>(const BoundParams&, cudaStream_t);
-extern template cudaError_t launch_bound_split_T<double>(const BoundParams&, const SplitItem*, const int64_t*,
-                                                         cudaStream_t);
+template cudaError_t launch_bound_base_T<float, 0>(const BoundParams&, cudaStream_t);
+template cudaError_t launch_bound_split_T<float, 0>(const BoundParams&, const SplitItem*, const int64_t*,
+                                                    cudaStream_t);
+// instantiated in bnb_bound64.cu (float64 reflection) and bnb_bound_refract.cu (refraction)
+extern template cudaError_t launch_bound_base_T<double, 0>(const BoundParams&, cudaStream_t);
+extern template cudaError_t launch_bound_split_T<double, 0>(const BoundParams&, const SplitItem*, const int64_t*,
+                                                            cudaStream_t);
+extern template cudaError_t launch_bound_base_T<float, 1>(const BoundParams&, cudaStream_t);
+extern template cudaError_t launch_bound_split_T<float, 1>(const BoundParams&, const SplitItem*, const int64_t*,
+                                                           cudaStream_t);
+extern template cudaError_t launch_bound_base_T<double, 1>(const BoundParams&, cudaStream_t);
+extern template cudaError_t launch_bound_split_T<double, 1>(const BoundParams&, const SplitItem*, const int64_t*,
+                                                            cudaStream_t);
 
 __global__ void pack_tris_k(const float* __restrict__ px, const float* __restrict__ py, const float* __restrict__ pz,
                             const float* __restrict__ nx, const float* __restrict__ ny, const float* __restrict__ nz,
@@ -42,12 +50,18 @@ cudaError_t launch_pack_tris(const bnb_surface* s, float4* out, cudaStream_t st)
 }
 
 cudaError_t launch_bound_base(const BoundParams& p, bool fp64, cudaStream_t st) {
-  return fp64 ? launch_bound_base_T<double>(p, st) : launch_bound_base_T<float>(p, st);
+  if (p.kind == BNB_REFRACT)
+    return fp64 ? launch_bound_base_T<double, 1>(p, st) : launch_bound_base_T<float, 1>(p, st);
+  return fp64 ? launch_bound_base_T<double, 0>(p, st) : launch_bound_base_T<float, 0>(p, st);
 }
 
 cudaError_t launch_bound_split(const BoundParams& p, const SplitItem* q_in, const int64_t* q_in_count, bool fp64,
                                cudaStream_t st) {
-  return fp64 ? launch_bound_split_T<double>(p, q_in, q_in_count, st) : launch_bound_split_T<float>(p, q_in, q_in_count, st);
+  if (p.kind == BNB_REFRACT)
+    return fp64 ? launch_bound_split_T<double, 1>(p, q_in, q_in_count, st)
+                : launch_bound_split_T<float, 1>(p, q_in, q_in_count, st);
+  return fp64 ? launch_bound_split_T<double, 0>(p, q_in, q_in_count, st)
+              : launch_bound_split_T<float, 0>(p, q_in, q_in_count, st);
 }
 
 }  // namespace bnb

@@ -3,6 +3,7 @@
 #include "bnb_bound_impl.cuh"
 
 namespace bnb {
-template cudaError_t launch_bound_base_T<double>(const BoundParams&, cudaStream_t);
-template cudaError_t launch_bound_split_T<double>(const BoundParams&, const SplitItem*, const int64_t*, cudaStream_t);
+template cudaError_t launch_bound_base_T<double, 0>(const BoundParams&, cudaStream_t);
+template cudaError_t launch_bound_split_T<double, 0>(const BoundParams&, const SplitItem*, const int64_t*,
+                                                     cudaStream_t);
 }  // namespace bnb

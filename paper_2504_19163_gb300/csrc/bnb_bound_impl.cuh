@@ -1001,13 +1001,337 @@ static __device__ __noinline__ void process_cell_fp64(const BoundParams& P, int 
   process_cell<double>(P, e, t, id, depth, slot, BNB_CELL_QSIGN_FP64);
 }
 
+// ------------------------------------------------------------------ refraction (one vertex)
+// Eq. eq_refr_rational, refraction: d~ = eta' ((n.n) d0 - (d0.n) n) - sqrt(beta) n with
+// beta = (1 - eta'^2)(n.n)(d0.d0) + eta'^2 (d0.n)^2.  sqrt(beta) is replaced by the remainder
+// form a beta + b + (1 - xi) dlo + xi dhi (Sec. 4.3 "Remainder variables"), xi in [0, 1], with
+// the chord of sqrt on the cell's range of beta; d~, Q, P_u, P_v are affine in it, so each is
+// carried as its two faces xi = 0 and xi = 1 and the ratio bound runs over both.  Normals face
+// the incident side.  The irradiance of refraction is not bounded (E_hi = +inf).
+
+// Range [lo, hi] of the classical coefficients of a tracked degree-4 form (rigorous).
+template <typename T>
+__device__ __forceinline__ void classical_range4(const TP<T, 4>& p, T& lo, T& hi) {
+  using F = FP<T>;
+  lo = F::inf();
+  hi = -F::inf();
+  static_for<nc(4)>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr T C = MULT<T, 4, i>;  // a small integer, exact
+    lo = fmin(lo, F::div_rd(F::fma_rd(-p.E, C, p.c[i]), C));
+    hi = fmax(hi, F::div_ru(F::fma_ru(p.E, C, p.c[i]), C));
+  });
+}
+
+// Chord a x + b of sqrt on [lo, hi] (0 <= lo <= hi, computed in round-to-nearest; any a, b are
+// admissible) and a rigorous range [dlo, dhi] of sqrt(x) - (a x + b) over [lo, hi]:
+//   dlo: sqrt minus a line is concave, so its minimum is at an end of the interval;
+//   dhi: sqrt(x) <= sqrt(x0) + (x - x0) / (2 sqrt(x0)) for any x0 > 0 (tangent of a concave
+//        function); that bound minus the line is linear in x, so its maximum is at an end.
+//        x0 = 1 / (4 a^2), where the chord's slope is attained, makes the bound tight.
+template <typename T>
+__device__ __forceinline__ void sqrt_chord(T lo, T hi, T& a, T& b, T& dlo, T& dhi) {
+  using F = FP<T>;
+  if (!(hi > lo)) {
+    a = T(0);
+    b = sqrt(hi);
+    dlo = F::add_rd(F::sqrt_rd(lo), -b);
+    dhi = F::add_ru(F::sqrt_ru(hi), -b);
+    return;
+  }
+  const T sl = sqrt(lo), sh = sqrt(hi);
+  a = (sh - sl) / (hi - lo);
+  if (!(a > T(0)) || !(a < F::inf())) a = T(0);
+  b = sl - a * lo;
+  auto low_at = [&](T x) { return F::add_rd(F::sqrt_rd(x), -F::fma_ru(a, x, b)); };
+  dlo = fmin(low_at(lo), low_at(hi));
+  T x0 = a > T(0) ? T(1) / (T(4) * a * a) : hi;
+  x0 = fmin(fmax(x0, lo), hi);
+  if (!(x0 > T(0))) x0 = hi;
+  const T s0u = F::sqrt_ru(x0), s0d = F::sqrt_rd(x0);
+  const T klo = F::div_rd(T(1), F::mul_ru(T(2), s0u)), khi = F::div_ru(T(1), F::mul_rd(T(2), s0d));
+  auto up_at = [&](T x) {
+    const T dx = F::add_ru(x, -x0);  // >= x - x0
+    // g'(x0) in [klo, khi]; an upper bound of g'(x0) (x - x0) on either side of x0
+    const T lin = dx >= T(0) ? F::mul_ru(khi, dx) : F::mul_ru(klo, dx);
+    return F::add_ru(F::add_ru(s0u, lin), -F::fma_rd(a, x, b));
+  };
+  dhi = fmax(up_at(lo), up_at(hi));
+}
+
+static __device__ __noinline__ void process_cell_refract_fp64(const BoundParams& P, int e, int t, uint32_t id,
+                                                              int depth, int64_t slot);
+
+template <typename T>
+__device__ __forceinline__ void process_cell_refract(const BoundParams& P, int e, int t, uint32_t id, int depth,
+                                                     int64_t slot, uint32_t extra_flags = 0) {
+  using F = FP<T>;
+  float pf[3][3], nf[3][3];
+  load_tri(P.tri, t, pf, nf);
+  const float x0f[3] = {__ldg(P.ex + e), __ldg(P.ey + e), __ldg(P.ez + e)};
+  T p[3][3], n[3][3], x0[3], e1[3], e2[3], rp0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      p[a][b] = (T)pf[a][b];
+      n[a][b] = (T)nf[a][b];
+    }
+    x0[a] = (T)x0f[a];
+    e1[a] = (T)P.re1[a];
+    e2[a] = (T)P.re2[a];
+    rp0[a] = (T)P.rp0[a];
+  }
+  const T eta = (T)P.eta;
+  uint32_t flags = ((uint32_t)depth << BNB_CELL_DEPTH_SHIFT) | extra_flags;
+  T cu[3], cv[3];
+  cell_corners<T>(id, depth, cu, cv);
+
+  // Receiver origin: the hit of the centroid's refracted ray, rounded to 2^-16 (any value is valid).
+  T uc = T(0.5), vc = T(0.5);
+  {
+    T xc[3], ncn[3], d[3];
+    const T third = T(1) / T(3);
+    const T w1 = (cu[0] + cu[1] + cu[2]) * third, w2 = (cv[0] + cv[1] + cv[2]) * third, w0 = T(1) - w1 - w2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      xc[c] = w0 * p[0][c] + w1 * p[1][c] + w2 * p[2][c];
+      ncn[c] = w0 * n[0][c] + w1 * n[1][c] + w2 * n[2][c];
+      d[c] = xc[c] - x0[c];
+    }
+    const T nn = ncn[0] * ncn[0] + ncn[1] * ncn[1] + ncn[2] * ncn[2];
+    const T dn = d[0] * ncn[0] + d[1] * ncn[1] + d[2] * ncn[2];
+    const T ss = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const T bc = (T(1) - eta * eta) * nn * ss + eta * eta * dn * dn;
+    if (bc > T(0)) {
+      const T wc = sqrt(bc);
+      T dt[3], w[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dt[c] = eta * (nn * d[c] - dn * ncn[c]) - wc * ncn[c];
+        w[c] = xc[c] - rp0[c];
+      }
+      const T g0 = e2[1] * e1[2] - e2[2] * e1[1], g1 = e2[2] * e1[0] - e2[0] * e1[2],
+              g2 = e2[0] * e1[1] - e2[1] * e1[0];
+      const T Qc = dt[0] * g0 + dt[1] * g1 + dt[2] * g2;
+      const T hu0 = e2[1] * w[2] - e2[2] * w[1], hu1 = e2[2] * w[0] - e2[0] * w[2], hu2 = e2[0] * w[1] - e2[1] * w[0];
+      const T hv0 = w[1] * e1[2] - w[2] * e1[1], hv1 = w[2] * e1[0] - w[0] * e1[2], hv2 = w[0] * e1[1] - w[1] * e1[0];
+      uc = (dt[0] * hu0 + dt[1] * hu1 + dt[2] * hu2) / Qc;
+      vc = (dt[0] * hv0 + dt[1] * hv1 + dt[2] * hv2) / Qc;
+    }
+    if (!(fabs(uc) < T(4))) uc = T(0.5);
+    if (!(fabs(vc) < T(4))) vc = T(0.5);
+    uc = rint(uc * T(65536)) * T(1.0 / 65536);
+    vc = rint(vc * T(65536)) * T(1.0 / 65536);
+  }
+
+  Leaves<T> L;
+  make_leaves<T, false>(p, n, x0, cu, cv, L);
+  // n.n, d0.n, d0.d0 (degree 2) and beta (degree 4)
+  TP<T, 2> NN, DN, SS;
+  tp_zero(NN);
+  tp_zero(DN);
+  tp_zero(SS);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    mac(NN, L.N[c], L.N[c]);
+    mac(DN, L.D0[c], L.N[c]);
+    mac(SS, L.D0[c], L.D0[c]);
+  }
+  renorm(NN);
+  renorm(DN);
+  renorm(SS);
+  TP<T, 4> beta;
+  tp_zero(beta);
+  {
+    TP<T, 4> A1, A2;
+    tp_zero(A1);
+    tp_zero(A2);
+    mac(A1, NN, SS);
+    mac(A2, DN, DN);
+    const T uu = (T)FP<T>::u;
+    const T e2v = eta * eta, e2err = F::mul_ru(uu, e2v);
+    const T c1 = T(1) - e2v, c1err = F::add_ru(e2err, F::mul_ru(uu, fabs(c1)));
+    mac(beta, tconst<T>(c1, c1err), A1);
+    mac(beta, tconst<T>(e2v, e2err), A2);
+    renorm(beta);
+  }
+  T blo, bhi;
+  classical_range4(beta, blo, bhi);
+  if (!(bhi > T(0))) {  // total internal reflection on the whole cell: no refracted path
+    put_rec(P, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, e, t, id, flags | BNB_CELL_TIR);
+    return;
+  }
+  T ca, cb, dlo, dhi;
+  sqrt_chord<T>(fmax(blo, T(0)), bhi, ca, cb, dlo, dhi);
+  // tangential part eta' ((n.n) d0 - (d0.n) n) (degree 3, elevated to 5)
+  TP<T, 5> TG5[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    TP<T, 3> tg, tge;
+    tp_zero(tg);
+    mac(tg, NN, L.D0[c]);
+    mac<true>(tg, DN, L.N[c]);
+    tp_zero(tge);
+    mac_s(tge, eta, tg);
+    TP<T, 4> t4;
+    elevate(t4, tge);
+    elevate(TG5[c], t4);
+  }
+  // receiver-side linear terms with the origin p' = p_k0 + uc e_k1 + vc e_k2
+  TP<T, 1> hu[3], hv[3];
+  {
+    constexpr T g2e = GAM<T, 2>, uu = (T)FP<T>::u;
+    TP<T, 1> W[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T pc = F::fma_rn(vc, e2[c], F::fma_rn(uc, e1[c], rp0[c]));
+      const T pmag = F::fma_ru(fabs(vc), fabs(e2[c]), F::fma_ru(fabs(uc), fabs(e1[c]), fabs(rp0[c])));
+      const T perr = F::mul_ru(g2e, pmag);
+      const T q = p[0][c] - pc;
+      const T qerr = F::add_ru(perr, F::mul_ru(uu, F::add_ru(F::add_ru(fabs(p[0][c]), fabs(pc)), perr)));
+#pragma unroll
+      for (int i = 0; i < 3; ++i) W[c].c[i] = L.XL[c].c[i] + q;
+      W[c].B = F::add_ru(F::add_ru(L.XL[c].B, fabs(q)), qerr);
+      W[c].E = F::add_ru(F::add_ru(L.XL[c].E, qerr),
+                         F::mul_ru(uu, F::add_ru(F::add_ru(L.XL[c].B, L.XL[c].E), F::add_ru(fabs(q), qerr))));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int a = (c + 1) % 3, b = (c + 2) % 3;
+      tp_zero(hu[c]);
+      mac_s(hu[c], e2[a], W[b]);
+      mac_s<true>(hu[c], e2[b], W[a]);
+      tp_zero(hv[c]);
+      mac_s(hv[c], e1[b], W[a]);
+      mac_s<true>(hv[c], e1[a], W[b]);
+    }
+  }
+  const TP<T, 0> g[3] = {cross_comp<T>(e2[1], e1[2], e2[2], e1[1]), cross_comp<T>(e2[2], e1[0], e2[0], e1[2]),
+                         cross_comp<T>(e2[0], e1[1], e2[1], e1[0])};
+  // the two xi faces: W_j = a beta + b + d_j, d~ = TG - W_j n, Q, A = d~.h_u, B = d~.h_v
+  TP<T, 5> Qf[2];
+  TP<T, 6> Af[2], Bf[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    TP<T, 4> Wj;
+    tp_zero(Wj);
+    mac_s(Wj, ca, beta);
+    const T cj = cb + (j == 0 ? dlo : dhi);
+    add_const(Wj, cj, F::mul_ru((T)FP<T>::u, fabs(cj)));
+    tp_zero(Qf[j]);
+    tp_zero(Af[j]);
+    tp_zero(Bf[j]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      TP<T, 5> DT = TG5[c];
+      mac<true>(DT, Wj, L.N[c]);
+      renorm(DT);
+      mac(Qf[j], g[c], DT);
+      mac(Af[j], DT, hu[c]);
+      mac(Bf[j], DT, hv[c]);
+    }
+    renorm(Qf[j]);
+    renorm(Af[j]);
+    renorm(Bf[j]);
+  }
+  const int s0 = cert_sign(Qf[0]), s1 = cert_sign(Qf[1]);
+  if constexpr (sizeof(T) == 4) {
+    if (s0 == 0 || s1 == 0) {  // the float32 intervals cannot decide: float64 decides (flag QSIGN_FP64)
+      process_cell_refract_fp64(P, e, t, id, depth, slot);
+      return;
+    }
+  }
+  const int sq = s0 == s1 ? s0 : 0;
+  if (sq == 0) {
+    // mixed-sign denominator: split up to the limit, then the universal box
+    if (depth < P.max_depth) {
+      const int64_t qi = (int64_t)atomicAdd((unsigned long long*)P.q_out_count, 1ull);
+      if (qi < P.q_cap) {
+        P.q_out[qi] = SplitItem{e, t, id, depth};
+      } else {
+        raise_status(P.status, BNB_ERR_CAPACITY);
+      }
+      put_rec(P, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, e, t, id, flags | BNB_CELL_SPLIT);
+    } else {
+      put_rec(P, slot, 0.f, 1.f, 0.f, 1.f, 0.f, F::inf(), e, t, id, flags | BNB_CELL_LIVE | BNB_CELL_POS_UNBOUNDED);
+    }
+    return;
+  }
+  if (sq < 0) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      negate(Qf[j]);
+      negate(Af[j]);
+      negate(Bf[j]);
+    }
+  }
+  {  // forward culling: t = Tn / Q with Tn = h_v . e2 (independent of d~)
+    TP<T, 1> Tn;
+    tp_zero(Tn);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mac_s(Tn, e2[c], hv[c]);
+    if (sq < 0) negate(Tn);
+    if (cert_sign(Tn) < 0) {
+      put_rec(P, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, e, t, id, flags | BNB_CELL_CULL_BEHIND);
+      return;
+    }
+  }
+  T umn = F::inf(), umx = -F::inf(), vmn = F::inf(), vmx = -F::inf();
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    TP<T, 6> Q6;
+    elevate(Q6, Qf[j]);
+    static_for<nc(6)>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      T ql, qh, al, ah, bl, bh;
+      coef_iv<i>(Q6, ql, qh);
+      coef_iv<i>(Af[j], al, ah);
+      coef_iv<i>(Bf[j], bl, bh);
+      const bool open = !(ql > tiny_pos<T>());
+      const T rl = open ? F::inf() : rcp_hi(ql), rh = rcp_lo(qh);
+      ratio_acc(al, ah, rl, rh, umn, umx);
+      ratio_acc(bl, bh, rl, rh, vmn, vmx);
+      if (open) {
+        if (al == T(0)) umn = fmin(umn, T(0));
+        if (ah == T(0)) umx = fmax(umx, T(0));
+        if (bl == T(0)) vmn = fmin(vmn, T(0));
+        if (bh == T(0)) vmx = fmax(vmx, T(0));
+      }
+    });
+  }
+  T ul = fmax(F::add_rd(uc, widen_lo(umn)), T(0));
+  T uh = fmin(F::add_ru(uc, widen_hi(umx)), T(1));
+  T vl = fmax(F::add_rd(vc, widen_lo(vmn)), T(0));
+  T vh = fmin(F::add_ru(vc, widen_hi(vmx)), T(1));
+  if (!(ul <= uh) || !(vl <= vh)) {
+    put_rec(P, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, e, t, id, flags | BNB_CELL_CULL_EMPTY);
+    return;
+  }
+  put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_LIVE);
+}
+
+static __device__ __noinline__ void process_cell_refract_fp64(const BoundParams& P, int e, int t, uint32_t id,
+                                                              int depth, int64_t slot) {
+  process_cell_refract<double>(P, e, t, id, depth, slot, BNB_CELL_QSIGN_FP64);
+}
+
 // ------------------------------------------------------------------ kernels
 // One 256-thread block per SM, persistent.  Every round starts with a block barrier so the
 // eight warps walk the (long, straight-line) cell program together and share instruction
 // fetches; the round count is uniform across the block, so every thread reaches every barrier.
 constexpr int kBoundThreads = 256;
 
-template <typename T>
+// KIND 0: reflection, 1: refraction (separate instantiations: each kernel holds one cell program).
+template <typename T, int KIND>
+__device__ __forceinline__ void process_any(const BoundParams& P, int e, int t, uint32_t id, int depth, int64_t slot) {
+  if constexpr (KIND == 0)
+    process_cell<T>(P, e, t, id, depth, slot);
+  else
+    process_cell_refract<T>(P, e, t, id, depth, slot);
+}
+
+template <typename T, int KIND>
 __global__ void __launch_bounds__(kBoundThreads, 1) bound_base_k(BoundParams P) {
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)P.count, (unsigned long long)P.n_base);
   const int64_t per_tuple = (int64_t)1 << (2 * P.depth);
@@ -1022,18 +1346,18 @@ __global__ void __launch_bounds__(kBoundThreads, 1) bound_base_k(BoundParams P) 
       const int64_t rr = w - (int64_t)e * per_em;
       const int t = (int)(rr / per_tuple);
       const uint32_t c = (uint32_t)(rr - (int64_t)t * per_tuple);
-      process_cell<T>(P, e, t, c, P.depth, w);
+      process_any<T, KIND>(P, e, t, c, P.depth, w);
     }
   }
 }
 
-template <typename T>
+template <typename T, int KIND>
 __global__ void __launch_bounds__(128) bound_split_k(BoundParams P, const SplitItem* __restrict__ q_in,
                                                       const int64_t* __restrict__ q_in_count) {
   const int64_t n = min(*q_in_count, P.q_cap);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 4 * n; i += (int64_t)gridDim.x * blockDim.x) {
     const SplitItem it = q_in[i >> 2];
-    process_cell<T>(P, it.emitter, it.tri, it.cell * 4u + (uint32_t)(i & 3), it.depth + 1, -1);
+    process_any<T, KIND>(P, it.emitter, it.tri, it.cell * 4u + (uint32_t)(i & 3), it.depth + 1, -1);
   }
 }
 
@@ -1047,19 +1371,19 @@ int grid_for_T(int64_t n, int block) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
 }
 
-template <typename T>
+template <typename T, int KIND>
 cudaError_t launch_bound_base_T(const BoundParams& p, cudaStream_t st) {
-  bound_base_k<T><<<grid_for_T<T>(p.n_base, kBoundThreads), kBoundThreads, 0, st>>>(p);
+  bound_base_k<T, KIND><<<grid_for_T<T>(p.n_base, kBoundThreads), kBoundThreads, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int KIND>
 cudaError_t launch_bound_split_T(const BoundParams& p, const SplitItem* q_in, const int64_t* q_in_count,
                                  cudaStream_t st) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  bound_split_k<T><<<sms * 2, 128, 0, st>>>(p, q_in, q_in_count);
+  bound_split_k<T, KIND><<<sms * 2, 128, 0, st>>>(p, q_in, q_in_count);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,8 @@ struct BoundParams {
   const float *ex, *ey, *ez, *ei;
   float rp0[3], re1[3], re2[3];
   int32_t depth, max_depth, irradiance;
+  int32_t kind;  // BNB_REFLECT or BNB_REFRACT
+  float eta;     // refraction: eta' = incident / transmitted index
   int64_t n_base;
   // outputs
   int64_t capacity;

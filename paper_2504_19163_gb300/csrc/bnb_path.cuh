@@ -38,19 +38,20 @@ __device__ __forceinline__ int grid_col_s(float x, int G) {
 }
 
 // ------------------------------------------------------------------ path evaluation (rational form)
-// For barycentrics (u, v) in T1: x1, interpolated n1, d0 = x1 - x0, reflected d~ (Eq.
-// eq_refr_rational), receiver coordinates (Eq. eq_rct), their Jacobian by the product
-// rule, and the path irradiance of Eq. eq_dwda.
+// For barycentrics (u, v) in T1: x1, interpolated n1, d0 = x1 - x0, the reflected or refracted
+// d~ (Eq. eq_refr_rational; refraction with eta' = eta, sqrt(beta) and its derivative
+// d beta / (2 sqrt(beta))), receiver coordinates (Eq. eq_rct), their Jacobian by the product
+// rule, and the path irradiance of Eq. eq_dwda.  ok is false where no refracted path exists.
 template <typename T>
 struct Path {
   T uk, vk, J00, J01, J10, J11, t, E;
   bool ok;
 };
 
-template <typename T>
+template <typename T, bool REFRACT>
 __device__ __forceinline__ Path<T> eval_path(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0f)[3],
                                             float I0, const float (&rp0)[3], const float (&re1)[3],
-                                            const float (&re2)[3], T u, T v) {
+                                            const float (&re2)[3], T u, T v, float etaf) {
   T p0[3], e1[3], e2[3], n0[3], f1[3], f2[3], x[3], n[3], d[3], P0[3], E1[3], E2[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -73,11 +74,22 @@ __device__ __forceinline__ Path<T> eval_path(const float (&pf)[3][3], const floa
     r[1] = a[2] * b[0] - a[0] * b[2];
     r[2] = a[0] * b[1] - a[1] * b[0];
   };
-  const T nn = dot(n, n), dn = dot(d, n);
+  const T nn = dot(n, n), dn = dot(d, n), ss = dot(d, d);
+  const T eta = (T)etaf;
+  T W = T(0);
+  bool tir = false;
+  if constexpr (REFRACT) {
+    const T beta = (T(1) - eta * eta) * nn * ss + eta * eta * dn * dn;
+    tir = !(beta > T(0));
+    W = sqrt(fmax(beta, T(0)));
+  }
   T dt[3], w[3], g[3], he2w[3], hwe1[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    dt[c] = nn * d[c] - T(2) * dn * n[c];
+    if constexpr (REFRACT)
+      dt[c] = eta * (nn * d[c] - dn * n[c]) - W * n[c];
+    else
+      dt[c] = nn * d[c] - T(2) * dn * n[c];
     w[c] = x[c] - P0[c];
   }
   cross(E2, E1, g);
@@ -92,8 +104,16 @@ __device__ __forceinline__ Path<T> eval_path(const float (&pf)[3][3], const floa
     const T dnn = T(2) * dot(n, dnv);
     const T ddn = dot(dx, n) + dot(d, dnv);
     T ddt[3], c1[3], c2[3];
+    if constexpr (REFRACT) {
+      const T dbeta = (T(1) - eta * eta) * (dnn * ss + nn * T(2) * dot(d, dx)) + eta * eta * T(2) * dn * ddn;
+      const T dW = dbeta / (T(2) * W);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) ddt[c] = dnn * d[c] + nn * dx[c] - T(2) * (ddn * n[c] + dn * dnv[c]);
+      for (int c = 0; c < 3; ++c)
+        ddt[c] = eta * (dnn * d[c] + nn * dx[c] - ddn * n[c] - dn * dnv[c]) - dW * n[c] - W * dnv[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ddt[c] = dnn * d[c] + nn * dx[c] - T(2) * (ddn * n[c] + dn * dnv[c]);
+    }
     cross(E2, dx, c1);
     cross(dx, E1, c2);
     dQ[j] = dot(ddt, g);
@@ -116,9 +136,8 @@ __device__ __forceinline__ Path<T> eval_path(const float (&pf)[3][3], const floa
 #pragma unroll
   for (int c = 0; c < 3; ++c) r0[c] = p0[c] - (T)x0f[c];
   const T C1 = dot(r0, N1);
-  const T s = dot(d, d);
-  r.E = (T)I0 * fabs(C1) / (s * sqrt(s) * sqrt(dot(Nk, Nk)) * fabs(det));
-  r.ok = isfinite(r.uk) && isfinite(r.vk) && isfinite(det) && Q != T(0);
+  r.E = (T)I0 * fabs(C1) / (ss * sqrt(ss) * sqrt(dot(Nk, Nk)) * fabs(det));
+  r.ok = !tir && isfinite(r.uk) && isfinite(r.vk) && isfinite(det) && Q != T(0);
   return r;
 }
 
@@ -162,14 +181,15 @@ __device__ __forceinline__ bool newton_step(const Path<T>& P, T tu, T tv, bool d
 //             the polish.
 //   polish64  float64 polish steps and the acceptance tests.  Returns the path irradiance E
 //             (float64), or a negative value when no admissible root is found.
+template <bool REFRACT>
 __device__ __forceinline__ bool newton32(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0)[3],
                                          float I0, const float (&rp0)[3], const float (&re1)[3], const float (&re2)[3],
-                                         float tuf, float tvf, int newton_iters, float& u, float& v) {
+                                         float tuf, float tvf, int newton_iters, float eta, float& u, float& v) {
   u = 1.0f / 3.0f;
   v = 1.0f / 3.0f;
   bool converged = false;
   for (int it = 0; it < newton_iters; ++it) {
-    const Path<float> P = eval_path<float>(pf, nf, x0, I0, rp0, re1, re2, u, v);
+    const Path<float> P = eval_path<float, REFRACT>(pf, nf, x0, I0, rp0, re1, re2, u, v, eta);
     float step;
     if (!newton_step<float>(P, tuf, tvf, true, u, v, step)) return false;
     if (step < 1e-6f) {
@@ -181,19 +201,20 @@ __device__ __forceinline__ bool newton32(const float (&pf)[3][3], const float (&
   return !(converged && fminf(fminf(u, v), 1.0f - u - v) < -kOutside);
 }
 
+template <bool REFRACT>
 __device__ __forceinline__ double polish64(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0)[3],
                                            float I0, const float (&rp0)[3], const float (&re1)[3],
                                            const float (&re2)[3], float tuf, float tvf, int polish_iters, float tol,
-                                           float u, float v) {
+                                           float eta, float u, float v) {
   double ud = u, vd = v;
   bool good = true;
   for (int it = 0; it < polish_iters && good; ++it) {
-    const Path<double> P = eval_path<double>(pf, nf, x0, I0, rp0, re1, re2, ud, vd);
+    const Path<double> P = eval_path<double, REFRACT>(pf, nf, x0, I0, rp0, re1, re2, ud, vd, eta);
     double step;
     good = newton_step<double>(P, (double)tuf, (double)tvf, false, ud, vd, step);
   }
   if (!good) return -1.0;
-  const Path<double> P = eval_path<double>(pf, nf, x0, I0, rp0, re1, re2, ud, vd);
+  const Path<double> P = eval_path<double, REFRACT>(pf, nf, x0, I0, rp0, re1, re2, ud, vd, eta);
   const double fu = P.uk - (double)tuf, fv = P.vk - (double)tvf;
   const double r0 = fu * re1[0] + fv * re2[0], r1 = fu * re1[1] + fv * re2[1], r2 = fu * re1[2] + fv * re2[2];
   const double res = sqrt(r0 * r0 + r1 * r1 + r2 * r2);

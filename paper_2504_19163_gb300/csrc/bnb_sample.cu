@@ -105,6 +105,7 @@ struct SolveParams {
   int64_t wl_cap;
   int32_t newton_iters, polish_iters;
   float tol;
+  float eta;  // refraction: eta'
   float* contrib;
   int64_t* counters;
   // tuples handed from the float32 phase to the float64 polish
@@ -115,6 +116,7 @@ struct SolveParams {
 
 // float32 Newton phase over every selection: contributions of the tuples without an admissible
 // root are 0 now; the others go to the polish list with their float32 root.
+template <bool REFRACT>
 __global__ void __launch_bounds__(256) solve32_k(SolveParams S) {
   const int64_t n = min(*S.n_wl, S.wl_cap);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -127,7 +129,8 @@ __global__ void __launch_bounds__(256) solve32_k(SolveParams S) {
       load_tri_s(S.tri, t, pf, nf);
       const float x0[3] = {__ldg(S.ex + e), __ldg(S.ey + e), __ldg(S.ez + e)};
       const int64_t pt = S.wl_point[i];
-      need = newton32(pf, nf, x0, __ldg(S.ei + e), S.rp0, S.re1, S.re2, S.su[pt], S.sv[pt], S.newton_iters, u, v);
+      need = newton32<REFRACT>(pf, nf, x0, __ldg(S.ei + e), S.rp0, S.re1, S.re2, S.su[pt], S.sv[pt], S.newton_iters,
+                               S.eta, u, v);
     }
     if (!need) S.contrib[i] = 0.0f;
     const int64_t j = warp_append(need, S.pl_count);
@@ -140,6 +143,7 @@ __global__ void __launch_bounds__(256) solve32_k(SolveParams S) {
 }
 
 // float64 polish of the listed tuples, acceptance tests, contribution E(root) / P.
+template <bool REFRACT>
 __global__ void __launch_bounds__(256) polish_k(SolveParams S) {
   const int64_t n = *S.pl_count;
   long long roots = 0;
@@ -151,8 +155,8 @@ __global__ void __launch_bounds__(256) polish_k(SolveParams S) {
     load_tri_s(S.tri, t, pf, nf);
     const float x0[3] = {__ldg(S.ex + e), __ldg(S.ey + e), __ldg(S.ez + e)};
     const int64_t pt = S.wl_point[i];
-    const double E = polish64(pf, nf, x0, __ldg(S.ei + e), S.rp0, S.re1, S.re2, S.su[pt], S.sv[pt],
-                              S.polish_iters, S.tol, S.pl_u[j], S.pl_v[j]);
+    const double E = polish64<REFRACT>(pf, nf, x0, __ldg(S.ei + e), S.rp0, S.re1, S.re2, S.su[pt], S.sv[pt],
+                                       S.polish_iters, S.tol, S.eta, S.pl_u[j], S.pl_v[j]);
     float c = 0.0f;
     if (E >= 0.0) {
       c = (float)(E / (double)S.wl_p[i]);
@@ -284,8 +288,14 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_receiver* r
   S.pl_u = w.pl_u;
   S.pl_v = w.pl_v;
   if ((e = cudaMemsetAsync(w.pl_count, 0, sizeof(int64_t), st)) != cudaSuccess) return e;
-  solve32_k<<<sms * 16, 256, 0, st>>>(S);
-  polish_k<<<sms * 16, 256, 0, st>>>(S);
+  S.eta = s1->eta;
+  if (s1->kind == BNB_REFRACT) {
+    solve32_k<true><<<sms * 16, 256, 0, st>>>(S);
+    polish_k<true><<<sms * 16, 256, 0, st>>>(S);
+  } else {
+    solve32_k<false><<<sms * 16, 256, 0, st>>>(S);
+    polish_k<false><<<sms * 16, 256, 0, st>>>(S);
+  }
   reduce_k<<<(unsigned)pblocks, 256, 0, st>>>(w.woff, w.contrib, n_points, cfg->worklist_capacity, E_out);
   return cudaGetLastError();
 }

@@ -103,3 +103,38 @@ def assert_bounds_parity(rep, allow_ambiguous_frac=1e-3, slack_median=2e-4, slac
         assert rep["encl_viol"] == 0, rep
         assert rep["slack_median"] <= slack_median and rep["slack_p99"] <= slack_p99, rep
     assert rep["e_checked"] > 0.9 * rep["live"], rep
+
+
+def compare_refraction(g, o):
+    """Refraction records: the GPU's sqrt chord is built from its own (outward float32) range of
+    beta, so its remainder envelope differs from the oracle's by rounding and neither box need
+    contain the other.  Compared: keys and flags (outside the ambiguity band), and the box
+    distance max(|lo_g - lo_o|, |hi_g - hi_o|); containment of the true paths is checked by a
+    dense sweep (sweep_violations_gpu)."""
+    gd = depth_of(g["flags"])
+    od = depth_of(o["flags"])
+    gkey = {(int(e), int(t), int(c), int(d)): i for i, (e, t, c, d) in
+            enumerate(zip(g["emitter"], g["tri0"], g["cell"], gd))}
+    rep = dict(n=len(o), missing=0, flag_mismatch=0, flag_ambiguous=0, live=0, box_diff=[], e_finite=0)
+    for oi in range(len(o)):
+        k = (int(o["emitter"][oi]), int(o["tri0"][oi]), int(o["cell"][oi]), int(od[oi]))
+        gi = gkey.get(k)
+        if gi is None:
+            rep["missing"] += 1
+            continue
+        gf = int(g["flags"][gi]) & FLAG_MASK
+        of = int(o["flags"][oi]) & 0xFF
+        if gf != of:
+            rep["flag_ambiguous" if o["q_cond"][oi] < Q_COND else "flag_mismatch"] += 1
+            continue
+        if not (of & 1):
+            continue
+        rep["live"] += 1
+        for a in ("u", "v"):
+            rep["box_diff"].append(max(abs(float(g[a + "_lo"][gi]) - float(o[a + "_lo"][oi])),
+                                       abs(float(g[a + "_hi"][gi]) - float(o[a + "_hi"][oi]))))
+        if np.isfinite(g["e_hi"][gi]):
+            rep["e_finite"] += 1
+    d = np.array(rep.pop("box_diff") or [0.0])
+    rep.update(box_diff_max=float(d.max()), box_diff_p99=float(np.percentile(d, 99)))
+    return rep
