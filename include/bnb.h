@@ -152,11 +152,15 @@ typedef struct bnb_sample_stats {
 } bnb_sample_stats;
 
 /* Precomputation pass.  Bounds every (emitter, triangle of s1, cell) with
- * Secs. 4.3-4.4: x1, n1 (Eqs. eq_xi, eq_ni), the reflected direction (Eq.
- * eq_refr_rational), receiver coordinates (Eq. eq_rct) and irradiance (Eqs.
- * eq_dwda, eq_irr_term3a) as Bernstein forms on the cell, their ratio bound
- * (Eq. eq_bbound), |d0|^-3 carried by a remainder variable (Sec. 4.3).  s2 must
- * be NULL (one specular vertex).  Requires out->capacity >= n_base =
+ * Secs. 4.3-4.4: x1, n1 (Eqs. eq_xi, eq_ni), the reflected or refracted
+ * direction (Eq. eq_refr_rational), receiver coordinates (Eq. eq_rct) and, for
+ * reflection, irradiance (Eqs. eq_dwda, eq_irr_term3a) as Bernstein forms on
+ * the cell, their ratio bound (Eq. eq_bbound), |d0|^-3 carried by a remainder
+ * variable (Sec. 4.3).  Refraction (s1->kind = BNB_REFRACT, normals facing the
+ * incident side, eta in (0, 1e6)) carries sqrt(beta) by a remainder variable
+ * (Sec. 4.3), culls cells in total internal reflection (flag TIR) and reports
+ * e_hi = +inf (its irradiance is not bounded).  s2 must be NULL (one specular
+ * vertex).  Requires out->capacity >= n_base =
  * em->n * s1->n_tris * 4^depth.  ws: bnb_bound_tuples_ws() bytes. */
 int32_t bnb_bound_tuples(const bnb_surface *s1, const bnb_surface *s2, const bnb_receiver *rec,
                          const bnb_emitters *em, const bnb_bound_cfg *cfg, bnb_cell_bounds *out,
