@@ -239,6 +239,18 @@ PV pv_crossc(const PV& a, V3 b) {  // a x b, b constant
           padd(pscale(a.x, b.y), pscale(a.y, b.x), -1.0)};
 }
 
+// p0 + W p1 with W = sqrt(beta) kept as a symbol: products reduce W^2 to beta, which is exact
+// wherever W = sqrt(beta) (refraction, Sec. 4.4 with the derivative of sqrt carried exactly).
+struct WP {
+  Poly p0, p1;
+};
+WP wp_add(const WP& a, const WP& b, double sb = 1.0) { return {padd(a.p0, b.p0, sb), padd(a.p1, b.p1, sb)}; }
+WP wp_mul(const WP& a, const WP& b, const Poly& beta) {
+  return {padd(pmul(a.p0, b.p0), pmul(pmul(a.p1, b.p1), beta)), padd(pmul(a.p0, b.p1), pmul(a.p1, b.p0))};
+}
+WP wp_mulp(const WP& a, const Poly& q) { return {pmul(a.p0, q), pmul(a.p1, q)}; }
+Poly wp_at(const WP& a, const Poly& W) { return padd(a.p0, pmul(W, a.p1)); }  // W replaced by a polynomial
+
 // ---------------------------------------------------------------------------
 // Scene views (own definitions; the field layout is the documented interface)
 // ---------------------------------------------------------------------------
@@ -584,8 +596,7 @@ void bound_cell_reflect(const Ctx& cx, int e, int t, uint32_t id, int depth, std
 // faces.  Readings: the normals face the incident side (d0.n < 0 on real paths); a cell where
 // beta < 0 everywhere has no refracted path (total internal reflection: flag TIR); beta < 0
 // elsewhere is clipped from the chord's range (no path exists there); a mixed-sign denominator
-// is split up to the extra-split limit and then kept with the universal box [0,1]^2; the
-// irradiance bound of refraction is not built: E_hi = +inf.
+// is split up to the extra-split limit and then kept with the universal box [0,1]^2.
 void bound_cell_refract(const Ctx& cx, int e, int t, uint32_t id, int depth, std::vector<orc_record>& out) {
   UV C[3];
   cell_corners(id, depth, C);
@@ -683,6 +694,94 @@ void bound_cell_refract(const Ctx& cx, int e, int t, uint32_t id, int depth, std
   r.flags |= F_LIVE;
   r.e_lo = 0.0;
   r.e_hi = std::numeric_limits<double>::infinity();
+  if (!cx.irradiance) {
+    out.push_back(r);
+    return;
+  }
+  // Irradiance (Eqs. eq_dwda, eq_irr_term3a) with sqrt(beta) kept as the symbol W: the
+  // derivatives of d~ are scaled by 2W, which clears dW = d beta / (2W):
+  //   2W d_j d~ = (-(d_j beta) n - 2 beta d_j n) + W (2 d_j G),   G = eta' ((n.n) d0 - (d0.n) n),
+  // and the same scaling of d_j A, d_j B, d_j Q gives M' = (2W)^2 M = 4 beta M, so
+  //   E = I0 |C1| |detA| |Q|^3 4 beta s^(-3/2) / (|N_k| |M'|).
+  // W is then replaced by the remainder form (xi1) and s^(-3/2) by its chord (xi2); the ratio
+  // bound runs over the (cell, xi1, xi2) product domain.  A mixed-sign M' is a fold (E = +inf).
+  {
+    Poly beta_d[2] = {pderiv(beta, 1), pderiv(beta, 2)};
+    Poly G[3], nc3[3] = {n1.x, n1.y, n1.z}, d0c[3] = {d0.x, d0.y, d0.z};
+    for (int c = 0; c < 3; ++c) G[c] = pscale(padd(pmul(nn, d0c[c]), pmul(dn, nc3[c]), -1.0), eta);
+    WP dt[3], Dt[2][3];
+    for (int c = 0; c < 3; ++c) {
+      dt[c] = {G[c], pscale(nc3[c], -1.0)};
+      for (int j = 0; j < 2; ++j)
+        Dt[j][c] = {padd(pscale(pmul(beta_d[j], nc3[c]), -1.0), pscale(pmul(beta, pderiv(nc3[c], j + 1)), -2.0)),
+                    pscale(pderiv(G[c], j + 1), 2.0)};
+    }
+    const V3 gv = cross(R.e2, R.e1);
+    const double g[3] = {gv.x, gv.y, gv.z};
+    PV hu = pv_crossc(w, R.e2);  // h_u = e2 x w  ->  w x e2 negated below
+    hu = pv_scale(hu, -1.0);
+    PV hv = pv_crossc(w, R.e1);  // h_v = w x e1
+    Poly huc[3] = {hu.x, hu.y, hu.z}, hvc[3] = {hv.x, hv.y, hv.z};
+    auto zero = [](int n) { return WP{pconst(2, n, 0.0), pconst(2, n, 0.0)}; };
+    WP Qw = zero(0), Aw = zero(0), Bw = zero(0), Qt[2] = {zero(0), zero(0)}, At[2] = {zero(0), zero(0)},
+       Bt[2] = {zero(0), zero(0)};
+    for (int c = 0; c < 3; ++c) {
+      Qw = wp_add(Qw, {pscale(dt[c].p0, g[c]), pscale(dt[c].p1, g[c])});
+      Aw = wp_add(Aw, wp_mulp(dt[c], huc[c]));
+      Bw = wp_add(Bw, wp_mulp(dt[c], hvc[c]));
+      for (int j = 0; j < 2; ++j) {
+        Qt[j] = wp_add(Qt[j], {pscale(Dt[j][c].p0, g[c]), pscale(Dt[j][c].p1, g[c])});
+        const Poly dhu = pderiv(huc[c], j + 1), dhv = pderiv(hvc[c], j + 1);
+        // 2W d~ . d_j h = (-2 beta n . d_j h) + W (2 G . d_j h)
+        const WP tu = {pscale(pmul(pmul(beta, nc3[c]), dhu), -2.0), pscale(pmul(G[c], dhu), 2.0)};
+        const WP tv = {pscale(pmul(pmul(beta, nc3[c]), dhv), -2.0), pscale(pmul(G[c], dhv), 2.0)};
+        At[j] = wp_add(At[j], wp_add(wp_mulp(Dt[j][c], huc[c]), tu));
+        Bt[j] = wp_add(Bt[j], wp_add(wp_mulp(Dt[j][c], hvc[c]), tv));
+      }
+    }
+    WP X = wp_add(wp_mul(At[0], Bt[1], beta), wp_mul(At[1], Bt[0], beta), -1.0);
+    WP Y = wp_add(wp_mul(At[0], Qt[1], beta), wp_mul(At[1], Qt[0], beta), -1.0);
+    WP Z = wp_add(wp_mul(Qt[0], Bt[1], beta), wp_mul(Qt[1], Bt[0], beta), -1.0);
+    WP Mp = wp_add(wp_add(wp_mul(Qw, X, beta), wp_mul(Bw, Y, beta), -1.0), wp_mul(Aw, Z, beta), -1.0);
+    WP Q3 = wp_mul(wp_mul(Qw, Qw, beta), Qw, beta);
+    Poly Mf[2], Q3f[2];
+    int sm[2];
+    for (int j = 0; j < 2; ++j) {
+      Poly W = padd(pscale(beta, a), pconst(2, 4, b + (j == 0 ? dlo : dhi)));
+      Mf[j] = wp_at(Mp, W);
+      Q3f[j] = pscale(wp_at(Q3, W), (double)sq);
+      sm[j] = psign(Mf[j]);
+    }
+    r.m_cond = std::min(cond_of(Mf[0]), cond_of(Mf[1]));
+    if (sm[0] == 0 || sm[0] != sm[1]) {
+      r.flags |= F_FOLD;
+      out.push_back(r);
+      return;
+    }
+    V3 N1 = cross(e11, e12);
+    double C1 = dot(T.p[0] - x0, N1);
+    V3 Nk = cross(R.e1, R.e2);
+    double detA = (C[1].u - C[0].u) * (C[2].v - C[0].v) - (C[1].v - C[0].v) * (C[2].u - C[0].u);
+    double K = cx.em->intensity[e] * std::fabs(C1) * std::fabs(detA) / norm(Nk);
+    double sa, sb, sdlo, sdhi;
+    chord_inv32(pmin(ss), pmax(ss), &sa, &sb, &sdlo, &sdhi);
+    const Poly beta4 = pscale(beta, 4.0);
+    double lo = std::numeric_limits<double>::infinity(), hi = -lo;
+    for (int j = 0; j < 2; ++j) {
+      const Poly num0 = pmul(Q3f[j], beta4);
+      Poly den = pscale(Mf[j], (double)sm[j]);
+      for (int k = 0; k < 2; ++k) {
+        Poly F = padd(pscale(ss, sa), pconst(2, 2, sb + (k == 0 ? sdlo : sdhi)));
+        Poly N = pmul(num0, F);
+        double l, h;
+        ratio_bound(N, pelevate_to(den, N.n), &l, &h);
+        lo = std::min(lo, l);
+        hi = std::max(hi, h);
+      }
+    }
+    r.e_lo = K * std::max(lo, 0.0);
+    r.e_hi = K * hi;
+  }
   out.push_back(r);
 }
 

@@ -204,11 +204,15 @@ def test_refraction_boxes_converge_under_subdivision(orc):
 
 
 def test_refraction_estimate_matches_root_enumeration(orc):
-    """With every tuple selected (E~ = +inf, so P = 1), the whole path's estimate at each point is
-    the sum of E over the roots, enumerated here independently (dense grid + Newton on the direct
-    evaluator) on a tiny mesh."""
+    """With every listed tuple selected (gamma = +inf, so P = 1), the whole path's estimate at each
+    point is the sum of E over the roots, enumerated here independently (dense grid + Newton on
+    the direct evaluator) on a tiny mesh; every root's tuple carries E~ >= E."""
     sc = S.config("water", n=3, depth=1, points=6, steep=0.05)
-    E_est = orc.render(sc, gamma=1.0, seed=3)["E"]
+    out = orc.render(sc, gamma=float("inf"), seed=3)
+    E_est = out["E"]
+    assert np.all(out["wl_p"] == 1.0)
+    roots = out["status"] == 1
+    assert np.all(out["contrib"][roots] <= out["etilde"].max())  # E(root) / 1 below the largest E~
     P = np.stack([sc.s1.px, sc.s1.py, sc.s1.pz], 1).astype(np.float64)
     K = 60
     mu = np.array([(i / K, j / K) for i in range(K + 1) for j in range(K + 1 - i)])
@@ -241,3 +245,24 @@ def test_refraction_estimate_matches_root_enumeration(orc):
             E_ref[p] += sum(r[2] for r in roots)
     assert np.count_nonzero(E_ref) >= 5
     np.testing.assert_allclose(E_est, E_ref, rtol=1e-6, atol=1e-12)
+
+
+def test_refraction_irradiance_encloses_and_converges(orc):
+    """Refraction irradiance bound (sqrt(beta) kept as a symbol, 2W-scaled derivatives, M' = 4 beta M,
+    remainder variables for sqrt(beta) and s^(-3/2)): every swept path's E lies in [E_lo, E_hi],
+    and E_hi approaches the cell's maximum as the cells shrink."""
+    sc = S.config("water", n=4, steep=0.05, lights=[(0.3, 0.2, 1.2)])
+    excess = []
+    for d in (0, 2, 3):
+        rec = orc.bound(sc, depth=d)
+        live = rec[((rec["flags"] & orc.LIVE) != 0) & np.isfinite(rec["e_hi"])]
+        assert len(live) > 0.9 * np.count_nonzero(rec["flags"] & orc.LIVE)
+        ex = []
+        for r in live[:: max(1, len(live) // 40)]:
+            u, v = cell_points(orc, r["cell"], d, 12)
+            uk, vk, E, t = orc.eval_path(sc, int(r["emitter"]), int(r["tri0"]), u, v, direct=True)
+            assert np.all(E <= r["e_hi"] * (1 + 1e-9)) and np.all(E >= r["e_lo"] * (1 - 1e-9))
+            ex.append(r["e_hi"] / E.max() - 1.0)
+        excess.append(np.median(ex))
+    assert excess[0] > excess[1] > excess[2] >= 0.0
+    assert excess[2] < 0.05 * excess[0]
