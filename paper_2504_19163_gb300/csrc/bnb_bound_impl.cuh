@@ -586,6 +586,47 @@ __device__ void recip01(const TP<T, 4>& P4, const TP<T, 4>& Q4, int sp, T& lo, T
 }
 
 // ------------------------------------------------------------------ one cell
+// K = I0 |(p10 - x0).N1| |det A_cell| / |N_k| (|det A_cell| = 4^-depth, exact), rounded outward:
+// the constant factor of the path irradiance (Eq. eq_dwda) on a cell.
+template <typename T>
+__device__ __forceinline__ void cell_K(const T (&p)[3][3], const T (&x0)[3], const T (&e1)[3], const T (&e2)[3],
+                                       float I0f, int depth, T& Klo, T& Khi) {
+  using F = FP<T>;
+  T a[3], b[3], r[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a[c] = p[1][c] - p[0][c];
+    b[c] = p[2][c] - p[0][c];
+    r[c] = p[0][c] - x0[c];
+  }
+  const T N1[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+  const T C1 = r[0] * N1[0] + r[1] * N1[1] + r[2] * N1[2];
+  T mag = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int i = (c + 1) % 3, j = (c + 2) % 3;
+    mag = F::fma_ru(fabs(r[c]), F::fma_ru(fabs(a[i]), fabs(b[j]), F::mul_ru(fabs(a[j]), fabs(b[i]))), mag);
+  }
+  const T cerr = F::mul_ru(GAM<T, 10>, mag);
+  const T C1hi = F::add_ru(fabs(C1), cerr), C1lo = fmax(F::add_rd(fabs(C1), -cerr), T(0));
+  T nkl2 = T(0), nkh2 = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int i = (c + 1) % 3, j = (c + 2) % 3;
+    const T v = e1[i] * e2[j] - e1[j] * e2[i];
+    const T err = F::mul_ru(GAM<T, 2>, F::fma_ru(fabs(e1[i]), fabs(e2[j]), F::mul_ru(fabs(e1[j]), fabs(e2[i]))));
+    const T lo = fmax(F::add_rd(fabs(v), -err), T(0)), hi = F::add_ru(fabs(v), err);
+    nkl2 = F::fma_rd(lo, lo, nkl2);
+    nkh2 = F::fma_ru(hi, hi, nkh2);
+  }
+  const T nkl = F::sqrt_rd(nkl2), nkh = F::sqrt_ru(nkh2);
+  T detA;
+  if constexpr (sizeof(T) == 4) detA = ldexpf(1.0f, -2 * depth); else detA = ldexp(1.0, -2 * depth);
+  const T I0 = (T)I0f;
+  Khi = F::div_ru(F::mul_ru(F::mul_ru(I0, C1hi), detA), nkl);
+  Klo = F::div_rd(F::mul_rd(F::mul_rd(I0, C1lo), detA), nkh);
+}
+
 static __device__ __noinline__ void process_cell_fp64(const BoundParams& P, int e, int t, uint32_t id, int depth,
                                                       int64_t slot);
 
@@ -951,43 +992,7 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
   }
   // K = I0 |(p10 - x0).N1| |det A_cell| / |N_k|   (|det A_cell| = 4^-depth, exact)
   T Klo, Khi;
-  {
-    const T uu = (T)FP<T>::u;
-    T a[3], b[3], r[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      a[c] = p[1][c] - p[0][c];
-      b[c] = p[2][c] - p[0][c];
-      r[c] = p[0][c] - x0[c];
-    }
-    const T N1[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
-    const T C1 = r[0] * N1[0] + r[1] * N1[1] + r[2] * N1[2];
-    T mag = T(0);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int i = (c + 1) % 3, j = (c + 2) % 3;
-      mag = F::fma_ru(fabs(r[c]), F::fma_ru(fabs(a[i]), fabs(b[j]), F::mul_ru(fabs(a[j]), fabs(b[i]))), mag);
-    }
-    const T cerr = F::mul_ru(GAM<T, 10>, mag);
-    const T C1hi = F::add_ru(fabs(C1), cerr), C1lo = fmax(F::add_rd(fabs(C1), -cerr), T(0));
-    T nkl2 = T(0), nkh2 = T(0);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int i = (c + 1) % 3, j = (c + 2) % 3;
-      const T v = e1[i] * e2[j] - e1[j] * e2[i];
-      const T err = F::mul_ru(GAM<T, 2>, F::fma_ru(fabs(e1[i]), fabs(e2[j]), F::mul_ru(fabs(e1[j]), fabs(e2[i]))));
-      const T lo = fmax(F::add_rd(fabs(v), -err), T(0)), hi = F::add_ru(fabs(v), err);
-      nkl2 = F::fma_rd(lo, lo, nkl2);
-      nkh2 = F::fma_ru(hi, hi, nkh2);
-    }
-    const T nkl = F::sqrt_rd(nkl2), nkh = F::sqrt_ru(nkh2);
-    T detA;
-    if constexpr (sizeof(T) == 4) detA = ldexpf(1.0f, -2 * depth); else detA = ldexp(1.0, -2 * depth);
-    const T I0 = (T)I0f;
-    Khi = F::div_ru(F::mul_ru(F::mul_ru(I0, C1hi), detA), nkl);
-    Klo = F::div_rd(F::mul_rd(F::mul_rd(I0, C1lo), detA), nkh);
-    (void)uu;
-  }
+  cell_K<T>(p, x0, e1, e2, I0f, depth, Klo, Khi);
   T eh = F::mul_ru(Khi, widen_hi(acc.eh_mx));
   T el = want_lo ? fmax(F::mul_rd(Klo, widen_lo(acc.el_mn)), T(0)) : T(0);
   if (!(eh >= T(0))) eh = F::inf();  // NaN guard: never report a finite bound by accident
@@ -1059,6 +1064,310 @@ __device__ __forceinline__ void sqrt_chord(T lo, T hi, T& a, T& b, T& dlo, T& dh
   dhi = fmax(up_at(lo), up_at(hi));
 }
 
+// ---- refraction irradiance (Eqs. eq_dwda, eq_irr_term3a) with W = sqrt(beta) kept as a symbol.
+// A pair (p0, p1) stands for p0 + W p1; products reduce W^2 to beta, exact on real paths.  The
+// edge derivatives of d~ are scaled by 2W, which clears d sqrt(beta) = d beta / (2W):
+//   2W d_j d~ = (-(d_j beta) n - 2 beta d_j n) + W (2 d_j G),   G = eta' ((n.n) d0 - (d0.n) n),
+// so the Jacobian numerator of (A/Q, B/Q) built from 2W-scaled derivatives is M' = 4 beta M and
+//   E = K |Q|^3 4 beta s^(-3/2) / |M'|.
+// W is then replaced by the position bound's remainder form (two xi1 faces) and s^(-3/2) by its
+// chord (two xi2 faces); the ratio bound runs over the four faces.
+template <typename T, int N>
+struct WPr {
+  TP<T, N> p0;
+  TP<T, N - 2> p1;
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void wp_zero(WPr<T, N>& r) {
+  tp_zero(r.p0);
+  tp_zero(r.p1);
+}
+
+// r (+/-)= a * b  with W^2 = beta
+template <bool NEG = false, typename T, int M, int N>
+__device__ __forceinline__ void wp_mac(WPr<T, M + N>& r, const WPr<T, M>& a, const WPr<T, N>& b, const TP<T, 4>& beta) {
+  mac<NEG>(r.p0, a.p0, b.p0);
+  TP<T, M + N - 4> t;
+  tp_zero(t);
+  mac(t, a.p1, b.p1);
+  renorm(t);
+  mac<NEG>(r.p0, t, beta);
+  mac<NEG>(r.p1, a.p0, b.p1);
+  mac<NEG>(r.p1, a.p1, b.p0);
+}
+
+// r += a * q for a plain form q
+template <typename T, int M, int N>
+__device__ __forceinline__ void wp_mac_p(WPr<T, M + N>& r, const WPr<T, M>& a, const TP<T, N>& q) {
+  mac(r.p0, a.p0, q);
+  mac(r.p1, a.p1, q);
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void wp_renorm(WPr<T, N>& r) {
+  renorm(r.p0);
+  renorm(r.p1);
+}
+
+// The face p0 + W_j p1 of a pair (degree N + 2).
+template <typename T, int N>
+__device__ __forceinline__ void wp_face(TP<T, N + 2>& r, const WPr<T, N>& a, const TP<T, 4>& Wj) {
+  TP<T, N + 1> e1;
+  elevate(e1, a.p0);
+  elevate(r, e1);
+  mac(r, Wj, a.p1);
+  renorm(r);
+}
+
+template <typename T>
+__device__ __forceinline__ void refract_irradiance(const Leaves<T>& L, const TP<T, 2>& NN, const TP<T, 2>& DN,
+                                                   const TP<T, 2>& SS, const TP<T, 4>& beta, T eta,
+                                                   const TP<T, 3> (&TG3)[3], const TP<T, 1> (&hu)[3],
+                                                   const TP<T, 1> (&hv)[3], const TP<T, 0> (&g)[3], const T (&e1)[3],
+                                                   const T (&e2)[3], int sq, T ca, T cb, T dlo, T dhi, T Klo, T Khi,
+                                                   T& el, T& eh, uint32_t& fold) {
+  using F = FP<T>;
+  const T uu = (T)FP<T>::u;
+  const T e2v = eta * eta, e2err = F::mul_ru(uu, e2v);
+  const T c1 = T(1) - e2v, c1err = F::add_ru(e2err, F::mul_ru(uu, fabs(c1)));
+  // d~ pairs and their 2W-scaled edge derivatives
+  WPr<T, 3> dt[3];
+  WPr<T, 4> Dt[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    dt[c].p0 = TG3[c];
+    tp_zero(dt[c].p1);
+    mac_s<true>(dt[c].p1, T(1), L.N[c]);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    // d(n.n) = 2 n.dn, d(d0.n) = dx.n + d0.dn, d(d0.d0) = 2 d0.dx   (degree 1)
+    TP<T, 1> dNN, dDN, dSS;
+    tp_zero(dNN);
+    tp_zero(dDN);
+    tp_zero(dSS);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      mac(dNN, L.N[c], L.DN[j][c]);
+      mac(dDN, L.N[c], L.DX[j][c]);
+      mac(dDN, L.D0[c], L.DN[j][c]);
+      mac(dSS, L.D0[c], L.DX[j][c]);
+    }
+    scale2(dNN);
+    scale2(dSS);
+    // d beta = (1 - eta^2)(d(n.n) s + (n.n) d s) + 2 eta^2 (d0.n) d(d0.n)   (degree 3)
+    TP<T, 3> dB, t1;
+    tp_zero(t1);
+    mac(t1, dNN, SS);
+    mac(t1, NN, dSS);
+    renorm(t1);
+    tp_zero(dB);
+    mac(dB, tconst<T>(c1, c1err), t1);
+    TP<T, 3> t2;
+    tp_zero(t2);
+    mac(t2, DN, dDN);
+    scale2(t2);
+    mac(dB, tconst<T>(e2v, e2err), t2);
+    renorm(dB);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      // d G_c = eta' (d(n.n) d0_c + (n.n) dx_c - d(d0.n) n_c - (d0.n) dn_c)   (degree 2)
+      TP<T, 2> dG, dGe;
+      tp_zero(dG);
+      mac(dG, dNN, L.D0[c]);
+      mac(dG, NN, L.DX[j][c]);
+      mac<true>(dG, dDN, L.N[c]);
+      mac<true>(dG, DN, L.DN[j][c]);
+      tp_zero(dGe);
+      mac_s(dGe, eta, dG);
+      scale2(dGe);
+      Dt[j][c].p1 = dGe;
+      tp_zero(Dt[j][c].p0);
+      mac<true>(Dt[j][c].p0, dB, L.N[c]);
+      TP<T, 0> dn2 = L.DN[j][c];
+      scale2(dn2);
+      mac<true>(Dt[j][c].p0, dn2, beta);
+      renorm(Dt[j][c].p0);
+    }
+  }
+  // Q, A, B and their scaled derivatives
+  WPr<T, 3> Qw;
+  WPr<T, 4> Aw, Bw, Qt[2];
+  WPr<T, 5> At[2], Bt[2];
+  wp_zero(Qw);
+  wp_zero(Aw);
+  wp_zero(Bw);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    wp_zero(Qt[j]);
+    wp_zero(At[j]);
+    wp_zero(Bt[j]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    mac(Qw.p0, g[c], dt[c].p0);
+    mac(Qw.p1, g[c], dt[c].p1);
+    wp_mac_p(Aw, dt[c], hu[c]);
+    wp_mac_p(Bw, dt[c], hv[c]);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const TP<T, 0> dhu[3] = {cross_comp<T>(e2[1], L.DX[j][2].c[0], e2[2], L.DX[j][1].c[0]),
+                             cross_comp<T>(e2[2], L.DX[j][0].c[0], e2[0], L.DX[j][2].c[0]),
+                             cross_comp<T>(e2[0], L.DX[j][1].c[0], e2[1], L.DX[j][0].c[0])};
+    const TP<T, 0> dhv[3] = {cross_comp<T>(L.DX[j][1].c[0], e1[2], L.DX[j][2].c[0], e1[1]),
+                             cross_comp<T>(L.DX[j][2].c[0], e1[0], L.DX[j][0].c[0], e1[2]),
+                             cross_comp<T>(L.DX[j][0].c[0], e1[1], L.DX[j][1].c[0], e1[0])};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      mac(Qt[j].p0, g[c], Dt[j][c].p0);
+      mac(Qt[j].p1, g[c], Dt[j][c].p1);
+      wp_mac_p(At[j], Dt[j][c], hu[c]);
+      wp_mac_p(Bt[j], Dt[j][c], hv[c]);
+      // 2W d~ . d(h) = (-2 beta n . dh) + W (2 G . dh)
+      TP<T, 1> n2;
+      tp_zero(n2);
+      mac_s(n2, T(-2), L.N[c]);
+      TP<T, 3> G2 = TG3[c];
+      scale2(G2);
+      TP<T, 1> nu, nv;
+      tp_zero(nu);
+      tp_zero(nv);
+      mac(nu, dhu[c], n2);
+      mac(nv, dhv[c], n2);
+      mac(At[j].p0, nu, beta);
+      mac(Bt[j].p0, nv, beta);
+      mac(At[j].p1, dhu[c], G2);
+      mac(Bt[j].p1, dhv[c], G2);
+    }
+    wp_renorm(Qt[j]);
+    wp_renorm(At[j]);
+    wp_renorm(Bt[j]);
+  }
+  wp_renorm(Qw);
+  wp_renorm(Aw);
+  wp_renorm(Bw);
+  // M' = Q (A1 B2 - A2 B1) - B (A1 Q2 - A2 Q1) - A (Q1 B2 - Q2 B1)
+  WPr<T, 13> Mp;
+  wp_zero(Mp);
+  {
+    WPr<T, 10> X;
+    wp_zero(X);
+    wp_mac(X, At[0], Bt[1], beta);
+    wp_mac<true>(X, At[1], Bt[0], beta);
+    wp_renorm(X);
+    wp_mac(Mp, Qw, X, beta);
+  }
+  {
+    WPr<T, 9> Y;
+    wp_zero(Y);
+    wp_mac(Y, At[0], Qt[1], beta);
+    wp_mac<true>(Y, At[1], Qt[0], beta);
+    wp_renorm(Y);
+    wp_mac<true>(Mp, Bw, Y, beta);
+  }
+  {
+    WPr<T, 9> Z;
+    wp_zero(Z);
+    wp_mac(Z, Qt[0], Bt[1], beta);
+    wp_mac<true>(Z, Qt[1], Bt[0], beta);
+    wp_renorm(Z);
+    wp_mac<true>(Mp, Aw, Z, beta);
+  }
+  wp_renorm(Mp);
+  WPr<T, 9> Q3;
+  {
+    WPr<T, 6> Q2;
+    wp_zero(Q2);
+    wp_mac(Q2, Qw, Qw, beta);
+    wp_renorm(Q2);
+    wp_zero(Q3);
+    wp_mac(Q3, Q2, Qw, beta);
+    wp_renorm(Q3);
+  }
+  // chord of s^(-3/2) on the range of s = d0.d0 (second remainder variable)
+  T sl = F::inf(), sh = T(0);
+  static_for<nc(2)>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const T cl = SS.c[i] * (T)(1.0 / mult_c(2, i));  // exact: C in {1, 2}
+    sl = fmin(sl, F::add_rd(cl, -SS.E));
+    sh = fmax(sh, F::add_ru(cl, SS.E));
+  });
+  if (!(sl > tiny_pos<T>())) {
+    fold = BNB_CELL_FOLD;
+    return;
+  }
+  T sa, sb, sdlo, sdhi;
+  chord_remainder<T>(sl, sh, sa, sb, sdlo, sdhi);
+  TP<T, 2> Fk[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const T ck = sb + (k == 0 ? sdlo : sdhi);
+    tp_zero(Fk[k]);
+    mac_s(Fk[k], sa, SS);
+    add_const(Fk[k], ck, F::mul_ru(uu, fabs(ck)));
+  }
+  TP<T, 4> beta4 = beta;
+  scale2(beta4);
+  scale2(beta4);
+  T mn = F::inf(), mx = -F::inf();
+  int sm0 = 0;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    TP<T, 4> Wj;
+    tp_zero(Wj);
+    mac_s(Wj, ca, beta);
+    const T cj = cb + (j == 0 ? dlo : dhi);
+    add_const(Wj, cj, F::mul_ru(uu, fabs(cj)));
+    TP<T, 15> Mj;
+    wp_face(Mj, Mp, Wj);
+    const int sm = cert_sign(Mj);
+    if (sm == 0 || (j == 1 && sm != sm0)) {
+      fold = BNB_CELL_FOLD;
+      return;
+    }
+    sm0 = sm;
+    if (sm < 0) negate(Mj);
+    TP<T, 17> Den;
+    {
+      TP<T, 16> m16;
+      elevate(m16, Mj);
+      elevate(Den, m16);
+    }
+    TP<T, 11> Q3j;
+    wp_face(Q3j, Q3, Wj);
+    if (sq < 0) negate(Q3j);
+    TP<T, 15> Nb;
+    tp_zero(Nb);
+    mac(Nb, Q3j, beta4);
+    renorm(Nb);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      TP<T, 17> Nm;
+      tp_zero(Nm);
+      mac(Nm, Nb, Fk[k]);
+      renorm(Nm);
+      bool open = false;
+      static_for<nc(17)>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        T nl, nh, dl, dh;
+        coef_iv<i>(Nm, nl, nh);
+        coef_iv<i>(Den, dl, dh);
+        open = open || !(dl > tiny_pos<T>());
+        ratio_acc(nl, nh, rcp_hi(dl), rcp_lo(dh), mn, mx);
+      });
+      if (open) {
+        fold = BNB_CELL_FOLD;
+        return;
+      }
+    }
+  }
+  eh = F::mul_ru(Khi, widen_hi(mx));
+  if (!(eh >= T(0))) eh = F::inf();
+  el = fmax(F::mul_rd(Klo, widen_lo(mn)), T(0));
+}
+
 static __device__ __noinline__ void process_cell_refract_fp64(const BoundParams& P, int e, int t, uint32_t id,
                                                               int depth, int64_t slot);
 
@@ -1126,7 +1435,7 @@ __device__ __forceinline__ void process_cell_refract(const BoundParams& P, int e
   }
 
   Leaves<T> L;
-  make_leaves<T, false>(p, n, x0, cu, cv, L);
+  make_leaves<T, true>(p, n, x0, cu, cv, L);
   // n.n, d0.n, d0.d0 (degree 2) and beta (degree 4)
   TP<T, 2> NN, DN, SS;
   tp_zero(NN);
@@ -1165,17 +1474,18 @@ __device__ __forceinline__ void process_cell_refract(const BoundParams& P, int e
   T ca, cb, dlo, dhi;
   sqrt_chord<T>(fmax(blo, T(0)), bhi, ca, cb, dlo, dhi);
   // tangential part eta' ((n.n) d0 - (d0.n) n) (degree 3, elevated to 5)
+  TP<T, 3> TG3[3];
   TP<T, 5> TG5[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    TP<T, 3> tg, tge;
+    TP<T, 3> tg;
     tp_zero(tg);
     mac(tg, NN, L.D0[c]);
     mac<true>(tg, DN, L.N[c]);
-    tp_zero(tge);
-    mac_s(tge, eta, tg);
+    tp_zero(TG3[c]);
+    mac_s(TG3[c], eta, tg);
     TP<T, 4> t4;
-    elevate(t4, tge);
+    elevate(t4, TG3[c]);
     elevate(TG5[c], t4);
   }
   // receiver-side linear terms with the origin p' = p_k0 + uc e_k1 + vc e_k2
@@ -1308,7 +1618,23 @@ __device__ __forceinline__ void process_cell_refract(const BoundParams& P, int e
     put_rec(P, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, e, t, id, flags | BNB_CELL_CULL_EMPTY);
     return;
   }
-  put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_LIVE);
+  // Irradiance: float32 only; a cell whose sign test fell back to float64 keeps E_hi = +inf.
+  T el = T(0), eh = F::inf();
+  uint32_t fold = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (P.irradiance) {
+      T Klo, Khi;
+      cell_K<T>(p, x0, e1, e2, __ldg(P.ei + e), depth, Klo, Khi);
+      refract_irradiance<T>(L, NN, DN, SS, beta, eta, TG3, hu, hv, g, e1, e2, sq, ca, cb, dlo, dhi, Klo, Khi, el,
+                            eh, fold);
+      if (fold) {
+        el = T(0);
+        eh = F::inf();
+      }
+    }
+  }
+  put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), f_dn(el), f_up(eh), e, t, id,
+          flags | BNB_CELL_LIVE | fold);
 }
 
 static __device__ __noinline__ void process_cell_refract_fp64(const BoundParams& P, int e, int t, uint32_t id,
@@ -1322,17 +1648,40 @@ static __device__ __noinline__ void process_cell_refract_fp64(const BoundParams&
 // fetches; the round count is uniform across the block, so every thread reaches every barrier.
 constexpr int kBoundThreads = 256;
 
+// The refraction cell program (with its irradiance part) is long: compiled once, as a function
+// that the base and the split kernels call.
+static __device__ __noinline__ void process_cell_refract_f32(const BoundParams& P, int e, int t, uint32_t id,
+                                                             int depth, int64_t slot) {
+  process_cell_refract<float>(P, e, t, id, depth, slot);
+}
+
 // KIND 0: reflection, 1: refraction (separate instantiations: each kernel holds one cell program).
 template <typename T, int KIND>
 __device__ __forceinline__ void process_any(const BoundParams& P, int e, int t, uint32_t id, int depth, int64_t slot) {
   if constexpr (KIND == 0)
     process_cell<T>(P, e, t, id, depth, slot);
+  else if constexpr (sizeof(T) == 4)
+    process_cell_refract_f32(P, e, t, id, depth, slot);
   else
     process_cell_refract<T>(P, e, t, id, depth, slot);
 }
 
+// Refraction: the same kernel also bounds the children of queued split cells (q_in != nullptr), so
+// its long cell program is reachable from one kernel entry only.
 template <typename T, int KIND>
-__global__ void __launch_bounds__(kBoundThreads, 1) bound_base_k(BoundParams P) {
+__global__ void __launch_bounds__(kBoundThreads, 1) bound_base_k(BoundParams P, const SplitItem* __restrict__ q_in,
+                                                                 const int64_t* __restrict__ q_in_count) {
+  if constexpr (KIND == 1) {
+    if (q_in != nullptr) {
+      const int64_t n = min(*q_in_count, P.q_cap);
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 4 * n;
+           i += (int64_t)gridDim.x * blockDim.x) {
+        const SplitItem it = q_in[i >> 2];
+        process_any<T, KIND>(P, it.emitter, it.tri, it.cell * 4u + (uint32_t)(i & 3), it.depth + 1, -1);
+      }
+      return;
+    }
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)P.count, (unsigned long long)P.n_base);
   const int64_t per_tuple = (int64_t)1 << (2 * P.depth);
   const int64_t per_em = per_tuple * P.n_tris;
@@ -1373,7 +1722,7 @@ int grid_for_T(int64_t n, int block) {
 
 template <typename T, int KIND>
 cudaError_t launch_bound_base_T(const BoundParams& p, cudaStream_t st) {
-  bound_base_k<T, KIND><<<grid_for_T<T>(p.n_base, kBoundThreads), kBoundThreads, 0, st>>>(p);
+  bound_base_k<T, KIND><<<grid_for_T<T>(p.n_base, kBoundThreads), kBoundThreads, 0, st>>>(p, nullptr, nullptr);
   return cudaGetLastError();
 }
 
@@ -1383,7 +1732,10 @@ cudaError_t launch_bound_split_T(const BoundParams& p, const SplitItem* q_in, co
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  bound_split_k<T, KIND><<<sms * 2, 128, 0, st>>>(p, q_in, q_in_count);
+  if constexpr (KIND == 1)
+    bound_base_k<T, KIND><<<sms, kBoundThreads, 0, st>>>(p, q_in, q_in_count);
+  else
+    bound_split_k<T, KIND><<<sms * 2, 128, 0, st>>>(p, q_in, q_in_count);
   return cudaGetLastError();
 }
 

@@ -105,17 +105,19 @@ def assert_bounds_parity(rep, allow_ambiguous_frac=1e-3, slack_median=2e-4, slac
     assert rep["e_checked"] > 0.9 * rep["live"], rep
 
 
-def compare_refraction(g, o):
+def compare_refraction(g, o, position_only=False):
     """Refraction records: the GPU's sqrt chord is built from its own (outward float32) range of
     beta, so its remainder envelope differs from the oracle's by rounding and neither box need
     contain the other.  Compared: keys and flags (outside the ambiguity band), and the box
     distance max(|lo_g - lo_o|, |hi_g - hi_o|); containment of the true paths is checked by a
-    dense sweep (sweep_violations_gpu)."""
+    dense sweep (sweep_violations_gpu).  position_only: the GPU pass bounded positions only (its
+    float64 mode), so the oracle's fold flag (an irradiance decision) is not compared."""
     gd = depth_of(g["flags"])
     od = depth_of(o["flags"])
     gkey = {(int(e), int(t), int(c), int(d)): i for i, (e, t, c, d) in
             enumerate(zip(g["emitter"], g["tri0"], g["cell"], gd))}
-    rep = dict(n=len(o), missing=0, flag_mismatch=0, flag_ambiguous=0, live=0, box_diff=[], e_finite=0)
+    rep = dict(n=len(o), missing=0, flag_mismatch=0, flag_ambiguous=0, live=0, box_diff=[], e_finite=0, e_rel=[],
+               e_below=0)
     for oi in range(len(o)):
         k = (int(o["emitter"][oi]), int(o["tri0"][oi]), int(o["cell"][oi]), int(od[oi]))
         gi = gkey.get(k)
@@ -124,6 +126,8 @@ def compare_refraction(g, o):
             continue
         gf = int(g["flags"][gi]) & FLAG_MASK
         of = int(o["flags"][oi]) & 0xFF
+        if position_only:
+            of &= ~16
         if gf != of:
             rep["flag_ambiguous" if o["q_cond"][oi] < Q_COND else "flag_mismatch"] += 1
             continue
@@ -133,8 +137,26 @@ def compare_refraction(g, o):
         for a in ("u", "v"):
             rep["box_diff"].append(max(abs(float(g[a + "_lo"][gi]) - float(o[a + "_lo"][oi])),
                                        abs(float(g[a + "_hi"][gi]) - float(o[a + "_hi"][oi]))))
-        if np.isfinite(g["e_hi"][gi]):
+        ge, oe = float(g["e_hi"][gi]), float(o["e_hi"][oi])
+        if np.isfinite(ge):
             rep["e_finite"] += 1
+            if np.isfinite(oe):
+                rep["e_rel"].append((ge - oe) / oe)
+                if ge < oe * (1 - REFR_E_BELOW):
+                    rep["e_below"] += 1
+            else:
+                rep["e_below"] += 1
     d = np.array(rep.pop("box_diff") or [0.0])
-    rep.update(box_diff_max=float(d.max()), box_diff_p99=float(np.percentile(d, 99)))
+    er = np.array(rep.pop("e_rel") or [0.0])
+    rep.update(box_diff_max=float(d.max()), box_diff_p99=float(np.percentile(d, 99)),
+               e_rel_median=float(np.median(er)), e_rel_p99=float(np.percentile(er, 99)),
+               e_rel_min=float(er.min()))
     return rep
+
+
+# Refraction irradiance (float32 kernel vs float64 oracle): the two chords differ by rounding, so the
+# GPU bound may sit below the oracle's by rounding only; its excess (the float32 error bound
+# through the cancellation of M') is bounded at the median and 99th percentile.
+REFR_E_BELOW = 1e-4
+REFR_E_MEDIAN = 5e-4
+REFR_E_P99 = 0.1
