@@ -304,28 +304,34 @@ __device__ __forceinline__ void reflect_dir(const Leaves<T>& L, Dir<T>& D) {
     add_const(DN2, k0f, k0e);
     scale2(DN2);
     (void)uu;
+    // the two edge directions j = 0, 1 run as pairs
+    TP<T, 1> DNN[2], DDN2[2];  // D(n.n) = 2 n.Dn ; 2 D(d0.n)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      TP<T, 1> DNN, DDN2;  // D(n.n) = 2 n.Dn ; 2 D(d0.n)
-      tp_zero(DNN);
-      tp_zero(DDN2);
+      tp_zero(DNN[j]);
+      tp_zero(DDN2[j]);
+    }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        mac(DNN, L.N[c], L.DN[j][c]);
-        mac(DDN2, L.N[c], L.DX[j][c]);
-        mac(DDN2, L.D0[c], L.DN[j][c]);
-      }
-      scale2(DNN);
-      scale2(DDN2);
+    for (int c = 0; c < 3; ++c) {
+      mac2(DNN[0], L.N[c], L.DN[0][c], DNN[1], L.N[c], L.DN[1][c]);
+      mac2(DDN2[0], L.N[c], L.DX[0][c], DDN2[1], L.N[c], L.DX[1][c]);
+      mac2(DDN2[0], L.D0[c], L.DN[0][c], DDN2[1], L.D0[c], L.DN[1][c]);
+    }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        tp_zero(D.DDT[j][c]);
-        mac(D.DDT[j][c], DNN, L.D0[c]);
-        mac(D.DDT[j][c], NN, L.DX[j][c]);
-        mac<true>(D.DDT[j][c], DDN2, L.N[c]);
-        mac<true>(D.DDT[j][c], DN2, L.DN[j][c]);
-        renorm(D.DDT[j][c]);
-      }
+    for (int j = 0; j < 2; ++j) {
+      scale2(DNN[j]);
+      scale2(DDN2[j]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      tp_zero(D.DDT[0][c]);
+      tp_zero(D.DDT[1][c]);
+      mac2(D.DDT[0][c], DNN[0], L.D0[c], D.DDT[1][c], DNN[1], L.D0[c]);
+      mac2(D.DDT[0][c], NN, L.DX[0][c], D.DDT[1][c], NN, L.DX[1][c]);
+      mac2<true>(D.DDT[0][c], DDN2[0], L.N[c], D.DDT[1][c], DDN2[1], L.N[c]);
+      mac2<true>(D.DDT[0][c], DN2, L.DN[0][c], D.DDT[1][c], DN2, L.DN[1][c]);
+      renorm(D.DDT[0][c]);
+      renorm(D.DDT[1][c]);
     }
   }
 }
@@ -456,6 +462,36 @@ template <bool LO, typename T, int... G>
 __device__ __forceinline__ void irr_all(const TP<T, 9>& Q3, const T (&F0)[6], const T (&F1)[6], const TP<T, 9>& M,
                                         IrrAcc<T>& acc, std::integer_sequence<int, G...>) {
   (irr_step<LO, T, G>(Q3, F0, F1, M, acc), ...);
+}
+
+
+// irradiance term G with the numerator and denominator sums paired: (n1, mm) += (F1[b], C(2;b)) (Q3, M)[G-b]
+template <int G, int... Bi>
+__device__ __forceinline__ float2 coef3_f2(const float2* __restrict__ QM, const float2 (&FC)[6],
+                                           std::integer_sequence<int, Bi...>) {
+  float2 acc = make_float2(0.0f, 0.0f);
+  ((Term2<9, G, Bi>::valid ? (acc = __ffma2_rn(FC[Bi], QM[Term2<9, G, Bi>::a], acc), 0) : 0), ...);
+  return acc;
+}
+
+template <int G>
+__device__ __forceinline__ void irr_step_f2(const float2* __restrict__ QM, const float2 (&FC)[6], IrrAcc<float>& acc) {
+  const float2 nm = coef3_f2<G>(QM, FC, std::make_integer_sequence<int, 6>{});
+  const float n1 = nm.x, mm = nm.y;
+  constexpr float C = MULTUP<float, 11, G>;
+  const float ml = FP<float>::fma_rd(-acc.EM, C, mm), mh = FP<float>::fma_ru(acc.EM, C, mm);
+  if (!(ml > tiny_pos<float>())) acc.unbounded = true;
+  const float n1h = FP<float>::fma_ru(acc.EN1, C, n1);
+  const bool pos = n1h >= 0.0f;
+  float r = FP<float>::rcp_fast(fminf(pos ? ml : mh, (float)FP<float>::rcp_big));
+  if (!pos && mh > (float)FP<float>::rcp_big) r = 0.0f;
+  acc.eh_mx = fmaxf(acc.eh_mx, n1h * r);
+}
+
+template <int... G>
+__device__ __forceinline__ void irr_all_f2(const float2* __restrict__ QM, const float2 (&FC)[6], IrrAcc<float>& acc,
+                                           std::integer_sequence<int, G...>) {
+  (irr_step_f2<G>(QM, FC, acc), ...);
 }
 
 // Chord of f(s) = s^(-3/2) on [sl, sh] with rigorous remainder bounds dlo <= f - (a s + b) <= dhi.
@@ -818,16 +854,13 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      mac(A, D.DT[c], hu[c]);
-      mac(B, D.DT[c], hv[c]);
+      mac2(A, D.DT[c], hu[c], B, D.DT[c], hv[c]);
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        mac(DA[j], D.DDT[j][c], hu[c]);
-        mac(DA[j], D.DT[c], Dhu[j][c]);
-        mac(DB[j], D.DDT[j][c], hv[c]);
-        mac(DB[j], D.DT[c], Dhv[j][c]);
-        mac(DQ[j], D.DDT[j][c], g[c]);
+        mac2(DA[j], D.DDT[j][c], hu[c], DB[j], D.DDT[j][c], hv[c]);
+        mac2(DA[j], D.DT[c], Dhu[j][c], DB[j], D.DT[c], Dhv[j][c]);
       }
+      mac2(DQ[0], D.DDT[0][c], g[c], DQ[1], D.DDT[1][c], g[c]);
     }
     renorm(A);
     renorm(B);
@@ -881,8 +914,10 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags);
     return;
   }
-  // Jacobian numerator M (degree 9).
-  TP<T, 9> M;
+  // Jacobian numerator M (degree 9) and Q^3 (Q > 0 after normalization):
+  //   X = DA1 DB2 - DA2 DB1,  Y = DA1 DQ2 - DA2 DQ1,  Z = DQ1 DB2 - DQ2 DB1,  M = Q X - B Y - A Z.
+  // B Y and A Z have the same shape: they run as one paired product, subtracted afterwards.
+  TP<T, 9> M, Q3;
   tp_zero(M);
   {
     TP<T, 6> X;
@@ -890,23 +925,32 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     mac(X, DA[0], DB[1]);
     mac<true>(X, DA[1], DB[0]);
     renorm(X);
-    mac(M, Q, X);
-  }
-  {
-    TP<T, 5> Y;
+    TP<T, 5> Y, Z;
     tp_zero(Y);
     mac(Y, DA[0], DQ[1]);
     mac<true>(Y, DA[1], DQ[0]);
     renorm(Y);
-    mac<true>(M, B, Y);
-  }
-  {
-    TP<T, 5> Z;
     tp_zero(Z);
     mac(Z, DQ[0], DB[1]);
     mac<true>(Z, DQ[1], DB[0]);
     renorm(Z);
-    mac<true>(M, A, Z);
+    TP<T, 9> QX, BY, AZ, T1;
+    tp_zero(QX);
+    mac(QX, Q, X);
+    tp_zero(BY);
+    tp_zero(AZ);
+    mac2(BY, B, Y, AZ, A, Z);
+    tp_sub(T1, QX, BY);
+    tp_sub(M, T1, AZ);
+  }
+  {
+    TP<T, 6> Q2;
+    tp_zero(Q2);
+    mac(Q2, Q, Q);
+    renorm(Q2);
+    tp_zero(Q3);
+    mac(Q3, Q2, Q);
+    renorm(Q3);
   }
   renorm(M);
   const int sm = cert_sign(M);
@@ -952,17 +996,6 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     FE0 = F::add_ru(F::add_ru(base, F::mul_ru(uu, fabs(c0))), F::mul_ru(GAM<T, 2>, F::add_ru(as, fabs(c0))));
     FE1 = F::add_ru(F::add_ru(base, F::mul_ru(uu, fabs(c1))), F::mul_ru(GAM<T, 2>, F::add_ru(as, fabs(c1))));
   }
-  // Q^3 (Q > 0 after normalization).
-  TP<T, 9> Q3;
-  {
-    TP<T, 6> Q2;
-    tp_zero(Q2);
-    mac(Q2, Q, Q);
-    renorm(Q2);
-    tp_zero(Q3);
-    mac(Q3, Q2, Q);
-    renorm(Q3);
-  }
   IrrAcc<T> acc;
   acc.eh_mx = -F::inf();
   acc.el_mn = F::inf();
@@ -982,10 +1015,21 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     acc.EM = rE;
   }
   const bool want_lo = P.e_lo != nullptr || P.e_hi_min != nullptr;  // uniform across the launch
-  if (want_lo)
+  if (want_lo) {
     irr_all<true, T>(Q3, F0, F1, M, acc, std::make_integer_sequence<int, nc(11)>{});
-  else
+  } else if constexpr (sizeof(T) == 4) {
+    float2 QM[nc(9)];
+#pragma unroll
+    for (int i = 0; i < nc(9); ++i) QM[i] = make_float2(Q3.c[i], M.c[i]);
+    float2 FC[6];
+    static_for<6>([&](auto I) {
+      constexpr int b = decltype(I)::value;
+      FC[b] = make_float2(F1[b], (float)mult_c(2, b));
+    });
+    irr_all_f2(QM, FC, acc, std::make_integer_sequence<int, nc(11)>{});
+  } else {
     irr_all<false, T>(Q3, F0, F1, M, acc, std::make_integer_sequence<int, nc(11)>{});
+  }
   if (acc.unbounded) {
     put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_FOLD);
     return;

@@ -180,6 +180,46 @@ __device__ __forceinline__ void mac(TP<T, M + N>& r, const TP<T, M>& p, const TP
   track_mac<kterms(M, N)>(r.B, r.E, p.B, p.E, q.B, q.E);
 }
 
+// Two independent products of the same shape, r1 (+/-)= p1 q1 and r2 (+/-)= p2 q2, one paired FMA
+// (__ffma2_rn) per term; each lane runs exactly the FMA chain of mac().
+template <typename T, int M, int N, bool NEG, int... I>
+__device__ __forceinline__ void conv_acc2(T* __restrict__ r1, T* __restrict__ r2, const T* __restrict__ p1,
+                                          const T* __restrict__ q1, const T* __restrict__ p2,
+                                          const T* __restrict__ q2, std::integer_sequence<int, I...>) {
+  if constexpr (sizeof(T) == 4) {
+    (([&] {
+       constexpr int a = Pair<M, N, I>::a, b = Pair<M, N, I>::b, g = Pair<M, N, I>::g;
+       const float2 pp = NEG ? make_float2(-p1[a], -p2[a]) : make_float2(p1[a], p2[a]);
+       const float2 acc = __ffma2_rn(pp, make_float2(q1[b], q2[b]), make_float2(r1[g], r2[g]));
+       r1[g] = acc.x;
+       r2[g] = acc.y;
+     }()),
+     ...);
+  } else {
+    conv_acc<T, M, N, NEG>(r1, p1, q1, std::integer_sequence<int, I...>{});
+    conv_acc<T, M, N, NEG>(r2, p2, q2, std::integer_sequence<int, I...>{});
+  }
+}
+
+template <bool NEG = false, typename T, int M, int N>
+__device__ __forceinline__ void mac2(TP<T, M + N>& r1, const TP<T, M>& p1, const TP<T, N>& q1, TP<T, M + N>& r2,
+                                     const TP<T, M>& p2, const TP<T, N>& q2) {
+  conv_acc2<T, M, N, NEG>(r1.c, r2.c, p1.c, q1.c, p2.c, q2.c, std::make_integer_sequence<int, nc(M) * nc(N)>{});
+  track_mac<kterms(M, N)>(r1.B, r1.E, p1.B, p1.E, q1.B, q1.E);
+  track_mac<kterms(M, N)>(r2.B, r2.E, p2.B, p2.E, q2.B, q2.E);
+}
+
+// r = a - b coefficientwise (one rounding each): |r - exact| <= a.E + b.E + u (|a| + |b|).
+template <typename T, int N>
+__device__ __forceinline__ void tp_sub(TP<T, N>& r, const TP<T, N>& a, const TP<T, N>& b) {
+  using F = FP<T>;
+#pragma unroll
+  for (int i = 0; i < nc(N); ++i) r.c[i] = a.c[i] - b.c[i];
+  r.B = F::add_ru(a.B, b.B);
+  r.E = F::add_ru(F::add_ru(a.E, b.E),
+                  F::mul_ru((T)FP<T>::u, F::add_ru(F::add_ru(a.B, a.E), F::add_ru(b.B, b.E))));
+}
+
 // r += s * p for an exact scalar s (a float input such as a receiver edge component).
 template <bool NEG = false, typename T, int N>
 __device__ __forceinline__ void mac_s(TP<T, N>& r, T s, const TP<T, N>& p) {
