@@ -111,7 +111,7 @@ class ClockSampler:
 # Per-point work of the workload: mean |U| (listed tuples) and |S| (selected, gamma calibrated to
 # E|S| = 4) per shading point, as measured by the GPU arm on this workload; used to extrapolate the
 # oracle's per-draw and per-solve costs to a full step.
-U_PER_POINT = 48.0
+U_PER_POINT = 144.0
 S_PER_POINT = 4.0
 
 
@@ -198,14 +198,10 @@ def run_gpu(args):
     from paper_2504_19163_gb300 import bnb, build
     from paper_2504_19163_gb300 import scenes as S
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2504_19163_gb300 import replicas as RP
+    rank, local, world = RP.rank_env()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist = RP.init("nccl", torch.device("cuda", local))
     build.build()
     dev = torch.device("cuda", local)
     sc = S.config("mirror256")
@@ -257,8 +253,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     st_ok = int(cb.status.item()) == 0 and int(idx.status.item()) == 0
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    if dist is not None:
-        dist.barrier()
+    RP.barrier(dist)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed steps
@@ -267,17 +262,13 @@ def run_gpu(args):
             r = step(i, evs[i])
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
+    RP.barrier(dist)
     stage = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs])
     ms_step = float(stage.sum(axis=1).mean())
     st_ok = st_ok and int(cb.status.item()) == 0 and int(idx.status.item()) == 0 and int(r.status.item()) == 0
     counters = r.counters.cpu().numpy()
-    t_total = torch.tensor([ms_step], device=dev)
-    if dist is not None:
-        dist.all_reduce(t_total, op=dist.ReduceOp.MAX)
-    ms_max = float(t_total.item())
-    value = n_cells * world / (ms_max / 1e3)
+    ms_max = RP.max_over_ranks(ms_step, dist, dev)
+    value = RP.whole_job_rate(n_cells, world, ms_max)
 
     # ---- end to end through the public API with host buffers (pinned), copies inside the region
     host = {k: v.cpu().pin_memory() for k, v in ds.t.items()}
@@ -299,10 +290,7 @@ def run_gpu(args):
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
     e2e_ms /= e2e_steps
-    e2e_t = torch.tensor([e2e_ms], device=dev)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = n_cells * world / (float(e2e_t.item()) / 1e3)
+    e2e_value = RP.whole_job_rate(n_cells, world, RP.max_over_ranks(e2e_ms, dist, dev))
 
     # ---- roofline of the dominant kernel (bound pass)
     bound_ms = float(stage[:, 0].mean())
@@ -353,8 +341,7 @@ def run_gpu(args):
         line["cpu_baseline"] = cpu_baseline(counters[0] / n_points, counters[1] / n_points)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    RP.finish(dist)
     return 0
 
 
