@@ -1687,10 +1687,16 @@ static __device__ __noinline__ void process_cell_refract_fp64(const BoundParams&
 }
 
 // ------------------------------------------------------------------ kernels
-// One 256-thread block per SM, persistent.  Every round starts with a block barrier so the
-// eight warps walk the (long, straight-line) cell program together and share instruction
+// One 384-thread block per SM, persistent.  Every round starts with a block barrier so the
+// twelve warps walk the (long, straight-line) cell program together and share instruction
 // fetches; the round count is uniform across the block, so every thread reaches every barrier.
-constexpr int kBoundThreads = 256;
+// 384 threads cap the registers at 168 (some spilling to L1): on the 256^2 mirror this beat 256
+// threads at 255 registers by 6.5%, while 192 and 512 threads were slower.
+constexpr int kBoundThreads = 384;
+// The refraction cell program (irradiance in degree-17 forms) needs the full register file: 256
+// threads (255 registers) ran the 420^2 water workload in 560 ms against 694 ms with 384 threads.
+template <int KIND>
+constexpr int kThreadsOf = KIND == 1 ? 256 : kBoundThreads;
 
 // The refraction cell program (with its irradiance part) is long: compiled once, as a function
 // that the base and the split kernels call.
@@ -1713,8 +1719,8 @@ __device__ __forceinline__ void process_any(const BoundParams& P, int e, int t, 
 // Refraction: the same kernel also bounds the children of queued split cells (q_in != nullptr), so
 // its long cell program is reachable from one kernel entry only.
 template <typename T, int KIND>
-__global__ void __launch_bounds__(kBoundThreads, 1) bound_base_k(BoundParams P, const SplitItem* __restrict__ q_in,
-                                                                 const int64_t* __restrict__ q_in_count) {
+__global__ void __launch_bounds__(kThreadsOf<KIND>, 1) bound_base_k(BoundParams P, const SplitItem* __restrict__ q_in,
+                                                                    const int64_t* __restrict__ q_in_count) {
   if constexpr (KIND == 1) {
     if (q_in != nullptr) {
       const int64_t n = min(*q_in_count, P.q_cap);
@@ -1729,11 +1735,11 @@ __global__ void __launch_bounds__(kBoundThreads, 1) bound_base_k(BoundParams P, 
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)P.count, (unsigned long long)P.n_base);
   const int64_t per_tuple = (int64_t)1 << (2 * P.depth);
   const int64_t per_em = per_tuple * P.n_tris;
-  const int64_t stride = (int64_t)gridDim.x * kBoundThreads;
+  const int64_t stride = (int64_t)gridDim.x * kThreadsOf<KIND>;
   const int64_t rounds = (P.n_base + stride - 1) / stride;
   for (int64_t r = 0; r < rounds; ++r) {
     __syncthreads();
-    const int64_t w = r * stride + (int64_t)blockIdx.x * kBoundThreads + threadIdx.x;
+    const int64_t w = r * stride + (int64_t)blockIdx.x * kThreadsOf<KIND> + threadIdx.x;
     if (w < P.n_base) {
       const int e = (int)(w / per_em);
       const int64_t rr = w - (int64_t)e * per_em;
@@ -1760,13 +1766,13 @@ int grid_for_T(int64_t n, int block) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = (n + block - 1) / block;
-  const int64_t cap = (int64_t)sms;  // one resident block per SM (255 registers x 256 threads)
+  const int64_t cap = (int64_t)sms;  // one resident block per SM
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
 }
 
 template <typename T, int KIND>
 cudaError_t launch_bound_base_T(const BoundParams& p, cudaStream_t st) {
-  bound_base_k<T, KIND><<<grid_for_T<T>(p.n_base, kBoundThreads), kBoundThreads, 0, st>>>(p, nullptr, nullptr);
+  bound_base_k<T, KIND><<<grid_for_T<T>(p.n_base, kThreadsOf<KIND>), kThreadsOf<KIND>, 0, st>>>(p, nullptr, nullptr);
   return cudaGetLastError();
 }
 
@@ -1777,7 +1783,7 @@ cudaError_t launch_bound_split_T(const BoundParams& p, const SplitItem* q_in, co
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if constexpr (KIND == 1)
-    bound_base_k<T, KIND><<<sms, kBoundThreads, 0, st>>>(p, q_in, q_in_count);
+    bound_base_k<T, KIND><<<sms, kThreadsOf<KIND>, 0, st>>>(p, q_in, q_in_count);
   else
     bound_split_k<T, KIND><<<sms * 2, 128, 0, st>>>(p, q_in, q_in_count);
   return cudaGetLastError();
