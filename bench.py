@@ -303,13 +303,7 @@ def run_gpu(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
     achieved = BOUND_FLOP_PER_CELL * n_cells / (bound_ms / 1e3) / 1e12
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "bound_traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            traffic = json.load(open(tr_path)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = bound_traffic()
 
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -350,6 +344,29 @@ def scan_launches(n: int) -> int:
     if tiles <= 1:
         return 2
     return 1 + scan_launches(tiles) + 2
+
+
+BOUND_SOURCES = ("paper_2504_19163_gb300/csrc/bnb_bound_impl.cuh", "paper_2504_19163_gb300/csrc/bnb_poly.cuh")
+
+
+def bound_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in BOUND_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
+
+
+def bound_traffic():
+    """DRAM bytes per launch of the bound kernel from the committed ncu capture, or None when the
+    kernel sources changed since the counters were taken."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "bound_traffic.json")))
+    except Exception:
+        return None
+    if d.get("sources_sha256") != bound_sources_sha():
+        return None
+    return d.get("bytes_per_launch")
 
 
 def launches_per_step(n_points: int, G: int) -> int:

@@ -914,9 +914,9 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags);
     return;
   }
-  // Jacobian numerator M (degree 9) and Q^3 (Q > 0 after normalization):
+  // Jacobian numerator M (degree 9):
   //   X = DA1 DB2 - DA2 DB1,  Y = DA1 DQ2 - DA2 DQ1,  Z = DQ1 DB2 - DQ2 DB1,  M = Q X - B Y - A Z.
-  // B Y and A Z have the same shape: they run as one paired product, subtracted afterwards.
+  // (Q^3 is formed later, next to its use, which keeps fewer forms live at once.)
   TP<T, 9> M, Q3;
   tp_zero(M);
   {
@@ -934,23 +934,9 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     mac(Z, DQ[0], DB[1]);
     mac<true>(Z, DQ[1], DB[0]);
     renorm(Z);
-    TP<T, 9> QX, BY, AZ, T1;
-    tp_zero(QX);
-    mac(QX, Q, X);
-    tp_zero(BY);
-    tp_zero(AZ);
-    mac2(BY, B, Y, AZ, A, Z);
-    tp_sub(T1, QX, BY);
-    tp_sub(M, T1, AZ);
-  }
-  {
-    TP<T, 6> Q2;
-    tp_zero(Q2);
-    mac(Q2, Q, Q);
-    renorm(Q2);
-    tp_zero(Q3);
-    mac(Q3, Q2, Q);
-    renorm(Q3);
+    mac(M, Q, X);
+    mac<true>(M, B, Y);
+    mac<true>(M, A, Z);
   }
   renorm(M);
   const int sm = cert_sign(M);
@@ -995,6 +981,15 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     const T base = F::mul_ru(fabs(ca), S.E);
     FE0 = F::add_ru(F::add_ru(base, F::mul_ru(uu, fabs(c0))), F::mul_ru(GAM<T, 2>, F::add_ru(as, fabs(c0))));
     FE1 = F::add_ru(F::add_ru(base, F::mul_ru(uu, fabs(c1))), F::mul_ru(GAM<T, 2>, F::add_ru(as, fabs(c1))));
+  }
+  {
+    TP<T, 6> Q2;
+    tp_zero(Q2);
+    mac(Q2, Q, Q);
+    renorm(Q2);
+    tp_zero(Q3);
+    mac(Q3, Q2, Q);
+    renorm(Q3);
   }
   IrrAcc<T> acc;
   acc.eh_mx = -F::inf();

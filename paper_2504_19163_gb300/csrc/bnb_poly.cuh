@@ -209,17 +209,6 @@ __device__ __forceinline__ void mac2(TP<T, M + N>& r1, const TP<T, M>& p1, const
   track_mac<kterms(M, N)>(r2.B, r2.E, p2.B, p2.E, q2.B, q2.E);
 }
 
-// r = a - b coefficientwise (one rounding each): |r - exact| <= a.E + b.E + u (|a| + |b|).
-template <typename T, int N>
-__device__ __forceinline__ void tp_sub(TP<T, N>& r, const TP<T, N>& a, const TP<T, N>& b) {
-  using F = FP<T>;
-#pragma unroll
-  for (int i = 0; i < nc(N); ++i) r.c[i] = a.c[i] - b.c[i];
-  r.B = F::add_ru(a.B, b.B);
-  r.E = F::add_ru(F::add_ru(a.E, b.E),
-                  F::mul_ru((T)FP<T>::u, F::add_ru(F::add_ru(a.B, a.E), F::add_ru(b.B, b.E))));
-}
-
 // r += s * p for an exact scalar s (a float input such as a receiver edge component).
 template <bool NEG = false, typename T, int N>
 __device__ __forceinline__ void mac_s(TP<T, N>& r, T s, const TP<T, N>& p) {
