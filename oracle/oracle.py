@@ -284,7 +284,7 @@ def sample(offsets, key, etilde, grid_res: int, su, sv, gamma: float, seed: int)
         return wp[:k], wk[:k], wP[:k], int(n_u[0])
 
 
-def solve(scene, wl_point, wl_key, wl_p, newton_iters: int = 16, polish_iters: int = 2, tol: float = 1e-5,
+def solve(scene, wl_point, wl_key, wl_p, newton_iters: int = 16, polish_iters: int = 1, tol: float = 1e-5,
           n_threads: int = 1):
     """Per worklist entry: contribution E/P (float64), root (u, v) and status (1 = root)."""
     L = lib()
@@ -328,7 +328,7 @@ def tuple_key(emitter, tri0, tri1=-1):
 
 
 def render(scene, gamma: float, seed: int, depth: Optional[int] = None, max_extra_split: int = 4,
-           newton_iters: int = 16, polish_iters: int = 2, tol: float = 1e-5, n_threads: int = 1):
+           newton_iters: int = 16, polish_iters: int = 1, tol: float = 1e-5, n_threads: int = 1):
     """Whole path on the CPU: bound -> index -> Algorithm 1 -> Newton -> per-point estimate."""
     rec = bound(scene, depth=depth, max_extra_split=max_extra_split, n_threads=n_threads)
     f = records_to_f32(rec)

@@ -143,7 +143,7 @@ class BatchRunner:
     the pinned table."""
 
     def __init__(self, max_jobs: int, max_points: int, worklist_capacity: int, newton_iters: int = 16,
-                 polish_iters: int = 2, tol: float = 1e-5, block_threads: int = 0, blocks_per_sm: int = 0,
+                 polish_iters: int = 1, tol: float = 1e-5, block_threads: int = 0, blocks_per_sm: int = 0,
                  device="cuda", use_graph: bool = True, stream: Optional[torch.cuda.Stream] = None):
         self.device = torch.device(device)
         self.cfg = bnb.bnb_batch_cfg(int(max_jobs), int(newton_iters), int(max_points), int(worklist_capacity),

@@ -387,7 +387,7 @@ class SampleResult:
 
 
 def sample_and_solve(ds: DeviceScene, index: Index, gamma: float, seed: int, newton_iters: int = 16,
-                     polish_iters: int = 2, tol: float = 1e-5, worklist_capacity: Optional[int] = None,
+                     polish_iters: int = 1, tol: float = 1e-5, worklist_capacity: Optional[int] = None,
                      su: Optional[torch.Tensor] = None, sv: Optional[torch.Tensor] = None,
                      E_out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None,
                      sync_check: bool = True, with_sel_count: bool = False) -> SampleResult:
