@@ -269,11 +269,47 @@ int32_t bnb_sample_and_solve_batched(const bnb_job *jobs, const int32_t *n_jobs,
                                      bnb_sample_stats *stats, void *ws, size_t ws_bytes, void *stream);
 size_t bnb_sample_and_solve_batched_ws(const bnb_batch_cfg *cfg);
 
+/* ---- Batched bound pass ------------------------------------------------------
+ * The precomputation of many scenes in one persistent launch (no counterpart in
+ * the paper).  A job is one scene: its packed triangles (bnb_pack_surface), its
+ * emitters and receiver, the subdivision depth and its own record outputs.  The
+ * job table and the job count are DEVICE memory; the launch is sized by the
+ * device's SM count only, so it can be captured in a CUDA graph.  Each cell is
+ * bounded by the same cell program as bnb_bound_tuples; jobs take no extra
+ * split levels: a cell whose denominator has mixed sign is bounded at once by
+ * the reciprocal rule (reflection) or the universal box (refraction), a valid
+ * but looser bound than splitting.  Base records land at the job's work index
+ * (as in bnb_bound_tuples); the job's *count receives its number of base
+ * cells.  The caller zeroes every job's count and status before the call. */
+typedef struct bnb_bound_job {
+  const void *packed_tris;            /* bnb_pack_surface output of the scene's specular surface */
+  const float *ex, *ey, *ez, *ei;     /* the scene's emitters */
+  int32_t n_tris, n_emitters;
+  int32_t kind, depth;                /* BNB_REFLECT / BNB_REFRACT; base depth 0..10 */
+  float eta;                          /* refraction: eta' */
+  int32_t irradiance;                 /* as bnb_bound_cfg */
+  float rp0[3], re1[3], re2[3];       /* the scene's receiver */
+  int32_t reserved;                   /* 0 */
+  int64_t capacity;                   /* records the outputs hold: >= n_emitters * n_tris * 4^depth */
+  int64_t *count;                     /* device int64 */
+  int32_t *status;                    /* device int32 */
+  float *u_lo, *u_hi, *v_lo, *v_hi, *e_hi;
+  float *e_lo;                        /* optional (NULL: not written) */
+  int32_t *emitter, *tri0, *tri1;
+  uint32_t *cell, *flags;
+} bnb_bound_job;
+
+/* Bounds every base cell of jobs[0 .. *n_jobs) (n_jobs: device int32, at most
+ * max_jobs, 1..65536).  ws: bnb_bound_tuples_batched_ws(max_jobs) bytes. */
+int32_t bnb_bound_tuples_batched(const bnb_bound_job *jobs, const int32_t *n_jobs, int32_t max_jobs, void *ws,
+                                 size_t ws_bytes, void *stream);
+size_t bnb_bound_tuples_batched_ws(int32_t max_jobs);
+
 /* Human-readable name of a status code (static string). */
 const char *bnb_status_string(int32_t status);
 
 /* ABI version of this header (increments on any struct or signature change). */
-int32_t bnb_abi_version(void);  /* 4 */
+int32_t bnb_abi_version(void);  /* 5 */
 
 #ifdef __cplusplus
 }

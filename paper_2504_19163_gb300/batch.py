@@ -223,6 +223,62 @@ class BatchRunner:
         return status, st[:3]
 
 
+# ----------------------------------------------------------------------------- batched bound pass
+BOUND_JOB_BYTES = C.sizeof(bnb.bnb_bound_job)
+
+
+def bound_batched(items: Sequence[Tuple[bnb.DeviceScene, int, bnb.CellBounds]], irradiance: bool = True,
+                  stream=None) -> List[bnb.CellBounds]:
+    """Bound the base cells of several scenes in one persistent launch (bnb_bound_tuples_batched).
+    items: (scene on the device, depth, output records); the outputs' count and status are zeroed
+    here and their host fields (n_base, depth, ...) set for the index pass.  Returns the outputs."""
+    if not items:
+        return []
+    dev = items[0][0].device
+    n = len(items)
+    host = torch.zeros(n * BOUND_JOB_BYTES, dtype=torch.uint8).pin_memory()
+    table = (bnb.bnb_bound_job * n).from_address(host.data_ptr())
+    keep = []
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.stream(s):
+        for i, (ds, depth, out) in enumerate(items):
+            nbytes = int(bnb.bnb_pack_surface_bytes(C.byref(ds.s1)))
+            packed = torch.empty(max(16, nbytes) // 4, dtype=torch.float32, device=dev)
+            _check(bnb.bnb_pack_surface(C.byref(ds.s1), _ptr(packed), C.c_size_t(nbytes), _stream(s)),
+                   "bnb_pack_surface")
+            keep.append(packed)
+            out.reset()
+            T = ds.t
+            j = table[i]
+            j.packed_tris = packed.data_ptr()
+            j.ex, j.ey, j.ez, j.ei = T["ex"].data_ptr(), T["ey"].data_ptr(), T["ez"].data_ptr(), T["ei"].data_ptr()
+            j.n_tris, j.n_emitters = ds.s1.n_tris, ds.em.n
+            j.kind, j.depth, j.eta, j.irradiance = ds.s1.kind, int(depth), ds.s1.eta, int(irradiance)
+            r = ds.rec
+            for c in range(3):
+                j.rp0[c], j.re1[c], j.re2[c] = r.p0[c], r.e1[c], r.e2[c]
+            j.reserved = 0
+            oc = out.c
+            j.capacity = oc.capacity
+            for f in ("count", "status", "u_lo", "u_hi", "v_lo", "v_hi", "e_hi", "e_lo", "emitter", "tri0", "tri1",
+                      "cell", "flags"):
+                setattr(j, f, getattr(oc, f))
+            oc.n_base = ds.em.n * ds.s1.n_tris * 4 ** int(depth)
+            oc.depth = int(depth)
+            oc.n_emitters = ds.em.n
+            oc.n_tris = ds.s1.n_tris
+        dev_table = host.to(dev, non_blocking=True)
+        n_jobs = torch.tensor([n], dtype=torch.int32).pin_memory().to(dev, non_blocking=True)
+        ws_bytes = int(bnb.bnb_bound_tuples_batched_ws(n))
+        ws = bnb._ws(ws_bytes, dev)
+        rc = bnb.bnb_bound_tuples_batched(C.c_void_p(dev_table.data_ptr()), C.c_void_p(n_jobs.data_ptr()), n,
+                                          _align(ws), C.c_size_t(ws_bytes), C.c_void_p(s.cuda_stream))
+        _check(rc, "bnb_bound_tuples_batched")
+    s.synchronize()  # the table, packed triangles and workspace are released on return
+    del keep
+    return [it[2] for it in items]
+
+
 # ----------------------------------------------------------------------------- autotuner
 CANDIDATES = [(t, b) for t in (128, 256, 512) for b in (2, 4, 8, 16) if t * b <= 4096]
 _cache_lock = threading.Lock()

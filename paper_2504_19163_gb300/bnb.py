@@ -78,6 +78,14 @@ class bnb_job(C.Structure):
                 ("E_out", vp)]
 
 
+class bnb_bound_job(C.Structure):
+    _fields_ = [("packed_tris", vp), ("ex", vp), ("ey", vp), ("ez", vp), ("ei", vp), ("n_tris", i32),
+                ("n_emitters", i32), ("kind", i32), ("depth", i32), ("eta", f32), ("irradiance", i32),
+                ("rp0", f32 * 3), ("re1", f32 * 3), ("re2", f32 * 3), ("reserved", i32), ("capacity", i64),
+                ("count", vp), ("status", vp), ("u_lo", vp), ("u_hi", vp), ("v_lo", vp), ("v_hi", vp), ("e_hi", vp),
+                ("e_lo", vp), ("emitter", vp), ("tri0", vp), ("tri1", vp), ("cell", vp), ("flags", vp)]
+
+
 class bnb_batch_cfg(C.Structure):
     _fields_ = [("max_jobs", i32), ("newton_iters", i32), ("max_points", i64), ("worklist_capacity", i64),
                 ("polish_iters", i32), ("tol", f32), ("block_threads", i32), ("blocks_per_sm", i32)]
@@ -87,7 +95,7 @@ _lib = None
 EXPORTS = ["bnb_bound_tuples", "bnb_bound_tuples_ws", "bnb_bound_tuples_noalloc", "bnb_build_index",
            "bnb_build_index_ws", "bnb_sample_and_solve", "bnb_sample_and_solve_ws", "bnb_status_string",
            "bnb_abi_version", "bnb_pack_surface", "bnb_pack_surface_bytes", "bnb_sample_and_solve_batched",
-           "bnb_sample_and_solve_batched_ws"]
+           "bnb_sample_and_solve_batched_ws", "bnb_bound_tuples_batched", "bnb_bound_tuples_batched_ws"]
 
 
 def lib():
@@ -125,6 +133,10 @@ def lib():
         L.bnb_pack_surface.argtypes = [P(bnb_surface), vp, sz, vp]
         L.bnb_sample_and_solve_batched.restype = i32
         L.bnb_sample_and_solve_batched.argtypes = [vp, vp, P(bnb_batch_cfg), P(bnb_sample_stats), vp, sz, vp]
+        L.bnb_bound_tuples_batched.restype = i32
+        L.bnb_bound_tuples_batched.argtypes = [vp, vp, i32, vp, sz, vp]
+        L.bnb_bound_tuples_batched_ws.restype = sz
+        L.bnb_bound_tuples_batched_ws.argtypes = [i32]
         L.bnb_sample_and_solve_batched_ws.restype = sz
         L.bnb_sample_and_solve_batched_ws.argtypes = [P(bnb_batch_cfg)]
         _lib = L
@@ -174,6 +186,14 @@ def bnb_sample_and_solve_batched(*a):
 
 def bnb_sample_and_solve_batched_ws(*a):
     return lib().bnb_sample_and_solve_batched_ws(*a)
+
+
+def bnb_bound_tuples_batched(*a):
+    return lib().bnb_bound_tuples_batched(*a)
+
+
+def bnb_bound_tuples_batched_ws(*a):
+    return lib().bnb_bound_tuples_batched_ws(*a)
 
 
 def bnb_status_string(s: int) -> str:

@@ -17,6 +17,9 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_receiver* r
                                     const bnb_sample_cfg* cfg, float* E_out, bnb_sample_stats* stats, void* ws,
                                     cudaStream_t st);
 size_t batch_ws_bytes(const bnb_batch_cfg* c);
+size_t bound_batch_ws_bytes(int32_t max_jobs);
+cudaError_t launch_bound_batched(const bnb_bound_job* jobs, const int32_t* n_jobs, int32_t max_jobs, void* ws,
+                                 cudaStream_t st);
 cudaError_t launch_sample_and_solve_batched(const bnb_job* jobs, const int32_t* n_jobs, const bnb_batch_cfg* c,
                                             bnb_sample_stats* stats, void* ws, cudaStream_t st);
 }  // namespace bnb
@@ -77,7 +80,7 @@ BoundWs carve_bound_ws(void* base, int64_t n_tris, int64_t qcap) {
 
 extern "C" {
 
-int32_t bnb_abi_version(void) { return 4; }
+int32_t bnb_abi_version(void) { return 5; }
 
 const char* bnb_status_string(int32_t s) {
   switch (s) {
@@ -264,6 +267,20 @@ int32_t bnb_sample_and_solve_batched(const bnb_job* jobs, const int32_t* n_jobs,
   return launch_sample_and_solve_batched(jobs, n_jobs, cfg, stats, ws, (cudaStream_t)stream) == cudaSuccess
              ? BNB_OK
              : BNB_ERR_CUDA;
+}
+
+size_t bnb_bound_tuples_batched_ws(int32_t max_jobs) {
+  if (max_jobs < 1 || max_jobs > 65536) return 0;
+  return bound_batch_ws_bytes(max_jobs);
+}
+
+int32_t bnb_bound_tuples_batched(const bnb_bound_job* jobs, const int32_t* n_jobs, int32_t max_jobs, void* ws,
+                                 size_t ws_bytes, void* stream) {
+  if (!jobs || !n_jobs || max_jobs < 1 || max_jobs > 65536) return BNB_ERR_INVALID;
+  if (((uintptr_t)jobs & 7u) != 0) return BNB_ERR_INVALID;
+  if (ws_bytes < bound_batch_ws_bytes(max_jobs) || !ws || !aligned256(ws)) return BNB_ERR_INVALID;
+  return launch_bound_batched(jobs, n_jobs, max_jobs, ws, (cudaStream_t)stream) == cudaSuccess ? BNB_OK
+                                                                                               : BNB_ERR_CUDA;
 }
 
 }  // extern "C"

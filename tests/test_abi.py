@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(bnb):
 def test_status_strings_and_version(bnb):
     assert bnb.bnb_status_string(0) == "ok"
     assert "capacity" in bnb.bnb_status_string(-2)
-    assert bnb.lib().bnb_abi_version() == 4
+    assert bnb.lib().bnb_abi_version() == 5
 
 
 def test_workspace_queries_are_host_only(bnb):
@@ -98,7 +98,7 @@ def test_ctypes_structs_match_the_header(bnb, tmp_path):
     """Field offsets and sizes of the Python mirrors equal the C compiler's for every struct."""
     structs = {n: getattr(bnb, n) for n in ("bnb_surface", "bnb_receiver", "bnb_emitters", "bnb_bound_cfg",
                                               "bnb_cell_bounds", "bnb_index", "bnb_sample_cfg", "bnb_sample_stats",
-                                              "bnb_job", "bnb_batch_cfg")}
+                                              "bnb_job", "bnb_batch_cfg", "bnb_bound_job")}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "bnb.h")}"',
              "int main(void) {"]
     for n, cls in structs.items():

@@ -232,3 +232,68 @@ def test_serving_results_same_alone_and_in_the_mix(B):
         assert s["completed"] == len(reqs)
     finally:
         cache.close()
+
+
+def bound_cases():
+    return [S.config("mirror32"),
+            S.config("tiny", n=5, depth=1, lights=[(0.1, -0.05, 2.0), (-0.4, 0.3, 1.7), (0.5, 0.5, 2.5)]),
+            S.config("water", n=6, depth=2, steep=0.08, lights=[(0.3, 0.2, 1.2)])]
+
+
+def test_batched_bound_equals_single_scene(B, BA):
+    """Three scenes (two mirrors, one refracting water surface) in one batched bound launch: every
+    job's base records are bit-identical to the single-scene pass with no extra split levels."""
+    items, singles = [], []
+    for sc in bound_cases():
+        ds = B.DeviceScene(sc)
+        nb = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
+        items.append((ds, sc.depth, B.CellBounds(nb, ds.device)))
+        singles.append(B.bound_tuples(ds, sc.depth, max_extra_split=0))
+    BA.bound_batched(items)
+    torch.cuda.synchronize()
+    for (ds, depth, out), single in zip(items, singles):
+        nb = out.c.n_base
+        assert int(out.status.item()) == 0 and int(out.count.item()) == nb == int(single.count.item())
+        a, b = out.to_numpy(), single.to_numpy()
+        for k in ("u_lo", "u_hi", "v_lo", "v_hi", "e_hi", "e_lo"):
+            assert np.array_equal(a[k].view(np.uint32), b[k].view(np.uint32)), k
+        for k in ("emitter", "tri0", "tri1", "cell", "flags"):
+            assert np.array_equal(a[k], b[k]), k
+    assert any(np.any(o.to_numpy()["flags"] & 1) for _, _, o in items)
+
+
+def test_batched_bound_capacity_is_per_job(B, BA):
+    sc1, sc2 = bound_cases()[:2]
+    ds1, ds2 = B.DeviceScene(sc1), B.DeviceScene(sc2)
+    n1 = sc1.emitters.n * sc1.s1.n_tris * 4 ** sc1.depth
+    n2 = sc2.emitters.n * sc2.s1.n_tris * 4 ** sc2.depth
+    small = B.CellBounds(n1 - 1, ds1.device)
+    ok = B.CellBounds(n2, ds2.device)
+    BA.bound_batched([(ds1, sc1.depth, small), (ds2, sc2.depth, ok)])
+    torch.cuda.synchronize()
+    assert int(small.status.item()) == B.BNB_ERR_CAPACITY and int(small.count.item()) == 0
+    assert int(ok.status.item()) == 0 and int(ok.count.item()) == n2
+
+
+def test_serving_prefetch_builds_scenes_in_one_batch(B):
+    """The cache builds two catalogue scenes with one batched bound launch; requests on both are
+    then served bit-identically in the mix and alone."""
+    from paper_2504_19163_gb300 import serving as SV
+    cache = SV.SceneCache(S.serving_scene, budget_bytes=8 << 30)
+    try:
+        es = cache.prefetch(["serve32", "serve256"])
+        for e in es:
+            assert e.ready.wait(600) and e.error is None and e.resident is not None
+        reqs = SV.make_requests(12, seed=4, scene_names=("serve32", "serve256"), sides=(64,))
+        SV.poisson_arrivals(reqs, rate=5000.0, seed=4)
+        srv = SV.Server(cache, max_jobs=8, max_points=1 << 16)
+        srv.warm_up()
+        srv.serve(reqs, timeout_s=120.0)
+        assert all(r.E is not None and r.status == 0 for r in reqs)
+        mixed = {r.rid: r.E.copy() for r in reqs}
+        SV.reset(reqs)
+        SV.plain_cached(reqs, cache, honour_arrivals=False)
+        for r in reqs:
+            assert same_bits(r.E, mixed[r.rid]), r.rid
+    finally:
+        cache.close()
