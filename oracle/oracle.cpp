@@ -24,6 +24,10 @@
 //   * Sec. 5.3, Algorithm 1, and Sec. 5.4: independent selection of each tuple
 //     with P = min(gamma * E~, 1), estimate sum E(T)/P over selected tuples.
 //   * Sec. 6.1 "Root-finding": Newton's method with deterministic initialization.
+//   * Two specular vertices (refraction at both, the TT chains of Table "tab:perf"):
+//     Sec. 6.1 "Tuple construction" (candidate T2 of a cell from the bound of x1 and
+//     of the direction ratios) and "Degree reduction" (u2 reduced to degree 1 plus a
+//     remainder, then the second vertex), and a direct-geometry chain evaluator.
 //
 // Readings where the paper is silent (cell split order, chord closed form,
 // forward culling, grid inclusion, RNG, Newton details) are listed in the
@@ -1024,6 +1028,470 @@ bool eval_direct_refract(const Tri& T, V3 x0, double I0, const Rec& R, double et
   return std::isfinite(Uk.v) && std::isfinite(Vk.v);
 }
 
+// ---------------------------------------------------------------------------
+// Two specular vertices: chains x0 -> T1 -> T2 -> receiver with refraction at both
+// vertices (the TT chains of Table "tab:perf", e.g. the glass slab).
+//
+//   * Tuple construction (Sec. 6.1): for one cell of T1, every refracted ray that reaches
+//     the z-band of a triangle T2 crosses it at x2 = x1 + s d~1 (s > 0), so
+//     x2.xy = x1.xy + (x2.z - x1.z) (d~1x / d~1z, d~1y / d~1z).  The box of x1 (its
+//     corner values) and the ratio bounds of the two direction ratios (Eq. eq_bbound,
+//     over both xi1 faces) give an xy footprint; T2 is a candidate of the cell when its
+//     xy box meets the footprint for T2's own z-range.
+//   * Composite position bound: u2 = P2 / Q2 (Eq. eq_rct with d~1 of Eq.
+//     eq_refr_rational) is reduced to degree 1 plus a remainder (Sec. 6.1 "Degree
+//     reduction"): l(u1) interpolates u2 at the cell corners (at xi1 = 1/2) and the
+//     ratio bound of (P2 - l Q2) / Q2 over the cell and xi1 bounds u2 - l.  The
+//     reduction drops xi1.  The second vertex is then built from that degree-1 form
+//     with its remainder carried as a radius: a "model" p + e, |e| <= r on the cell,
+//     with r(a b) = |a| r_b + |b| r_a + r_a r_b (|a| the largest classical coefficient,
+//     a bound of |a| on the cell).  The second refraction and the receiver forms are
+//     those of a single refraction, and the final ratio bound divides the coefficient
+//     intervals [b - r, b + r].
+//   * The irradiance of a chain is not bounded (e_hi = +inf, so P = 1 in Algorithm 1).
+// ---------------------------------------------------------------------------
+double pmaxabs(const Poly& p) {
+  double m = 0.0;
+  for (double v : p.c) m = std::max(m, std::fabs(v));
+  return m;
+}
+
+struct MP {  // model: polynomial p plus a remainder bounded by r on the whole cell
+  Poly p;
+  double r = 0.0;
+};
+MP mp_add(const MP& a, const MP& b, double sb = 1.0) { return {padd(a.p, b.p, sb), a.r + std::fabs(sb) * b.r}; }
+MP mp_mul(const MP& a, const MP& b) { return {pmul(a.p, b.p), pmaxabs(a.p) * b.r + pmaxabs(b.p) * a.r + a.r * b.r}; }
+MP mp_scale(const MP& a, double s) { return {pscale(a.p, s), std::fabs(s) * a.r}; }
+MP mp_shift(MP a, double c) {
+  for (auto& v : a.p.c) v += c;
+  return a;
+}
+MP mp_elev(const MP& a, int n) { return {pelevate_to(a.p, n), a.r}; }
+// +1 / -1 when every coefficient interval [b - r, b + r] lies above / below zero.
+int mp_sign(const MP& a) {
+  bool pos = true, neg = true;
+  for (double v : a.p.c) {
+    if (!(v - a.r > 0.0)) pos = false;
+    if (!(v + a.r < 0.0)) neg = false;
+  }
+  return pos ? 1 : (neg ? -1 : 0);
+}
+// Ratio bound with interval coefficients (p/q is a weighted mean of (b_p + e_p)/(b_q + e_q) for the
+// one pair of remainders e_p, e_q at each point); sq = the certified sign of q's intervals.
+void mp_ratio_bound(const MP& p, const MP& q, int sq, double* lo, double* hi) {
+  double l = std::numeric_limits<double>::infinity(), h = -l;
+  for (size_t i = 0; i < p.p.c.size(); ++i) {
+    double pl = p.p.c[i] - p.r, ph = p.p.c[i] + p.r, ql = q.p.c[i] - q.r, qh = q.p.c[i] + q.r;
+    if (sq < 0) {
+      double t = pl;
+      pl = -ph;
+      ph = -t;
+      t = ql;
+      ql = -qh;
+      qh = -t;
+    }
+    l = std::min(l, pl >= 0.0 ? pl / qh : pl / ql);
+    h = std::max(h, ph >= 0.0 ? ph / ql : ph / qh);
+  }
+  *lo = l;
+  *hi = h;
+}
+double mp_cond(const MP& a) {
+  double mn = std::numeric_limits<double>::infinity(), mx = 0.0;
+  for (double v : a.p.c) {
+    mn = std::min(mn, std::fabs(v) - a.r);
+    mx = std::max(mx, std::fabs(v));
+  }
+  return mx > 0 ? std::max(mn, 0.0) / mx : 0.0;
+}
+
+struct MV {
+  MP x, y, z;
+};
+MP mv_dot(const MV& a, const MV& b) { return mp_add(mp_add(mp_mul(a.x, b.x), mp_mul(a.y, b.y)), mp_mul(a.z, b.z)); }
+MP mv_dotc(const MV& a, V3 c) { return mp_add(mp_add(mp_scale(a.x, c.x), mp_scale(a.y, c.y)), mp_scale(a.z, c.z)); }
+MV mv_mul(const MP& s, const MV& a) { return {mp_mul(s, a.x), mp_mul(s, a.y), mp_mul(s, a.z)}; }
+MV mv_sub(const MV& a, const MV& b) { return {mp_add(a.x, b.x, -1.0), mp_add(a.y, b.y, -1.0), mp_add(a.z, b.z, -1.0)}; }
+MV mv_scale(const MV& a, double s) { return {mp_scale(a.x, s), mp_scale(a.y, s), mp_scale(a.z, s)}; }
+MV mv_elev(const MV& a, int n) { return {mp_elev(a.x, n), mp_elev(a.y, n), mp_elev(a.z, n)}; }
+MV mv_crossc(const MV& a, V3 b) {  // a x b, b constant
+  return {mp_add(mp_scale(a.y, b.z), mp_scale(a.z, b.y), -1.0), mp_add(mp_scale(a.z, b.x), mp_scale(a.x, b.z), -1.0),
+          mp_add(mp_scale(a.x, b.y), mp_scale(a.y, b.x), -1.0)};
+}
+
+// The first vertex on one cell of T1: x1 (degree 1) and the refracted d~1 on the faces xi1 = 0, 1
+// (degree 5), as in the single-refraction bound.
+struct Vertex1 {
+  bool tir = false;
+  PV x1;
+  PV dt[2];
+};
+
+Vertex1 first_vertex(const Tri& T, V3 x0, double eta, const UV C[3]) {
+  Vertex1 S;
+  V3 e11 = T.p[1] - T.p[0], e12 = T.p[2] - T.p[0];
+  V3 n1d = T.n[1] - T.n[0], n2d = T.n[2] - T.n[0];
+  V3 xc[3], nc[3];
+  for (int k = 0; k < 3; ++k) {
+    xc[k] = T.p[0] + C[k].u * e11 + C[k].v * e12;  // Eq. eq_xi
+    nc[k] = T.n[0] + C[k].u * n1d + C[k].v * n2d;  // Eq. eq_ni
+  }
+  S.x1 = pv_affine(xc[0], xc[1], xc[2]);
+  PV n1 = pv_affine(nc[0], nc[1], nc[2]);
+  PV d0 = pv_subc(S.x1, x0);
+  Poly nn = pv_dot(n1, n1), dn = pv_dot(d0, n1), ss = pv_dot(d0, d0);
+  Poly beta = padd(pscale(pmul(nn, ss), 1.0 - eta * eta), pscale(pmul(dn, dn), eta * eta));
+  const double blo = pmin(beta), bhi = pmax(beta);
+  if (!(bhi > 0.0)) {
+    S.tir = true;
+    return S;
+  }
+  double a, b, dlo, dhi;
+  chord_sqrt(std::max(blo, 0.0), bhi, &a, &b, &dlo, &dhi);
+  PV tang = pv_elev(pv_scale(pv_sub(pv_mul(nn, d0), pv_mul(dn, n1)), eta), 5);
+  for (int j = 0; j < 2; ++j) {
+    Poly W = padd(pscale(beta, a), pconst(2, 4, b + (j == 0 ? dlo : dhi)));
+    S.dt[j] = pv_sub(tang, pv_mul(W, n1));
+  }
+  return S;
+}
+
+// The cell's ray bundle for tuple construction: the x1 box (corner values), the certified sign of
+// d~1z and the ratio bounds of d~1x / d~1z, d~1y / d~1z over both xi1 faces.  kind 0: no refracted
+// ray (total internal reflection); 1: bounded; 2: the sign of d~1z is not certified.
+struct Bundle {
+  int kind = 0, sz = 0;
+  double x[2], y[2], z[2], rx[2], ry[2];
+};
+
+Bundle ray_bundle(const Vertex1& S) {
+  Bundle B;
+  if (S.tir) return B;
+  const int s0 = psign(S.dt[0].z), s1 = psign(S.dt[1].z);
+  if (s0 == 0 || s0 != s1) {
+    B.kind = 2;
+    return B;
+  }
+  B.kind = 1;
+  B.sz = s0;
+  B.rx[0] = B.ry[0] = std::numeric_limits<double>::infinity();
+  B.rx[1] = B.ry[1] = -std::numeric_limits<double>::infinity();
+  for (int j = 0; j < 2; ++j) {
+    double l, h;
+    ratio_bound(S.dt[j].x, S.dt[j].z, &l, &h);
+    B.rx[0] = std::min(B.rx[0], l);
+    B.rx[1] = std::max(B.rx[1], h);
+    ratio_bound(S.dt[j].y, S.dt[j].z, &l, &h);
+    B.ry[0] = std::min(B.ry[0], l);
+    B.ry[1] = std::max(B.ry[1], h);
+  }
+  B.x[0] = pmin(S.x1.x);
+  B.x[1] = pmax(S.x1.x);
+  B.y[0] = pmin(S.x1.y);
+  B.y[1] = pmax(S.x1.y);
+  B.z[0] = pmin(S.x1.z);
+  B.z[1] = pmax(S.x1.z);
+  return B;
+}
+
+// Footprint f = {xlo, xhi, ylo, yhi} of a bounded bundle on the band zlo <= z <= zhi.  Returns
+// false when no forward ray reaches the band.
+bool footprint(const Bundle& B, double zlo, double zhi, double f[4]) {
+  double dzl = zlo - B.z[1], dzh = zhi - B.z[0];
+  if (B.sz < 0)
+    dzh = std::min(dzh, 0.0);
+  else
+    dzl = std::max(dzl, 0.0);
+  if (dzl > dzh) return false;
+  auto span = [&](const double x[2], const double r[2], double* ol, double* oh) {
+    const double p[4] = {dzl * r[0], dzl * r[1], dzh * r[0], dzh * r[1]};
+    *ol = x[0] + *std::min_element(p, p + 4);
+    *oh = x[1] + *std::max_element(p, p + 4);
+  };
+  span(B.x, B.rx, &f[0], &f[1]);
+  span(B.y, B.ry, &f[2], &f[3]);
+  return true;
+}
+
+struct Box3 {
+  double lo[3], hi[3];
+};
+Box3 tri_box(const Tri& T) {
+  Box3 b;
+  for (int c = 0; c < 3; ++c) {
+    auto comp = [&](const V3& v) { return c == 0 ? v.x : (c == 1 ? v.y : v.z); };
+    b.lo[c] = std::min(comp(T.p[0]), std::min(comp(T.p[1]), comp(T.p[2])));
+    b.hi[c] = std::max(comp(T.p[0]), std::max(comp(T.p[1]), comp(T.p[2])));
+  }
+  return b;
+}
+
+// Candidate test of T2 for a cell (Sec. 6.1 "Tuple construction"); *gap > 0 is the distance by which
+// T2's xy box misses the footprint for T2's own z-range (<= 0: they meet), +inf when no ray reaches
+// T2's band, -inf when every triangle is a candidate.
+bool pair_candidate(const Bundle& B, const Box3& b, double* gap) {
+  const double inf = std::numeric_limits<double>::infinity();
+  if (B.kind == 0) {
+    *gap = inf;
+    return false;
+  }
+  if (B.kind == 2) {
+    *gap = -inf;
+    return true;
+  }
+  double f[4];
+  if (!footprint(B, b.lo[2], b.hi[2], f)) {
+    *gap = inf;
+    return false;
+  }
+  *gap = std::max(std::max(b.lo[0] - f[1], f[0] - b.hi[0]), std::max(b.lo[1] - f[3], f[2] - b.hi[1]));
+  return *gap <= 0.0;
+}
+
+// Direct geometry of the chain: unit normals, the vector form of Snell's law at both vertices,
+// ray/plane hits (T2's plane, then the receiver's), derivatives by duals.  u2, v2: barycentrics of
+// the hit on T2's plane; t1, t2: ray parameters of the two hits (forward when > 0).
+struct PairEval {
+  double uk, vk, detJ, u2, v2, t1, t2, E;
+  double J[2][2];
+  bool ok;
+};
+
+void plane_coords(DV3 rel, V3 a, V3 b, Dual* U, Dual* V) {  // rel = U a + V b in the plane of a, b
+  const double g11 = dot(a, a), g12 = dot(a, b), g22 = dot(b, b);
+  const double det = g11 * g22 - g12 * g12;
+  Dual pa = ddot(rel, dconst(a)), pb = ddot(rel, dconst(b));
+  *U = (dc(g22) * pa - dc(g12) * pb) / dc(det);
+  *V = (dc(g11) * pb - dc(g12) * pa) / dc(det);
+}
+
+bool snell(DV3 ih, DV3 n, double eta, DV3* out) {  // ih unit incident direction, n normal (any length)
+  Dual ln = dsqrt(ddot(n, n));
+  DV3 nh = {n.x / ln, n.y / ln, n.z / ln};
+  Dual c1 = dc(0.0) - ddot(ih, nh);
+  Dual k = dc(1.0) - dc(eta * eta) * (dc(1.0) - c1 * c1);
+  if (!(k.v > 0.0)) return false;
+  *out = dc(eta) * ih + (dc(eta) * c1 - dsqrt(k)) * nh;
+  return true;
+}
+
+PairEval eval_pair_direct(const Tri& A, const Tri& B, V3 x0, double I0, const Rec& R, double eta1, double eta2,
+                          double u, double v) {
+  PairEval P{};
+  P.ok = false;
+  Dual U = dmk(u, 1, 0), W = dmk(v, 0, 1);
+  DV3 x1 = dconst(A.p[0]) + U * dconst(A.p[1] - A.p[0]) + W * dconst(A.p[2] - A.p[0]);
+  DV3 n1 = dconst(A.n[0]) + U * dconst(A.n[1] - A.n[0]) + W * dconst(A.n[2] - A.n[0]);
+  DV3 d0 = x1 - dconst(x0);
+  Dual l0 = dsqrt(ddot(d0, d0));
+  DV3 i1 = {d0.x / l0, d0.y / l0, d0.z / l0};
+  DV3 r1;
+  if (!snell(i1, n1, eta1, &r1)) return P;
+  const V3 e21 = B.p[1] - B.p[0], e22 = B.p[2] - B.p[0], N2 = cross(e21, e22);
+  Dual s1 = ddot(dconst(B.p[0]) - x1, dconst(N2)) / ddot(r1, dconst(N2));
+  DV3 x2 = x1 + s1 * r1;
+  Dual U2, V2;
+  plane_coords(x2 - dconst(B.p[0]), e21, e22, &U2, &V2);
+  DV3 n2 = dconst(B.n[0]) + U2 * dconst(B.n[1] - B.n[0]) + V2 * dconst(B.n[2] - B.n[0]);
+  Dual lr = dsqrt(ddot(r1, r1));
+  DV3 i2 = {r1.x / lr, r1.y / lr, r1.z / lr};
+  DV3 r2;
+  if (!snell(i2, n2, eta2, &r2)) return P;
+  const V3 Nk = cross(R.e1, R.e2);
+  Dual s2 = ddot(dconst(R.p0) - x2, dconst(Nk)) / ddot(r2, dconst(Nk));
+  DV3 X = x2 + s2 * r2;
+  Dual Uk, Vk;
+  plane_coords(X - dconst(R.p0), R.e1, R.e2, &Uk, &Vk);
+  P.uk = Uk.v;
+  P.vk = Vk.v;
+  P.J[0][0] = Uk.d[0];
+  P.J[0][1] = Uk.d[1];
+  P.J[1][0] = Vk.d[0];
+  P.J[1][1] = Vk.d[1];
+  P.detJ = Uk.d[0] * Vk.d[1] - Uk.d[1] * Vk.d[0];
+  P.u2 = U2.v;
+  P.v2 = V2.v;
+  P.t1 = s1.v;
+  P.t2 = s2.v;
+  V3 dd = {d0.x.v, d0.y.v, d0.z.v};
+  const double s = dot(dd, dd);
+  const V3 N1 = cross(A.p[1] - A.p[0], A.p[2] - A.p[0]);
+  // GGT (Eq. eq_dwda) through both vertices: |d0.N1| / |d0|^3 / (|det du_k/du_1| |N_k|)
+  P.E = I0 * std::fabs(dot(dd, N1)) / (s * std::sqrt(s)) / (std::fabs(P.detJ) * norm(Nk));
+  P.ok = std::isfinite(P.uk) && std::isfinite(P.vk) && std::isfinite(P.detJ) && std::isfinite(P.u2) &&
+         std::isfinite(P.v2);
+  return P;
+}
+
+struct Ctx2 {
+  const orc_surface *s1, *s2;
+  Rec rec;
+  const orc_emitters* em;
+};
+
+// Expansion point of the second vertex's receiver forms: the receiver coordinates of the chain
+// through the cell's centroid (no containment test), rounded to 2^-16; per coordinate 0.5 where
+// that chain has no refracted path or the coordinate is not below 4 in magnitude.  Any point gives
+// a valid bound.
+void centroid_hit(const Ctx2& cx, const Tri& A, const Tri& B, V3 x0, const UV C[3], double* uc, double* vc) {
+  const double cu = (C[0].u + C[1].u + C[2].u) / 3.0, cv = (C[0].v + C[1].v + C[2].v) / 3.0;
+  PairEval P = eval_pair_direct(A, B, x0, 1.0, cx.rec, cx.s1->eta, cx.s2->eta, cu, cv);
+  const double a = P.ok && std::fabs(P.uk) < 4.0 ? P.uk : 0.5;
+  const double b = P.ok && std::fabs(P.vk) < 4.0 ? P.vk : 0.5;
+  *uc = std::nearbyint(a * 65536.0) / 65536.0;
+  *vc = std::nearbyint(b * 65536.0) / 65536.0;
+}
+
+void bound_cell_pair(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int t2, orc_record& r) {
+  UV C[3];
+  cell_corners(id, depth, C);
+  const Tri A = get_tri(cx.s1, t1), B = get_tri(cx.s2, t2);
+  const V3 x0 = {cx.em->x[e], cx.em->y[e], cx.em->z[e]};
+  const Rec& R = cx.rec;
+  std::memset(&r, 0, sizeof(r));
+  r.emitter = e;
+  r.tri0 = t1;
+  r.tri1 = t2;
+  r.cell = id;
+  r.flags = (uint32_t)depth << 24;
+  const double inf = std::numeric_limits<double>::infinity();
+  auto unbounded = [&]() {
+    r.u_lo = r.v_lo = 0.0;
+    r.u_hi = r.v_hi = 1.0;
+    r.e_hi = inf;
+    r.flags |= F_LIVE | F_POS_UNBOUNDED;
+  };
+  const Vertex1 S = first_vertex(A, x0, cx.s1->eta, C);
+  if (S.tir) {
+    r.flags |= F_TIR;
+    return;
+  }
+  // u2 on T2's plane (Eq. eq_rct), both xi1 faces
+  const V3 p20 = B.p[0], e21 = B.p[1] - p20, e22 = B.p[2] - p20;
+  const PV w2 = pv_subc(S.x1, p20);
+  Poly Q2[2], A2[2], B2[2], Q2e[2];
+  for (int j = 0; j < 2; ++j) {
+    PV dxe = pv_crossc(S.dt[j], e22);
+    Q2[j] = pv_dotc(dxe, e21);
+    A2[j] = pv_dot(dxe, w2);
+    B2[j] = pv_dot(pv_crossc(w2, e21), S.dt[j]);
+    Q2e[j] = pelevate(Q2[j]);
+  }
+  r.q_cond = std::min(cond_of(Q2[0]), cond_of(Q2[1]));
+  const int s0 = psign(Q2[0]), s1 = psign(Q2[1]);
+  const int sq = s0 == s1 ? s0 : 0;
+  if (sq == 0) {
+    unbounded();
+    return;
+  }
+  const int st = psign(pv_dotc(pv_crossc(w2, e21), e22));
+  if (st != 0 && st != sq) {
+    r.flags |= F_CULL_BEHIND;
+    return;
+  }
+  double u2l = inf, u2h = -inf, v2l = inf, v2h = -inf;
+  for (int j = 0; j < 2; ++j) {
+    double l, h;
+    ratio_bound(A2[j], Q2e[j], &l, &h);
+    u2l = std::min(u2l, l);
+    u2h = std::max(u2h, h);
+    ratio_bound(B2[j], Q2e[j], &l, &h);
+    v2l = std::min(v2l, l);
+    v2h = std::max(v2h, h);
+  }
+  if (u2h < 0.0 || v2h < 0.0 || u2l + v2l > 1.0) {  // no ray of the cell meets the closed triangle T2
+    r.flags |= F_CULL_EMPTY;
+    return;
+  }
+  // Degree reduction of u2, v2 to the corner interpolant at xi1 = 1/2 plus a remainder
+  const int cidx[3] = {pidx(2, 6, 0, 0), pidx(2, 6, 6, 0), pidx(2, 6, 0, 6)};
+  double lu[3], lv[3];
+  for (int k = 0; k < 3; ++k) {
+    const double q = Q2e[0].c[cidx[k]] + Q2e[1].c[cidx[k]];
+    lu[k] = (A2[0].c[cidx[k]] + A2[1].c[cidx[k]]) / q;
+    lv[k] = (B2[0].c[cidx[k]] + B2[1].c[cidx[k]]) / q;
+  }
+  const Poly Lu = paffine(lu[0], lu[1], lu[2]), Lv = paffine(lv[0], lv[1], lv[2]);
+  double rul = inf, ruh = -inf, rvl = inf, rvh = -inf;
+  for (int j = 0; j < 2; ++j) {
+    double l, h;
+    ratio_bound(padd(A2[j], pmul(Lu, Q2[j]), -1.0), Q2e[j], &l, &h);
+    rul = std::min(rul, l);
+    ruh = std::max(ruh, h);
+    ratio_bound(padd(B2[j], pmul(Lv, Q2[j]), -1.0), Q2e[j], &l, &h);
+    rvl = std::min(rvl, l);
+    rvh = std::max(rvh, h);
+  }
+  const MP U2 = {mp_shift(MP{Lu, 0.0}, 0.5 * (rul + ruh)).p, 0.5 * (ruh - rul)};
+  const MP V2 = {mp_shift(MP{Lv, 0.0}, 0.5 * (rvl + rvh)).p, 0.5 * (rvh - rvl)};
+  // Second vertex: x2, n2 (Eqs. eq_xi, eq_ni on T2) affine in (U2, V2), d1 = x2 - x1
+  const V3 n20 = B.n[0], f21 = B.n[1] - n20, f22 = B.n[2] - n20;
+  auto on_t2 = [&](double base, double a, double b) { return mp_shift(mp_add(mp_scale(U2, a), mp_scale(V2, b)), base); };
+  const MV x2 = {on_t2(p20.x, e21.x, e22.x), on_t2(p20.y, e21.y, e22.y), on_t2(p20.z, e21.z, e22.z)};
+  const MV n2 = {on_t2(n20.x, f21.x, f22.x), on_t2(n20.y, f21.y, f22.y), on_t2(n20.z, f21.z, f22.z)};
+  const MV d1 = mv_sub(x2, MV{{S.x1.x, 0.0}, {S.x1.y, 0.0}, {S.x1.z, 0.0}});
+  const double eta = cx.s2->eta;
+  const MP nn = mv_dot(n2, n2), dn = mv_dot(d1, n2), ss = mv_dot(d1, d1);
+  const MP beta = mp_add(mp_scale(mp_mul(nn, ss), 1.0 - eta * eta), mp_scale(mp_mul(dn, dn), eta * eta));
+  const double blo = pmin(beta.p) - beta.r, bhi = pmax(beta.p) + beta.r;
+  if (!(bhi > 0.0)) {
+    r.flags |= F_TIR;
+    return;
+  }
+  double a, b, dlo, dhi;
+  chord_sqrt(std::max(blo, 0.0), bhi, &a, &b, &dlo, &dhi);
+  const MV tang = mv_elev(mv_scale(mv_sub(mv_mul(nn, d1), mv_mul(dn, n2)), eta), 5);
+  double uc, vc;
+  centroid_hit(cx, A, B, x0, C, &uc, &vc);
+  const V3 pp = R.p0 + uc * R.e1 + vc * R.e2;
+  const MV w3 = {mp_shift(x2.x, -pp.x), mp_shift(x2.y, -pp.y), mp_shift(x2.z, -pp.z)};
+  MP Q3[2], A3[2], B3[2];
+  for (int j = 0; j < 2; ++j) {
+    const MP Wj = mp_shift(mp_scale(beta, a), b + (j == 0 ? dlo : dhi));
+    const MV dt = mv_sub(tang, mv_mul(Wj, n2));
+    const MV dxe = mv_crossc(dt, R.e2);
+    Q3[j] = mv_dotc(dxe, R.e1);
+    A3[j] = mv_dot(dxe, w3);
+    B3[j] = mv_dot(mv_crossc(w3, R.e1), dt);
+  }
+  r.m_cond = std::min(mp_cond(Q3[0]), mp_cond(Q3[1]));
+  const int m0 = mp_sign(Q3[0]), m1 = mp_sign(Q3[1]);
+  const int sq3 = m0 == m1 ? m0 : 0;
+  if (sq3 == 0) {
+    unbounded();
+    return;
+  }
+  const int st3 = mp_sign(mv_dotc(mv_crossc(w3, R.e1), R.e2));
+  if (st3 != 0 && st3 != sq3) {
+    r.flags |= F_CULL_BEHIND;
+    return;
+  }
+  double ul = inf, uh = -inf, vl = inf, vh = -inf;
+  for (int j = 0; j < 2; ++j) {
+    const MP Qe = mp_elev(Q3[j], 6);
+    double l, h;
+    mp_ratio_bound(A3[j], Qe, sq3, &l, &h);
+    ul = std::min(ul, l);
+    uh = std::max(uh, h);
+    mp_ratio_bound(B3[j], Qe, sq3, &l, &h);
+    vl = std::min(vl, l);
+    vh = std::max(vh, h);
+  }
+  r.u_lo = std::max(uc + ul, 0.0);
+  r.u_hi = std::min(uc + uh, 1.0);
+  r.v_lo = std::max(vc + vl, 0.0);
+  r.v_hi = std::min(vc + vh, 1.0);
+  if (r.u_lo > r.u_hi || r.v_lo > r.v_hi) {
+    r.u_lo = r.u_hi = r.v_lo = r.v_hi = 0.0;
+    r.flags |= F_CULL_EMPTY;
+    return;
+  }
+  r.flags |= F_LIVE;
+  r.e_lo = 0.0;
+  r.e_hi = inf;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1276,6 +1744,153 @@ int orc_eval_direct(const orc_surface* s1, const orc_receiver* rec, const orc_em
       ok = eval_direct_refract(T, x0, em->intensity[e], R, s1->eta, u[i], v[i], &uk[i], &vk[i], &E[i], &tt[i]);
     if (!ok) uk[i] = vk[i] = E[i] = tt[i] = std::numeric_limits<double>::quiet_NaN();
   }
+  return 0;
+}
+
+// Candidate pairs (Sec. 6.1 "Tuple construction") by brute force over every triangle of s2:
+// items (emitter, tri0, cell, tri1) in that lexicographic order, for both surfaces refractive.
+int orc_pair_candidates(const orc_surface* s1, const orc_surface* s2, const orc_emitters* em, int32_t depth,
+                        int32_t* out_e, int32_t* out_t1, uint32_t* out_cell, int32_t* out_t2, int64_t cap,
+                        int64_t* n_out, int32_t n_threads) {
+  if (s1->kind != 1 || s2->kind != 1) return -4;
+  std::vector<Box3> boxes(s2->n_tris);
+  for (int t = 0; t < s2->n_tris; ++t) boxes[t] = tri_box(get_tri(s2, t));
+  const int64_t total = (int64_t)em->n * s1->n_tris * ((int64_t)1 << (2 * depth));
+  const int nt = std::max(1, (int)n_threads);
+  std::vector<std::vector<std::array<int64_t, 4>>> parts(nt);
+  parallel_for(total, nt, [&](int k, int64_t a, int64_t b) {
+    for (int64_t i = a; i < b; ++i) {
+      int e, t;
+      uint32_t c;
+      decode_work(i, s1->n_tris, depth, &e, &t, &c);
+      UV C[3];
+      cell_corners(c, depth, C);
+      const V3 x0 = {em->x[e], em->y[e], em->z[e]};
+      const Bundle B = ray_bundle(first_vertex(get_tri(s1, t), x0, s1->eta, C));
+      if (B.kind == 0) continue;
+      for (int t2 = 0; t2 < s2->n_tris; ++t2) {
+        double gap;
+        if (pair_candidate(B, boxes[t2], &gap)) parts[k].push_back({e, t, (int64_t)c, t2});
+      }
+    }
+  });
+  int64_t n = 0;
+  for (auto& v : parts) n += (int64_t)v.size();
+  *n_out = n;
+  if (n > cap) return -2;
+  int64_t o = 0;
+  for (auto& v : parts)
+    for (auto& q : v) {
+      out_e[o] = (int32_t)q[0];
+      out_t1[o] = (int32_t)q[1];
+      out_cell[o] = (uint32_t)q[2];
+      out_t2[o] = (int32_t)q[3];
+      ++o;
+    }
+  return 0;
+}
+
+// Footprint gap of each queried (emitter, tri0, cell, tri1) (see pair_candidate).
+int orc_pair_gap(const orc_surface* s1, const orc_surface* s2, const orc_emitters* em, int32_t depth,
+                 const int32_t* e, const int32_t* t1, const uint32_t* cell, const int32_t* t2, int64_t n,
+                 double* gap) {
+  for (int64_t i = 0; i < n; ++i) {
+    UV C[3];
+    cell_corners(cell[i], depth, C);
+    const V3 x0 = {em->x[e[i]], em->y[e[i]], em->z[e[i]]};
+    pair_candidate(ray_bundle(first_vertex(get_tri(s1, t1[i]), x0, s1->eta, C)), tri_box(get_tri(s2, t2[i])),
+                   &gap[i]);
+  }
+  return 0;
+}
+
+// Records of the given pair items (composite position bound; e_hi = +inf).
+int orc_bound_pairs(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec, const orc_emitters* em,
+                    int32_t depth, const int32_t* e, const int32_t* t1, const uint32_t* cell, const int32_t* t2,
+                    int64_t n, orc_record* out, int32_t n_threads) {
+  if (s1->kind != 1 || s2->kind != 1) return -4;
+  Ctx2 cx{s1, s2, get_rec(rec), em};
+  parallel_for(n, std::max(1, (int)n_threads), [&](int, int64_t a, int64_t b) {
+    for (int64_t i = a; i < b; ++i) bound_cell_pair(cx, e[i], t1[i], cell[i], depth, t2[i], out[i]);
+  });
+  return 0;
+}
+
+// Direct chain evaluation at (u1, v1): out[i*8 + 0..7] = uk, vk, E, u2, v2, t1, t2, detJ (NaN: no path).
+int orc_eval_pair(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec, const orc_emitters* em,
+                  int32_t e, int32_t t1, int32_t t2, const double* u, const double* v, int64_t n, double* out) {
+  const Rec R = get_rec(rec);
+  const Tri A = get_tri(s1, t1), B = get_tri(s2, t2);
+  const V3 x0 = {em->x[e], em->y[e], em->z[e]};
+  for (int64_t i = 0; i < n; ++i) {
+    PairEval P = eval_pair_direct(A, B, x0, em->intensity[e], R, s1->eta, s2->eta, u[i], v[i]);
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    const double vals[8] = {P.uk, P.vk, P.E, P.u2, P.v2, P.t1, P.t2, P.detJ};
+    for (int k = 0; k < 8; ++k) out[i * 8 + k] = P.ok ? vals[k] : nan;
+  }
+  return 0;
+}
+
+// Newton root-finding for pair tuples (Sec. 6.1 "Root-finding", deterministic init) with the same
+// schedule as orc_solve; a root is accepted when the hit is within tol scene units of the target,
+// u1 lies in the closed T1, u2 in the closed T2, and both ray parameters are positive.
+int orc_solve_pair(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec, const orc_emitters* em,
+                   const int64_t* wl_point, const uint64_t* wl_key, const float* wl_p, int64_t n_wl, const float* su,
+                   const float* sv, int32_t newton_iters, int32_t polish_iters, double tol, double* contrib,
+                   double* root_u, double* root_v, int32_t* status, int32_t n_threads) {
+  const Rec R = get_rec(rec);
+  parallel_for(n_wl, std::max(1, (int)n_threads), [&](int, int64_t a, int64_t b) {
+    for (int64_t i = a; i < b; ++i) {
+      const uint64_t k = wl_key[i];
+      const int e = (int)(k >> 48), t1 = (int)(k & 0xFFFFFFu), t2 = (int)((k >> 24) & 0xFFFFFFu) - 1;
+      contrib[i] = 0.0;
+      status[i] = 0;
+      root_u[i] = root_v[i] = 0.0;
+      if (t2 < 0 || t2 >= s2->n_tris || t1 >= s1->n_tris) continue;
+      const Tri A = get_tri(s1, t1), B = get_tri(s2, t2);
+      const V3 x0 = {em->x[e], em->y[e], em->z[e]};
+      const double I0 = em->intensity[e];
+      const double tu = su[wl_point[i]], tv = sv[wl_point[i]];
+      double u = 1.0 / 3.0, v = 1.0 / 3.0;
+      bool bad = false;
+      for (int it = 0; it < newton_iters + polish_iters; ++it) {
+        PairEval P = eval_pair_direct(A, B, x0, I0, R, s1->eta, s2->eta, u, v);
+        const double det = P.detJ;
+        if (!P.ok || !(det != 0.0) || !std::isfinite(det)) {
+          bad = true;
+          break;
+        }
+        const double fu = P.uk - tu, fv = P.vk - tv;
+        double du = -(P.J[1][1] * fu - P.J[0][1] * fv) / det;
+        double dv = -(-P.J[1][0] * fu + P.J[0][0] * fv) / det;
+        const double mx = std::max(std::fabs(du), std::fabs(dv));
+        const bool damped = it < newton_iters;
+        if (damped && mx > 0.5) {
+          du *= 0.5 / mx;
+          dv *= 0.5 / mx;
+        }
+        u += du;
+        v += dv;
+        if (!std::isfinite(u) || !std::isfinite(v)) {
+          bad = true;
+          break;
+        }
+        if (damped && mx < 1e-6) it = newton_iters - 1;
+      }
+      root_u[i] = u;
+      root_v[i] = v;
+      if (bad) continue;
+      PairEval P = eval_pair_direct(A, B, x0, I0, R, s1->eta, s2->eta, u, v);
+      if (!P.ok) continue;
+      const V3 res = (P.uk - tu) * R.e1 + (P.vk - tv) * R.e2;
+      const bool in1 = u >= 0.0 && v >= 0.0 && u + v <= 1.0;
+      const bool in2 = P.u2 >= 0.0 && P.v2 >= 0.0 && P.u2 + P.v2 <= 1.0;
+      if (norm(res) < tol && in1 && in2 && P.t1 > 0.0 && P.t2 > 0.0 && std::isfinite(P.E)) {
+        status[i] = 1;
+        contrib[i] = P.E / (double)wl_p[i];
+      }
+    }
+  });
   return 0;
 }
 

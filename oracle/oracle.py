@@ -91,6 +91,11 @@ def lib():
             L.orc_chord_sqrt.argtypes = [f64, f64, vp]
             L.orc_philox4x32_10.argtypes = [vp, vp, vp]
             L.orc_cell_corners.argtypes = [C.c_uint32, C.c_int, vp]
+            L.orc_pair_candidates.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, i64, vp, i32]
+            L.orc_pair_gap.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, i64, vp]
+            L.orc_bound_pairs.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, vp, i32]
+            L.orc_eval_pair.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i64, vp]
+            L.orc_solve_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32, i32, f64, vp, vp, vp, vp, i32]
             _lib = L
     return _lib
 
@@ -103,7 +108,6 @@ class _SceneViews:
     """Keeps the contiguous arrays alive while ctypes structs point at them."""
 
     def __init__(self, scene):
-        s = scene.s1
         self.keep = []
 
         def c(a, dt):
@@ -111,9 +115,13 @@ class _SceneViews:
             self.keep.append(a)
             return _p(a)
 
-        self.surf = Surface(s.n_verts, s.n_tris, c(s.px, np.float32), c(s.py, np.float32), c(s.pz, np.float32),
-                            c(s.nx, np.float32), c(s.ny, np.float32), c(s.nz, np.float32),
-                            c(s.i0, np.int32), c(s.i1, np.int32), c(s.i2, np.int32), s.kind, s.eta)
+        def surface(s):
+            return Surface(s.n_verts, s.n_tris, c(s.px, np.float32), c(s.py, np.float32), c(s.pz, np.float32),
+                           c(s.nx, np.float32), c(s.ny, np.float32), c(s.nz, np.float32),
+                           c(s.i0, np.int32), c(s.i1, np.int32), c(s.i2, np.int32), s.kind, s.eta)
+
+        self.surf = surface(scene.s1)
+        self.surf2 = surface(scene.s2) if scene.s2 is not None else None
         r = scene.receiver
         self.rec = Receiver((C.c_float * 3)(*r.p0), (C.c_float * 3)(*r.e1), (C.c_float * 3)(*r.e2))
         e = scene.emitters
@@ -336,6 +344,106 @@ def render(scene, gamma: float, seed: int, depth: Optional[int] = None, max_extr
                          f["tri1"], f["flags"], scene.grid_res)
     wp, wk, wP, n_u = sample(off, key, et, scene.grid_res, scene.su, scene.sv, gamma, seed)
     contrib, ru, rv, st = solve(scene, wp, wk, wP, newton_iters, polish_iters, tol, n_threads)
+    E = accumulate(scene.su.shape[0], wp, contrib)
+    return dict(records=rec, offsets=off, key=key, etilde=et, wl_point=wp, wl_key=wk, wl_p=wP, n_U=n_u,
+                contrib=contrib, root_u=ru, root_v=rv, status=st, E=E)
+
+
+# ------------------------------------------------------------------ two specular vertices (pairs)
+def pair_candidates(scene, depth: Optional[int] = None, n_threads: int = 1):
+    """(emitter, tri0, cell, tri1) items whose footprint meets T2 (brute force over every T2)."""
+    L = lib()
+    V = _SceneViews(scene)
+    d = scene.depth if depth is None else depth
+    cap = max(1024, scene.emitters.n * scene.s1.n_tris * 4 ** d * 4)
+    while True:
+        e, t1, t2 = (np.zeros(cap, np.int32) for _ in range(3))
+        cell = np.zeros(cap, np.uint32)
+        n_out = np.zeros(1, np.int64)
+        rc = L.orc_pair_candidates(C.byref(V.surf), C.byref(V.surf2), C.byref(V.em), d, _p(e), _p(t1), _p(cell),
+                                   _p(t2), cap, _p(n_out), n_threads)
+        if rc == -2:
+            cap = int(n_out[0])
+            continue
+        if rc != 0:
+            raise RuntimeError(f"orc_pair_candidates failed: {rc}")
+        n = int(n_out[0])
+        return e[:n], t1[:n], cell[:n], t2[:n]
+
+
+def pair_gap(scene, e, t1, cell, t2, depth: Optional[int] = None):
+    """Distance by which T2's xy box misses the cell's footprint (<= 0: candidate)."""
+    L = lib()
+    V = _SceneViews(scene)
+    d = scene.depth if depth is None else depth
+    arr = [np.ascontiguousarray(a, dt) for a, dt in ((e, np.int32), (t1, np.int32), (cell, np.uint32), (t2, np.int32))]
+    gap = np.zeros(arr[0].shape[0])
+    L.orc_pair_gap(C.byref(V.surf), C.byref(V.surf2), C.byref(V.em), d, *[_p(a) for a in arr], arr[0].shape[0],
+                   _p(gap))
+    return gap
+
+
+def bound_pairs(scene, e, t1, cell, t2, depth: Optional[int] = None, n_threads: int = 1) -> np.ndarray:
+    """Records (RECORD_DTYPE) of the given pair items."""
+    L = lib()
+    V = _SceneViews(scene)
+    d = scene.depth if depth is None else depth
+    arr = [np.ascontiguousarray(a, dt) for a, dt in ((e, np.int32), (t1, np.int32), (cell, np.uint32), (t2, np.int32))]
+    n = arr[0].shape[0]
+    out = np.zeros(n, RECORD_DTYPE)
+    rc = L.orc_bound_pairs(C.byref(V.surf), C.byref(V.surf2), C.byref(V.rec), C.byref(V.em), d,
+                           *[_p(a) for a in arr], n, _p(out), n_threads)
+    if rc != 0:
+        raise RuntimeError(f"orc_bound_pairs failed: {rc}")
+    return out
+
+
+def bound_pair_scene(scene, depth: Optional[int] = None, n_threads: int = 1) -> np.ndarray:
+    """Candidates then their records, in candidate order."""
+    e, t1, cell, t2 = pair_candidates(scene, depth, n_threads)
+    return bound_pairs(scene, e, t1, cell, t2, depth, n_threads)
+
+
+def eval_pair(scene, emitter: int, tri0: int, tri1: int, u, v) -> dict:
+    """Direct chain evaluation: uk, vk, E, u2, v2, t1, t2, detJ per (u1, v1) (NaN: no refracted path)."""
+    L = lib()
+    V = _SceneViews(scene)
+    u = np.ascontiguousarray(u, np.float64)
+    v = np.ascontiguousarray(v, np.float64)
+    out = np.zeros((u.shape[0], 8))
+    L.orc_eval_pair(C.byref(V.surf), C.byref(V.surf2), C.byref(V.rec), C.byref(V.em), emitter, tri0, tri1, _p(u),
+                    _p(v), u.shape[0], _p(out))
+    return {k: out[:, i] for i, k in enumerate(("uk", "vk", "E", "u2", "v2", "t1", "t2", "detJ"))}
+
+
+def solve_pair(scene, wl_point, wl_key, wl_p, newton_iters: int = 16, polish_iters: int = 1, tol: float = 1e-5,
+               n_threads: int = 1):
+    """Pair-tuple Newton: contribution E/P, root (u1, v1), status (1 = root) per worklist entry."""
+    L = lib()
+    V = _SceneViews(scene)
+    wl_point = np.ascontiguousarray(wl_point, np.int64)
+    wl_key = np.ascontiguousarray(wl_key, np.uint64)
+    wl_p = np.ascontiguousarray(wl_p, np.float32)
+    su = np.ascontiguousarray(scene.su, np.float32)
+    sv = np.ascontiguousarray(scene.sv, np.float32)
+    n = wl_point.shape[0]
+    contrib, ru, rv = np.zeros(n), np.zeros(n), np.zeros(n)
+    st = np.zeros(n, np.int32)
+    L.orc_solve_pair(C.byref(V.surf), C.byref(V.surf2), C.byref(V.rec), C.byref(V.em), _p(wl_point), _p(wl_key),
+                     _p(wl_p), n, _p(su), _p(sv), newton_iters, polish_iters, tol, _p(contrib), _p(ru), _p(rv),
+                     _p(st), n_threads)
+    return contrib, ru, rv, st
+
+
+def render_pairs(scene, gamma: float, seed: int, depth: Optional[int] = None, newton_iters: int = 16,
+                 polish_iters: int = 1, tol: float = 1e-5, n_threads: int = 1):
+    """Whole two-vertex path on the CPU: candidates -> pair bounds -> index -> Algorithm 1 -> Newton."""
+    rec = bound_pair_scene(scene, depth, n_threads)
+    f = records_to_f32(rec)
+    off, key, et = index(f["u_lo"], f["u_hi"], f["v_lo"], f["v_hi"], f["e_hi"], f["emitter"], f["tri0"],
+                         f["tri1"], f["flags"], scene.grid_res)
+    wp, wk, wP, n_u = sample(off, key, et, scene.grid_res, scene.su, scene.sv, gamma, seed)
+    contrib, ru, rv, st = solve_pair(scene, wp, wk, wP, newton_iters, polish_iters, tol, n_threads)
     E = accumulate(scene.su.shape[0], wp, contrib)
     return dict(records=rec, offsets=off, key=key, etilde=et, wl_point=wp, wl_key=wk, wl_p=wP, n_U=n_u,
                 contrib=contrib, root_u=ru, root_v=rv, status=st, E=E)

@@ -235,6 +235,25 @@ def gerstner(n: int, seed: int, n_waves: int = 16, extent: float = 2.0, steep: f
     return _to_surface(P, N, _grid_triangles(n), SURFACE_REFRACT, eta)
 
 
+def slab(n: int, seed: int, amp_total: float = 0.02, thickness: float = 0.2, ior: float = 1.5,
+         extent: float = 1.0, flat: bool = False):
+    """Glass slab: top face z = h1 and bottom face z = -thickness + h2 over [-extent,extent]^2,
+    each an n^2 heightfield of 4 seeded sinusoids (amplitude ``amp_total`` in all), analytic
+    normals.  Rays enter through the top (eta' = 1/ior) and leave through the bottom (eta' = ior);
+    both faces' normals point up, toward the incident side.  ``flat``: two planes with normals
+    (0, 0, 1) (closed-form checks)."""
+    if flat:
+        top = heightfield(n, seed, n_waves=1, amp_total=0.0, normals="flat_up", extent=extent,
+                          kind=SURFACE_REFRACT, eta=1.0 / ior)
+        bot = heightfield(n, seed + 1, n_waves=1, amp_total=0.0, normals="flat_up", extent=extent,
+                          z0=-thickness, kind=SURFACE_REFRACT, eta=ior)
+        return top, bot
+    top = heightfield(n, seed, n_waves=4, amp_total=amp_total, extent=extent, kind=SURFACE_REFRACT, eta=1.0 / ior)
+    bot = heightfield(n, seed + 1000, n_waves=4, amp_total=amp_total, extent=extent, z0=-thickness,
+                      kind=SURFACE_REFRACT, eta=ior)
+    return top, bot
+
+
 def point_emitters(positions, intensity=1.0) -> Emitters:
     P = np.asarray(positions, dtype=np.float64).reshape(-1, 3)
     I = np.broadcast_to(np.asarray(intensity, dtype=np.float64), (P.shape[0],))
@@ -334,6 +353,23 @@ def config(name: str, **kw) -> Scene:
         p = kw.get("points", 32)
         su, sv = shading_points(p, p, 1004)
         return Scene(name, s1, None, rec, em, kw.get("depth", 1), su, sv)
+    if name == "slab48":
+        # glass slab (ior 1.5) with two 48^2 faces (4608 triangles each) over [-1,1]^2, 0.2 thick,
+        # light (0,0,2), receiver [-1.5,1.5]^2 at z=-1, 512^2 points, depth 2
+        top, bot = slab(48, 4)
+        em = point_emitters([(0.0, 0.0, 2.0)], 1.0)
+        su, sv = shading_points(kw.get("points", 512), kw.get("points", 512), 1005)
+        return Scene(name, top, bot, receiver_square(-1.0, 1.5), em, kw.get("depth", 2), su, sv)
+    if name == "slab":
+        # small slab: n^2 faces over [-ext,ext]^2 (same law as slab48), receiver [-rec,rec]^2 at z=-1
+        n = kw.get("n", 4)
+        ext = kw.get("extent", 0.5)
+        top, bot = slab(n, kw.get("seed", 4), amp_total=kw.get("amp", 0.02), extent=ext,
+                        thickness=kw.get("thickness", 0.2), flat=kw.get("flat", False))
+        em = point_emitters(kw.get("lights", [(0.05, -0.03, 2.0)]), 1.0)
+        p = kw.get("points", 32)
+        su, sv = shading_points(p, p, 1006)
+        return Scene(name, top, bot, receiver_square(-1.0, kw.get("rec_half", 0.8)), em, kw.get("depth", 1), su, sv)
     if name == "tiny":
         # A few triangles: exhaustive enumeration fits in milliseconds.
         n = kw.get("n", 4)
