@@ -228,7 +228,7 @@ def run_gpu(args):
     pre_cap = int(idx.count[1].item()) + idx.count[1].item() // 4 + 4096
     ix_ws = bnb._ws(bnb.bnb_build_index_ws(bnb.C.byref(cb.c), sc.grid_res, pre_cap), dev)
     idx = bnb.Index(sc.grid_res, pre_cap, dev)
-    sm_ws = bnb._ws(bnb.bnb_sample_and_solve_ws(bnb.C.byref(ds.s1), n_points, wl_cap), dev)
+    sm_ws = bnb._ws(bnb.bnb_sample_and_solve_ws(bnb.C.byref(ds.s1), None, n_points, wl_cap), dev)
     E_out = torch.empty(n_points, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 

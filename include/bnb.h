@@ -159,9 +159,25 @@ typedef struct bnb_sample_stats {
  * variable (Sec. 4.3).  Refraction (s1->kind = BNB_REFRACT, normals facing the
  * incident side, eta in (0, 1e6)) carries sqrt(beta) by a remainder variable
  * (Sec. 4.3), culls cells in total internal reflection (flag TIR) and reports
- * e_hi = +inf (its irradiance is not bounded).  s2 must be NULL (one specular
- * vertex).  Requires out->capacity >= n_base =
- * em->n * s1->n_tris * 4^depth.  ws: bnb_bound_tuples_ws() bytes. */
+ * e_hi = +inf (its irradiance is not bounded).  Requires out->capacity >= n_base =
+ * em->n * s1->n_tris * 4^depth.  ws: bnb_bound_tuples_ws() bytes.
+ *
+ * Two specular vertices (s2 != NULL; both surfaces BNB_REFRACT, eta in (0, 1e6),
+ * else BNB_ERR_UNSUPPORTED): chains x0 -> T1 (s1) -> T2 (s2) -> receiver.
+ * Tuple construction (Sec. 6.1): for every (emitter, T1, cell at `depth`), the
+ * triangles T2 whose xy box meets the footprint of the cell's refracted rays on
+ * T2's z-range (from the x1 box and the ratio bounds of d~1x/d~1z, d~1y/d~1z) are
+ * candidates; each candidate is one record (tri1 = T2), records of one cell
+ * contiguous, cells in base order.  Its box is the composite position bound:
+ * u2 reduced to degree 1 plus a remainder (Sec. 6.1 "Degree reduction"), then
+ * the second refraction and the receiver forms.  e_hi = +inf for every record
+ * (chains carry no irradiance bound; P = 1 in the rendering pass).  A float32
+ * sign test that cannot decide is redone in float64 (QSIGN_FP64); a certified
+ * mixed-sign denominator gives the full box (POS_UNBOUNDED; no splits:
+ * max_extra_split is ignored, and so is irradiance).  *count receives the number
+ * of candidates; when it exceeds out->capacity, status = BNB_ERR_CAPACITY and the
+ * records are invalid: re-call with capacity >= *count.  Host fields: n_base = 0
+ * and depth = 0 (the index pass takes every record on its own). */
 int32_t bnb_bound_tuples(const bnb_surface *s1, const bnb_surface *s2, const bnb_receiver *rec,
                          const bnb_emitters *em, const bnb_bound_cfg *cfg, bnb_cell_bounds *out,
                          void *ws, size_t ws_bytes, void *stream);
@@ -198,12 +214,17 @@ size_t bnb_build_index_ws(const bnb_cell_bounds *cells, int32_t grid_res, int64_
  * su, sv, device float arrays).  E_out[p] (device float, n_points) receives the
  * estimate sum_{T in S} E(T) / P_T (Sec. 5.3) with E the path irradiance
  * I0 dOmega0/dA_k of Eq. eq_dwda (visibility and Fresnel ignored, Sec. 4.4).
- * ws: bnb_sample_and_solve_ws(s1, n_points, cfg->worklist_capacity) bytes. */
+ * With s2 != NULL (pair tuples of a two-vertex bound pass, both surfaces
+ * BNB_REFRACT) every listed key names (emitter, T1, T2) and the Newton solve runs
+ * through the chain x0 -> T1 -> T2 -> receiver; a root is accepted when u1 lies in
+ * the closed T1, u2 in the closed T2 and both hits are in front.
+ * ws: bnb_sample_and_solve_ws(s1, s2, n_points, cfg->worklist_capacity) bytes. */
 int32_t bnb_sample_and_solve(const bnb_surface *s1, const bnb_surface *s2, const bnb_receiver *rec,
                              const bnb_emitters *em, const bnb_index *index, const float *su, const float *sv,
                              int64_t n_points, const bnb_sample_cfg *cfg, float *E_out,
                              bnb_sample_stats *stats, void *ws, size_t ws_bytes, void *stream);
-size_t bnb_sample_and_solve_ws(const bnb_surface *s1, int64_t n_points, int64_t worklist_capacity);
+size_t bnb_sample_and_solve_ws(const bnb_surface *s1, const bnb_surface *s2, int64_t n_points,
+                               int64_t worklist_capacity);
 
 /* ---- Batched rendering pass ------------------------------------------------
  * The paper renders one frame at a time; these calls serve many rendering
@@ -309,7 +330,7 @@ size_t bnb_bound_tuples_batched_ws(int32_t max_jobs);
 const char *bnb_status_string(int32_t status);
 
 /* ABI version of this header (increments on any struct or signature change). */
-int32_t bnb_abi_version(void);  /* 5 */
+int32_t bnb_abi_version(void);  /* 6 */
 
 #ifdef __cplusplus
 }

@@ -123,7 +123,7 @@ def lib():
                                            P(bnb_index), vp, vp, i64, P(bnb_sample_cfg), vp, P(bnb_sample_stats),
                                            vp, sz, vp]
         L.bnb_sample_and_solve_ws.restype = sz
-        L.bnb_sample_and_solve_ws.argtypes = [P(bnb_surface), i64, i64]
+        L.bnb_sample_and_solve_ws.argtypes = [P(bnb_surface), P(bnb_surface), i64, i64]
         L.bnb_status_string.restype = C.c_char_p
         L.bnb_status_string.argtypes = [i32]
         L.bnb_abi_version.restype = i32
@@ -242,10 +242,21 @@ class DeviceScene:
                       ex=t(scene.emitters.x, torch.float32), ey=t(scene.emitters.y, torch.float32),
                       ez=t(scene.emitters.z, torch.float32), ei=t(scene.emitters.intensity, torch.float32),
                       su=t(scene.su, torch.float32), sv=t(scene.sv, torch.float32))
+        s2 = scene.s2
+        if s2 is not None:  # second specular surface (two-vertex chains)
+            for k, a in (("px", s2.px), ("py", s2.py), ("pz", s2.pz), ("nx", s2.nx), ("ny", s2.ny), ("nz", s2.nz)):
+                self.t["s2_" + k] = t(a, torch.float32)
+            for k, a in (("i0", s2.i0), ("i1", s2.i1), ("i2", s2.i2)):
+                self.t["s2_" + k] = t(a, torch.int32)
         T = self.t
         self.s1 = bnb_surface(s.n_verts, s.n_tris, _ptr(T["px"]), _ptr(T["py"]), _ptr(T["pz"]), _ptr(T["nx"]),
                               _ptr(T["ny"]), _ptr(T["nz"]), _ptr(T["i0"]), _ptr(T["i1"]), _ptr(T["i2"]), s.kind,
                               s.eta)
+        self.s2 = None
+        if s2 is not None:
+            self.s2 = bnb_surface(s2.n_verts, s2.n_tris, *[_ptr(T["s2_" + k]) for k in
+                                                           ("px", "py", "pz", "nx", "ny", "nz", "i0", "i1", "i2")],
+                                  s2.kind, s2.eta)
         r = scene.receiver
         self.rec = bnb_receiver((f32 * 3)(*r.p0), (f32 * 3)(*r.e1), (f32 * 3)(*r.e2))
         self.em = bnb_emitters(scene.emitters.n, _ptr(T["ex"]), _ptr(T["ey"]), _ptr(T["ez"]), _ptr(T["ei"]))
@@ -253,6 +264,10 @@ class DeviceScene:
     @property
     def n_points(self) -> int:
         return int(self.t["su"].shape[0])
+
+    def s2_ref(self):
+        """bnb_surface pointer of the second surface, or None (one specular vertex)."""
+        return C.byref(self.s2) if self.s2 is not None else None
 
     def with_emitters(self, which) -> "DeviceScene":
         """The same resident mesh, receiver and points lit by the emitters `which` (indices into
@@ -268,6 +283,7 @@ class DeviceScene:
         for k in ("ex", "ey", "ez", "ei"):
             out.t[k] = self.t[k].index_select(0, idx)
         out.s1 = self.s1
+        out.s2 = self.s2
         out.rec = self.rec
         T = out.t
         out.em = bnb_emitters(int(sel.shape[0]), _ptr(T["ex"]), _ptr(T["ey"]), _ptr(T["ez"]), _ptr(T["ei"]))
@@ -344,15 +360,16 @@ def bound_tuples(ds: DeviceScene, depth: int, max_extra_split: int = 4, irradian
     cfg = bnb_bound_cfg(depth, max_extra_split, int(irradiance), int(fp64))
     n_base = ds.scene.emitters.n * ds.s1.n_tris * 4 ** depth
     if out is None:
-        out = CellBounds(capacity if capacity is not None else n_base + n_base // 8 + 1024, ds.device, with_e_hi_min,
-                         with_e_lo)
-    need = bnb_bound_tuples_ws(C.byref(ds.s1), None, C.byref(ds.em), C.byref(cfg))
+        # pairs: one record per (cell, candidate T2), a few per cell; the call reports the count
+        default = n_base * 4 + 1024 if ds.s2 is not None else n_base + n_base // 8 + 1024
+        out = CellBounds(capacity if capacity is not None else default, ds.device, with_e_hi_min, with_e_lo)
+    need = bnb_bound_tuples_ws(C.byref(ds.s1), ds.s2_ref(), C.byref(ds.em), C.byref(cfg))
     if ws is None or ws.numel() < need + 256:
         ws = _ws(need, ds.device)
     for _ in range(2):
         out.reset()
-        rc = bnb_bound_tuples(C.byref(ds.s1), None, C.byref(ds.rec), C.byref(ds.em), C.byref(cfg), C.byref(out.c),
-                              _align(ws), C.c_size_t(need), _stream(stream))
+        rc = bnb_bound_tuples(C.byref(ds.s1), ds.s2_ref(), C.byref(ds.rec), C.byref(ds.em), C.byref(cfg),
+                              C.byref(out.c), _align(ws), C.c_size_t(need), _stream(stream))
         _check(rc, "bnb_bound_tuples")
         if not sync_check:
             return out
@@ -421,13 +438,13 @@ def sample_and_solve(ds: DeviceScene, index: Index, gamma: float, seed: int, new
     sel = torch.zeros(n_points, dtype=torch.int32, device=ds.device) if with_sel_count else None
     for _ in range(2):
         cfg = bnb_sample_cfg(gamma, seed, newton_iters, polish_iters, tol, wl)
-        need = bnb_sample_and_solve_ws(C.byref(ds.s1), n_points, wl)
+        need = bnb_sample_and_solve_ws(C.byref(ds.s1), ds.s2_ref(), n_points, wl)
         if ws is None or ws.numel() < need + 256:
             ws = _ws(need, ds.device)
         counters.zero_()
         status.zero_()
         stats = bnb_sample_stats(_ptr(counters), _ptr(status), _ptr(sel))
-        rc = bnb_sample_and_solve(C.byref(ds.s1), None, C.byref(ds.rec), C.byref(ds.em), C.byref(index.c),
+        rc = bnb_sample_and_solve(C.byref(ds.s1), ds.s2_ref(), C.byref(ds.rec), C.byref(ds.em), C.byref(index.c),
                                   _ptr(su), _ptr(sv), n_points, C.byref(cfg), _ptr(E), C.byref(stats), _align(ws),
                                   C.c_size_t(need), _stream(stream))
         _check(rc, "bnb_sample_and_solve")

@@ -11,11 +11,15 @@ namespace bnb {
 size_t index_ws_bytes(int32_t G, int64_t pre_cap);
 cudaError_t launch_build_index(const bnb_cell_bounds* c, float m, int64_t pre_cap, bnb_index* out, void* ws,
                                cudaStream_t st);
-size_t sample_ws_bytes(int64_t n_tris, int64_t n_points, int64_t wl_cap);
-cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_receiver* rec, const bnb_emitters* em,
-                                    const bnb_index* idx, const float* su, const float* sv, int64_t n_points,
-                                    const bnb_sample_cfg* cfg, float* E_out, bnb_sample_stats* stats, void* ws,
-                                    cudaStream_t st);
+size_t sample_ws_bytes(int64_t n_tris, int64_t n_tris2, int64_t n_points, int64_t wl_cap);
+cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
+                                    const bnb_emitters* em, const bnb_index* idx, const float* su, const float* sv,
+                                    int64_t n_points, const bnb_sample_cfg* cfg, float* E_out,
+                                    bnb_sample_stats* stats, void* ws, cudaStream_t st);
+size_t pair_ws_bytes(int64_t n_tris1, int64_t n_tris2, int64_t n_base);
+cudaError_t launch_bound_pairs(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
+                               const bnb_emitters* em, int32_t depth, bool fp64, bnb_cell_bounds* out, void* ws,
+                               cudaStream_t st);
 size_t batch_ws_bytes(const bnb_batch_cfg* c);
 size_t bound_batch_ws_bytes(int32_t max_jobs);
 cudaError_t launch_bound_batched(const bnb_bound_job* jobs, const int32_t* n_jobs, int32_t max_jobs, void* ws,
@@ -46,6 +50,12 @@ bool emitters_ok(const bnb_emitters* e) {
 }
 
 bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
+
+// Two specular vertices: both surfaces refractive with eta' in (0, 1e6).
+bool pair_ok(const bnb_surface* s1, const bnb_surface* s2) {
+  return s1->kind == BNB_REFRACT && s2->kind == BNB_REFRACT && s1->eta > 0.0f && s1->eta < 1e6f &&
+         s2->eta > 0.0f && s2->eta < 1e6f;
+}
 
 int64_t n_base_of(const bnb_surface* s1, const bnb_emitters* em, int depth) {
   return (int64_t)em->n * (int64_t)s1->n_tris * ((int64_t)1 << (2 * depth));
@@ -80,7 +90,7 @@ BoundWs carve_bound_ws(void* base, int64_t n_tris, int64_t qcap) {
 
 extern "C" {
 
-int32_t bnb_abi_version(void) { return 5; }
+int32_t bnb_abi_version(void) { return 6; }
 
 const char* bnb_status_string(int32_t s) {
   switch (s) {
@@ -96,9 +106,9 @@ const char* bnb_status_string(int32_t s) {
 
 size_t bnb_bound_tuples_ws(const bnb_surface* s1, const bnb_surface* s2, const bnb_emitters* em,
                            const bnb_bound_cfg* cfg) {
-  (void)s2;
   if (!surface_ok(s1) || !emitters_ok(em) || !cfg || cfg->depth < 0 || cfg->depth > kMaxBaseDepth) return 0;
   const int64_t nb = n_base_of(s1, em, cfg->depth);
+  if (s2 != nullptr) return surface_ok(s2) ? pair_ws_bytes(s1->n_tris, s2->n_tris, nb) : 0;
   return carve_bound_ws(nullptr, s1->n_tris, split_queue_cap(nb)).bytes;
 }
 
@@ -106,7 +116,26 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
                          const bnb_emitters* em, const bnb_bound_cfg* cfg, bnb_cell_bounds* out, void* ws,
                          size_t ws_bytes, void* stream) {
   if (!surface_ok(s1) || !emitters_ok(em) || !rec || !cfg || !out) return BNB_ERR_INVALID;
-  if (s2 != nullptr) return BNB_ERR_UNSUPPORTED;
+  if (s2 != nullptr) {
+    if (!surface_ok(s2)) return BNB_ERR_INVALID;
+    if (!pair_ok(s1, s2)) return BNB_ERR_UNSUPPORTED;
+    if (cfg->depth < 0 || cfg->depth > kMaxBaseDepth) return BNB_ERR_INVALID;
+    if (!out->count || !out->status || out->capacity < 0) return BNB_ERR_INVALID;
+    if (out->capacity > 0 && (!out->u_lo || !out->u_hi || !out->v_lo || !out->v_hi || !out->e_hi ||
+                              !out->emitter || !out->tri0 || !out->tri1 || !out->cell || !out->flags))
+      return BNB_ERR_INVALID;
+    const int64_t nb = n_base_of(s1, em, cfg->depth);
+    const size_t need = pair_ws_bytes(s1->n_tris, s2->n_tris, nb);
+    if (ws_bytes < need || (need > 0 && (!ws || !aligned256(ws)))) return BNB_ERR_INVALID;
+    out->n_base = 0;  // records are not in base-cell order: every record is indexed on its own
+    out->depth = 0;
+    out->n_emitters = em->n;
+    out->n_tris = s1->n_tris;
+    return launch_bound_pairs(s1, s2, rec, em, cfg->depth, cfg->fp64 != 0, out, ws, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? BNB_OK
+               : BNB_ERR_CUDA;
+  }
   if (s1->kind != BNB_REFLECT && s1->kind != BNB_REFRACT) return BNB_ERR_INVALID;
   if (s1->kind == BNB_REFRACT && !(s1->eta > 0.0f && s1->eta < 1e6f)) return BNB_ERR_INVALID;
   if (cfg->depth < 0 || cfg->depth > kMaxBaseDepth || cfg->max_extra_split < 0 || cfg->max_extra_split > kMaxExtra ||
@@ -202,9 +231,10 @@ int32_t bnb_build_index(const bnb_cell_bounds* cells, float m, int64_t pre_capac
                                                                                                   : BNB_ERR_CUDA;
 }
 
-size_t bnb_sample_and_solve_ws(const bnb_surface* s1, int64_t n_points, int64_t worklist_capacity) {
-  if (!surface_ok(s1) || n_points < 0 || worklist_capacity < 0) return 0;
-  return sample_ws_bytes(s1->n_tris, n_points, worklist_capacity);
+size_t bnb_sample_and_solve_ws(const bnb_surface* s1, const bnb_surface* s2, int64_t n_points,
+                               int64_t worklist_capacity) {
+  if (!surface_ok(s1) || (s2 && !surface_ok(s2)) || n_points < 0 || worklist_capacity < 0) return 0;
+  return sample_ws_bytes(s1->n_tris, s2 ? s2->n_tris : 0, n_points, worklist_capacity);
 }
 
 int32_t bnb_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
@@ -212,7 +242,8 @@ int32_t bnb_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2, const
                              int64_t n_points, const bnb_sample_cfg* cfg, float* E_out, bnb_sample_stats* stats,
                              void* ws, size_t ws_bytes, void* stream) {
   if (!surface_ok(s1) || !emitters_ok(em) || !rec || !index || !cfg || !stats) return BNB_ERR_INVALID;
-  if (s2 != nullptr) return BNB_ERR_UNSUPPORTED;
+  if (s2 != nullptr && !surface_ok(s2)) return BNB_ERR_INVALID;
+  if (s2 != nullptr && !pair_ok(s1, s2)) return BNB_ERR_UNSUPPORTED;
   if (s1->kind != BNB_REFLECT && s1->kind != BNB_REFRACT) return BNB_ERR_INVALID;
   if (s1->kind == BNB_REFRACT && !(s1->eta > 0.0f && s1->eta < 1e6f)) return BNB_ERR_INVALID;
   if (n_points < 0 || (n_points > 0 && (!su || !sv || !E_out))) return BNB_ERR_INVALID;
@@ -221,9 +252,9 @@ int32_t bnb_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2, const
   if (cfg->worklist_capacity < 0 || cfg->newton_iters < 0 || cfg->newton_iters > 64 || cfg->polish_iters < 0 ||
       cfg->polish_iters > 8 || !(cfg->gamma >= 0.0f) || !(cfg->tol > 0.0f))
     return BNB_ERR_INVALID;
-  const size_t need = sample_ws_bytes(s1->n_tris, n_points, cfg->worklist_capacity);
+  const size_t need = sample_ws_bytes(s1->n_tris, s2 ? s2->n_tris : 0, n_points, cfg->worklist_capacity);
   if (ws_bytes < need || !ws || !aligned256(ws)) return BNB_ERR_INVALID;
-  return launch_sample_and_solve(s1, rec, em, index, su, sv, n_points, cfg, E_out, stats, ws,
+  return launch_sample_and_solve(s1, s2, rec, em, index, su, sv, n_points, cfg, E_out, stats, ws,
                                  (cudaStream_t)stream) == cudaSuccess
              ? BNB_OK
              : BNB_ERR_CUDA;

@@ -223,6 +223,201 @@ __device__ __forceinline__ double polish64(const float (&pf)[3][3], const float 
   return -1.0;
 }
 
+// ------------------------------------------------------------------ two-vertex chains
+// x0 -> x1 on T1 -> x2 on T2 -> receiver with refraction at both vertices, in the same
+// un-normalized rational forms (Eqs. eq_xi, eq_ni, eq_refr_rational, eq_rct; d1 = x2 - x1),
+// differentiated in (u1, v1) by forward-mode duals.
+template <typename T>
+struct Dl {
+  T v, du, dv;
+};
+template <typename T>
+__device__ __forceinline__ Dl<T> operator+(Dl<T> a, Dl<T> b) { return {a.v + b.v, a.du + b.du, a.dv + b.dv}; }
+template <typename T>
+__device__ __forceinline__ Dl<T> operator-(Dl<T> a, Dl<T> b) { return {a.v - b.v, a.du - b.du, a.dv - b.dv}; }
+template <typename T>
+__device__ __forceinline__ Dl<T> operator*(Dl<T> a, Dl<T> b) {
+  return {a.v * b.v, a.du * b.v + a.v * b.du, a.dv * b.v + a.v * b.dv};
+}
+template <typename T>
+__device__ __forceinline__ Dl<T> operator*(T s, Dl<T> a) { return {s * a.v, s * a.du, s * a.dv}; }
+template <typename T>
+__device__ __forceinline__ Dl<T> operator/(Dl<T> a, Dl<T> b) {
+  const T i = T(1) / b.v, q = a.v * i;
+  return {q, (a.du - q * b.du) * i, (a.dv - q * b.dv) * i};
+}
+template <typename T>
+__device__ __forceinline__ Dl<T> dl_sqrt(Dl<T> a) {
+  const T s = sqrt(a.v), h = T(0.5) / s;
+  return {s, a.du * h, a.dv * h};
+}
+template <typename T>
+__device__ __forceinline__ Dl<T> dl_dot(const Dl<T> (&a)[3], const Dl<T> (&b)[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+template <typename T>
+__device__ __forceinline__ Dl<T> dl_dotc(const Dl<T> (&a)[3], const T (&b)[3]) {
+  return b[0] * a[0] + b[1] * a[1] + b[2] * a[2];
+}
+template <typename T>
+__device__ __forceinline__ void dl_cross_cd(const T (&a)[3], const Dl<T> (&b)[3], Dl<T> (&r)[3]) {  // a x b
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+template <typename T>
+__device__ __forceinline__ void dl_cross_dc(const Dl<T> (&a)[3], const T (&b)[3], Dl<T> (&r)[3]) {  // a x b
+  r[0] = b[2] * a[1] - b[1] * a[2];
+  r[1] = b[0] * a[2] - b[2] * a[0];
+  r[2] = b[1] * a[0] - b[0] * a[1];
+}
+
+// The triangles and constants of one pair tuple.
+struct PairGeom {
+  float p1[3][3], n1[3][3], p2[3][3], n2[3][3], x0[3], I0, rp0[3], re1[3], re2[3], eta1, eta2;
+};
+
+template <typename T>
+struct Path2 : Path<T> {
+  T u2, v2, t2;  // barycentrics of the hit on T2's plane; ray parameter of the receiver hit
+};
+
+// d~ = eta' ((n.n) d - (d.n) n) - sqrt(beta) n; false when beta <= 0 (no refracted path).
+template <typename T>
+__device__ __forceinline__ bool dl_refract(const Dl<T> (&n)[3], const Dl<T> (&d)[3], T eta, Dl<T> (&out)[3]) {
+  const Dl<T> nn = dl_dot(n, n), dn = dl_dot(d, n), ss = dl_dot(d, d);
+  const Dl<T> beta = (T(1) - eta * eta) * (nn * ss) + (eta * eta) * (dn * dn);
+  if (!(beta.v > T(0))) return false;
+  const Dl<T> W = dl_sqrt(beta);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[c] = eta * (nn * d[c] - dn * n[c]) - W * n[c];
+  return true;
+}
+
+// Plane coordinates (Eq. eq_rct) of the ray x + t d on o + a e1 + b e2, and its parameter t.
+template <typename T>
+__device__ __forceinline__ void dl_plane(const Dl<T> (&x)[3], const Dl<T> (&d)[3], const T (&o)[3], const T (&e1)[3],
+                                         const T (&e2)[3], Dl<T>& a, Dl<T>& b, Dl<T>& t) {
+  Dl<T> w[3], h1[3], h2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) w[c] = x[c] - Dl<T>{o[c], T(0), T(0)};
+  const T g[3] = {e2[1] * e1[2] - e2[2] * e1[1], e2[2] * e1[0] - e2[0] * e1[2], e2[0] * e1[1] - e2[1] * e1[0]};
+  dl_cross_cd(e2, w, h1);
+  dl_cross_dc(w, e1, h2);
+  const Dl<T> q = dl_dotc(d, g);
+  a = dl_dot(d, h1) / q;
+  b = dl_dot(h2, d) / q;
+  t = dl_dotc(h2, e2) / q;
+}
+
+template <typename T>
+__device__ __forceinline__ Path2<T> eval_pair(const PairGeom& G, T u, T v) {
+  Path2<T> r{};
+  r.ok = false;
+  T e1[3], e2[3], f1[3], f2[3], o2[3], e21[3], e22[3], R0[3], R1[3], R2[3];
+  Dl<T> x1[3], n1[3], d0[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    e1[c] = (T)G.p1[1][c] - (T)G.p1[0][c];
+    e2[c] = (T)G.p1[2][c] - (T)G.p1[0][c];
+    f1[c] = (T)G.n1[1][c] - (T)G.n1[0][c];
+    f2[c] = (T)G.n1[2][c] - (T)G.n1[0][c];
+    x1[c] = {(T)G.p1[0][c] + u * e1[c] + v * e2[c], e1[c], e2[c]};
+    n1[c] = {(T)G.n1[0][c] + u * f1[c] + v * f2[c], f1[c], f2[c]};
+    d0[c] = {x1[c].v - (T)G.x0[c], e1[c], e2[c]};
+    o2[c] = (T)G.p2[0][c];
+    e21[c] = (T)G.p2[1][c] - o2[c];
+    e22[c] = (T)G.p2[2][c] - o2[c];
+    R0[c] = (T)G.rp0[c];
+    R1[c] = (T)G.re1[c];
+    R2[c] = (T)G.re2[c];
+  }
+  Dl<T> t1d[3];
+  if (!dl_refract(n1, d0, (T)G.eta1, t1d)) return r;
+  Dl<T> u2, v2, s1;
+  dl_plane(x1, t1d, o2, e21, e22, u2, v2, s1);
+  Dl<T> x2[3], n2[3], d1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    x2[c] = Dl<T>{o2[c], T(0), T(0)} + e21[c] * u2 + e22[c] * v2;
+    n2[c] = Dl<T>{(T)G.n2[0][c], T(0), T(0)} + ((T)G.n2[1][c] - (T)G.n2[0][c]) * u2 +
+            ((T)G.n2[2][c] - (T)G.n2[0][c]) * v2;
+    d1[c] = x2[c] - x1[c];
+  }
+  Dl<T> t2d[3];
+  if (!dl_refract(n2, d1, (T)G.eta2, t2d)) return r;
+  Dl<T> uk, vk, s2;
+  dl_plane(x2, t2d, R0, R1, R2, uk, vk, s2);
+  r.uk = uk.v;
+  r.vk = vk.v;
+  r.J00 = uk.du;
+  r.J01 = uk.dv;
+  r.J10 = vk.du;
+  r.J11 = vk.dv;
+  r.t = s1.v;
+  r.t2 = s2.v;
+  r.u2 = u2.v;
+  r.v2 = v2.v;
+  const T det = r.J00 * r.J11 - r.J01 * r.J10;
+  const T N1[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  const T Nk[3] = {R1[1] * R2[2] - R1[2] * R2[1], R1[2] * R2[0] - R1[0] * R2[2], R1[0] * R2[1] - R1[1] * R2[0]};
+  T C1 = T(0), ss = T(0), nk = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    C1 += ((T)G.p1[0][c] - (T)G.x0[c]) * N1[c];
+    ss += d0[c].v * d0[c].v;
+    nk += Nk[c] * Nk[c];
+  }
+  // GGT (Eq. eq_dwda) through both vertices: I0 |d0.N1| / (|d0|^3 |N_k| |det du_k/du_1|)
+  r.E = (T)G.I0 * fabs(C1) / (ss * sqrt(ss) * sqrt(nk) * fabs(det));
+  r.ok = isfinite(r.uk) && isfinite(r.vk) && isfinite(det) && isfinite(r.u2) && isfinite(r.v2);
+  return r;
+}
+
+// Pair counterparts of newton32 / polish64: the same damped float32 phase (also rejecting a
+// root converged more than kOutside outside T2), then float64 polish steps and the acceptance
+// tests (u1 in the closed T1, u2 in the closed T2, both hits in front).
+__device__ __forceinline__ bool newton32_pair(const PairGeom& G, float tuf, float tvf, int newton_iters, float& u,
+                                              float& v) {
+  u = 1.0f / 3.0f;
+  v = 1.0f / 3.0f;
+  bool converged = false;
+  Path2<float> P{};
+  for (int it = 0; it < newton_iters; ++it) {
+    P = eval_pair<float>(G, u, v);
+    float step;
+    if (!newton_step<float>(P, tuf, tvf, true, u, v, step)) return false;
+    if (step < 1e-6f) {
+      converged = true;
+      break;
+    }
+  }
+  constexpr float kOutside = 1e-3f;
+  if (!converged) return true;
+  if (fminf(fminf(u, v), 1.0f - u - v) < -kOutside) return false;
+  return !(fminf(fminf(P.u2, P.v2), 1.0f - P.u2 - P.v2) < -kOutside);
+}
+
+__device__ __forceinline__ double polish64_pair(const PairGeom& G, float tuf, float tvf, int polish_iters, float tol,
+                                                float u, float v) {
+  double ud = u, vd = v;
+  bool good = true;
+  for (int it = 0; it < polish_iters && good; ++it) {
+    const Path2<double> P = eval_pair<double>(G, ud, vd);
+    double step;
+    good = newton_step<double>(P, (double)tuf, (double)tvf, false, ud, vd, step);
+  }
+  if (!good) return -1.0;
+  const Path2<double> P = eval_pair<double>(G, ud, vd);
+  const double fu = P.uk - (double)tuf, fv = P.vk - (double)tvf;
+  const double r0 = fu * G.re1[0] + fv * G.re2[0], r1 = fu * G.re1[1] + fv * G.re2[1], r2 = fu * G.re1[2] + fv * G.re2[2];
+  const double res = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+  const bool in1 = ud >= 0.0 && vd >= 0.0 && ud + vd <= 1.0;
+  const bool in2 = P.u2 >= 0.0 && P.v2 >= 0.0 && P.u2 + P.v2 <= 1.0;
+  if (P.ok && res < (double)tol && in1 && in2 && P.t > 0.0 && P.t2 > 0.0 && isfinite(P.E)) return P.E;
+  return -1.0;
+}
+
 // Appends the calling lane to a device list when `need` is set (one atomic per warp); returns the
 // lane's list position, or -1.  Every lane active at the call must make it.
 __device__ __forceinline__ int64_t warp_append(bool need, int64_t* count) {

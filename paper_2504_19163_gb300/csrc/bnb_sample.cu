@@ -13,6 +13,8 @@
 //                     damped steps; tuples left with a possible root are listed.
 //   polish_k          per listed tuple: float64 polish steps, acceptance tests,
 //                     contribution E(root) / P.
+//   (pair tuples, s2 given: solve32_pair_k / polish_pair_k through the two-vertex
+//    chain x0 -> T1 -> T2 -> receiver, Newton in T1's barycentric coordinates)
 //   reduce_k          per point, contributions summed in worklist order.
 #include <stdint.h>
 
@@ -106,6 +108,10 @@ struct SolveParams {
   int32_t newton_iters, polish_iters;
   float tol;
   float eta;  // refraction: eta'
+  // pair tuples (s2 given): T2's packed triangles and eta'
+  const float4* tri2;
+  int32_t n_tris2;
+  float eta2;
   float* contrib;
   int64_t* counters;
   // tuples handed from the float32 phase to the float64 polish
@@ -169,6 +175,68 @@ __global__ void __launch_bounds__(256) polish_k(SolveParams S) {
   if ((threadIdx.x & 31) == 0 && roots) atomicAdd((unsigned long long*)&S.counters[2], (unsigned long long)roots);
 }
 
+// Pair tuples (key tri1 >= 0): the same two phases through the two-vertex chain.
+__device__ __forceinline__ bool pair_geom(const SolveParams& S, uint64_t k, PairGeom& G) {
+  const int e = (int)(k >> 48), t1 = (int)(k & 0xFFFFFFull), t2 = (int)((k >> 24) & 0xFFFFFFull) - 1;
+  if (t1 >= S.n_tris || t2 < 0 || t2 >= S.n_tris2 || e >= S.n_emitters) return false;
+  load_tri_s(S.tri, t1, G.p1, G.n1);
+  load_tri_s(S.tri2, t2, G.p2, G.n2);
+  G.x0[0] = __ldg(S.ex + e);
+  G.x0[1] = __ldg(S.ey + e);
+  G.x0[2] = __ldg(S.ez + e);
+  G.I0 = __ldg(S.ei + e);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    G.rp0[c] = S.rp0[c];
+    G.re1[c] = S.re1[c];
+    G.re2[c] = S.re2[c];
+  }
+  G.eta1 = S.eta;
+  G.eta2 = S.eta2;
+  return true;
+}
+
+__global__ void __launch_bounds__(256) solve32_pair_k(SolveParams S) {
+  const int64_t n = min(*S.n_wl, S.wl_cap);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    PairGeom G;
+    bool need = false;
+    float u = 0.0f, v = 0.0f;
+    if (pair_geom(S, S.wl_key[i], G)) {
+      const int64_t pt = S.wl_point[i];
+      need = newton32_pair(G, S.su[pt], S.sv[pt], S.newton_iters, u, v);
+    }
+    if (!need) S.contrib[i] = 0.0f;
+    const int64_t j = warp_append(need, S.pl_count);
+    if (need) {
+      S.pl_idx[j] = i;
+      S.pl_u[j] = u;
+      S.pl_v[j] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) polish_pair_k(SolveParams S) {
+  const int64_t n = *S.pl_count;
+  long long roots = 0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = S.pl_idx[j];
+    PairGeom G;
+    pair_geom(S, S.wl_key[i], G);  // listed by solve32_pair_k: the key is valid
+    const int64_t pt = S.wl_point[i];
+    const double E = polish64_pair(G, S.su[pt], S.sv[pt], S.polish_iters, S.tol, S.pl_u[j], S.pl_v[j]);
+    float c = 0.0f;
+    if (E >= 0.0) {
+      c = (float)(E / (double)S.wl_p[i]);
+      ++roots;
+    }
+    S.contrib[i] = c;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) roots += __shfl_xor_sync(0xffffffffu, roots, o);
+  if ((threadIdx.x & 31) == 0 && roots) atomicAdd((unsigned long long*)&S.counters[2], (unsigned long long)roots);
+}
+
 __global__ void reduce_k(const int64_t* __restrict__ woff, const float* __restrict__ contrib, int64_t n_points,
                          int64_t wl_cap, float* __restrict__ E_out) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_points; p += (int64_t)gridDim.x * blockDim.x) {
@@ -182,6 +250,7 @@ __global__ void reduce_k(const int64_t* __restrict__ woff, const float* __restri
 // ------------------------------------------------------------------ host side
 struct SampleWs {
   float4* tri;
+  float4* tri2;
   int64_t* n_sel;
   int64_t* woff;
   int64_t* wl_point;
@@ -195,7 +264,7 @@ struct SampleWs {
   size_t bytes;
 };
 
-static SampleWs carve_sample_ws(void* base, int64_t n_tris, int64_t n_points, int64_t wl_cap) {
+static SampleWs carve_sample_ws(void* base, int64_t n_tris, int64_t n_tris2, int64_t n_points, int64_t wl_cap) {
   SampleWs w{};
   size_t o = 0;
   auto take = [&](size_t b) -> char* {
@@ -204,6 +273,7 @@ static SampleWs carve_sample_ws(void* base, int64_t n_tris, int64_t n_points, in
     return p;
   };
   w.tri = (float4*)take((size_t)n_tris * kTriF4 * sizeof(float4));
+  w.tri2 = (float4*)take((size_t)n_tris2 * kTriF4 * sizeof(float4));
   w.n_sel = (int64_t*)take((size_t)n_points * 8);
   w.woff = (int64_t*)take((size_t)(n_points + 1) * 8);
   w.wl_point = (int64_t*)take((size_t)wl_cap * 8);
@@ -219,20 +289,21 @@ static SampleWs carve_sample_ws(void* base, int64_t n_tris, int64_t n_points, in
   return w;
 }
 
-size_t sample_ws_bytes(int64_t n_tris, int64_t n_points, int64_t wl_cap) {
-  return carve_sample_ws(nullptr, n_tris, n_points, wl_cap).bytes;
+size_t sample_ws_bytes(int64_t n_tris, int64_t n_tris2, int64_t n_points, int64_t wl_cap) {
+  return carve_sample_ws(nullptr, n_tris, n_tris2, n_points, wl_cap).bytes;
 }
 
-cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_receiver* rec, const bnb_emitters* em,
-                                    const bnb_index* idx, const float* su, const float* sv, int64_t n_points,
-                                    const bnb_sample_cfg* cfg, float* E_out, bnb_sample_stats* stats, void* ws,
-                                    cudaStream_t st) {
-  SampleWs w = carve_sample_ws(ws, s1->n_tris, n_points, cfg->worklist_capacity);
+cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
+                                    const bnb_emitters* em, const bnb_index* idx, const float* su, const float* sv,
+                                    int64_t n_points, const bnb_sample_cfg* cfg, float* E_out,
+                                    bnb_sample_stats* stats, void* ws, cudaStream_t st) {
+  SampleWs w = carve_sample_ws(ws, s1->n_tris, s2 ? s2->n_tris : 0, n_points, cfg->worklist_capacity);
   cudaError_t e;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if ((e = launch_pack_tris(s1, w.tri, st)) != cudaSuccess) return e;
+  if (s2 && (e = launch_pack_tris(s2, w.tri2, st)) != cudaSuccess) return e;
   if (n_points == 0) return cudaSuccess;
   SampleParams P{};
   P.offsets = idx->offsets;
@@ -289,7 +360,13 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_receiver* r
   S.pl_v = w.pl_v;
   if ((e = cudaMemsetAsync(w.pl_count, 0, sizeof(int64_t), st)) != cudaSuccess) return e;
   S.eta = s1->eta;
-  if (s1->kind == BNB_REFRACT) {
+  S.tri2 = w.tri2;
+  S.n_tris2 = s2 ? s2->n_tris : 0;
+  S.eta2 = s2 ? s2->eta : 1.0f;
+  if (s2) {
+    solve32_pair_k<<<sms * 16, 256, 0, st>>>(S);
+    polish_pair_k<<<sms * 16, 256, 0, st>>>(S);
+  } else if (s1->kind == BNB_REFRACT) {
     solve32_k<true><<<sms * 16, 256, 0, st>>>(S);
     polish_k<true><<<sms * 16, 256, 0, st>>>(S);
   } else {

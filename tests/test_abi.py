@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(bnb):
 def test_status_strings_and_version(bnb):
     assert bnb.bnb_status_string(0) == "ok"
     assert "capacity" in bnb.bnb_status_string(-2)
-    assert bnb.lib().bnb_abi_version() == 5
+    assert bnb.lib().bnb_abi_version() == 6
 
 
 def test_workspace_queries_are_host_only(bnb):
@@ -55,7 +55,15 @@ def test_workspace_queries_are_host_only(bnb):
     assert wb >= 2048 * 80
     assert bnb.bnb_build_index_ws(None, 512, 1000) > 512 * 512 * 8 * 3
     assert bnb.bnb_build_index_ws(None, 0, 1000) == 0
-    assert bnb.bnb_sample_and_solve_ws(C.byref(s), 4096, 10000) > 10000 * 24
+    assert bnb.bnb_sample_and_solve_ws(C.byref(s), None, 4096, 10000) > 10000 * 24
+    s2 = bnb.bnb_surface()
+    C.pointer(s2)[0] = s
+    s2.n_tris = 4608
+    s2.kind = s.kind = bnb.BNB_REFRACT
+    wp = bnb.bnb_bound_tuples_ws(C.byref(s), C.byref(s2), C.byref(em), C.byref(cfg))
+    assert wp >= (2048 + 4608) * 80 + 2048 * 16 * 16  # both packed meshes, per-cell counts and offsets
+    assert (bnb.bnb_sample_and_solve_ws(C.byref(s), C.byref(s2), 4096, 10000) -
+            bnb.bnb_sample_and_solve_ws(C.byref(s), None, 4096, 10000)) >= 4608 * 80
     bad = bnb.bnb_bound_cfg(11, 0, 1, 0)
     assert bnb.bnb_bound_tuples_ws(C.byref(s), None, C.byref(em), C.byref(bad)) == 0
 
@@ -70,10 +78,13 @@ def test_invalid_arguments_rejected_before_launch(bnb):
     out = bnb.bnb_cell_bounds()
     rc = bnb.bnb_bound_tuples(C.byref(s), None, C.byref(rec), C.byref(em), C.byref(cfg), C.byref(out), None, 0, None)
     assert rc == bnb.BNB_ERR_INVALID
-    # a second specular surface is not supported by this build
-    rc = bnb.bnb_bound_tuples(C.byref(s), C.byref(s), C.byref(rec), C.byref(em), C.byref(cfg), C.byref(out), None,
+    # two reflective vertices: chains need refraction at both
+    em_ok = bnb.bnb_emitters(1, 4096, 4096, 4096, 4096)
+    for f in ("px", "py", "pz", "nx", "ny", "nz", "i0", "i1", "i2"):
+        setattr(s, f, 4096)
+    rc = bnb.bnb_bound_tuples(C.byref(s), C.byref(s), C.byref(rec), C.byref(em_ok), C.byref(cfg), C.byref(out), None,
                               0, None)
-    assert rc in (bnb.BNB_ERR_INVALID, bnb.BNB_ERR_UNSUPPORTED)
+    assert rc == bnb.BNB_ERR_UNSUPPORTED
     idx = bnb.bnb_index()
     assert bnb.bnb_build_index(None, 1.0, 0, C.byref(idx), None, 0, None) == bnb.BNB_ERR_INVALID
     cells = bnb.bnb_cell_bounds()
