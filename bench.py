@@ -59,6 +59,29 @@ def bound_fma_per_cell() -> int:
 BOUND_FLOP_PER_CELL = 2 * bound_fma_per_cell()
 
 
+def pair_fma_per_record() -> int:
+    """FMAs of the value chain of one two-vertex record (tuple construction's candidate, composite
+    position bound with the degree reduction of u2), excluding error tracking and ratio logic."""
+    def refract_faces():  # degree-1 n, d -> the two faces of d~ (degree 5)
+        f = 3 * 3 * nc(1) * nc(1)               # n.n, d.n, d.d
+        f += 2 * nc(2) * nc(2) + 2 * nc(4)      # beta
+        f += 3 * 2 * nc(2) * nc(1) + 3 * nc(3)  # eta' ((n.n) d - (d.n) n)
+        f += 2 * (nc(4) + 3 * nc(4) * nc(1))    # W_j = a beta + b_j, d~ = T - W_j n
+        return f
+    f = refract_faces()                         # first vertex
+    f += 2 * 3 * 2 * nc(1)                      # e22 x w2, w2 x e21
+    f += 2 * (3 * nc(5) + 2 * 3 * nc(5) * nc(1))  # Q2, A2, B2 on both xi1 faces
+    f += 2 * 2 * nc(1) * nc(5)                  # remainder numerators P2 - l Q2
+    f += 3 * 2 * 2 * nc(1) + 3 * nc(1)          # x2, n2 from (u2, v2); d1 = x2 - x1
+    f += refract_faces()                        # second vertex
+    f += 2 * 3 * 2 * nc(1)                      # receiver h_u, h_v
+    f += 2 * (3 * nc(5) + 2 * 3 * nc(5) * nc(1))  # Q3, A3, B3 on both xi2 faces
+    return f
+
+
+PAIR_FLOP_PER_RECORD = 2 * pair_fma_per_record()
+
+
 def fp32_peak_tflops(sms: int, mhz: float) -> float:
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
@@ -331,6 +354,11 @@ def run_gpu(args):
         del cb, idx, cb_ws, ix_ws, sm_ws, flush
         torch.cuda.empty_cache()
         line["serving"] = serving_summary(args.serving_requests, dev)
+    if args.pairs_steps > 0 and rank == 0 and world == 1:
+        try:
+            line["pairs"] = pairs_summary(dev, args.pairs_steps, not args.no_cpu_baseline and not args.emitters)
+        except Exception as ex:  # reported in the line; the bound benchmark above stands
+            line["pairs"] = {"error": f"{type(ex).__name__}: {ex}"}
     if not args.no_cpu_baseline and rank == 0 and world == 1 and not args.emitters:
         line["cpu_baseline"] = cpu_baseline(counters[0] / n_points, counters[1] / n_points)
     if rank == 0:
@@ -425,6 +453,103 @@ def serving_summary(n_requests: int, dev) -> dict:
     return out
 
 
+def pairs_summary(dev, steps: int, oracle_too: bool) -> dict:
+    """The two-vertex workload (slab48: glass slab, two 48^2 faces, 512^2 points, depth 2), run after
+    the main timed region: bound pass (s2 grid, tuple construction, composite bounds), index,
+    rendering pass (chains carry no irradiance bound: P = 1), each timed with CUDA events over
+    `steps` steps after 3 warm-up steps, with a 256 MiB L2 flush between steps."""
+    import torch
+    from paper_2504_19163_gb300 import bnb
+    from paper_2504_19163_gb300 import scenes as S
+    sc = S.config("slab48")
+    ds = bnb.DeviceScene(sc, dev)
+    stream = torch.cuda.current_stream(dev)
+    cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False)
+    idx = bnb.build_index(cb, grid_res=sc.grid_res)
+    res = bnb.sample_and_solve(ds, idx, 1.0, 1)
+    torch.cuda.synchronize()
+    n_points = ds.n_points
+    n_base = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
+    wl_cap = int(res.counters[1].item()) * 2 + 4096
+    cfg = bnb.bnb_bound_cfg(sc.depth, 0, 0, 0)
+    cb_ws = bnb._ws(bnb.bnb_bound_tuples_ws(bnb.C.byref(ds.s1), ds.s2_ref(), bnb.C.byref(ds.em),
+                                            bnb.C.byref(cfg)), dev)
+    pre_cap = int(idx.count[1].item()) + int(idx.count[1].item()) // 4 + 4096
+    ix_ws = bnb._ws(bnb.bnb_build_index_ws(bnb.C.byref(cb.c), sc.grid_res, pre_cap), dev)
+    idx = bnb.Index(sc.grid_res, pre_cap, dev)
+    sm_ws = bnb._ws(bnb.bnb_sample_and_solve_ws(bnb.C.byref(ds.s1), ds.s2_ref(), n_points, wl_cap), dev)
+    E_out = torch.empty(n_points, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(seed, ev):
+        ev[0].record(stream)
+        bnb.bound_tuples(ds, sc.depth, out=cb, ws=cb_ws, sync_check=False)
+        ev[1].record(stream)
+        bnb.build_index(cb, grid_res=sc.grid_res, pre_capacity=pre_cap, capacity=pre_cap, out=idx, ws=ix_ws,
+                        sync_check=False)
+        ev[2].record(stream)
+        r = bnb.sample_and_solve(ds, idx, 1.0, seed, worklist_capacity=wl_cap, E_out=E_out, ws=sm_ws,
+                                 sync_check=False)
+        ev[3].record(stream)
+        return r
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(3 + steps)]
+    for i in range(3 + steps):
+        if i == 3:
+            torch.cuda.nvtx.range_push("pairs")  # lets a profiler select the timed steps
+        flush.zero_()
+        r = step(i, evs[i])
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    st = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs[3:]])
+    ok = int(cb.status.item()) == 0 and int(idx.status.item()) == 0 and int(r.status.item()) == 0
+    flags = cb.flags[: cb.n_records()]
+    n_rec = cb.n_records()
+    live = int(((flags & 1) != 0).sum().item())
+    c = r.counters.cpu().numpy()
+    ms = st.mean(axis=0)
+    props = torch.cuda.get_device_properties(dev)
+    try:
+        sm_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0))
+    except Exception:
+        sm_max = 2070.0
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    achieved = PAIR_FLOP_PER_RECORD * n_rec / (ms[0] / 1e3) / 1e12
+    out = {"workload": "slab48: glass slab (ior 1.5), two 48^2 heightfield faces (4608 tris each), point light "
+                       "(0,0,2), receiver z=-1, 512^2 shading points, depth 2 (73,728 base cells), FP32",
+           "status_ok": ok, "steps": steps, "base_cells": n_base, "pair_records": n_rec, "live_records": live,
+           "records_per_base_cell": n_rec / n_base,
+           "stage_ms": {"bound": float(ms[0]), "index": float(ms[1]), "sample_solve": float(ms[2])},
+           "pair_records_per_s": n_rec / (ms[0] / 1e3), "base_cells_per_s": n_base / (ms[0] / 1e3),
+           "shading_samples_per_s": n_points / (ms[2] / 1e3),
+           "per_point": {"U": c[0] / n_points, "S": c[1] / n_points, "roots": c[2] / n_points},
+           "roofline": {"bound": "alu", "kernel": "pair bound stage (s2 grid, candidates, pair_bound_k<float>)",
+                        "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "flop_per_record": PAIR_FLOP_PER_RECORD}}
+    del cb, idx, cb_ws, ix_ws, sm_ws, flush
+    torch.cuda.empty_cache()
+    if oracle_too:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(1) as pool:
+            out["oracle"] = pool.apply(_pairs_oracle_worker, ())
+    return out
+
+
+def _pairs_oracle_worker():
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2504_19163_gb300 import scenes as S
+    oracle.build()
+    sc = S.config("slab48")
+    n_threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    rec = oracle.bound_pair_scene(sc, n_threads=n_threads)
+    dt = time.perf_counter() - t0
+    return {"kind": "oracle", "cores": n_threads, "bound_s": dt, "pair_records": int(rec.shape[0]),
+            "pair_records_per_s": rec.shape[0] / dt,
+            "sample": "the whole slab48 bound pass (candidates by brute force over every T2, then the records)"}
+
+
 def cpu_baseline(u_per_point: float, s_per_point: float) -> dict:
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
@@ -457,6 +582,8 @@ def main():
     ap.add_argument("--emitters", type=int, default=0, help="use only the first N area-light samples (profiling case)")
     ap.add_argument("--serving-requests", type=int, default=256,
                     help="requests of the serving workload reported under 'serving' (0: skip)")
+    ap.add_argument("--pairs-steps", type=int, default=10,
+                    help="timed steps of the two-vertex slab48 workload reported under 'pairs' (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -764,10 +764,21 @@ static __device__ __noinline__ void process_pair_fp64(const PairParams& P, int64
   process_pair<double>(P, slot, BNB_CELL_QSIGN_FP64);
 }
 
+// Persistent: the blocks resident on the GPU step through the records in rounds with a block
+// barrier per round, so the warps of a block walk the long record program together and share its
+// instruction fetches.  Three 128-thread blocks per SM (<= 170 registers, ~3 KB of spills) ran the
+// slab48 bound stage in 0.600 ms against 0.688 ms with two (255 registers) and 0.733 ms with four.
+constexpr int kPairThreads = 128;
+
 template <bool FP64>
-__global__ void __launch_bounds__(128) pair_bound_k(PairParams P) {
+__global__ void __launch_bounds__(kPairThreads, 3) pair_bound_k(PairParams P) {
   const int64_t n = min(*P.count, P.capacity);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * kPairThreads;
+  const int64_t rounds = (n + stride - 1) / stride;
+  for (int64_t r = 0; r < rounds; ++r) {
+    __syncthreads();
+    const int64_t i = r * stride + (int64_t)blockIdx.x * kPairThreads + threadIdx.x;
+    if (i >= n) continue;
     if constexpr (FP64) {
       process_pair<double>(P, i, 0u);
     } else {
@@ -893,10 +904,14 @@ cudaError_t launch_bound_pairs(const bnb_surface* s1, const bnb_surface* s2, con
   if ((e = launch_exclusive_scan(w.cand_count, w.cand_off, n_base, w.scan, st)) != cudaSuccess) return e;
   pair_cand_k<true><<<cb, 128, 0, st>>>(P);
   pair_total_k<<<1, 1, 0, st>>>(w.cand_off, n_base, out->capacity, out->count, out->status);
-  if (fp64)
-    pair_bound_k<true><<<sms * 8, 128, 0, st>>>(P);
-  else
-    pair_bound_k<false><<<sms * 8, 128, 0, st>>>(P);
+  int per_sm = 1;  // resident blocks per SM of the record kernel
+  if (fp64) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_bound_k<true>, kPairThreads, 0);
+    pair_bound_k<true><<<sms * std::max(1, per_sm), kPairThreads, 0, st>>>(P);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_bound_k<false>, kPairThreads, 0);
+    pair_bound_k<false><<<sms * std::max(1, per_sm), kPairThreads, 0, st>>>(P);
+  }
   return cudaGetLastError();
 }
 

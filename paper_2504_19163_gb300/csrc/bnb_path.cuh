@@ -374,9 +374,8 @@ __device__ __forceinline__ Path2<T> eval_pair(const PairGeom& G, T u, T v) {
   return r;
 }
 
-// Pair counterparts of newton32 / polish64: the same damped float32 phase (also rejecting a
-// root converged more than kOutside outside T2), then float64 polish steps and the acceptance
-// tests (u1 in the closed T1, u2 in the closed T2, both hits in front).
+// Pair counterpart of newton32: the same damped float32 phase, also rejecting a root converged more
+// than kOutside outside T2.
 __device__ __forceinline__ bool newton32_pair(const PairGeom& G, float tuf, float tvf, int newton_iters, float& u,
                                               float& v) {
   u = 1.0f / 3.0f;
@@ -398,24 +397,108 @@ __device__ __forceinline__ bool newton32_pair(const PairGeom& G, float tuf, floa
   return !(fminf(fminf(P.u2, P.v2), 1.0f - P.u2 - P.v2) < -kOutside);
 }
 
+// The chain's values only (no derivatives): receiver coordinates, T2 barycentrics and both ray
+// parameters; ok is false where a vertex has no refracted path.
+template <typename T>
+struct Hit2 {
+  T uk, vk, u2, v2, t1, t2;
+  bool ok;
+};
+
+template <typename T>
+__device__ __forceinline__ Hit2<T> eval_pair_value(const PairGeom& G, T u, T v) {
+  Hit2<T> h{};
+  h.ok = false;
+  auto dot = [](const T* a, const T* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+  auto cross = [](const T* a, const T* b, T* r) {
+    r[0] = a[1] * b[2] - a[2] * b[1];
+    r[1] = a[2] * b[0] - a[0] * b[2];
+    r[2] = a[0] * b[1] - a[1] * b[0];
+  };
+  auto refract = [&](const T* n, const T* d, T eta, T* out) {
+    const T nn = dot(n, n), dn = dot(d, n), ss = dot(d, d);
+    const T beta = (T(1) - eta * eta) * (nn * ss) + (eta * eta) * (dn * dn);
+    if (!(beta > T(0))) return false;
+    const T W = sqrt(beta);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = eta * (nn * d[c] - dn * n[c]) - W * n[c];
+    return true;
+  };
+  auto plane = [&](const T* x, const T* d, const T* o, const T* e1, const T* e2, T& a, T& b, T& t) {
+    T w[3], g[3], h1[3], h2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w[c] = x[c] - o[c];
+    cross(e2, e1, g);
+    cross(e2, w, h1);
+    cross(w, e1, h2);
+    const T q = dot(d, g);
+    a = dot(d, h1) / q;
+    b = dot(h2, d) / q;
+    t = dot(h2, e2) / q;
+  };
+  T x1[3], n1[3], d0[3], o2[3], e21[3], e22[3], R0[3], R1[3], R2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T p0 = (T)G.p1[0][c];
+    x1[c] = p0 + u * ((T)G.p1[1][c] - p0) + v * ((T)G.p1[2][c] - p0);
+    const T m0 = (T)G.n1[0][c];
+    n1[c] = m0 + u * ((T)G.n1[1][c] - m0) + v * ((T)G.n1[2][c] - m0);
+    d0[c] = x1[c] - (T)G.x0[c];
+    o2[c] = (T)G.p2[0][c];
+    e21[c] = (T)G.p2[1][c] - o2[c];
+    e22[c] = (T)G.p2[2][c] - o2[c];
+    R0[c] = (T)G.rp0[c];
+    R1[c] = (T)G.re1[c];
+    R2[c] = (T)G.re2[c];
+  }
+  T t1d[3];
+  if (!refract(n1, d0, (T)G.eta1, t1d)) return h;
+  plane(x1, t1d, o2, e21, e22, h.u2, h.v2, h.t1);
+  T x2[3], n2[3], d1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    x2[c] = o2[c] + h.u2 * e21[c] + h.v2 * e22[c];
+    const T m0 = (T)G.n2[0][c];
+    n2[c] = m0 + h.u2 * ((T)G.n2[1][c] - m0) + h.v2 * ((T)G.n2[2][c] - m0);
+    d1[c] = x2[c] - x1[c];
+  }
+  T t2d[3];
+  if (!refract(n2, d1, (T)G.eta2, t2d)) return h;
+  plane(x2, t2d, R0, R1, R2, h.uk, h.vk, h.t2);
+  h.ok = isfinite(h.uk) && isfinite(h.vk) && isfinite(h.u2) && isfinite(h.v2);
+  return h;
+}
+
+// Mixed-precision polish: Newton steps whose residual is evaluated in float64 (the chain's values
+// only) and whose Jacobian is the float32 one at the float32 root (iterative refinement: from a
+// root known to ~1e-6 with a Jacobian accurate to ~1e-6, one step leaves ~1e-12).  Acceptance
+// tests in float64 at the polished root; E from the float32 derivatives there.
 __device__ __forceinline__ double polish64_pair(const PairGeom& G, float tuf, float tvf, int polish_iters, float tol,
                                                 float u, float v) {
+  const Path2<float> Pf = eval_pair<float>(G, u, v);
+  const double J00 = Pf.J00, J01 = Pf.J01, J10 = Pf.J10, J11 = Pf.J11;
+  const double det = J00 * J11 - J01 * J10;
+  if (!Pf.ok || !(det != 0.0) || !isfinite(det)) return -1.0;
   double ud = u, vd = v;
-  bool good = true;
-  for (int it = 0; it < polish_iters && good; ++it) {
-    const Path2<double> P = eval_pair<double>(G, ud, vd);
-    double step;
-    good = newton_step<double>(P, (double)tuf, (double)tvf, false, ud, vd, step);
+  for (int it = 0; it < polish_iters; ++it) {
+    const Hit2<double> H = eval_pair_value<double>(G, ud, vd);
+    if (!H.ok) return -1.0;
+    const double fu = H.uk - (double)tuf, fv = H.vk - (double)tvf;
+    ud -= (J11 * fu - J01 * fv) / det;
+    vd -= (-J10 * fu + J00 * fv) / det;
+    if (!isfinite(ud) || !isfinite(vd)) return -1.0;
   }
-  if (!good) return -1.0;
-  const Path2<double> P = eval_pair<double>(G, ud, vd);
-  const double fu = P.uk - (double)tuf, fv = P.vk - (double)tvf;
+  const Hit2<double> H = eval_pair_value<double>(G, ud, vd);
+  if (!H.ok) return -1.0;
+  const double fu = H.uk - (double)tuf, fv = H.vk - (double)tvf;
   const double r0 = fu * G.re1[0] + fv * G.re2[0], r1 = fu * G.re1[1] + fv * G.re2[1], r2 = fu * G.re1[2] + fv * G.re2[2];
   const double res = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
   const bool in1 = ud >= 0.0 && vd >= 0.0 && ud + vd <= 1.0;
-  const bool in2 = P.u2 >= 0.0 && P.v2 >= 0.0 && P.u2 + P.v2 <= 1.0;
-  if (P.ok && res < (double)tol && in1 && in2 && P.t > 0.0 && P.t2 > 0.0 && isfinite(P.E)) return P.E;
-  return -1.0;
+  const bool in2 = H.u2 >= 0.0 && H.v2 >= 0.0 && H.u2 + H.v2 <= 1.0;
+  if (!(res < (double)tol && in1 && in2 && H.t1 > 0.0 && H.t2 > 0.0)) return -1.0;
+  const Path2<float> Pe = eval_pair<float>(G, (float)ud, (float)vd);
+  if (!Pe.ok || !isfinite(Pe.E)) return -1.0;
+  return (double)Pe.E;
 }
 
 // Appends the calling lane to a device list when `need` is set (one atomic per warp); returns the
