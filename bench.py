@@ -82,6 +82,15 @@ def pair_fma_per_record() -> int:
 PAIR_FLOP_PER_RECORD = 2 * pair_fma_per_record()
 
 
+# Algorithmic bytes of the HBM-bound stages: the index reads a live cell's box, E_hi, keys and flags
+# (36 B; 4 B of flags for the others) and writes 12 B (key, E~) per (grid cell, tuple) entry plus the
+# offsets; the sampling pass reads 12 B per listed entry and writes 16 B per selection (point, key,
+# P), the solve reads 72 B of geometry + 12 B of emitter per selection and writes 4 B; per point
+# 8 B of coordinates + 4 B of estimate.
+INDEX_BYTES_LIVE, INDEX_BYTES_ENTRY = 36, 12
+SAMPLE_BYTES_LISTED, SOLVE_BYTES_SELECTED, SAMPLE_BYTES_POINT = 12, 16 + 72 + 12 + 4, 12
+
+
 def fp32_peak_tflops(sms: int, mhz: float) -> float:
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
@@ -327,6 +336,23 @@ def run_gpu(args):
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
     achieved = BOUND_FLOP_PER_CELL * n_cells / (bound_ms / 1e3) / 1e12
     traffic = bound_traffic()
+    # HBM accounting of the other stages (algorithmic bytes over their CUDA-event stage times)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    n_rec = cb.n_records()
+    n_live = int(((cb.flags[:n_rec] & 1) != 0).sum().item())
+    n_entries = int(idx.count[0].item())
+    index_bytes = INDEX_BYTES_LIVE * n_live + 4 * (n_rec - n_live) + INDEX_BYTES_ENTRY * n_entries + \
+        8 * (sc.grid_res ** 2 + 1)
+    ss_bytes = SAMPLE_BYTES_LISTED * float(counters[0]) + SOLVE_BYTES_SELECTED * float(counters[1]) + \
+        SAMPLE_BYTES_POINT * n_points
+    stage_ms = {"bound": bound_ms, "index": float(stage[:, 1].mean()), "sample_solve": float(stage[:, 2].mean())}
+    stage_roofline = {
+        "index": {"bound": "hbm", "bytes": index_bytes, "achieved": index_bytes / (stage_ms["index"] / 1e3) / 1e9,
+                  "peak": hbm, "unit": "GB/s", "live_cells": n_live, "entries": n_entries},
+        "sample_solve": {"bound": "hbm", "bytes": ss_bytes,
+                         "achieved": ss_bytes / (stage_ms["sample_solve"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"}}
+    for v in stage_roofline.values():
+        v["frac"] = v["achieved"] / v["peak"]
 
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -338,8 +364,8 @@ def run_gpu(args):
                        "gamma": gamma, "cells_per_step": n_cells, "points_per_step": n_points,
                        "status_ok": st_ok},
             "shading_samples_per_s": n_points * world / (ms_max / 1e3),
-            "stage_ms": {"bound": bound_ms, "index": float(stage[:, 1].mean()),
-                         "sample_solve": float(stage[:, 2].mean())},
+            "stage_ms": stage_ms,
+            "stage_roofline": stage_roofline,
             "per_point": {"U": counters[0] / n_points, "S": counters[1] / n_points, "roots": counters[2] / n_points},
             "roofline": {"bound": "alu", "kernel": "bound_base_k<float>", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
@@ -440,7 +466,7 @@ def serving_summary(n_requests: int, dev) -> dict:
         res = SV.run_workload(n_requests, device=dev, log=lambda *a: None)
     except Exception as ex:  # reported in the line; the bound benchmark above stands
         return {"error": f"{type(ex).__name__}: {ex}"}
-    keep = ("p50_ms", "p99_ms", "samples_per_s", "requests_per_s", "mean_batch")
+    keep = ("p50_ms", "p99_ms", "samples_per_s", "requests_per_s", "mean_batch", "traces")
     out = {"workload": res["workload"], "capacity_req_per_s": res["capacity_req_per_s"],
            "served_equals_alone": res["served_equals_alone"], "autotuned_launch": res.get("autotuned_launch"),
            "scene_build_s": res["scene_build_s"]}

@@ -538,8 +538,27 @@ def summarize(reqs: List[Request]) -> dict:
             "samples_per_s": pts / span, "requests_per_s": len(ok) / span, "span_s": span}
 
 
+def pooled(traces: List[dict]) -> dict:
+    """Several traces of the same requests: percentiles over every trace's latencies (key `_lat`),
+    throughput and the other figures averaged over the traces."""
+    if len(traces) == 1:
+        return {k: v for k, v in traces[0].items() if k != "_lat"}
+    lat = np.concatenate([t["_lat"] for t in traces])
+    out = {k: float(np.mean([t[k] for t in traces])) for k in traces[0]
+           if k not in ("_lat", "requests", "completed") and isinstance(traces[0][k], (int, float))}
+    out.update(requests=int(sum(t["requests"] for t in traces)), completed=int(sum(t["completed"] for t in traces)),
+               traces=len(traces), p50_ms=float(np.percentile(lat, 50) * 1e3),
+               p99_ms=float(np.percentile(lat, 99) * 1e3), mean_ms=float(lat.mean() * 1e3))
+    return out
+
+
+def with_latencies(res: dict, reqs: List[Request]) -> dict:
+    res["_lat"] = np.array([r.latency for r in reqs if r.E is not None and r.status == 0])
+    return res
+
+
 def run_workload(n_requests: int = 256, seed: int = 5, load: float = 0.7, device="cuda", max_jobs: int = 64,
-                 max_points: int = 1 << 22, autotune_launch: bool = True, log=print) -> dict:
+                 max_points: int = 1 << 22, autotune_launch: bool = True, log=print, trace_reps: int = 3) -> dict:
     """The serving workload: `n_requests` requests over the catalogue (scene uniform, 64^2..1024^2
     points, 1..8 lights of the scene's pool), served three ways (plain per request, plain on
     resident scenes, continuous batching) on three arrival traces:
@@ -549,12 +568,16 @@ def run_workload(n_requests: int = 256, seed: int = 5, load: float = 0.7, device
     * load_cached: Poisson arrivals at `load` x the measured capacity of the plain path on
                    resident scenes (one request at a time, no batching);
     * burst      : every request arrives at once (throughput).
+    The load_cached and burst traces are run `trace_reps` times (arrival seeds seed+1, seed+2, ...)
+    and their latency percentiles pooled: a p99 of one 256-request trace is its third-largest
+    latency and varies by 2x between runs of the same trace.
     Every served estimate is checked bit for bit against the same request served alone."""
     from . import batch as BA
     cache = SceneCache(S.serving_scene, device=device)
     out = {"workload": f"{n_requests} requests, scenes {'/'.join(S.SERVING_SCENES)}, {SIDES[0]}^2..{SIDES[-1]}^2 "
                        f"points, 1..{S.SERVING_POOL} lights of a pool of {S.SERVING_POOL}; Poisson arrivals at "
-                       f"{load} x the capacity of each plain path, and a burst"}
+                       f"{load} x the capacity of each plain path, and a burst; load_cached and burst latencies pooled over "
+                       f"{max(1, trace_reps)} traces"}
     try:
         t = time.perf_counter()
         entries = cache.prefetch(S.SERVING_SCENES)  # one batched bound launch for the catalogue
@@ -614,29 +637,33 @@ def run_workload(n_requests: int = 256, seed: int = 5, load: float = 0.7, device
             same = all(r.E is not None and np.array_equal(r.E.view(np.uint32), alone[r.rid].view(np.uint32))
                        for r in reqs)
             identical = identical and same
-            log(f"{tag:12s} served       {res}")
+            log(f"{tag:12s} served       {res['p50_ms']:.2f} / {res['p99_ms']:.2f} ms, mean batch {res['mean_batch']:.2f}")
             return res
 
-        for tag, rate, modes in (("load_plain", load * cap_plain, ("plain", "plain_cached", "served")),
-                                 ("load_cached", load * cap_cached, ("plain_cached", "served")),
-                                 ("burst", math.inf, ("plain_cached", "served"))):
-            if math.isinf(rate):
-                for r in reqs:
-                    r.arrival = 0.0
-            else:
-                poisson_arrivals(reqs, rate, seed + 1)
+        for tag, rate, modes, reps in (("load_plain", load * cap_plain, ("plain", "plain_cached", "served"), 1),
+                                       ("load_cached", load * cap_cached, ("plain_cached", "served"), trace_reps),
+                                       ("burst", math.inf, ("plain_cached", "served"), trace_reps)):
             block = {"arrival_rate_req_per_s": None if math.isinf(rate) else rate}
-            for m in modes:
-                if m == "served":
-                    block[m] = serve_trace(tag)
-                    continue
-                reset(reqs)
-                if m == "plain":
-                    plain_per_request(reqs, S.serving_scene, gammas, device)
+            runs: Dict[str, List[dict]] = {m: [] for m in modes}
+            for k in range(max(1, reps)):
+                if math.isinf(rate):
+                    for r in reqs:
+                        r.arrival = 0.0
                 else:
-                    plain_cached(reqs, cache, runners=runners)
-                block[m] = summarize(reqs)
-                log(f"{tag:12s} {m:12s} {block[m]}")
+                    poisson_arrivals(reqs, rate, seed + 1 + k)
+                for m in modes:
+                    if m == "served":
+                        runs[m].append(with_latencies(serve_trace(tag), reqs))
+                        continue
+                    reset(reqs)
+                    if m == "plain":
+                        plain_per_request(reqs, S.serving_scene, gammas, device)
+                    else:
+                        plain_cached(reqs, cache, runners=runners)
+                    runs[m].append(with_latencies(summarize(reqs), reqs))
+                    log(f"{tag:12s} {m:12s} {runs[m][-1]['p50_ms']:.2f} / {runs[m][-1]['p99_ms']:.2f} ms")
+            for m in modes:
+                block[m] = pooled(runs[m])
             out[tag] = block
         out["served_equals_alone"] = identical
         log(f"every served estimate identical to the request served alone: {identical}")
@@ -654,8 +681,9 @@ if __name__ == "__main__":
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--load", type=float, default=0.7)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--trace-reps", type=int, default=3, help="repetitions of the load_cached and burst traces")
     a = ap.parse_args()
     from . import build as _build
     _build.build()
-    res = run_workload(a.requests, a.seed, a.load, autotune_launch=not a.no_autotune)
+    res = run_workload(a.requests, a.seed, a.load, autotune_launch=not a.no_autotune, trace_reps=a.trace_reps)
     print(json.dumps(res))

@@ -111,3 +111,16 @@ def test_summary_percentiles():
     assert abs(s["p50_ms"] - 50.5) < 1e-6
     assert abs(s["p99_ms"] - np.percentile(np.arange(1, 101), 99)) < 1e-6
     assert abs(s["samples_per_s"] - 100 * 64 * 64 / (99 + 0.1)) < 1e-6
+
+
+def test_pooled_traces_take_percentiles_over_all_latencies():
+    a = {"requests": 100, "completed": 100, "p50_ms": 0.0, "p99_ms": 0.0, "mean_ms": 0.0, "samples_per_s": 10.0,
+         "requests_per_s": 1.0, "span_s": 1.0, "_lat": np.linspace(0.001, 0.100, 100)}
+    b = dict(a, samples_per_s=30.0, _lat=np.linspace(0.101, 0.200, 100))
+    p = SV.pooled([a, b])
+    lat = np.concatenate([a["_lat"], b["_lat"]])
+    assert p["traces"] == 2 and p["requests"] == 200 and p["completed"] == 200
+    assert abs(p["p99_ms"] - np.percentile(lat, 99) * 1e3) < 1e-9
+    assert abs(p["p50_ms"] - np.percentile(lat, 50) * 1e3) < 1e-9
+    assert p["samples_per_s"] == 20.0
+    assert "_lat" not in SV.pooled([a])
