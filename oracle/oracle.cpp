@@ -438,7 +438,38 @@ struct Ctx {
   const orc_emitters* em;
   int irradiance;
   int max_total_depth;
+  // adaptive subdivision (Sec. 6.1 "Domain subdivision"): off when adapt_depth <= the base depth
+  int adapt_depth = 0;
+  float sigma = 0.0f, alpha = 0.0f;
 };
+
+float f32_down(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = std::nextafter(f, -std::numeric_limits<float>::infinity());
+  return f;
+}
+float f32_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+  return f;
+}
+
+// Adaptive subdivision (Sec. 6.1 "Domain subdivision"): a live cell with a bounded box, above the
+// depth limit, is subdivided again unless its receiver box (U_k) has area below sigma or its
+// irradiance bounds satisfy E_hi < alpha E_lo.  The decision is taken on the record as stored in
+// float32 (box rounded outward, area and alpha E_lo as float32 products), the precision in which
+// the CUDA path takes it.  Returns true (and turns r into a SPLIT record) when the cell splits.
+bool adaptive_split(const Ctx& cx, orc_record& r, int depth) {
+  if (depth >= cx.adapt_depth || !(r.flags & F_LIVE) || (r.flags & F_POS_UNBOUNDED)) return false;
+  const float du = f32_up(r.u_hi) - f32_down(r.u_lo), dv = f32_up(r.v_hi) - f32_down(r.v_lo);
+  const float area = du * dv;
+  if (area < cx.sigma) return false;
+  const float el = f32_down(r.e_lo), eh = f32_up(r.e_hi);
+  if (eh < cx.alpha * el) return false;
+  r.flags = (r.flags & ~(F_LIVE | F_FOLD)) | F_SPLIT;
+  r.u_lo = r.u_hi = r.v_lo = r.v_hi = r.e_lo = r.e_hi = 0.0;
+  return true;
+}
 
 double cond_of(const Poly& p) {
   double mn = std::numeric_limits<double>::infinity(), mx = 0.0;
@@ -538,10 +569,16 @@ void bound_cell_reflect(const Ctx& cx, int e, int t, uint32_t id, int depth, std
     return;
   }
   r.flags |= F_LIVE;
+  auto finish = [&]() {
+    const bool split = adaptive_split(cx, r, depth);
+    out.push_back(r);
+    if (split)
+      for (int k = 0; k < 4; ++k) bound_cell_reflect(cx, e, t, id * 4u + (uint32_t)k, depth + 1, out);
+  };
   if (!cx.irradiance) {
     r.e_lo = 0.0;
     r.e_hi = std::numeric_limits<double>::infinity();
-    out.push_back(r);
+    finish();
     return;
   }
   // Eq. eq_irr_term3a: det(du_k/dmu) = M / Q^3 with a = Pu, b = Pv.
@@ -567,7 +604,7 @@ void bound_cell_reflect(const Ctx& cx, int e, int t, uint32_t id, int depth, std
     r.flags |= F_FOLD;
     r.e_lo = 0.0;
     r.e_hi = std::numeric_limits<double>::infinity();
-    out.push_back(r);
+    finish();
     return;
   }
   Poly s = pv_dot(d0, d0);
@@ -588,7 +625,7 @@ void bound_cell_reflect(const Ctx& cx, int e, int t, uint32_t id, int depth, std
   }
   r.e_lo = K * lo;
   r.e_hi = K * hi;
-  out.push_back(r);
+  finish();
 }
 
 // Bound one cell of one (emitter, triangle) tuple for single refraction (Eq. eq_refr_rational,
@@ -698,8 +735,14 @@ void bound_cell_refract(const Ctx& cx, int e, int t, uint32_t id, int depth, std
   r.flags |= F_LIVE;
   r.e_lo = 0.0;
   r.e_hi = std::numeric_limits<double>::infinity();
-  if (!cx.irradiance) {
+  auto finish = [&]() {
+    const bool split = adaptive_split(cx, r, depth);
     out.push_back(r);
+    if (split)
+      for (int k = 0; k < 4; ++k) bound_cell_refract(cx, e, t, id * 4u + (uint32_t)k, depth + 1, out);
+  };
+  if (!cx.irradiance) {
+    finish();
     return;
   }
   // Irradiance (Eqs. eq_dwda, eq_irr_term3a) with sqrt(beta) kept as the symbol W: the
@@ -759,7 +802,7 @@ void bound_cell_refract(const Ctx& cx, int e, int t, uint32_t id, int depth, std
     r.m_cond = std::min(cond_of(Mf[0]), cond_of(Mf[1]));
     if (sm[0] == 0 || sm[0] != sm[1]) {
       r.flags |= F_FOLD;
-      out.push_back(r);
+      finish();
       return;
     }
     V3 N1 = cross(e11, e12);
@@ -786,7 +829,7 @@ void bound_cell_refract(const Ctx& cx, int e, int t, uint32_t id, int depth, std
     r.e_lo = K * std::max(lo, 0.0);
     r.e_hi = K * hi;
   }
-  out.push_back(r);
+  finish();
 }
 
 void decode_work(int64_t i, int n_tris, int depth, int* e, int* t, uint32_t* c) {
@@ -1541,9 +1584,11 @@ void orc_cell_corners(uint32_t id, int depth, double* out6) {
 // order.  Returns 0, or -2 when cap is too small (n_out then holds the need).
 int orc_bound(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, int32_t depth,
               int32_t max_extra_split, int32_t irradiance, const int64_t* work, int64_t n_work,
-              orc_record* out, int64_t cap, int64_t* n_out, int32_t n_threads) {
+              orc_record* out, int64_t cap, int64_t* n_out, int32_t n_threads, int32_t adapt_depth, float sigma,
+              float alpha) {
   if (s1->kind != 0 && s1->kind != 1) return -4;
-  Ctx cx{s1, get_rec(rec), em, irradiance, depth + max_extra_split};
+  // sign-test splits may go max_extra_split levels below the deepest adaptive level
+  Ctx cx{s1, get_rec(rec), em, irradiance, std::max(depth, adapt_depth) + max_extra_split, adapt_depth, sigma, alpha};
   int64_t total = work ? n_work : (int64_t)em->n * s1->n_tris * ((int64_t)1 << (2 * depth));
   int nt = std::max(1, (int)n_threads);
   std::vector<std::vector<orc_record>> parts(nt);

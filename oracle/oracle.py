@@ -77,7 +77,7 @@ def lib():
             L.orc_bb_eval.restype = f64
             L.orc_philox_uniform.restype = f32
             L.orc_philox_uniform.argtypes = [u64, i64, u64]
-            L.orc_bound.argtypes = [vp, vp, vp, i32, i32, i32, vp, i64, vp, i64, vp, i32]
+            L.orc_bound.argtypes = [vp, vp, vp, i32, i32, i32, vp, i64, vp, i64, vp, i32, i32, f32, f32]
             L.orc_index.argtypes = [vp] * 9 + [i64, i32, f32, vp, vp, vp, i64, vp]
             L.orc_sample.argtypes = [vp, vp, vp, i32, vp, vp, i64, f32, u64, vp, vp, vp, i64, vp, vp]
             L.orc_solve.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, i32, i32, f64, vp, vp, vp, vp, i32]
@@ -202,8 +202,11 @@ def cell_corners(cell_id: int, depth: int) -> np.ndarray:
 
 # ------------------------------------------------------------------ pipeline stages
 def bound(scene, depth: Optional[int] = None, max_extra_split: int = 4, irradiance: bool = True,
-          work: Optional[np.ndarray] = None, n_threads: int = 1) -> np.ndarray:
-    """Cell records (structured array, RECORD_DTYPE) for all base cells or the given work items."""
+          work: Optional[np.ndarray] = None, n_threads: int = 1, adapt_depth: int = 0, sigma: float = 0.0,
+          alpha: float = 0.0) -> np.ndarray:
+    """Cell records (structured array, RECORD_DTYPE) for all base cells or the given work items.
+    adapt_depth > depth: adaptive subdivision (Sec. 6.1) down to adapt_depth, stopping at box area
+    < sigma or E_hi < alpha E_lo."""
     L = lib()
     V = _SceneViews(scene)
     d = scene.depth if depth is None else depth
@@ -218,7 +221,7 @@ def bound(scene, depth: Optional[int] = None, max_extra_split: int = 4, irradian
         out = np.zeros(cap, RECORD_DTYPE)
         n_out = np.zeros(1, np.int64)
         rc = L.orc_bound(C.byref(V.surf), C.byref(V.rec), C.byref(V.em), d, max_extra_split, int(irradiance),
-                         wp, n_work, _p(out), cap, _p(n_out), n_threads)
+                         wp, n_work, _p(out), cap, _p(n_out), n_threads, adapt_depth, sigma, alpha)
         if rc == -2:
             cap = int(n_out[0])
             continue
