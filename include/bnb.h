@@ -99,6 +99,17 @@ typedef struct bnb_bound_cfg {
   int32_t max_extra_split; /* extra splits of a cell whose denominator sign test fails (0..4) */
   int32_t irradiance;      /* 1: irradiance bound (Sec. 4.4); 0: position only, e_hi = +inf */
   int32_t fp64;            /* 1: the whole bound pass in float64 (same arithmetic, u = 2^-53) */
+  /* Adaptive subdivision (Sec. 6.1 "Domain subdivision"), on when adapt_depth > depth: a live cell
+   * with a bounded box at depth < adapt_depth is subdivided again unless its receiver box has area
+   * (u_hi - u_lo)(v_hi - v_lo) < sigma or e_hi < alpha * e_lo, both taken in float32 on the stored
+   * record (e_hi = +inf never stops by the ratio).  Sign-test splits may then go max_extra_split
+   * levels below adapt_depth.  One emitter/triangle pass, not the batched or the two-vertex pass. */
+  int32_t adapt_depth;     /* 0 or depth..15 (adapt_depth + max_extra_split <= 15) */
+  float sigma;             /* >= 0 */
+  float alpha;             /* >= 0 */
+  int32_t reserved;        /* 0 */
+  int64_t split_capacity;  /* split-queue entries per level (0: 4096 + n_base / 32); a level that
+                              queues more raises BNB_ERR_CAPACITY */
 } bnb_bound_cfg;
 
 /* Per-cell bound records, SoA device arrays of `capacity` entries.  Slots
@@ -330,7 +341,7 @@ size_t bnb_bound_tuples_batched_ws(int32_t max_jobs);
 const char *bnb_status_string(int32_t status);
 
 /* ABI version of this header (increments on any struct or signature change). */
-int32_t bnb_abi_version(void);  /* 6 */
+int32_t bnb_abi_version(void);  /* 7 */
 
 #ifdef __cplusplus
 }

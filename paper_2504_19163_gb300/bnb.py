@@ -46,7 +46,8 @@ class bnb_emitters(C.Structure):
 
 
 class bnb_bound_cfg(C.Structure):
-    _fields_ = [("depth", i32), ("max_extra_split", i32), ("irradiance", i32), ("fp64", i32)]
+    _fields_ = [("depth", i32), ("max_extra_split", i32), ("irradiance", i32), ("fp64", i32), ("adapt_depth", i32),
+                ("sigma", f32), ("alpha", f32), ("reserved", i32), ("split_capacity", i64)]
 
 
 class bnb_cell_bounds(C.Structure):
@@ -356,17 +357,28 @@ class Index:
 def bound_tuples(ds: DeviceScene, depth: int, max_extra_split: int = 4, irradiance: bool = True,
                  fp64: bool = False, capacity: Optional[int] = None, out: Optional[CellBounds] = None,
                  ws: Optional[torch.Tensor] = None, stream=None, sync_check: bool = True,
-                 with_e_hi_min: bool = False, with_e_lo: bool = True) -> CellBounds:
-    cfg = bnb_bound_cfg(depth, max_extra_split, int(irradiance), int(fp64))
+                 with_e_hi_min: bool = False, with_e_lo: bool = True, adapt_depth: int = 0, sigma: float = 0.0,
+                 alpha: float = 0.0, split_capacity: int = 0) -> CellBounds:
+    """Bound pass (one or two specular vertices).  adapt_depth > depth: adaptive subdivision
+    (Sec. 6.1) down to adapt_depth, a cell stopping when its box area is below sigma or
+    E_hi < alpha E_lo; split_capacity sizes the per-level split queue (0: the library default)."""
     n_base = ds.scene.emitters.n * ds.s1.n_tris * 4 ** depth
+    adaptive = adapt_depth > depth
+    if adaptive and split_capacity == 0:
+        split_capacity = n_base + 4096
     if out is None:
-        # pairs: one record per (cell, candidate T2), a few per cell; the call reports the count
-        default = n_base * 4 + 1024 if ds.s2 is not None else n_base + n_base // 8 + 1024
+        # pairs: one record per (cell, candidate T2), a few per cell; adaptive: the tree's cells;
+        # the call reports the count
+        default = n_base * 4 + 1024 if (ds.s2 is not None or adaptive) else n_base + n_base // 8 + 1024
         out = CellBounds(capacity if capacity is not None else default, ds.device, with_e_hi_min, with_e_lo)
-    need = bnb_bound_tuples_ws(C.byref(ds.s1), ds.s2_ref(), C.byref(ds.em), C.byref(cfg))
-    if ws is None or ws.numel() < need + 256:
-        ws = _ws(need, ds.device)
-    for _ in range(2):
+    for _ in range(6):
+        cfg = bnb_bound_cfg(depth, max_extra_split, int(irradiance), int(fp64), adapt_depth if adaptive else 0,
+                            sigma, alpha, 0, split_capacity)
+        need = bnb_bound_tuples_ws(C.byref(ds.s1), ds.s2_ref(), C.byref(ds.em), C.byref(cfg))
+        if need == 0:
+            raise BnbError("bnb_bound_tuples_ws: invalid configuration")
+        if ws is None or ws.numel() < need + 256:
+            ws = _ws(need, ds.device)
         out.reset()
         rc = bnb_bound_tuples(C.byref(ds.s1), ds.s2_ref(), C.byref(ds.rec), C.byref(ds.em), C.byref(cfg),
                               C.byref(out.c), _align(ws), C.c_size_t(need), _stream(stream))
@@ -375,8 +387,12 @@ def bound_tuples(ds: DeviceScene, depth: int, max_extra_split: int = 4, irradian
             return out
         if int(out.status.item()) == BNB_OK:
             return out
-        out = CellBounds(int(out.count.item()) + 1024, ds.device, with_e_hi_min, with_e_lo)
-    raise BnbError("bnb_bound_tuples: capacity exceeded twice")
+        count = int(out.count.item())
+        if count > out.capacity:  # records: re-call with room for all of them
+            out = CellBounds(count + count // 8 + 1024, ds.device, with_e_hi_min, with_e_lo)
+        else:  # a split level overflowed its queue
+            split_capacity = 2 * (split_capacity or (4096 + n_base // 32))
+    raise BnbError("bnb_bound_tuples: capacity exceeded repeatedly")
 
 
 def _align(ws: torch.Tensor):

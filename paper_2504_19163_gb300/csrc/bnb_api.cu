@@ -63,6 +63,17 @@ int64_t n_base_of(const bnb_surface* s1, const bnb_emitters* em, int depth) {
 
 int64_t split_queue_cap(int64_t n_base) { return 4096 + n_base / 32; }
 
+int64_t queue_cap(const bnb_bound_cfg* cfg, int64_t n_base) {
+  return cfg->split_capacity > 0 ? cfg->split_capacity : split_queue_cap(n_base);
+}
+
+// Adaptive-subdivision fields: off (adapt_depth <= depth) or within the cell-id depth limit.
+bool adapt_ok(const bnb_bound_cfg* cfg) {
+  if (cfg->adapt_depth < 0 || cfg->adapt_depth > kMaxDepth || cfg->split_capacity < 0) return false;
+  if (cfg->adapt_depth > cfg->depth && cfg->adapt_depth + cfg->max_extra_split > kMaxDepth) return false;
+  return cfg->sigma >= 0.0f && cfg->alpha >= 0.0f;  // NaN fails
+}
+
 struct BoundWs {
   float4* tri;
   SplitItem* q[2];
@@ -90,7 +101,7 @@ BoundWs carve_bound_ws(void* base, int64_t n_tris, int64_t qcap) {
 
 extern "C" {
 
-int32_t bnb_abi_version(void) { return 6; }
+int32_t bnb_abi_version(void) { return 7; }
 
 const char* bnb_status_string(int32_t s) {
   switch (s) {
@@ -107,9 +118,10 @@ const char* bnb_status_string(int32_t s) {
 size_t bnb_bound_tuples_ws(const bnb_surface* s1, const bnb_surface* s2, const bnb_emitters* em,
                            const bnb_bound_cfg* cfg) {
   if (!surface_ok(s1) || !emitters_ok(em) || !cfg || cfg->depth < 0 || cfg->depth > kMaxBaseDepth) return 0;
+  if (cfg->split_capacity < 0) return 0;
   const int64_t nb = n_base_of(s1, em, cfg->depth);
   if (s2 != nullptr) return surface_ok(s2) ? pair_ws_bytes(s1->n_tris, s2->n_tris, nb) : 0;
-  return carve_bound_ws(nullptr, s1->n_tris, split_queue_cap(nb)).bytes;
+  return carve_bound_ws(nullptr, s1->n_tris, queue_cap(cfg, nb)).bytes;
 }
 
 int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
@@ -139,7 +151,7 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
   if (s1->kind != BNB_REFLECT && s1->kind != BNB_REFRACT) return BNB_ERR_INVALID;
   if (s1->kind == BNB_REFRACT && !(s1->eta > 0.0f && s1->eta < 1e6f)) return BNB_ERR_INVALID;
   if (cfg->depth < 0 || cfg->depth > kMaxBaseDepth || cfg->max_extra_split < 0 || cfg->max_extra_split > kMaxExtra ||
-      cfg->depth + cfg->max_extra_split > kMaxDepth)
+      cfg->depth + cfg->max_extra_split > kMaxDepth || !adapt_ok(cfg))
     return BNB_ERR_INVALID;
   const int64_t nb = n_base_of(s1, em, cfg->depth);
   if (!out->count || !out->status) return BNB_ERR_INVALID;
@@ -147,7 +159,7 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
   if (out->capacity > 0 && (!out->u_lo || !out->u_hi || !out->v_lo || !out->v_hi || !out->e_hi ||
                             !out->emitter || !out->tri0 || !out->tri1 || !out->cell || !out->flags))
     return BNB_ERR_INVALID;
-  const int64_t qcap = split_queue_cap(nb);
+  const int64_t qcap = queue_cap(cfg, nb);
   const BoundWs need = carve_bound_ws(nullptr, s1->n_tris, qcap);
   if (ws_bytes < need.bytes || (need.bytes > 0 && (!ws || !aligned256(ws)))) return BNB_ERR_INVALID;
   out->n_base = nb;
@@ -173,7 +185,12 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
     P.re2[c] = rec->e2[c];
   }
   P.depth = cfg->depth;
-  P.max_depth = cfg->depth + cfg->max_extra_split;
+  const bool adaptive = cfg->adapt_depth > cfg->depth;
+  P.adapt_depth = adaptive ? cfg->adapt_depth : 0;
+  P.sigma = cfg->sigma;
+  P.alpha = cfg->alpha;
+  // sign-test splits may go max_extra_split levels below the deepest adaptive level
+  P.max_depth = (adaptive ? cfg->adapt_depth : cfg->depth) + cfg->max_extra_split;
   P.irradiance = cfg->irradiance ? 1 : 0;
   P.kind = s1->kind;
   P.eta = s1->eta;
@@ -198,7 +215,7 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
   P.q_out_count = w.qcount + 0;
   const bool fp64 = cfg->fp64 != 0;
   if (launch_bound_base(P, fp64, st) != cudaSuccess) return BNB_ERR_CUDA;
-  for (int lvl = 0; lvl < cfg->max_extra_split; ++lvl) {
+  for (int lvl = 0; lvl < P.max_depth - cfg->depth; ++lvl) {
     const int cur = lvl & 1, nxt = cur ^ 1;
     if (cudaMemsetAsync(w.qcount + nxt, 0, sizeof(int64_t), st) != cudaSuccess) return BNB_ERR_CUDA;
     P.q_out = w.q[nxt];

@@ -573,6 +573,25 @@ __device__ __forceinline__ void put_rec(const BoundParams& P, int64_t slot, floa
   if (P.e_hi_min) P.e_hi_min[slot] = eh_min;
 }
 
+// Adaptive subdivision (Sec. 6.1 "Domain subdivision"): a live cell with a bounded box above the
+// depth limit is queued for its four children (its record becomes SPLIT) unless its receiver box
+// has area below sigma or E_hi < alpha E_lo.  The decision is taken on the float32 values the
+// record stores, with round-to-nearest differences and products.  Returns true when queued.
+__device__ __forceinline__ bool adapt_split(const BoundParams& P, int64_t slot, float ul, float uh, float vl, float vh,
+                                            float el, float eh, int e, int t, uint32_t id, int depth, uint32_t flags) {
+  if (depth >= P.adapt_depth) return false;
+  if (__fmul_rn(__fsub_rn(uh, ul), __fsub_rn(vh, vl)) < P.sigma) return false;
+  if (eh < __fmul_rn(P.alpha, el)) return false;
+  const int64_t qi = (int64_t)atomicAdd((unsigned long long*)P.q_out_count, 1ull);
+  if (qi < P.q_cap) {
+    P.q_out[qi] = SplitItem{e, t, id, depth};
+  } else {
+    raise_status(P.status, BNB_ERR_CAPACITY);
+  }
+  put_rec(P, slot, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, e, t, id, (flags & ~(BNB_CELL_LIVE | BNB_CELL_FOLD)) | BNB_CELL_SPLIT);
+  return true;
+}
+
 // Reciprocal rule after the split limit (Sec. 4.1): with the denominator of mixed sign, bound
 // q/p when p has one sign; p/q then lies in 1/[rl, rh]; return the hull of that set and [0,1].
 template <typename T>
@@ -911,7 +930,8 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
   }
   flags |= BNB_CELL_LIVE;
   if (!P.irradiance) {
-    put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags);
+    if (!adapt_split(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, depth, flags))
+      put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags);
     return;
   }
   // Jacobian numerator M (degree 9):
@@ -941,7 +961,9 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
   renorm(M);
   const int sm = cert_sign(M);
   if (sm == 0) {
-    put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_FOLD);
+    if (!adapt_split(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, depth,
+                     flags | BNB_CELL_FOLD))
+      put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_FOLD);
     return;
   }
   if (sm < 0) negate(M);
@@ -959,7 +981,9 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     sh = fmax(sh, F::add_ru(cl, S.E));
   });
   if (!(sl > tiny_pos<T>())) {
-    put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_FOLD);
+    if (!adapt_split(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, depth,
+                     flags | BNB_CELL_FOLD))
+      put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_FOLD);
     return;
   }
   T ca, cb, dlo, dhi;
@@ -1009,7 +1033,8 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     track_mac<6>(rB, rE, M.B, M.E, T(1), T(0));
     acc.EM = rE;
   }
-  const bool want_lo = P.e_lo != nullptr || P.e_hi_min != nullptr;  // uniform across the launch
+  // uniform across the launch (adaptive subdivision needs E_lo for its ratio test)
+  const bool want_lo = P.e_lo != nullptr || P.e_hi_min != nullptr || P.adapt_depth > 0;
   if (want_lo) {
     irr_all<true, T>(Q3, F0, F1, M, acc, std::make_integer_sequence<int, nc(11)>{});
   } else if constexpr (sizeof(T) == 4) {
@@ -1026,7 +1051,9 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     irr_all<false, T>(Q3, F0, F1, M, acc, std::make_integer_sequence<int, nc(11)>{});
   }
   if (acc.unbounded) {
-    put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_FOLD);
+    if (!adapt_split(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, depth,
+                     flags | BNB_CELL_FOLD))
+      put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), 0.f, F::inf(), e, t, id, flags | BNB_CELL_FOLD);
     return;
   }
   // K = I0 |(p10 - x0).N1| |det A_cell| / |N_k|   (|det A_cell| = 4^-depth, exact)
@@ -1037,6 +1064,7 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
   if (!(eh >= T(0))) eh = F::inf();  // NaN guard: never report a finite bound by accident
   T ehm = fmax(F::mul_rd(Klo, widen_lo(acc.eh_in)), T(0));
   if (!(ehm <= eh)) ehm = T(0);
+  if (adapt_split(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), f_dn(el), f_up(eh), e, t, id, depth, flags)) return;
   put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), f_dn(el), f_up(eh), e, t, id, flags, f_dn(ehm));
 }
 
@@ -1672,6 +1700,9 @@ __device__ __forceinline__ void process_cell_refract(const BoundParams& P, int e
       }
     }
   }
+  if (adapt_split(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), f_dn(el), f_up(eh), e, t, id, depth,
+                  flags | BNB_CELL_LIVE | fold))
+    return;
   put_rec(P, slot, f_dn(ul), f_up(uh), f_dn(vl), f_up(vh), f_dn(el), f_up(eh), e, t, id,
           flags | BNB_CELL_LIVE | fold);
 }

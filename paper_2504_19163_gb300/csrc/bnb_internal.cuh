@@ -27,6 +27,8 @@ struct BoundParams {
   int32_t depth, max_depth, irradiance;
   int32_t kind;  // BNB_REFLECT or BNB_REFRACT
   float eta;     // refraction: eta' = incident / transmitted index
+  int32_t adapt_depth;  // adaptive subdivision above this depth (0: off)
+  float sigma, alpha;   // its stopping thresholds (box area, E_hi / E_lo)
   int64_t n_base;
   // outputs
   int64_t capacity;

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(bnb):
 def test_status_strings_and_version(bnb):
     assert bnb.bnb_status_string(0) == "ok"
     assert "capacity" in bnb.bnb_status_string(-2)
-    assert bnb.lib().bnb_abi_version() == 6
+    assert bnb.lib().bnb_abi_version() == 7
 
 
 def test_workspace_queries_are_host_only(bnb):
@@ -64,6 +64,11 @@ def test_workspace_queries_are_host_only(bnb):
     assert wp >= (2048 + 4608) * 80 + 2048 * 16 * 16  # both packed meshes, per-cell counts and offsets
     assert (bnb.bnb_sample_and_solve_ws(C.byref(s), C.byref(s2), 4096, 10000) -
             bnb.bnb_sample_and_solve_ws(C.byref(s), None, 4096, 10000)) >= 4608 * 80
+    # adaptive subdivision: a caller-sized split queue widens the workspace; bad fields are refused
+    ad = bnb.bnb_bound_cfg(2, 4, 1, 0, 6, 1e-4, 2.0, 0, 1 << 20)
+    assert bnb.bnb_bound_tuples_ws(C.byref(s), None, C.byref(em), C.byref(ad)) >= 2 * (1 << 20) * 16  # two queues
+    assert bnb.bnb_bound_tuples_ws(C.byref(s), None, C.byref(em), C.byref(
+        bnb.bnb_bound_cfg(2, 4, 1, 0, 0, 0.0, 0.0, 0, -1))) == 0
     bad = bnb.bnb_bound_cfg(11, 0, 1, 0)
     assert bnb.bnb_bound_tuples_ws(C.byref(s), None, C.byref(em), C.byref(bad)) == 0
 
