@@ -380,6 +380,11 @@ def run_gpu(args):
         del cb, idx, cb_ws, ix_ws, sm_ws, flush
         torch.cuda.empty_cache()
         line["serving"] = serving_summary(args.serving_requests, dev)
+    if args.adaptive_steps > 0 and rank == 0 and world == 1 and not args.emitters:
+        try:
+            line["adaptive"] = adaptive_summary(dev, args.adaptive_steps)
+        except Exception as ex:  # reported in the line; the bound benchmark above stands
+            line["adaptive"] = {"error": f"{type(ex).__name__}: {ex}"}
     if args.pairs_steps > 0 and rank == 0 and world == 1:
         try:
             line["pairs"] = pairs_summary(dev, args.pairs_steps, not args.no_cpu_baseline and not args.emitters)
@@ -561,6 +566,78 @@ def pairs_summary(dev, steps: int, oracle_too: bool) -> dict:
     return out
 
 
+ADAPT = dict(depth=0, adapt_depth=6, sigma=1e-6, alpha=2.0)
+
+
+def adaptive_summary(dev, steps: int) -> dict:
+    """Adaptive subdivision (Sec. 6.1) on the benchmark mirror: every triangle and light sample
+    starts as one cell and is subdivided down to depth 6 until its receiver box has area below
+    1e-6 (a quarter of a 512^2 grid cell) or E_hi < 2 E_lo (the paper's alpha for single
+    scattering); then the index and the rendering pass at E|S| = 4.  Timed like the main steps."""
+    import torch
+    from paper_2504_19163_gb300 import bnb
+    from paper_2504_19163_gb300 import scenes as S
+    sc = S.config("mirror256")
+    ds = bnb.DeviceScene(sc, dev)
+    stream = torch.cuda.current_stream(dev)
+    kw = dict(adapt_depth=ADAPT["adapt_depth"], sigma=ADAPT["sigma"], alpha=ADAPT["alpha"], with_e_lo=False)
+    cb = bnb.bound_tuples(ds, ADAPT["depth"], **kw)
+    split_cap = cb.capacity
+    idx = bnb.build_index(cb, grid_res=sc.grid_res)
+    gamma = calibrate_gamma(bnb, ds, idx, target=4.0)
+    res = bnb.sample_and_solve(ds, idx, gamma, 1)
+    torch.cuda.synchronize()
+    n_points = ds.n_points
+    wl_cap = int(res.counters[1].item()) * 2 + 4096
+    cfg = bnb.bnb_bound_cfg(ADAPT["depth"], 4, 1, 0, ADAPT["adapt_depth"], ADAPT["sigma"], ADAPT["alpha"], 0, split_cap)
+    cb_ws = bnb._ws(bnb.bnb_bound_tuples_ws(bnb.C.byref(ds.s1), None, bnb.C.byref(ds.em), bnb.C.byref(cfg)), dev)
+    pre_cap = int(idx.count[1].item()) + int(idx.count[1].item()) // 4 + 4096
+    ix_ws = bnb._ws(bnb.bnb_build_index_ws(bnb.C.byref(cb.c), sc.grid_res, pre_cap), dev)
+    idx = bnb.Index(sc.grid_res, pre_cap, dev)
+    sm_ws = bnb._ws(bnb.bnb_sample_and_solve_ws(bnb.C.byref(ds.s1), None, n_points, wl_cap), dev)
+    E_out = torch.empty(n_points, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(seed, ev):
+        ev[0].record(stream)
+        bnb.bound_tuples(ds, ADAPT["depth"], out=cb, ws=cb_ws, sync_check=False, split_capacity=split_cap, **kw)
+        ev[1].record(stream)
+        bnb.build_index(cb, grid_res=sc.grid_res, pre_capacity=pre_cap, capacity=pre_cap, out=idx, ws=ix_ws,
+                        sync_check=False)
+        ev[2].record(stream)
+        r = bnb.sample_and_solve(ds, idx, gamma, seed, worklist_capacity=wl_cap, E_out=E_out, ws=sm_ws,
+                                 sync_check=False)
+        ev[3].record(stream)
+        return r
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(3 + steps)]
+    for i in range(3 + steps):
+        flush.zero_()
+        r = step(i, evs[i])
+    torch.cuda.synchronize()
+    st = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs[3:]])
+    ms = st.mean(axis=0)
+    ok = int(cb.status.item()) == 0 and int(idx.status.item()) == 0 and int(r.status.item()) == 0
+    n_rec = cb.n_records()
+    fl = cb.flags[:n_rec]
+    live = int(((fl & 1) != 0).sum().item())
+    split = int(((fl & 2) != 0).sum().item())
+    dep = ((fl.to(torch.int64) >> 24) & 63)[(fl & 1) != 0]
+    hist = torch.bincount(dep, minlength=ADAPT["adapt_depth"] + 1).cpu().tolist()
+    c = r.counters.cpu().numpy()
+    n_base = sc.emitters.n * sc.s1.n_tris * 4 ** ADAPT["depth"]
+    out = {"workload": "mirror256 (131,072 tris x 16 area-light samples) from depth 0, adaptive to depth "
+                       f"{ADAPT['adapt_depth']}: sigma {ADAPT['sigma']} (box area), alpha {ADAPT['alpha']}; "
+                       "1024^2 points, E|S| = 4", "status_ok": ok, "steps": steps, "base_cells": n_base,
+           "records": n_rec, "live_leaves": live, "split_cells": split, "live_depth_histogram": hist,
+           "gamma": gamma, "stage_ms": {"bound": float(ms[0]), "index": float(ms[1]), "sample_solve": float(ms[2])},
+           "cells_per_s": n_rec / (ms[0] / 1e3), "shading_samples_per_s": n_points / (ms[2] / 1e3),
+           "per_point": {"U": c[0] / n_points, "S": c[1] / n_points, "roots": c[2] / n_points}}
+    del cb, idx, cb_ws, ix_ws, sm_ws, flush
+    torch.cuda.empty_cache()
+    return out
+
+
 def _pairs_oracle_worker():
     sys.path.insert(0, ROOT)
     import oracle
@@ -608,6 +685,8 @@ def main():
     ap.add_argument("--emitters", type=int, default=0, help="use only the first N area-light samples (profiling case)")
     ap.add_argument("--serving-requests", type=int, default=256,
                     help="requests of the serving workload reported under 'serving' (0: skip)")
+    ap.add_argument("--adaptive-steps", type=int, default=5,
+                    help="timed steps of the adaptive-subdivision mirror256 pass reported under 'adaptive' (0: skip)")
     ap.add_argument("--pairs-steps", type=int, default=10,
                     help="timed steps of the two-vertex slab48 workload reported under 'pairs' (0: skip)")
     args = ap.parse_args()
