@@ -1667,19 +1667,38 @@ int orc_index(const float* u_lo, const float* u_hi, const float* v_lo, const flo
 // P > 0 whenever E~ > 0 (unbiasedness condition of Sec. 5.3).
 int orc_sample(const int64_t* offsets, const uint64_t* key, const float* etilde, int32_t G, const float* su,
                const float* sv, int64_t n_points, float gamma, uint64_t seed, int64_t* wl_point, uint64_t* wl_key,
-               float* wl_p, int64_t cap, int64_t* n_out, int64_t* n_U) {
-  int64_t o = 0, nu = 0;
+               float* wl_p, int64_t cap, int64_t* n_out, int64_t* n_U, int32_t bins, int64_t* n_B) {
+  int64_t o = 0, nu = 0, nb = 0;
   for (int64_t p = 0; p < n_points; ++p) {
     auto gi = [&](float x) {
       int i = (int)std::floor(x * (float)G);
       return std::min(G - 1, std::max(0, i));
     };
     int64_t g = (int64_t)gi(sv[p]) * G + gi(su[p]);
+    // bins (Sec. 5.3): the listed tuples packed greedily in list order into groups whose
+    // probabilities sum to at most 1 (a tuple that does not fit closes the group and opens the
+    // next); one draw per group (counter = (point, key of its first tuple)) picks the tuple whose
+    // cumulative interval [c_prev, c) holds it, or none past the group's total.  Float32 sums.
+    float acc = 0.0f, rb = 0.0f;
+    bool open = false;
     for (int64_t j = offsets[g]; j < offsets[g + 1]; ++j) {
       ++nu;
       float P = std::fmin(fmul_ru32(gamma, etilde[j]), 1.0f);  // fmin: a NaN product (0 * inf) selects
-      float r = philox_uniform(seed, p, key[j]);
-      if (r < P) {
+      bool sel;
+      if (bins) {
+        if (!open || acc + P > 1.0f) {
+          open = true;
+          acc = 0.0f;
+          rb = philox_uniform(seed, p, key[j]);
+          ++nb;
+        }
+        const float lo = acc;
+        acc = acc + P;
+        sel = rb >= lo && rb < acc;
+      } else {
+        sel = philox_uniform(seed, p, key[j]) < P;
+      }
+      if (sel) {
         if (o < cap) {
           wl_point[o] = p;
           wl_key[o] = key[j];
@@ -1691,6 +1710,7 @@ int orc_sample(const int64_t* offsets, const uint64_t* key, const float* etilde,
   }
   *n_out = o;
   *n_U = nu;
+  if (n_B) *n_B = nb;
   return o > cap ? -2 : 0;
 }
 

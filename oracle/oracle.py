@@ -79,7 +79,7 @@ def lib():
             L.orc_philox_uniform.argtypes = [u64, i64, u64]
             L.orc_bound.argtypes = [vp, vp, vp, i32, i32, i32, vp, i64, vp, i64, vp, i32, i32, f32, f32]
             L.orc_index.argtypes = [vp] * 9 + [i64, i32, f32, vp, vp, vp, i64, vp]
-            L.orc_sample.argtypes = [vp, vp, vp, i32, vp, vp, i64, f32, u64, vp, vp, vp, i64, vp, vp]
+            L.orc_sample.argtypes = [vp, vp, vp, i32, vp, vp, i64, f32, u64, vp, vp, vp, i64, vp, vp, i32, vp]
             L.orc_solve.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, i32, i32, f64, vp, vp, vp, vp, i32]
             L.orc_eval_path.argtypes = [vp, vp, vp, i32, i32, vp, vp, i64, vp, vp, vp, vp]
             L.orc_eval_direct.argtypes = [vp, vp, vp, i32, i32, vp, vp, i64, vp, vp, vp, vp]
@@ -271,8 +271,11 @@ def index(u_lo, u_hi, v_lo, v_hi, e_hi, emitter, tri0, tri1, flags, grid_res: in
         return offsets, key[: int(n_out[0])], et[: int(n_out[0])]
 
 
-def sample(offsets, key, etilde, grid_res: int, su, sv, gamma: float, seed: int):
-    """Worklist (point, key, P) in (point, key) order, and |U| summed over points."""
+def sample(offsets, key, etilde, grid_res: int, su, sv, gamma: float, seed: int, bins: bool = False,
+           with_bins: bool = False):
+    """Worklist (point, key, P) in (point, key) order, and |U| summed over points.  bins: the
+    bin-packed selection (one draw per bin of Sec. 5.3) instead of one draw per tuple; with_bins
+    also returns |B| summed over points."""
     L = lib()
     offsets = np.ascontiguousarray(offsets, np.int64)
     key = np.ascontiguousarray(key, np.uint64)
@@ -286,12 +289,15 @@ def sample(offsets, key, etilde, grid_res: int, su, sv, gamma: float, seed: int)
         wP = np.zeros(cap, np.float32)
         n_out = np.zeros(1, np.int64)
         n_u = np.zeros(1, np.int64)
+        n_b = np.zeros(1, np.int64)
         rc = L.orc_sample(_p(offsets), _p(key), _p(etilde), grid_res, _p(su), _p(sv), su.shape[0], gamma, seed,
-                          _p(wp), _p(wk), _p(wP), cap, _p(n_out), _p(n_u))
+                          _p(wp), _p(wk), _p(wP), cap, _p(n_out), _p(n_u), int(bins), _p(n_b))
         if rc == -2:
             cap = int(n_out[0])
             continue
         k = int(n_out[0])
+        if with_bins:
+            return wp[:k], wk[:k], wP[:k], int(n_u[0]), int(n_b[0])
         return wp[:k], wk[:k], wP[:k], int(n_u[0])
 
 
@@ -339,13 +345,15 @@ def tuple_key(emitter, tri0, tri1=-1):
 
 
 def render(scene, gamma: float, seed: int, depth: Optional[int] = None, max_extra_split: int = 4,
-           newton_iters: int = 16, polish_iters: int = 1, tol: float = 1e-5, n_threads: int = 1):
-    """Whole path on the CPU: bound -> index -> Algorithm 1 -> Newton -> per-point estimate."""
+           newton_iters: int = 16, polish_iters: int = 1, tol: float = 1e-5, n_threads: int = 1,
+           bins: bool = False):
+    """Whole path on the CPU: bound -> index -> Algorithm 1 (or its bin-packed form) -> Newton ->
+    per-point estimate."""
     rec = bound(scene, depth=depth, max_extra_split=max_extra_split, n_threads=n_threads)
     f = records_to_f32(rec)
     off, key, et = index(f["u_lo"], f["u_hi"], f["v_lo"], f["v_hi"], f["e_hi"], f["emitter"], f["tri0"],
                          f["tri1"], f["flags"], scene.grid_res)
-    wp, wk, wP, n_u = sample(off, key, et, scene.grid_res, scene.su, scene.sv, gamma, seed)
+    wp, wk, wP, n_u = sample(off, key, et, scene.grid_res, scene.su, scene.sv, gamma, seed, bins=bins)
     contrib, ru, rv, st = solve(scene, wp, wk, wP, newton_iters, polish_iters, tol, n_threads)
     E = accumulate(scene.su.shape[0], wp, contrib)
     return dict(records=rec, offsets=off, key=key, etilde=et, wl_point=wp, wl_key=wk, wl_p=wP, n_U=n_u,
