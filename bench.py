@@ -324,6 +324,21 @@ def run_gpu(args):
     e2e_ms /= e2e_steps
     e2e_value = RP.whole_job_rate(n_cells, world, RP.max_over_ranks(e2e_ms, dist, dev))
 
+    # ---- bin-packed selection (Sec. 5.3) on the same index: one draw per group instead of per tuple
+    bev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(8)]
+    for i in range(8):
+        flush.zero_()
+        bev[i][0].record(stream)
+        rb = bnb.sample_and_solve(ds, idx, gamma, 900 + i, worklist_capacity=wl_cap, E_out=E_out, ws=sm_ws,
+                                  sync_check=False, bins=True)
+        bev[i][1].record(stream)
+    torch.cuda.synchronize()
+    cb_n = rb.counters.cpu().numpy()
+    bins_line = {"sample_solve_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in bev[3:]])),
+                 "per_point": {"U": cb_n[0] / n_points, "B": cb_n[3] / n_points, "S": cb_n[1] / n_points,
+                               "roots": cb_n[2] / n_points},
+                 "status_ok": int(rb.status.item()) == 0}
+
     # ---- roofline of the dominant kernel (bound pass)
     bound_ms = float(stage[:, 0].mean())
     props = torch.cuda.get_device_properties(dev)
@@ -372,6 +387,7 @@ def run_gpu(args):
                          "flop_per_cell": BOUND_FLOP_PER_CELL,
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                        f"(max SM clock of MEASURED_PEAKS.json)"},
+            "bins": bins_line,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches_per_step(n_points, sc.grid_res) * args.steps,

@@ -154,10 +154,19 @@ typedef struct bnb_sample_cfg {
   int32_t polish_iters;       /* float64 polish steps (<= 8) */
   float tol;                  /* acceptance: |hit - target| < tol scene units */
   int64_t worklist_capacity;  /* selected (point, tuple) pairs the workspace holds */
+  /* 0: Algorithm 1, one draw per listed tuple.  1: bin-packed selection (Sec. 5.3): the listed
+   * tuples of a point, in list order, are packed greedily into groups whose probabilities sum to at
+   * most 1 (a tuple that does not fit, fl(sum + P) > 1, opens the next group); one draw per group
+   * (counter = (point, key of the group's first tuple)) selects the tuple whose float32 cumulative
+   * interval [sum before it, sum with it) holds the draw, none past the group's sum.  Each tuple is
+   * still selected with probability P; at most one per group. */
+  int32_t bins;
+  int32_t reserved;           /* 0 */
 } bnb_sample_cfg;
 
 typedef struct bnb_sample_stats {
-  int64_t *counters;  /* device int64[4]: |U| summed, |S| summed (= worklist entries needed), roots found, 0 */
+  int64_t *counters;  /* device int64[4]: |U| summed, |S| summed (= worklist entries needed), roots found,
+                         |B| summed (groups drawn; bins = 1 only, else 0) */
   int32_t *status;    /* device int32: BNB_OK or BNB_ERR_CAPACITY */
   int32_t *sel_count; /* optional device int32[n_points]: |S| per shading point (NULL: not written) */
 } bnb_sample_stats;
@@ -341,7 +350,7 @@ size_t bnb_bound_tuples_batched_ws(int32_t max_jobs);
 const char *bnb_status_string(int32_t status);
 
 /* ABI version of this header (increments on any struct or signature change). */
-int32_t bnb_abi_version(void);  /* 7 */
+int32_t bnb_abi_version(void);  /* 8 */
 
 #ifdef __cplusplus
 }

@@ -5,7 +5,10 @@
 //                     listed tuple P = min(gamma E~, 1) (float32 product rounded
 //                     up, so P > 0 whenever E~ > 0) and one Philox4x32-10
 //                     uniform r (key = seed, counter = (point, tuple key));
-//                     the tuple is selected when r < P.  Counts per point.
+//                     the tuple is selected when r < P.  Counts per point.  With
+//                     bins = 1, the bin-packed form (Sec. 5.3): the list is
+//                     packed greedily into groups of probability sum <= 1 and
+//                     one draw per group selects at most one of its tuples.
 //   scan              -> worklist offsets (point order, then key order).
 //   sample_k (fill)   the same draws, writing (point, key, P).
 //   solve32_k         per selected tuple: Newton's method in T1's barycentric
@@ -44,11 +47,12 @@ struct SampleParams {
   int64_t* counters;   // device int64[4]
   int32_t* status;
   int32_t* sel_count;  // optional, per point
+  int32_t bins;        // 1: bin-packed selection (one draw per group), 0: one draw per tuple
 };
 
 template <bool FILL>
 __global__ void __launch_bounds__(256) sample_k(SampleParams P) {
-  long long nu = 0, ns = 0;
+  long long nu = 0, ns = 0, nb = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n_points;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int g = grid_col_s(P.sv[p], P.G) * P.G + grid_col_s(P.su[p], P.G);
@@ -56,11 +60,27 @@ __global__ void __launch_bounds__(256) sample_k(SampleParams P) {
     const int64_t e = min(P.offsets[g + 1], P.index_capacity);
     int64_t cnt = 0;
     int64_t out = FILL ? P.woff[p] : 0;
+    // bins: the current group's running probability sum and draw (groups are runs of the list)
+    float acc = 0.0f, rb = 0.0f;
+    bool open = false;
     for (int64_t j = s; j < e; ++j) {
       const float Pt = fminf(__fmul_ru(P.gamma, P.etilde[j]), 1.0f);
       const uint64_t k = P.key[j];
-      const float r = uniform24(P.seed, p, k);
-      if (r < Pt) {
+      bool sel;
+      if (P.bins) {
+        if (!open || __fadd_rn(acc, Pt) > 1.0f) {  // the tuple does not fit: it opens the next group
+          open = true;
+          acc = 0.0f;
+          rb = uniform24(P.seed, p, k);
+          ++nb;
+        }
+        const float lo = acc;
+        acc = __fadd_rn(acc, Pt);
+        sel = rb >= lo && rb < acc;
+      } else {
+        sel = uniform24(P.seed, p, k) < Pt;
+      }
+      if (sel) {
         if (FILL) {
           if (out < P.wl_cap) {
             P.wl_point[out] = p;
@@ -86,10 +106,12 @@ __global__ void __launch_bounds__(256) sample_k(SampleParams P) {
     for (int o = 16; o > 0; o >>= 1) {
       nu += __shfl_xor_sync(0xffffffffu, nu, o);
       ns += __shfl_xor_sync(0xffffffffu, ns, o);
+      nb += __shfl_xor_sync(0xffffffffu, nb, o);
     }
     if ((threadIdx.x & 31) == 0) {
       if (nu) atomicAdd((unsigned long long*)&P.counters[0], (unsigned long long)nu);
       if (ns) atomicAdd((unsigned long long*)&P.counters[1], (unsigned long long)ns);
+      if (nb) atomicAdd((unsigned long long*)&P.counters[3], (unsigned long long)nb);
     }
   }
 }
@@ -325,6 +347,7 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2
   P.counters = stats->counters;
   P.status = stats->status;
   P.sel_count = stats->sel_count;
+  P.bins = cfg->bins;
   const int64_t pblocks = std::min<int64_t>((n_points + 255) / 256, (int64_t)sms * 32);
   sample_k<false><<<(unsigned)pblocks, 256, 0, st>>>(P);
   if ((e = launch_exclusive_scan(w.n_sel, w.woff, n_points, w.scan, st)) != cudaSuccess) return e;
