@@ -1714,16 +1714,78 @@ int orc_sample(const int64_t* offsets, const uint64_t* key, const float* etilde,
   return o > cap ? -2 : 0;
 }
 
-// Newton root-finding in the tuple's triangle (Sec. 6.1, deterministic init):
-// start at the centroid, newton_iters damped steps (step clamped to 0.5 in
-// barycentric units; early exit when the step is below 1e-6), then
-// polish_iters full steps; accept when the hit is within tol scene units of the
-// target, u1 lies in the closed triangle and the hit is in front (t > 0).
-// contrib = E(root) / P.  status: 1 root, 0 none.
+}  // extern "C"
+
+namespace {
+
+// Newton's method for one tuple from the start (u, v): newton_iters damped steps (step clamped to
+// 0.5 in barycentric units; once a step is below 1e-6 the damped phase ends), then polish_iters
+// full steps; the root is accepted when the hit is within tol scene units of the target, u1 lies in
+// the closed triangle and the hit is in front (t > 0).  Returns E(root) >= 0, or -1.
+double newton_from(const Tri& T, V3 x0, double I0, const Rec& R, int kind, double eta, double tu, double tv,
+                   int newton_iters, int polish_iters, double tol, double* u_io, double* v_io) {
+  double u = *u_io, v = *v_io;
+  for (int it = 0; it < newton_iters + polish_iters; ++it) {
+    PathEval P = eval_path(T, x0, I0, R, u, v, kind, eta);
+    double det = P.J[0][0] * P.J[1][1] - P.J[0][1] * P.J[1][0];
+    if (!P.ok || !(det != 0.0) || !std::isfinite(det)) return -1.0;
+    double fu = P.uk - tu, fv = P.vk - tv;
+    double du = -(P.J[1][1] * fu - P.J[0][1] * fv) / det;
+    double dv = -(-P.J[1][0] * fu + P.J[0][0] * fv) / det;
+    double mx = std::max(std::fabs(du), std::fabs(dv));
+    bool damped = it < newton_iters;
+    if (damped && mx > 0.5) {
+      du *= 0.5 / mx;
+      dv *= 0.5 / mx;
+    }
+    u += du;
+    v += dv;
+    if (!std::isfinite(u) || !std::isfinite(v)) return -1.0;
+    if (damped && mx < 1e-6) it = newton_iters - 1;  // converged: go to the polish steps
+  }
+  *u_io = u;
+  *v_io = v;
+  PathEval P = eval_path(T, x0, I0, R, u, v, kind, eta);
+  if (!P.ok) return -1.0;
+  V3 res = (P.uk - tu) * R.e1 + (P.vk - tv) * R.e2;
+  bool inside = u >= 0.0 && v >= 0.0 && u + v <= 1.0;
+  if (norm(res) < tol && inside && P.t > 0.0 && std::isfinite(P.E)) return P.E;
+  return -1.0;
+}
+
+// Start of stochastic trial t (t >= 0) for (point, tuple key): the first two outputs of
+// Philox4x32-10 with counter (point, key) and key seed + (t + 1) * 0x9E3779B97F4A7C15 (mod 2^64),
+// as 24-bit uniforms (a, b), folded into the triangle (a + b > 1 -> (1 - a, 1 - b)).
+void stoc_start(uint64_t seed, int64_t point, uint64_t key, int t, double* u, double* v) {
+  const uint64_t k = seed + (uint64_t)(t + 1) * 0x9E3779B97F4A7C15ull;
+  const uint32_t ctr[4] = {(uint32_t)point, (uint32_t)((uint64_t)point >> 32), (uint32_t)key, (uint32_t)(key >> 32)};
+  const uint32_t kk[2] = {(uint32_t)k, (uint32_t)(k >> 32)};
+  uint32_t o[4];
+  philox4x32_10(ctr, kk, o);
+  double a = (double)(o[0] >> 8) * (1.0 / 16777216.0), b = (double)(o[1] >> 8) * (1.0 / 16777216.0);
+  if (a + b > 1.0) {
+    a = 1.0 - a;
+    b = 1.0 - b;
+  }
+  *u = a;
+  *v = b;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Newton root-finding in the tuple's triangle (Sec. 6.1).  stoc_trials = 0: deterministic start at
+// the centroid (Det).  stoc_trials > 0: stochastic start with the unbiased reciprocal weighting
+// (Stoc, Sec. 6.1 after Zeltner et al. 2020): a root u* found from a uniform random start is
+// weighted by the number N of further random starts up to the first that reaches u* again (within
+// 1e-4 in barycentrics), E[N] = 1 / P(reach u*), capped at stoc_trials (N = stoc_trials when no
+// start in the cap reaches it).  contrib = E(root) N / P; status 1 root, 0 none; trials[i] = N.
 int orc_solve(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, const int64_t* wl_point,
               const uint64_t* wl_key, const float* wl_p, int64_t n_wl, const float* su, const float* sv,
               int32_t newton_iters, int32_t polish_iters, double tol, double* contrib, double* root_u,
-              double* root_v, int32_t* status, int32_t n_threads) {
+              double* root_v, int32_t* status, int32_t n_threads, int32_t stoc_trials, uint64_t seed,
+              int32_t* trials) {
   Rec R = get_rec(rec);
   parallel_for(n_wl, std::max(1, (int)n_threads), [&](int, int64_t a, int64_t b) {
     for (int64_t i = a; i < b; ++i) {
@@ -1732,49 +1794,58 @@ int orc_solve(const orc_surface* s1, const orc_receiver* rec, const orc_emitters
       Tri T = get_tri(s1, t);
       V3 x0 = {em->x[e], em->y[e], em->z[e]};
       double I0 = em->intensity[e];
-      double tu = su[wl_point[i]], tv = sv[wl_point[i]];
+      const int64_t pt = wl_point[i];
+      double tu = su[pt], tv = sv[pt];
       double u = 1.0 / 3.0, v = 1.0 / 3.0;
-      bool bad = false;
-      for (int it = 0; it < newton_iters + polish_iters; ++it) {
-        PathEval P = eval_path(T, x0, I0, R, u, v, s1->kind, s1->eta);
-        double det = P.J[0][0] * P.J[1][1] - P.J[0][1] * P.J[1][0];
-        if (!P.ok || !(det != 0.0) || !std::isfinite(det)) {
-          bad = true;
-          break;
-        }
-        double fu = P.uk - tu, fv = P.vk - tv;
-        double du = -(P.J[1][1] * fu - P.J[0][1] * fv) / det;
-        double dv = -(-P.J[1][0] * fu + P.J[0][0] * fv) / det;
-        double mx = std::max(std::fabs(du), std::fabs(dv));
-        bool damped = it < newton_iters;
-        if (damped && mx > 0.5) {
-          du *= 0.5 / mx;
-          dv *= 0.5 / mx;
-        }
-        u += du;
-        v += dv;
-        if (!std::isfinite(u) || !std::isfinite(v)) {
-          bad = true;
-          break;
-        }
-        if (damped && mx < 1e-6) it = newton_iters - 1;  // converged: go to the polish steps
-      }
+      if (stoc_trials > 0) stoc_start(seed, pt, k, 0, &u, &v);
+      const double E = newton_from(T, x0, I0, R, s1->kind, s1->eta, tu, tv, newton_iters, polish_iters, tol, &u, &v);
       contrib[i] = 0.0;
       status[i] = 0;
       root_u[i] = u;
       root_v[i] = v;
-      if (bad) continue;
-      PathEval P = eval_path(T, x0, I0, R, u, v, s1->kind, s1->eta);
-      if (!P.ok) continue;
-      double fu = P.uk - tu, fv = P.vk - tv;
-      V3 res = fu * R.e1 + fv * R.e2;
-      bool inside = u >= 0.0 && v >= 0.0 && u + v <= 1.0;
-      if (norm(res) < tol && inside && P.t > 0.0 && std::isfinite(P.E)) {
-        status[i] = 1;
-        contrib[i] = P.E / (double)wl_p[i];
+      if (trials) trials[i] = 0;
+      if (!(E >= 0.0)) continue;
+      int n = 1;
+      if (stoc_trials > 0) {
+        for (n = 1; n < stoc_trials; ++n) {
+          double u2, v2;
+          stoc_start(seed, pt, k, n, &u2, &v2);
+          const double E2 =
+              newton_from(T, x0, I0, R, s1->kind, s1->eta, tu, tv, newton_iters, polish_iters, tol, &u2, &v2);
+          if (E2 >= 0.0 && std::fabs(u2 - u) <= 1e-4 && std::fabs(v2 - v) <= 1e-4) break;
+        }
       }
+      status[i] = 1;
+      contrib[i] = E * n / (double)wl_p[i];
+      if (trials) trials[i] = n;
     }
   });
+  return 0;
+}
+
+// Every root of tuple (e, t) at target (tu, tv): Newton from an n x n grid of starts over the
+// triangle (Det steps), distinct accepted roots (1e-7 apart) summed.  For the pins.
+int orc_roots(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, int32_t e, int32_t t,
+              double tu, double tv, int32_t n, int32_t newton_iters, int32_t polish_iters, double tol,
+              double* sum_E, int32_t* n_roots) {
+  const Rec R = get_rec(rec);
+  const Tri T = get_tri(s1, t);
+  const V3 x0 = {em->x[e], em->y[e], em->z[e]};
+  std::vector<std::array<double, 3>> found;
+  for (int i = 0; i <= n; ++i)
+    for (int j = 0; i + j <= n; ++j) {
+      double u = (i + 1.0 / 3.0) / (n + 1.0), v = (j + 1.0 / 3.0) / (n + 1.0);
+      const double E = newton_from(T, x0, em->intensity[e], R, s1->kind, s1->eta, tu, tv, newton_iters,
+                                   polish_iters, tol, &u, &v);
+      if (!(E >= 0.0)) continue;
+      bool dup = false;
+      for (auto& f : found) dup = dup || (std::fabs(f[0] - u) < 1e-7 && std::fabs(f[1] - v) < 1e-7);
+      if (!dup) found.push_back({u, v, E});
+    }
+  double s = 0.0;
+  for (auto& f : found) s += f[2];
+  *sum_E = s;
+  *n_roots = (int32_t)found.size();
   return 0;
 }
 

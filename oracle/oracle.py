@@ -80,7 +80,9 @@ def lib():
             L.orc_bound.argtypes = [vp, vp, vp, i32, i32, i32, vp, i64, vp, i64, vp, i32, i32, f32, f32]
             L.orc_index.argtypes = [vp] * 9 + [i64, i32, f32, vp, vp, vp, i64, vp]
             L.orc_sample.argtypes = [vp, vp, vp, i32, vp, vp, i64, f32, u64, vp, vp, vp, i64, vp, vp, i32, vp]
-            L.orc_solve.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, i32, i32, f64, vp, vp, vp, vp, i32]
+            L.orc_solve.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp, vp, i32, i32, f64, vp, vp, vp, vp, i32, i32, u64,
+                                    vp]
+            L.orc_roots.argtypes = [vp, vp, vp, i32, i32, f64, f64, i32, i32, i32, f64, vp, vp]
             L.orc_eval_path.argtypes = [vp, vp, vp, i32, i32, vp, vp, i64, vp, vp, vp, vp]
             L.orc_eval_direct.argtypes = [vp, vp, vp, i32, i32, vp, vp, i64, vp, vp, vp, vp]
             L.orc_bb_mul.argtypes = [C.c_int, C.c_int, vp, C.c_int, vp, vp]
@@ -302,8 +304,10 @@ def sample(offsets, key, etilde, grid_res: int, su, sv, gamma: float, seed: int,
 
 
 def solve(scene, wl_point, wl_key, wl_p, newton_iters: int = 16, polish_iters: int = 1, tol: float = 1e-5,
-          n_threads: int = 1):
-    """Per worklist entry: contribution E/P (float64), root (u, v) and status (1 = root)."""
+          n_threads: int = 1, stoc_trials: int = 0, seed: int = 0, with_trials: bool = False):
+    """Per worklist entry: contribution E/P (float64), root (u, v) and status (1 = root).
+    stoc_trials > 0: stochastic starts with the reciprocal weighting (Sec. 6.1 "Stoc"), capped at
+    stoc_trials; with_trials also returns the weight N of each entry."""
     L = lib()
     V = _SceneViews(scene)
     wl_point = np.ascontiguousarray(wl_point, np.int64)
@@ -316,9 +320,26 @@ def solve(scene, wl_point, wl_key, wl_p, newton_iters: int = 16, polish_iters: i
     ru = np.zeros(n)
     rv = np.zeros(n)
     st = np.zeros(n, np.int32)
+    tr = np.zeros(n, np.int32)
     L.orc_solve(C.byref(V.surf), C.byref(V.rec), C.byref(V.em), _p(wl_point), _p(wl_key), _p(wl_p), n, _p(su),
-                _p(sv), newton_iters, polish_iters, tol, _p(contrib), _p(ru), _p(rv), _p(st), n_threads)
+                _p(sv), newton_iters, polish_iters, tol, _p(contrib), _p(ru), _p(rv), _p(st), n_threads,
+                stoc_trials, seed, _p(tr))
+    if with_trials:
+        return contrib, ru, rv, st, tr
     return contrib, ru, rv, st
+
+
+def roots(scene, emitter: int, tri: int, tu: float, tv: float, n: int = 24, newton_iters: int = 16,
+          polish_iters: int = 1, tol: float = 1e-5):
+    """Sum of E over every distinct root of one tuple at one target (Newton from an n x n grid of
+    starts), and the number of roots."""
+    L = lib()
+    V = _SceneViews(scene)
+    s = np.zeros(1)
+    k = np.zeros(1, np.int32)
+    L.orc_roots(C.byref(V.surf), C.byref(V.rec), C.byref(V.em), emitter, tri, tu, tv, n, newton_iters, polish_iters,
+                tol, _p(s), _p(k))
+    return float(s[0]), int(k[0])
 
 
 def accumulate(n_points: int, wl_point, contrib) -> np.ndarray:
