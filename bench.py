@@ -338,6 +338,18 @@ def run_gpu(args):
                  "per_point": {"U": cb_n[0] / n_points, "B": cb_n[3] / n_points, "S": cb_n[1] / n_points,
                                "roots": cb_n[2] / n_points},
                  "status_ok": int(rb.status.item()) == 0}
+    # ---- stochastic Newton starts with the reciprocal weighting (Sec. 6.1 "Stoc"), weights capped at 64
+    for i in range(8):
+        flush.zero_()
+        bev[i][0].record(stream)
+        rs = bnb.sample_and_solve(ds, idx, gamma, 700 + i, worklist_capacity=wl_cap, E_out=E_out, ws=sm_ws,
+                                  sync_check=False, stoc_trials=64)
+        bev[i][1].record(stream)
+    torch.cuda.synchronize()
+    cs_n = rs.counters.cpu().numpy()
+    stoc_line = {"sample_solve_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in bev[3:]])),
+                 "stoc_trials": 64, "per_point": {"S": cs_n[1] / n_points, "roots": cs_n[2] / n_points},
+                 "status_ok": int(rs.status.item()) == 0}
 
     # ---- roofline of the dominant kernel (bound pass)
     bound_ms = float(stage[:, 0].mean())
@@ -388,6 +400,7 @@ def run_gpu(args):
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                        f"(max SM clock of MEASURED_PEAKS.json)"},
             "bins": bins_line,
+            "stoc": stoc_line,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches_per_step(n_points, sc.grid_res) * args.steps,

@@ -161,7 +161,13 @@ typedef struct bnb_sample_cfg {
    * interval [sum before it, sum with it) holds the draw, none past the group's sum.  Each tuple is
    * still selected with probability P; at most one per group. */
   int32_t bins;
-  int32_t reserved;           /* 0 */
+  /* 0: Newton from the centroid (Det, Sec. 6.1).  > 0: stochastic starts with the reciprocal
+   * weighting (Stoc, Sec. 6.1): per selected tuple Newton from a uniform random start (Philox4x32-10,
+   * counter = (point, key), key = seed + (trial + 1) * 0x9E3779B97F4A7C15, two 24-bit uniforms folded
+   * into the triangle); an accepted root is weighted by the number N of further random starts up to
+   * the first that reaches it again (within 1e-4), N capped at stoc_trials (unbiased for roots reached
+   * from more than ~1 / stoc_trials of the triangle).  One specular vertex only. */
+  int32_t stoc_trials;
 } bnb_sample_cfg;
 
 typedef struct bnb_sample_stats {
@@ -350,7 +356,7 @@ size_t bnb_bound_tuples_batched_ws(int32_t max_jobs);
 const char *bnb_status_string(int32_t status);
 
 /* ABI version of this header (increments on any struct or signature change). */
-int32_t bnb_abi_version(void);  /* 8 */
+int32_t bnb_abi_version(void);  /* 9 */
 
 #ifdef __cplusplus
 }

@@ -64,7 +64,7 @@ class bnb_index(C.Structure):
 
 class bnb_sample_cfg(C.Structure):
     _fields_ = [("gamma", f32), ("seed", u64), ("newton_iters", i32), ("polish_iters", i32), ("tol", f32),
-                ("worklist_capacity", i64), ("bins", i32), ("reserved", i32)]
+                ("worklist_capacity", i64), ("bins", i32), ("stoc_trials", i32)]
 
 
 class bnb_sample_stats(C.Structure):
@@ -443,9 +443,11 @@ def sample_and_solve(ds: DeviceScene, index: Index, gamma: float, seed: int, new
                      polish_iters: int = 1, tol: float = 1e-5, worklist_capacity: Optional[int] = None,
                      su: Optional[torch.Tensor] = None, sv: Optional[torch.Tensor] = None,
                      E_out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None,
-                     sync_check: bool = True, with_sel_count: bool = False, bins: bool = False) -> SampleResult:
+                     sync_check: bool = True, with_sel_count: bool = False, bins: bool = False,
+                     stoc_trials: int = 0) -> SampleResult:
     """Rendering pass.  bins: the bin-packed selection (one draw per group of Sec. 5.3) instead of
-    Algorithm 1's draw per tuple; counters[3] then holds |B|."""
+    Algorithm 1's draw per tuple; counters[3] then holds |B|.  stoc_trials > 0: stochastic Newton
+    starts with the reciprocal weighting (Sec. 6.1 "Stoc"), weights capped at stoc_trials."""
     su = ds.t["su"] if su is None else su
     sv = ds.t["sv"] if sv is None else sv
     n_points = int(su.shape[0])
@@ -455,7 +457,7 @@ def sample_and_solve(ds: DeviceScene, index: Index, gamma: float, seed: int, new
     E = E_out if E_out is not None else torch.empty(n_points, dtype=torch.float32, device=ds.device)
     sel = torch.zeros(n_points, dtype=torch.int32, device=ds.device) if with_sel_count else None
     for _ in range(2):
-        cfg = bnb_sample_cfg(gamma, seed, newton_iters, polish_iters, tol, wl, int(bins), 0)
+        cfg = bnb_sample_cfg(gamma, seed, newton_iters, polish_iters, tol, wl, int(bins), int(stoc_trials))
         need = bnb_sample_and_solve_ws(C.byref(ds.s1), ds.s2_ref(), n_points, wl)
         if ws is None or ws.numel() < need + 256:
             ws = _ws(need, ds.device)

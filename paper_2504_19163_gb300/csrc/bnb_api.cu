@@ -101,7 +101,7 @@ BoundWs carve_bound_ws(void* base, int64_t n_tris, int64_t qcap) {
 
 extern "C" {
 
-int32_t bnb_abi_version(void) { return 8; }
+int32_t bnb_abi_version(void) { return 9; }
 
 const char* bnb_status_string(int32_t s) {
   switch (s) {
@@ -267,8 +267,10 @@ int32_t bnb_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2, const
   if (!stats->counters || !stats->status || !index->offsets) return BNB_ERR_INVALID;
   if (index->grid_res < 1 || index->grid_res > 4096) return BNB_ERR_INVALID;
   if (cfg->worklist_capacity < 0 || cfg->newton_iters < 0 || cfg->newton_iters > 64 || cfg->polish_iters < 0 ||
-      cfg->polish_iters > 8 || !(cfg->gamma >= 0.0f) || !(cfg->tol > 0.0f) || (cfg->bins != 0 && cfg->bins != 1))
+      cfg->polish_iters > 8 || !(cfg->gamma >= 0.0f) || !(cfg->tol > 0.0f) || (cfg->bins != 0 && cfg->bins != 1) ||
+      cfg->stoc_trials < 0 || cfg->stoc_trials > (1 << 20))
     return BNB_ERR_INVALID;
+  if (s2 != nullptr && cfg->stoc_trials > 0) return BNB_ERR_UNSUPPORTED;
   const size_t need = sample_ws_bytes(s1->n_tris, s2 ? s2->n_tris : 0, n_points, cfg->worklist_capacity);
   if (ws_bytes < need || !ws || !aligned256(ws)) return BNB_ERR_INVALID;
   return launch_sample_and_solve(s1, s2, rec, em, index, su, sv, n_points, cfg, E_out, stats, ws,

@@ -181,12 +181,12 @@ __device__ __forceinline__ bool newton_step(const Path<T>& P, T tu, T tv, bool d
 //             the polish.
 //   polish64  float64 polish steps and the acceptance tests.  Returns the path irradiance E
 //             (float64), or a negative value when no admissible root is found.
+// From the start (u, v) given on entry (the deterministic start is the centroid).
 template <bool REFRACT>
-__device__ __forceinline__ bool newton32(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0)[3],
-                                         float I0, const float (&rp0)[3], const float (&re1)[3], const float (&re2)[3],
-                                         float tuf, float tvf, int newton_iters, float eta, float& u, float& v) {
-  u = 1.0f / 3.0f;
-  v = 1.0f / 3.0f;
+__device__ __forceinline__ bool newton32_from(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0)[3],
+                                              float I0, const float (&rp0)[3], const float (&re1)[3],
+                                              const float (&re2)[3], float tuf, float tvf, int newton_iters, float eta,
+                                              float& u, float& v) {
   bool converged = false;
   for (int it = 0; it < newton_iters; ++it) {
     const Path<float> P = eval_path<float, REFRACT>(pf, nf, x0, I0, rp0, re1, re2, u, v, eta);
@@ -202,10 +202,21 @@ __device__ __forceinline__ bool newton32(const float (&pf)[3][3], const float (&
 }
 
 template <bool REFRACT>
+__device__ __forceinline__ bool newton32(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0)[3],
+                                         float I0, const float (&rp0)[3], const float (&re1)[3], const float (&re2)[3],
+                                         float tuf, float tvf, int newton_iters, float eta, float& u, float& v) {
+  u = 1.0f / 3.0f;
+  v = 1.0f / 3.0f;
+  return newton32_from<REFRACT>(pf, nf, x0, I0, rp0, re1, re2, tuf, tvf, newton_iters, eta, u, v);
+}
+
+// The float64 polish; the polished root is returned through ur, vr when given.
+template <bool REFRACT>
 __device__ __forceinline__ double polish64(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0)[3],
                                            float I0, const float (&rp0)[3], const float (&re1)[3],
                                            const float (&re2)[3], float tuf, float tvf, int polish_iters, float tol,
-                                           float eta, float u, float v) {
+                                           float eta, float u, float v, double* ur = nullptr,
+                                           double* vr = nullptr) {
   double ud = u, vd = v;
   bool good = true;
   for (int it = 0; it < polish_iters && good; ++it) {
@@ -214,6 +225,8 @@ __device__ __forceinline__ double polish64(const float (&pf)[3][3], const float 
     good = newton_step<double>(P, (double)tuf, (double)tvf, false, ud, vd, step);
   }
   if (!good) return -1.0;
+  if (ur) *ur = ud;
+  if (vr) *vr = vd;
   const Path<double> P = eval_path<double, REFRACT>(pf, nf, x0, I0, rp0, re1, re2, ud, vd, eta);
   const double fu = P.uk - (double)tuf, fv = P.vk - (double)tvf;
   const double r0 = fu * re1[0] + fv * re2[0], r1 = fu * re1[1] + fv * re2[1], r2 = fu * re1[2] + fv * re2[2];
@@ -221,6 +234,23 @@ __device__ __forceinline__ double polish64(const float (&pf)[3][3], const float 
   const bool inside = ud >= 0.0 && vd >= 0.0 && ud + vd <= 1.0;
   if (P.ok && res < (double)tol && inside && P.t > 0.0 && isfinite(P.E)) return P.E;
   return -1.0;
+}
+
+// Start of stochastic trial t (t >= 0) of (point, tuple key) (Sec. 6.1 "Stoc"): the first two
+// outputs of Philox4x32-10 with counter (point, key) and key seed + (t + 1) * 0x9E3779B97F4A7C15
+// (mod 2^64), as 24-bit integers (a, b) folded into the triangle (a + b > 2^24 -> 2^24 - a, 2^24 - b,
+// decided on the integers), scaled by 2^-24 (exact in float32).
+__device__ __forceinline__ void stoc_start(uint64_t seed, int64_t point, uint64_t key, int t, float& u, float& v) {
+  const uint64_t k = seed + (uint64_t)(t + 1) * 0x9E3779B97F4A7C15ull;
+  uint32_t c[4] = {(uint32_t)point, (uint32_t)((uint64_t)point >> 32), (uint32_t)key, (uint32_t)(key >> 32)};
+  philox4x32_10(c, (uint32_t)k, (uint32_t)(k >> 32));
+  uint32_t a = c[0] >> 8, b = c[1] >> 8;
+  if (a + b > (1u << 24)) {
+    a = (1u << 24) - a;
+    b = (1u << 24) - b;
+  }
+  u = (float)a * (1.0f / 16777216.0f);
+  v = (float)b * (1.0f / 16777216.0f);
 }
 
 // ------------------------------------------------------------------ two-vertex chains

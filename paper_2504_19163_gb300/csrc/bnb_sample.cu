@@ -130,6 +130,8 @@ struct SolveParams {
   int32_t newton_iters, polish_iters;
   float tol;
   float eta;  // refraction: eta'
+  int32_t stoc_trials;  // > 0: stochastic starts with the reciprocal weighting, capped at this count
+  uint64_t seed;
   // pair tuples (s2 given): T2's packed triangles and eta'
   const float4* tri2;
   int32_t n_tris2;
@@ -189,6 +191,53 @@ __global__ void __launch_bounds__(256) polish_k(SolveParams S) {
     if (E >= 0.0) {
       c = (float)(E / (double)S.wl_p[i]);
       ++roots;
+    }
+    S.contrib[i] = c;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) roots += __shfl_xor_sync(0xffffffffu, roots, o);
+  if ((threadIdx.x & 31) == 0 && roots) atomicAdd((unsigned long long*)&S.counters[2], (unsigned long long)roots);
+}
+
+// Stochastic starts with the reciprocal weighting (Sec. 6.1 "Stoc"): per selected tuple, Newton from
+// a uniform random start (the float32 phase and the float64 polish); an accepted root u* is weighted
+// by the number N of further random starts up to the first whose accepted root lies within 1e-4 of
+// u* (geometric, mean 1 / P(reach u*)), N capped at stoc_trials.  contrib = E(u*) N / P.
+template <bool REFRACT>
+__global__ void __launch_bounds__(256) solve_stoc_k(SolveParams S) {
+  const int64_t n = min(*S.n_wl, S.wl_cap);
+  long long roots = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = S.wl_key[i];
+    const int e = (int)(k >> 48), t = (int)(k & 0xFFFFFFull);
+    float c = 0.0f;
+    if (t < S.n_tris && e < S.n_emitters) {
+      float pf[3][3], nf[3][3];
+      load_tri_s(S.tri, t, pf, nf);
+      const float x0[3] = {__ldg(S.ex + e), __ldg(S.ey + e), __ldg(S.ez + e)};
+      const float I0 = __ldg(S.ei + e);
+      const int64_t pt = S.wl_point[i];
+      const float tu = S.su[pt], tv = S.sv[pt];
+      auto solve_from = [&](int trial, double& ur, double& vr) -> double {
+        float u, v;
+        stoc_start(S.seed, pt, k, trial, u, v);
+        if (!newton32_from<REFRACT>(pf, nf, x0, I0, S.rp0, S.re1, S.re2, tu, tv, S.newton_iters, S.eta, u, v))
+          return -1.0;
+        return polish64<REFRACT>(pf, nf, x0, I0, S.rp0, S.re1, S.re2, tu, tv, S.polish_iters, S.tol, S.eta, u, v,
+                                 &ur, &vr);
+      };
+      double ur = 0.0, vr = 0.0;
+      const double E = solve_from(0, ur, vr);
+      if (E >= 0.0) {
+        int nw = 1;
+        for (; nw < S.stoc_trials; ++nw) {
+          double u2 = 0.0, v2 = 0.0;
+          const double E2 = solve_from(nw, u2, v2);
+          if (E2 >= 0.0 && fabs(u2 - ur) <= 1e-4 && fabs(v2 - vr) <= 1e-4) break;
+        }
+        c = (float)(E * (double)nw / (double)S.wl_p[i]);
+        ++roots;
+      }
     }
     S.contrib[i] = c;
   }
@@ -386,7 +435,14 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2
   S.tri2 = w.tri2;
   S.n_tris2 = s2 ? s2->n_tris : 0;
   S.eta2 = s2 ? s2->eta : 1.0f;
-  if (s2) {
+  S.stoc_trials = cfg->stoc_trials;
+  S.seed = cfg->seed;
+  if (!s2 && cfg->stoc_trials > 0) {
+    if (s1->kind == BNB_REFRACT)
+      solve_stoc_k<true><<<sms * 16, 256, 0, st>>>(S);
+    else
+      solve_stoc_k<false><<<sms * 16, 256, 0, st>>>(S);
+  } else if (s2) {
     solve32_pair_k<<<sms * 16, 256, 0, st>>>(S);
     polish_pair_k<<<sms * 16, 256, 0, st>>>(S);
   } else if (s1->kind == BNB_REFRACT) {

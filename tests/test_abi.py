@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(bnb):
 def test_status_strings_and_version(bnb):
     assert bnb.bnb_status_string(0) == "ok"
     assert "capacity" in bnb.bnb_status_string(-2)
-    assert bnb.lib().bnb_abi_version() == 8
+    assert bnb.lib().bnb_abi_version() == 9
 
 
 def test_workspace_queries_are_host_only(bnb):
