@@ -101,6 +101,44 @@ def test_invalid_arguments_rejected_before_launch(bnb):
     assert rc == bnb.BNB_ERR_INVALID
 
 
+def test_new_configuration_fields_rejected_before_launch(bnb):
+    """Adaptive depth beyond the cell-id limit, a negative split capacity, a bins flag other than 0/1
+    and a negative stochastic-trial cap are refused by the argument checks (nothing is launched)."""
+    s = bnb.bnb_surface()
+    s.n_tris, s.n_verts = 8, 9
+    for f in ("px", "py", "pz", "nx", "ny", "nz", "i0", "i1", "i2"):
+        setattr(s, f, 4096)
+    em = bnb.bnb_emitters(1, 4096, 4096, 4096, 4096)
+    rec = bnb.bnb_receiver()
+    out = bnb.bnb_cell_bounds()
+    out.capacity = 0
+    out.count = out.status = 4096
+    for cfg in (bnb.bnb_bound_cfg(1, 4, 1, 0, 16, 0.0, 0.0, 0, 0),   # adapt_depth > 15
+                bnb.bnb_bound_cfg(1, 4, 1, 0, 12, 0.0, 0.0, 0, 0),   # adapt_depth + extra splits > 15
+                bnb.bnb_bound_cfg(1, 4, 1, 0, 3, -1.0, 0.0, 0, 0),   # sigma < 0
+                bnb.bnb_bound_cfg(1, 4, 1, 0, 3, 0.0, float("nan"), 0, 0),
+                bnb.bnb_bound_cfg(1, 4, 1, 0, 0, 0.0, 0.0, 0, -5)):  # split capacity < 0
+        rc = bnb.bnb_bound_tuples(C.byref(s), None, C.byref(rec), C.byref(em), C.byref(cfg), C.byref(out), None, 0,
+                                  None)
+        assert rc == bnb.BNB_ERR_INVALID
+    idx = bnb.bnb_index()
+    idx.grid_res, idx.capacity, idx.count, idx.status, idx.offsets = 512, 0, 4096, 4096, 4096
+    stats = bnb.bnb_sample_stats(4096, 4096, None)
+    for scfg in (bnb.bnb_sample_cfg(1.0, 0, 16, 1, 1e-5, 0, 2, 0), bnb.bnb_sample_cfg(1.0, 0, 16, 1, 1e-5, 0, 0, -1)):
+        rc = bnb.bnb_sample_and_solve(C.byref(s), None, C.byref(rec), C.byref(em), C.byref(idx), None, None, 0,
+                                      C.byref(scfg), None, C.byref(stats), None, 0, None)
+        assert rc == bnb.BNB_ERR_INVALID
+    # stochastic starts for two-vertex chains are not built
+    s2 = bnb.bnb_surface()
+    C.pointer(s2)[0] = s
+    s.kind = s2.kind = bnb.BNB_REFRACT
+    s.eta, s2.eta = 0.66, 1.5
+    scfg = bnb.bnb_sample_cfg(1.0, 0, 16, 1, 1e-5, 0, 0, 8)
+    rc = bnb.bnb_sample_and_solve(C.byref(s), C.byref(s2), C.byref(rec), C.byref(em), C.byref(idx), None, None, 0,
+                                  C.byref(scfg), None, C.byref(stats), None, 0, None)
+    assert rc == bnb.BNB_ERR_UNSUPPORTED
+
+
 def test_no_oracle_import_in_library_path():
     """The product path never imports or links the oracle."""
     pkg = os.path.join(ROOT, "paper_2504_19163_gb300")
