@@ -48,7 +48,8 @@ struct Path {
   bool ok;
 };
 
-template <typename T, bool REFRACT>
+// DERIV = false: the receiver coordinates, t and ok only (no Jacobian, no E).
+template <typename T, bool REFRACT, bool DERIV = true>
 __device__ __forceinline__ Path<T> eval_path(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0f)[3],
                                             float I0, const float (&rp0)[3], const float (&re1)[3],
                                             const float (&re2)[3], T u, T v, float etaf) {
@@ -96,9 +97,9 @@ __device__ __forceinline__ Path<T> eval_path(const float (&pf)[3][3], const floa
   cross(E2, w, he2w);
   cross(w, E1, hwe1);
   const T Q = dot(dt, g), A = dot(dt, he2w), B = dot(hwe1, dt);
-  T dA[2], dB[2], dQ[2];
+  T dA[2] = {T(0), T(0)}, dB[2] = {T(0), T(0)}, dQ[2] = {T(0), T(0)};
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < (DERIV ? 2 : 0); ++j) {
     const T* dx = j == 0 ? e1 : e2;
     const T* dnv = j == 0 ? f1 : f2;
     const T dnn = T(2) * dot(n, dnv);
@@ -124,6 +125,13 @@ __device__ __forceinline__ Path<T> eval_path(const float (&pf)[3][3], const floa
   const T iq = T(1) / Q;
   r.uk = A * iq;
   r.vk = B * iq;
+  if constexpr (!DERIV) {
+    r.J00 = r.J01 = r.J10 = r.J11 = T(0);
+    r.E = T(0);
+    r.t = dot(hwe1, E2) * iq;
+    r.ok = !tir && isfinite(r.uk) && isfinite(r.vk) && Q != T(0);
+    return r;
+  }
   r.J00 = (dA[0] * Q - A * dQ[0]) * iq * iq;
   r.J01 = (dA[1] * Q - A * dQ[1]) * iq * iq;
   r.J10 = (dB[0] * Q - B * dQ[0]) * iq * iq;
@@ -210,30 +218,42 @@ __device__ __forceinline__ bool newton32(const float (&pf)[3][3], const float (&
   return newton32_from<REFRACT>(pf, nf, x0, I0, rp0, re1, re2, tuf, tvf, newton_iters, eta, u, v);
 }
 
-// The float64 polish; the polished root is returned through ur, vr when given.
+// The float64 polish, mixed precision: Newton steps whose residual is evaluated in float64 (the
+// receiver coordinates only) and whose Jacobian is the float32 one at the float32 root (iterative
+// refinement: from a root known to ~1e-6 with a Jacobian accurate to ~1e-6 one step leaves
+// ~1e-12); the acceptance tests in float64 at the polished root, E from the float32 derivatives
+// there (relative error ~1e-6).  The polished root is returned through ur, vr when given.
 template <bool REFRACT>
 __device__ __forceinline__ double polish64(const float (&pf)[3][3], const float (&nf)[3][3], const float (&x0)[3],
                                            float I0, const float (&rp0)[3], const float (&re1)[3],
                                            const float (&re2)[3], float tuf, float tvf, int polish_iters, float tol,
                                            float eta, float u, float v, double* ur = nullptr,
                                            double* vr = nullptr) {
+  const Path<float> Pf = eval_path<float, REFRACT>(pf, nf, x0, I0, rp0, re1, re2, u, v, eta);
+  const double J00 = Pf.J00, J01 = Pf.J01, J10 = Pf.J10, J11 = Pf.J11;
+  const double det = J00 * J11 - J01 * J10;
+  if (!Pf.ok || !(det != 0.0) || !isfinite(det)) return -1.0;
   double ud = u, vd = v;
-  bool good = true;
-  for (int it = 0; it < polish_iters && good; ++it) {
-    const Path<double> P = eval_path<double, REFRACT>(pf, nf, x0, I0, rp0, re1, re2, ud, vd, eta);
-    double step;
-    good = newton_step<double>(P, (double)tuf, (double)tvf, false, ud, vd, step);
+  for (int it = 0; it < polish_iters; ++it) {
+    const Path<double> H = eval_path<double, REFRACT, false>(pf, nf, x0, I0, rp0, re1, re2, ud, vd, eta);
+    if (!H.ok) return -1.0;
+    const double fu = H.uk - (double)tuf, fv = H.vk - (double)tvf;
+    ud -= (J11 * fu - J01 * fv) / det;
+    vd -= (-J10 * fu + J00 * fv) / det;
+    if (!isfinite(ud) || !isfinite(vd)) return -1.0;
   }
-  if (!good) return -1.0;
   if (ur) *ur = ud;
   if (vr) *vr = vd;
-  const Path<double> P = eval_path<double, REFRACT>(pf, nf, x0, I0, rp0, re1, re2, ud, vd, eta);
-  const double fu = P.uk - (double)tuf, fv = P.vk - (double)tvf;
+  const Path<double> H = eval_path<double, REFRACT, false>(pf, nf, x0, I0, rp0, re1, re2, ud, vd, eta);
+  if (!H.ok) return -1.0;
+  const double fu = H.uk - (double)tuf, fv = H.vk - (double)tvf;
   const double r0 = fu * re1[0] + fv * re2[0], r1 = fu * re1[1] + fv * re2[1], r2 = fu * re1[2] + fv * re2[2];
   const double res = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
   const bool inside = ud >= 0.0 && vd >= 0.0 && ud + vd <= 1.0;
-  if (P.ok && res < (double)tol && inside && P.t > 0.0 && isfinite(P.E)) return P.E;
-  return -1.0;
+  if (!(res < (double)tol && inside && H.t > 0.0)) return -1.0;
+  const Path<float> Pe = eval_path<float, REFRACT>(pf, nf, x0, I0, rp0, re1, re2, (float)ud, (float)vd, eta);
+  if (!Pe.ok || !isfinite(Pe.E)) return -1.0;
+  return (double)Pe.E;
 }
 
 // Start of stochastic trial t (t >= 0) of (point, tuple key) (Sec. 6.1 "Stoc"): the first two
