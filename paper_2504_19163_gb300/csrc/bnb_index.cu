@@ -286,7 +286,6 @@ __global__ void __launch_bounds__(kSegThreads) segsort_k(const int64_t* __restri
                                                          int n_cells) {
   __shared__ uint64_t K[kSegCap];
   __shared__ float V[kSegCap];
-  __shared__ int nu;
   const int g = blockIdx.x;
   if (g >= n_cells) return;
   const int64_t s = goff[g];
@@ -321,25 +320,40 @@ __global__ void __launch_bounds__(kSegThreads) segsort_k(const int64_t* __restri
         V[b] = tv;
       },
       true);
-  if (threadIdx.x == 0) {
-    int o = 0;
-    for (int i = 0; i < n; ++i) {
-      if (o > 0 && K[o - 1] == K[i]) {
-        V[o - 1] = fmaxf(V[o - 1], V[i]);
-      } else {
-        K[o] = K[i];
-        V[o] = V[i];
-        ++o;
-      }
-    }
-    nu = o;
+  // Merge runs of equal keys (max of E~) in parallel: each thread takes a contiguous chunk, counts
+  // the run heads in it, a block scan turns the counts into output positions, and each head writes
+  // its key with the max over its run (runs are short: a tuple is usually listed once per cell).
+  const int per = (n + kSegThreads - 1) / kSegThreads;
+  const int i0 = min(n, (int)threadIdx.x * per), i1 = min(n, i0 + per);
+  int heads = 0;
+  for (int i = i0; i < i1; ++i) heads += (i == 0 || K[i] != K[i - 1]);
+  __shared__ int wsum[kSegThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = heads;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
   }
+  if (lane == 31) wsum[wid] = incl;
   __syncthreads();
-  for (int i = threadIdx.x; i < nu; i += blockDim.x) {
-    s_key[s + i] = K[i];
-    s_e[s + i] = V[i];
+  int before = 0;
+  for (int w = 0; w < wid; ++w) before += wsum[w];
+  int pos = before + incl - heads;
+  for (int i = i0; i < i1; ++i) {
+    if (i == 0 || K[i] != K[i - 1]) {
+      float m = V[i];
+      for (int j = i + 1; j < n && K[j] == K[i]; ++j) m = fmaxf(m, V[j]);
+      s_key[s + pos] = K[i];
+      s_e[s + pos] = m;
+      ++pos;
+    }
   }
-  if (threadIdx.x == 0) rcount[g] = nu;
+  if (threadIdx.x == kSegThreads - 1) {
+    int total = 0;
+    for (int w = 0; w < kSegThreads / 32; ++w) total += wsum[w];
+    rcount[g] = total;
+  }
 }
 
 __global__ void __launch_bounds__(512) segsort_big_k(const int64_t* __restrict__ goff, uint64_t* __restrict__ s_key,
