@@ -123,6 +123,23 @@ def test_pair_bounds_match_oracle(B, orc, n, depth, amp):
     assert_pair_parity(rep)
 
 
+def test_pairs_with_two_lights_match_oracle(B, orc):
+    """Tuple construction and the composite bound per emitter: the emitter is part of every
+    candidate's key, and both lights' chains render like the oracle's."""
+    sc = S.config("slab", n=4, depth=1, amp=0.04, points=32, lights=[(0.1, -0.05, 2.0), (-0.3, 0.2, 1.6)])
+    _, _, g = gpu_pairs(B, sc)
+    assert set(np.unique(g["emitter"]).tolist()) == {0, 1}
+    rep, _ = compare_pairs(orc, sc, g)
+    assert_pair_parity(rep)
+    _, _, res = render_gpu(B, sc)
+    out = orc.render_pairs(sc, gamma=1.0, seed=1, n_threads=8)
+    E, Eo = res.E.cpu().numpy().astype(np.float64), out["E"]
+    pos = Eo > 0
+    assert pos.sum() > 200
+    rel = np.abs(E[pos] - Eo[pos]) / Eo[pos]
+    assert np.mean(rel <= E_REL) >= 0.998, np.sort(rel)[-5:]
+
+
 def test_pair_fp64_mode_matches_oracle(B, orc):
     sc = S.config("slab", n=4, depth=1, amp=0.04)
     _, _, g = gpu_pairs(B, sc, fp64=True)
