@@ -1163,15 +1163,16 @@ MV mv_crossc(const MV& a, V3 b) {  // a x b, b constant
           mp_add(mp_scale(a.x, b.y), mp_scale(a.y, b.x), -1.0)};
 }
 
-// The first vertex on one cell of T1: x1 (degree 1) and the refracted d~1 on the faces xi1 = 0, 1
-// (degree 5), as in the single-refraction bound.
+// The first vertex on one cell of T1: x1 (degree 1) and the scattered d~1 on the faces xi1 = 0, 1
+// (degree 5): refraction as in the single-refraction bound; reflection (kind 0) has no remainder,
+// d~1 = (n.n) d0 - 2 (d0.n) n on both faces (degree 3, elevated).
 struct Vertex1 {
   bool tir = false;
   PV x1;
   PV dt[2];
 };
 
-Vertex1 first_vertex(const Tri& T, V3 x0, double eta, const UV C[3]) {
+Vertex1 first_vertex(const Tri& T, V3 x0, int kind, double eta, const UV C[3]) {
   Vertex1 S;
   V3 e11 = T.p[1] - T.p[0], e12 = T.p[2] - T.p[0];
   V3 n1d = T.n[1] - T.n[0], n2d = T.n[2] - T.n[0];
@@ -1184,6 +1185,10 @@ Vertex1 first_vertex(const Tri& T, V3 x0, double eta, const UV C[3]) {
   PV n1 = pv_affine(nc[0], nc[1], nc[2]);
   PV d0 = pv_subc(S.x1, x0);
   Poly nn = pv_dot(n1, n1), dn = pv_dot(d0, n1), ss = pv_dot(d0, d0);
+  if (kind == 0) {  // Eq. eq_refr_rational, reflection
+    S.dt[0] = S.dt[1] = pv_elev(pv_sub(pv_mul(nn, d0), pv_mul(dn, n1), 2.0), 5);
+    return S;
+  }
   Poly beta = padd(pscale(pmul(nn, ss), 1.0 - eta * eta), pscale(pmul(dn, dn), eta * eta));
   const double blo = pmin(beta), bhi = pmax(beta);
   if (!(bhi > 0.0)) {
@@ -1292,7 +1297,8 @@ bool pair_candidate(const Bundle& B, const Box3& b, double* gap) {
   return *gap <= 0.0;
 }
 
-// Direct geometry of the chain: unit normals, the vector form of Snell's law at both vertices,
+// Direct geometry of the chain: unit normals, the vector form of Snell's law (or of the mirror law) at
+// each vertex,
 // ray/plane hits (T2's plane, then the receiver's), derivatives by duals.  u2, v2: barycentrics of
 // the hit on T2's plane; t1, t2: ray parameters of the two hits (forward when > 0).
 struct PairEval {
@@ -1312,6 +1318,10 @@ void plane_coords(DV3 rel, V3 a, V3 b, Dual* U, Dual* V) {  // rel = U a + V b i
 bool snell(DV3 ih, DV3 n, double eta, DV3* out) {  // ih unit incident direction, n normal (any length)
   Dual ln = dsqrt(ddot(n, n));
   DV3 nh = {n.x / ln, n.y / ln, n.z / ln};
+  if (eta < 0.0) {  // a mirror (kind 0, passed as eta < 0): r = i - 2 (i.n) n
+    *out = ih - (dc(2.0) * ddot(ih, nh)) * nh;
+    return true;
+  }
   Dual c1 = dc(0.0) - ddot(ih, nh);
   Dual k = dc(1.0) - dc(eta * eta) * (dc(1.0) - c1 * c1);
   if (!(k.v > 0.0)) return false;
@@ -1319,6 +1329,7 @@ bool snell(DV3 ih, DV3 n, double eta, DV3* out) {  // ih unit incident direction
   return true;
 }
 
+// eta1 / eta2 < 0 mark a reflecting vertex.
 PairEval eval_pair_direct(const Tri& A, const Tri& B, V3 x0, double I0, const Rec& R, double eta1, double eta2,
                           double u, double v) {
   PairEval P{};
@@ -1372,6 +1383,8 @@ struct Ctx2 {
   Rec rec;
   const orc_emitters* em;
 };
+// The vertex law for the direct evaluator: eta' for refraction, -1 for reflection.
+double law(const orc_surface* s) { return s->kind == 0 ? -1.0 : (double)s->eta; }
 
 // Expansion point of the second vertex's receiver forms: the receiver coordinates of the chain
 // through the cell's centroid (no containment test), rounded to 2^-16; per coordinate 0.5 where
@@ -1379,7 +1392,7 @@ struct Ctx2 {
 // a valid bound.
 void centroid_hit(const Ctx2& cx, const Tri& A, const Tri& B, V3 x0, const UV C[3], double* uc, double* vc) {
   const double cu = (C[0].u + C[1].u + C[2].u) / 3.0, cv = (C[0].v + C[1].v + C[2].v) / 3.0;
-  PairEval P = eval_pair_direct(A, B, x0, 1.0, cx.rec, cx.s1->eta, cx.s2->eta, cu, cv);
+  PairEval P = eval_pair_direct(A, B, x0, 1.0, cx.rec, law(cx.s1), law(cx.s2), cu, cv);
   const double a = P.ok && std::fabs(P.uk) < 4.0 ? P.uk : 0.5;
   const double b = P.ok && std::fabs(P.vk) < 4.0 ? P.vk : 0.5;
   *uc = std::nearbyint(a * 65536.0) / 65536.0;
@@ -1405,7 +1418,7 @@ void bound_cell_pair(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int 
     r.e_hi = inf;
     r.flags |= F_LIVE | F_POS_UNBOUNDED;
   };
-  const Vertex1 S = first_vertex(A, x0, cx.s1->eta, C);
+  const Vertex1 S = first_vertex(A, x0, cx.s1->kind, cx.s1->eta, C);
   if (S.tir) {
     r.flags |= F_TIR;
     return;
@@ -1476,23 +1489,31 @@ void bound_cell_pair(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int 
   const MV d1 = mv_sub(x2, MV{{S.x1.x, 0.0}, {S.x1.y, 0.0}, {S.x1.z, 0.0}});
   const double eta = cx.s2->eta;
   const MP nn = mv_dot(n2, n2), dn = mv_dot(d1, n2), ss = mv_dot(d1, d1);
-  const MP beta = mp_add(mp_scale(mp_mul(nn, ss), 1.0 - eta * eta), mp_scale(mp_mul(dn, dn), eta * eta));
-  const double blo = pmin(beta.p) - beta.r, bhi = pmax(beta.p) + beta.r;
-  if (!(bhi > 0.0)) {
-    r.flags |= F_TIR;
-    return;
+  MV dtf[2];  // d~2 on the faces xi2 = 0, 1 (degree 5)
+  if (cx.s2->kind == 0) {  // reflection: (n.n) d1 - 2 (d1.n) n, no remainder
+    dtf[0] = dtf[1] = mv_elev(mv_sub(mv_mul(nn, d1), mv_scale(mv_mul(dn, n2), 2.0)), 5);
+  } else {
+    const MP beta = mp_add(mp_scale(mp_mul(nn, ss), 1.0 - eta * eta), mp_scale(mp_mul(dn, dn), eta * eta));
+    const double blo = pmin(beta.p) - beta.r, bhi = pmax(beta.p) + beta.r;
+    if (!(bhi > 0.0)) {
+      r.flags |= F_TIR;
+      return;
+    }
+    double a, b, dlo, dhi;
+    chord_sqrt(std::max(blo, 0.0), bhi, &a, &b, &dlo, &dhi);
+    const MV tang = mv_elev(mv_scale(mv_sub(mv_mul(nn, d1), mv_mul(dn, n2)), eta), 5);
+    for (int j = 0; j < 2; ++j) {
+      const MP Wj = mp_shift(mp_scale(beta, a), b + (j == 0 ? dlo : dhi));
+      dtf[j] = mv_sub(tang, mv_mul(Wj, n2));
+    }
   }
-  double a, b, dlo, dhi;
-  chord_sqrt(std::max(blo, 0.0), bhi, &a, &b, &dlo, &dhi);
-  const MV tang = mv_elev(mv_scale(mv_sub(mv_mul(nn, d1), mv_mul(dn, n2)), eta), 5);
   double uc, vc;
   centroid_hit(cx, A, B, x0, C, &uc, &vc);
   const V3 pp = R.p0 + uc * R.e1 + vc * R.e2;
   const MV w3 = {mp_shift(x2.x, -pp.x), mp_shift(x2.y, -pp.y), mp_shift(x2.z, -pp.z)};
   MP Q3[2], A3[2], B3[2];
   for (int j = 0; j < 2; ++j) {
-    const MP Wj = mp_shift(mp_scale(beta, a), b + (j == 0 ? dlo : dhi));
-    const MV dt = mv_sub(tang, mv_mul(Wj, n2));
+    const MV& dt = dtf[j];
     const MV dxe = mv_crossc(dt, R.e2);
     Q3[j] = mv_dotc(dxe, R.e1);
     A3[j] = mv_dot(dxe, w3);
@@ -1888,7 +1909,7 @@ int orc_eval_direct(const orc_surface* s1, const orc_receiver* rec, const orc_em
 int orc_pair_candidates(const orc_surface* s1, const orc_surface* s2, const orc_emitters* em, int32_t depth,
                         int32_t* out_e, int32_t* out_t1, uint32_t* out_cell, int32_t* out_t2, int64_t cap,
                         int64_t* n_out, int32_t n_threads) {
-  if (s1->kind != 1 || s2->kind != 1) return -4;
+  if (s1->kind < 0 || s1->kind > 1 || s2->kind < 0 || s2->kind > 1) return -4;
   std::vector<Box3> boxes(s2->n_tris);
   for (int t = 0; t < s2->n_tris; ++t) boxes[t] = tri_box(get_tri(s2, t));
   const int64_t total = (int64_t)em->n * s1->n_tris * ((int64_t)1 << (2 * depth));
@@ -1902,7 +1923,7 @@ int orc_pair_candidates(const orc_surface* s1, const orc_surface* s2, const orc_
       UV C[3];
       cell_corners(c, depth, C);
       const V3 x0 = {em->x[e], em->y[e], em->z[e]};
-      const Bundle B = ray_bundle(first_vertex(get_tri(s1, t), x0, s1->eta, C));
+      const Bundle B = ray_bundle(first_vertex(get_tri(s1, t), x0, s1->kind, s1->eta, C));
       if (B.kind == 0) continue;
       for (int t2 = 0; t2 < s2->n_tris; ++t2) {
         double gap;
@@ -1934,7 +1955,7 @@ int orc_pair_gap(const orc_surface* s1, const orc_surface* s2, const orc_emitter
     UV C[3];
     cell_corners(cell[i], depth, C);
     const V3 x0 = {em->x[e[i]], em->y[e[i]], em->z[e[i]]};
-    pair_candidate(ray_bundle(first_vertex(get_tri(s1, t1[i]), x0, s1->eta, C)), tri_box(get_tri(s2, t2[i])),
+    pair_candidate(ray_bundle(first_vertex(get_tri(s1, t1[i]), x0, s1->kind, s1->eta, C)), tri_box(get_tri(s2, t2[i])),
                    &gap[i]);
   }
   return 0;
@@ -1944,7 +1965,7 @@ int orc_pair_gap(const orc_surface* s1, const orc_surface* s2, const orc_emitter
 int orc_bound_pairs(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec, const orc_emitters* em,
                     int32_t depth, const int32_t* e, const int32_t* t1, const uint32_t* cell, const int32_t* t2,
                     int64_t n, orc_record* out, int32_t n_threads) {
-  if (s1->kind != 1 || s2->kind != 1) return -4;
+  if (s1->kind < 0 || s1->kind > 1 || s2->kind < 0 || s2->kind > 1) return -4;
   Ctx2 cx{s1, s2, get_rec(rec), em};
   parallel_for(n, std::max(1, (int)n_threads), [&](int, int64_t a, int64_t b) {
     for (int64_t i = a; i < b; ++i) bound_cell_pair(cx, e[i], t1[i], cell[i], depth, t2[i], out[i]);
@@ -1959,7 +1980,7 @@ int orc_eval_pair(const orc_surface* s1, const orc_surface* s2, const orc_receiv
   const Tri A = get_tri(s1, t1), B = get_tri(s2, t2);
   const V3 x0 = {em->x[e], em->y[e], em->z[e]};
   for (int64_t i = 0; i < n; ++i) {
-    PairEval P = eval_pair_direct(A, B, x0, em->intensity[e], R, s1->eta, s2->eta, u[i], v[i]);
+    PairEval P = eval_pair_direct(A, B, x0, em->intensity[e], R, law(s1), law(s2), u[i], v[i]);
     const double nan = std::numeric_limits<double>::quiet_NaN();
     const double vals[8] = {P.uk, P.vk, P.E, P.u2, P.v2, P.t1, P.t2, P.detJ};
     for (int k = 0; k < 8; ++k) out[i * 8 + k] = P.ok ? vals[k] : nan;
@@ -1990,7 +2011,7 @@ int orc_solve_pair(const orc_surface* s1, const orc_surface* s2, const orc_recei
       double u = 1.0 / 3.0, v = 1.0 / 3.0;
       bool bad = false;
       for (int it = 0; it < newton_iters + polish_iters; ++it) {
-        PairEval P = eval_pair_direct(A, B, x0, I0, R, s1->eta, s2->eta, u, v);
+        PairEval P = eval_pair_direct(A, B, x0, I0, R, law(s1), law(s2), u, v);
         const double det = P.detJ;
         if (!P.ok || !(det != 0.0) || !std::isfinite(det)) {
           bad = true;
@@ -2016,7 +2037,7 @@ int orc_solve_pair(const orc_surface* s1, const orc_surface* s2, const orc_recei
       root_u[i] = u;
       root_v[i] = v;
       if (bad) continue;
-      PairEval P = eval_pair_direct(A, B, x0, I0, R, s1->eta, s2->eta, u, v);
+      PairEval P = eval_pair_direct(A, B, x0, I0, R, law(s1), law(s2), u, v);
       if (!P.ok) continue;
       const V3 res = (P.uk - tu) * R.e1 + (P.vk - tv) * R.e2;
       const bool in1 = u >= 0.0 && v >= 0.0 && u + v <= 1.0;

@@ -370,6 +370,28 @@ def config(name: str, **kw) -> Scene:
         p = kw.get("points", 32)
         su, sv = shading_points(p, p, 1006)
         return Scene(name, top, bot, receiver_square(-1.0, kw.get("rec_half", 0.8)), em, kw.get("depth", 1), su, sv)
+    if name in ("periscope", "mirror_glass"):
+        # two specular vertices with reflection: a mirror heightfield at z=0 (normals up) lit from
+        # above, then at z=1 either a second mirror facing down (periscope; receiver between them at
+        # z=0.5) or a refracting interface into glass (eta' 1/1.5, normals facing down, the incident
+        # side; receiver above at z=1.5); n^2 faces over [-ext, ext]^2, 4 sinusoids each
+        n = kw.get("n", 3)
+        ext = kw.get("extent", 0.5)
+        flat = kw.get("flat", False)
+        amp = kw.get("amp", 0.02)
+        mk = lambda seed, **a: (heightfield(n, seed, n_waves=1, amp_total=0.0, normals="flat_up", extent=ext, **a)
+                                if flat else heightfield(n, seed, n_waves=4, amp_total=amp, extent=ext, **a))
+        bottom = mk(kw.get("seed", 8))
+        if name == "periscope":
+            top = mk(kw.get("seed", 8) + 1000, z0=1.0, flip_normals=True)
+            rec = receiver_square(0.5, kw.get("rec_half", 1.0))
+        else:
+            top = mk(kw.get("seed", 8) + 1000, z0=1.0, flip_normals=True, kind=SURFACE_REFRACT, eta=1.0 / 1.5)
+            rec = receiver_square(1.5, kw.get("rec_half", 1.0))
+        em = point_emitters(kw.get("lights", [(0.05, -0.03, 2.0)]), 1.0)
+        p = kw.get("points", 32)
+        su, sv = shading_points(p, p, 1007)
+        return Scene(name, bottom, top, rec, em, kw.get("depth", 1), su, sv)
     if name == "tiny":
         # A few triangles: exhaustive enumeration fits in milliseconds.
         n = kw.get("n", 4)

@@ -127,7 +127,32 @@ def through_t2(P):
 # sqrt chord (the xi faces) and the degree reduction are large enough for a sweep to resolve them
 @pytest.mark.parametrize("n,depth,amp,k", [(4, 1, 0.02, 30), (4, 1, 0.06, 30), (2, 0, 0.15, 90)])
 def test_pair_boxes_contain_dense_sweep_and_prune_nothing(n, depth, amp, k):
-    sc = S.config("slab", n=n, depth=depth, amp=amp)
+    check_containment(S.config("slab", n=n, depth=depth, amp=amp), depth, k)
+
+
+# reflection at the first vertex (then a mirror or a refracting interface), curved faces
+@pytest.mark.parametrize("name,amp", [("periscope", 0.04), ("mirror_glass", 0.04), ("periscope", 0.12)])
+def test_reflecting_chains_contain_dense_sweep_and_prune_nothing(name, amp):
+    check_containment(S.config(name, n=4, depth=1, amp=amp), 1, 30)
+
+
+def test_flat_periscope_closed_form():
+    """Two flat parallel mirrors (z = 0 facing up, z = 1 facing down) and a light at (0,0,2): the
+    chain unfolds into the straight ray from the double image (0,0,4), so the hit on the receiver
+    z = 0.5 is x3 = 1.75 x1 and E = I0 3.5 / |x3 - (0,0,4)|^3."""
+    sc = S.config("periscope", n=2, flat=True, extent=1.0, lights=[(0.0, 0.0, 2.0)], rec_half=1.5)
+    rng = np.random.default_rng(2)
+    for t in range(sc.s1.n_tris):
+        u = rng.uniform(0, 1, 40)
+        v = rng.uniform(0, 1, 40) * (1 - u)
+        P = O.eval_pair(sc, 0, t, 0, u, v)
+        x1 = tri_points(sc.s1, t, u, v)[:, :2]
+        X = receiver_xy(sc, P["uk"], P["vk"])
+        np.testing.assert_allclose(X, 1.75 * x1, atol=1e-12)
+        np.testing.assert_allclose(P["E"], 3.5 / (np.sum(X ** 2, axis=1) + 3.5 ** 2) ** 1.5, rtol=1e-12)
+
+
+def check_containment(sc, depth, k):
     e, t1, cell, t2 = O.pair_candidates(sc)
     cand = set(zip(e.tolist(), t1.tolist(), cell.tolist(), t2.tolist()))
     rec = O.bound_pairs(sc, e, t1, cell, t2)
@@ -176,11 +201,12 @@ def test_pair_boxes_tighten_under_subdivision():
     assert ratios[3] < ratios[0] and ratios[3] < 1.01
 
 
-def test_estimator_equals_exhaustive_enumeration():
+@pytest.mark.parametrize("name", ["slab", "periscope", "mirror_glass"])
+def test_estimator_equals_exhaustive_enumeration(name):
     """With P = 1 the estimate at a point is the sum of E over the roots of the tuples listed there;
     running the same Newton solve over every (T1, T2) pair must give the same sum: no tuple that
     carries a root was pruned by tuple construction, the bounds or the index."""
-    sc = S.config("slab", n=3, depth=1, amp=0.04, points=20)
+    sc = S.config(name, n=3, depth=1, amp=0.04, points=20)
     out = O.render_pairs(sc, gamma=1.0, seed=1)
     n_pts = sc.su.shape[0]
     pts = np.repeat(np.arange(n_pts), sc.s1.n_tris * sc.s2.n_tris)
