@@ -188,15 +188,16 @@ typedef struct bnb_sample_stats {
  * e_hi = +inf (its irradiance is not bounded).  Requires out->capacity >= n_base =
  * em->n * s1->n_tris * 4^depth.  ws: bnb_bound_tuples_ws() bytes.
  *
- * Two specular vertices (s2 != NULL; both surfaces BNB_REFRACT, eta in (0, 1e6),
- * else BNB_ERR_UNSUPPORTED): chains x0 -> T1 (s1) -> T2 (s2) -> receiver.
+ * Two specular vertices (s2 != NULL; each surface BNB_REFLECT, or BNB_REFRACT with
+ * eta in (0, 1e6), else BNB_ERR_UNSUPPORTED): chains x0 -> T1 (s1) -> T2 (s2) ->
+ * receiver, each vertex reflecting or refracting by its surface's kind.
  * Tuple construction (Sec. 6.1): for every (emitter, T1, cell at `depth`), the
- * triangles T2 whose xy box meets the footprint of the cell's refracted rays on
+ * triangles T2 whose xy box meets the footprint of the cell's scattered rays on
  * T2's z-range (from the x1 box and the ratio bounds of d~1x/d~1z, d~1y/d~1z) are
  * candidates; each candidate is one record (tri1 = T2), records of one cell
  * contiguous, cells in base order.  Its box is the composite position bound:
  * u2 reduced to degree 1 plus a remainder (Sec. 6.1 "Degree reduction"), then
- * the second refraction and the receiver forms.  e_hi = +inf for every record
+ * the second reflection or refraction and the receiver forms.  e_hi = +inf for every record
  * (chains carry no irradiance bound; P = 1 in the rendering pass).  A float32
  * sign test that cannot decide is redone in float64 (QSIGN_FP64); a certified
  * mixed-sign denominator gives the full box (POS_UNBOUNDED; no splits:
@@ -240,8 +241,8 @@ size_t bnb_build_index_ws(const bnb_cell_bounds *cells, int32_t grid_res, int64_
  * su, sv, device float arrays).  E_out[p] (device float, n_points) receives the
  * estimate sum_{T in S} E(T) / P_T (Sec. 5.3) with E the path irradiance
  * I0 dOmega0/dA_k of Eq. eq_dwda (visibility and Fresnel ignored, Sec. 4.4).
- * With s2 != NULL (pair tuples of a two-vertex bound pass, both surfaces
- * BNB_REFRACT) every listed key names (emitter, T1, T2) and the Newton solve runs
+ * With s2 != NULL (pair tuples of a two-vertex bound pass, surfaces as there)
+ * every listed key names (emitter, T1, T2) and the Newton solve runs
  * through the chain x0 -> T1 -> T2 -> receiver; a root is accepted when u1 lies in
  * the closed T1, u2 in the closed T2 and both hits are in front.
  * ws: bnb_sample_and_solve_ws(s1, s2, n_points, cfg->worklist_capacity) bytes. */

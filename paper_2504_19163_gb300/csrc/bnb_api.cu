@@ -51,11 +51,11 @@ bool emitters_ok(const bnb_emitters* e) {
 
 bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 
-// Two specular vertices: both surfaces refractive with eta' in (0, 1e6).
-bool pair_ok(const bnb_surface* s1, const bnb_surface* s2) {
-  return s1->kind == BNB_REFRACT && s2->kind == BNB_REFRACT && s1->eta > 0.0f && s1->eta < 1e6f &&
-         s2->eta > 0.0f && s2->eta < 1e6f;
+// Two specular vertices: each reflecting, or refracting with eta' in (0, 1e6).
+bool vertex_ok(const bnb_surface* s) {
+  return s->kind == BNB_REFLECT || (s->kind == BNB_REFRACT && s->eta > 0.0f && s->eta < 1e6f);
 }
+bool pair_ok(const bnb_surface* s1, const bnb_surface* s2) { return vertex_ok(s1) && vertex_ok(s2); }
 
 int64_t n_base_of(const bnb_surface* s1, const bnb_emitters* em, int depth) {
   return (int64_t)em->n * (int64_t)s1->n_tris * ((int64_t)1 << (2 * depth));

@@ -1,5 +1,5 @@
-// Two specular vertices: the bound pass of chains x0 -> T1 -> T2 -> receiver with refraction at
-// both vertices (the TT chains of Table "tab:perf", e.g. a glass slab).
+// Two specular vertices: the bound pass of chains x0 -> T1 -> T2 -> receiver, each vertex
+// reflecting or refracting (e.g. the TT chains of Table "tab:perf" through a glass slab).
 //
 //   s2 grid        s2_bbox_k, s2_bin_k, scan, s2_fill_k, s2_sort_k: a uniform grid over the xy box
 //                  of s2; every triangle is listed once, in the grid cell of its xy box's lower
@@ -39,6 +39,7 @@ struct PairParams {
   const float *ex, *ey, *ez;
   float rp0[3], re1[3], re2[3];
   float eta1, eta2;
+  int32_t kind1, kind2;  // BNB_REFLECT or BNB_REFRACT per vertex
   int32_t depth;
   int64_t n_base;
   int32_t G;
@@ -164,14 +165,42 @@ __global__ void s2_sort_k(int cells, const int64_t* __restrict__ cell_off, int32
   }
 }
 
-// ------------------------------------------------------------------ refraction faces
-// d~ = eta' ((n.n) d - (d.n) n) - r~(beta) n on the two faces of the remainder variable of
-// sqrt(beta) (Sec. 4.3), from degree-1 forms n and d (tracked errors may hold remainders).
-// Returns false when beta <= 0 on the whole cell (total internal reflection).
+// ------------------------------------------------------------------ vertex faces
+// The scattered direction at a vertex from degree-1 forms n and d (tracked errors may hold
+// remainders), on the two faces of a remainder variable: refraction (Eq. eq_refr_rational)
+// d~ = eta' ((n.n) d - (d.n) n) - r~(beta) n with sqrt(beta)'s remainder (Sec. 4.3); reflection
+// d~ = (n.n) d - 2 (d.n) n on both faces (no remainder).  Returns false when beta <= 0 on the whole
+// cell (total internal reflection).
 template <typename T>
-__device__ __forceinline__ bool refract_faces(const TP<T, 1> (&N)[3], const TP<T, 1> (&D)[3], T eta,
-                                              TP<T, 5> (&DT)[2][3]) {
+__device__ __forceinline__ bool vertex_faces(const TP<T, 1> (&N)[3], const TP<T, 1> (&D)[3], int kind, T eta,
+                                             TP<T, 5> (&DT)[2][3]) {
   using F = FP<T>;
+  if (kind == BNB_REFLECT) {
+    TP<T, 2> NN, DN2;
+    tp_zero(NN);
+    tp_zero(DN2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      mac(NN, N[c], N[c]);
+      mac(DN2, D[c], N[c]);
+    }
+    renorm(NN);
+    renorm(DN2);
+    scale2(DN2);  // 2 (d.n), exact
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      TP<T, 3> r;
+      tp_zero(r);
+      mac(r, NN, D[c]);
+      mac<true>(r, DN2, N[c]);
+      TP<T, 4> r4;
+      elevate(r4, r);
+      elevate(DT[0][c], r4);
+      renorm(DT[0][c]);
+      DT[1][c] = DT[0][c];
+    }
+    return true;
+  }
   TP<T, 2> NN, DN, SS;
   tp_zero(NN);
   tp_zero(DN);
@@ -261,7 +290,7 @@ __device__ __forceinline__ bool first_vertex(const PairParams& P, int e, int t1,
   x0[2] = (T)__ldg(P.ez + e);
   cell_corners<T>(id, P.depth, cu, cv);
   make_leaves<T, false>(p, n, x0, cu, cv, L);
-  return refract_faces<T>(L.N, L.D0, (T)P.eta1, DT);
+  return vertex_faces<T>(L.N, L.D0, P.kind1, (T)P.eta1, DT);
 }
 
 // Ratio bound [lo, hi] of num/den over both faces (den's certified sign sq; degrees 5 and 5).
@@ -438,7 +467,7 @@ __device__ __forceinline__ void put_pair(const PairParams& P, int64_t slot, floa
 
 // Receiver coordinates of the chain through the cell centroid (un-normalized forms, exact square
 // roots, no containment test), rounded to 2^-16; per coordinate 0.5 where the chain has no
-// refracted path or the coordinate is not below 4 in magnitude.  The expansion point of the second
+// scattered path (total internal reflection) or the coordinate is not below 4 in magnitude.  The expansion point of the second
 // vertex's receiver forms (any point is valid).
 template <typename T>
 __device__ __forceinline__ void centroid_hit(const PairParams& P, const T (&p)[3][3], const float (&nf1)[3][3],
@@ -450,8 +479,13 @@ __device__ __forceinline__ void centroid_hit(const PairParams& P, const T (&p)[3
     r[1] = a[2] * b[0] - a[0] * b[2];
     r[2] = a[0] * b[1] - a[1] * b[0];
   };
-  auto refract = [&](const T* n, const T* d, T eta, T* out) {
+  auto refract = [&](const T* n, const T* d, int kind, T eta, T* out) {
     const T nn = dot(n, n), dn = dot(d, n), ss = dot(d, d);
+    if (kind == BNB_REFLECT) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[c] = nn * d[c] - T(2) * dn * n[c];
+      return true;
+    }
     const T beta = (T(1) - eta * eta) * nn * ss + eta * eta * dn * dn;
     if (!(beta > T(0))) return false;
     const T W = sqrt(beta);
@@ -486,7 +520,7 @@ __device__ __forceinline__ void centroid_hit(const PairParams& P, const T (&p)[3
     R2[c] = (T)P.re2[c];
   }
   T a = T(0.5), b = T(0.5);
-  if (refract(n1, d0, (T)P.eta1, t1)) {
+  if (refract(n1, d0, P.kind1, (T)P.eta1, t1)) {
     T u2, v2;
     plane(x1, t1, o2, e21, e22, u2, v2);
 #pragma unroll
@@ -495,7 +529,7 @@ __device__ __forceinline__ void centroid_hit(const PairParams& P, const T (&p)[3
       n2[c] = (T)nf2[0][c] + u2 * ((T)nf2[1][c] - (T)nf2[0][c]) + v2 * ((T)nf2[2][c] - (T)nf2[0][c]);
       d1[c] = x2[c] - x1[c];
     }
-    if (refract(n2, d1, (T)P.eta2, t2)) plane(x2, t2, R0, R1, R2, a, b);
+    if (refract(n2, d1, P.kind2, (T)P.eta2, t2)) plane(x2, t2, R0, R1, R2, a, b);
   }
   if (!(fabs(a) < T(4))) a = T(0.5);
   if (!(fabs(b) < T(4))) b = T(0.5);
@@ -663,7 +697,7 @@ __device__ __forceinline__ bool process_pair(const PairParams& P, int64_t slot, 
     renorm(D1[c]);
   }
   TP<T, 5> DT2[2][3];
-  if (!refract_faces<T>(N2, D1, (T)P.eta2, DT2)) {
+  if (!vertex_faces<T>(N2, D1, P.kind2, (T)P.eta2, DT2)) {
     put_pair(P, slot, 0.f, 0.f, 0.f, 0.f, flags | BNB_CELL_TIR);
     return true;
   }
@@ -876,6 +910,8 @@ cudaError_t launch_bound_pairs(const bnb_surface* s1, const bnb_surface* s2, con
   }
   P.eta1 = s1->eta;
   P.eta2 = s2->eta;
+  P.kind1 = s1->kind;
+  P.kind2 = s2->kind;
   P.depth = depth;
   P.n_base = n_base;
   P.G = G;

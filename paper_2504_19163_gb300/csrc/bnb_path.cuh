@@ -322,9 +322,10 @@ __device__ __forceinline__ void dl_cross_dc(const Dl<T> (&a)[3], const T (&b)[3]
   r[2] = b[1] * a[0] - b[0] * a[1];
 }
 
-// The triangles and constants of one pair tuple.
+// The triangles and constants of one pair tuple; kind1 / kind2: BNB_REFLECT or BNB_REFRACT.
 struct PairGeom {
   float p1[3][3], n1[3][3], p2[3][3], n2[3][3], x0[3], I0, rp0[3], re1[3], re2[3], eta1, eta2;
+  int kind1, kind2;
 };
 
 template <typename T>
@@ -333,9 +334,16 @@ struct Path2 : Path<T> {
 };
 
 // d~ = eta' ((n.n) d - (d.n) n) - sqrt(beta) n; false when beta <= 0 (no refracted path).
+// Reflection: d~ = (n.n) d - 2 (d.n) n.
 template <typename T>
-__device__ __forceinline__ bool dl_refract(const Dl<T> (&n)[3], const Dl<T> (&d)[3], T eta, Dl<T> (&out)[3]) {
+__device__ __forceinline__ bool dl_refract(const Dl<T> (&n)[3], const Dl<T> (&d)[3], int kind, T eta,
+                                           Dl<T> (&out)[3]) {
   const Dl<T> nn = dl_dot(n, n), dn = dl_dot(d, n), ss = dl_dot(d, d);
+  if (kind == BNB_REFLECT) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = nn * d[c] - T(2) * (dn * n[c]);
+    return true;
+  }
   const Dl<T> beta = (T(1) - eta * eta) * (nn * ss) + (eta * eta) * (dn * dn);
   if (!(beta.v > T(0))) return false;
   const Dl<T> W = dl_sqrt(beta);
@@ -383,7 +391,7 @@ __device__ __forceinline__ Path2<T> eval_pair(const PairGeom& G, T u, T v) {
     R2[c] = (T)G.re2[c];
   }
   Dl<T> t1d[3];
-  if (!dl_refract(n1, d0, (T)G.eta1, t1d)) return r;
+  if (!dl_refract(n1, d0, G.kind1, (T)G.eta1, t1d)) return r;
   Dl<T> u2, v2, s1;
   dl_plane(x1, t1d, o2, e21, e22, u2, v2, s1);
   Dl<T> x2[3], n2[3], d1[3];
@@ -395,7 +403,7 @@ __device__ __forceinline__ Path2<T> eval_pair(const PairGeom& G, T u, T v) {
     d1[c] = x2[c] - x1[c];
   }
   Dl<T> t2d[3];
-  if (!dl_refract(n2, d1, (T)G.eta2, t2d)) return r;
+  if (!dl_refract(n2, d1, G.kind2, (T)G.eta2, t2d)) return r;
   Dl<T> uk, vk, s2;
   dl_plane(x2, t2d, R0, R1, R2, uk, vk, s2);
   r.uk = uk.v;
@@ -465,8 +473,13 @@ __device__ __forceinline__ Hit2<T> eval_pair_value(const PairGeom& G, T u, T v) 
     r[1] = a[2] * b[0] - a[0] * b[2];
     r[2] = a[0] * b[1] - a[1] * b[0];
   };
-  auto refract = [&](const T* n, const T* d, T eta, T* out) {
+  auto refract = [&](const T* n, const T* d, int kind, T eta, T* out) {
     const T nn = dot(n, n), dn = dot(d, n), ss = dot(d, d);
+    if (kind == BNB_REFLECT) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[c] = nn * d[c] - T(2) * (dn * n[c]);
+      return true;
+    }
     const T beta = (T(1) - eta * eta) * (nn * ss) + (eta * eta) * (dn * dn);
     if (!(beta > T(0))) return false;
     const T W = sqrt(beta);
@@ -502,7 +515,7 @@ __device__ __forceinline__ Hit2<T> eval_pair_value(const PairGeom& G, T u, T v) 
     R2[c] = (T)G.re2[c];
   }
   T t1d[3];
-  if (!refract(n1, d0, (T)G.eta1, t1d)) return h;
+  if (!refract(n1, d0, G.kind1, (T)G.eta1, t1d)) return h;
   plane(x1, t1d, o2, e21, e22, h.u2, h.v2, h.t1);
   T x2[3], n2[3], d1[3];
 #pragma unroll
@@ -513,7 +526,7 @@ __device__ __forceinline__ Hit2<T> eval_pair_value(const PairGeom& G, T u, T v) 
     d1[c] = x2[c] - x1[c];
   }
   T t2d[3];
-  if (!refract(n2, d1, (T)G.eta2, t2d)) return h;
+  if (!refract(n2, d1, G.kind2, (T)G.eta2, t2d)) return h;
   plane(x2, t2d, R0, R1, R2, h.uk, h.vk, h.t2);
   h.ok = isfinite(h.uk) && isfinite(h.vk) && isfinite(h.u2) && isfinite(h.v2);
   return h;

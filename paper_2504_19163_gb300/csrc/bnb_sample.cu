@@ -136,6 +136,7 @@ struct SolveParams {
   const float4* tri2;
   int32_t n_tris2;
   float eta2;
+  int32_t kind1, kind2;
   float* contrib;
   int64_t* counters;
   // tuples handed from the float32 phase to the float64 polish
@@ -264,6 +265,8 @@ __device__ __forceinline__ bool pair_geom(const SolveParams& S, uint64_t k, Pair
   }
   G.eta1 = S.eta;
   G.eta2 = S.eta2;
+  G.kind1 = S.kind1;
+  G.kind2 = S.kind2;
   return true;
 }
 
@@ -435,6 +438,8 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2
   S.tri2 = w.tri2;
   S.n_tris2 = s2 ? s2->n_tris : 0;
   S.eta2 = s2 ? s2->eta : 1.0f;
+  S.kind1 = s1->kind;
+  S.kind2 = s2 ? s2->kind : BNB_REFLECT;
   S.stoc_trials = cfg->stoc_trials;
   S.seed = cfg->seed;
   if (!s2 && cfg->stoc_trials > 0) {

@@ -83,12 +83,15 @@ def test_invalid_arguments_rejected_before_launch(bnb):
     out = bnb.bnb_cell_bounds()
     rc = bnb.bnb_bound_tuples(C.byref(s), None, C.byref(rec), C.byref(em), C.byref(cfg), C.byref(out), None, 0, None)
     assert rc == bnb.BNB_ERR_INVALID
-    # two reflective vertices: chains need refraction at both
+    # chains: a refracting second vertex with eta' outside (0, 1e6) is unsupported
     em_ok = bnb.bnb_emitters(1, 4096, 4096, 4096, 4096)
     for f in ("px", "py", "pz", "nx", "ny", "nz", "i0", "i1", "i2"):
         setattr(s, f, 4096)
-    rc = bnb.bnb_bound_tuples(C.byref(s), C.byref(s), C.byref(rec), C.byref(em_ok), C.byref(cfg), C.byref(out), None,
-                              0, None)
+    s2 = bnb.bnb_surface()
+    C.pointer(s2)[0] = s
+    s2.kind, s2.eta = bnb.BNB_REFRACT, 0.0
+    rc = bnb.bnb_bound_tuples(C.byref(s), C.byref(s2), C.byref(rec), C.byref(em_ok), C.byref(cfg), C.byref(out),
+                              None, 0, None)
     assert rc == bnb.BNB_ERR_UNSUPPORTED
     idx = bnb.bnb_index()
     assert bnb.bnb_build_index(None, 1.0, 0, C.byref(idx), None, 0, None) == bnb.BNB_ERR_INVALID

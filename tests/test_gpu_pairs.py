@@ -1,7 +1,8 @@
-"""GPU parity of two-vertex chains (refraction at T1 and T2; Sec. 6.1 tuple construction and degree
-reduction): the candidate (cell, T2) lists against the oracle's brute force over every T2, the
-composite boxes against the oracle and against dense sweeps of the true chains, the whole path
-(bounds -> index -> Algorithm 1 with P = 1 -> chain Newton), and the slab48 workload at full size."""
+"""GPU parity of two-vertex chains (refraction at T1 and T2, or reflection at either vertex; Sec. 6.1
+tuple construction and degree reduction): the candidate (cell, T2) lists against the oracle's brute
+force over every T2, the composite boxes against the oracle and against dense sweeps of the true
+chains, the whole path (bounds -> index -> Algorithm 1 with P = 1 -> chain Newton), two flat
+closed forms, and the slab48 workload at full size."""
 import dataclasses
 
 import numpy as np
@@ -69,7 +70,7 @@ def compare_pairs(orc, sc, g, n_threads=8):
     orec = orc.bound_pairs(sc, oe, ot1, oc, ot2, n_threads=n_threads)
     rep = dict(n=len(okeys), missing=len(missing), extra=len(extra), extra_far=int(np.sum(gap > GAP_TOL)),
                flag_mismatch=0, flag_ambiguous=0, live=0, qsign_fp64=int(np.sum((g["flags"] & 64) != 0)))
-    diffs = []
+    diffs, inside = [], []
     for oi, k in enumerate(okeys):
         gi = gidx.get(k)
         if gi is None:
@@ -93,20 +94,25 @@ def compare_pairs(orc, sc, g, n_threads=8):
         if of & 1:
             rep["live"] += 1
             for a in ("u", "v"):
-                diffs.append(max(abs(float(g[a + "_lo"][gi]) - orec[a + "_lo"][oi]),
-                                 abs(float(g[a + "_hi"][gi]) - orec[a + "_hi"][oi])))
+                lo_in = float(g[a + "_lo"][gi]) - orec[a + "_lo"][oi]
+                hi_in = orec[a + "_hi"][oi] - float(g[a + "_hi"][gi])
+                diffs.append(max(abs(lo_in), abs(hi_in)))
+                inside.append(max(lo_in, hi_in))
     d = np.array(diffs or [0.0])
-    rep.update(box_diff_max=float(d.max()), box_diff_median=float(np.median(d)))
+    rep.update(box_diff_max=float(d.max()), box_diff_median=float(np.median(d)),
+               box_inside_max=float(max(inside or [0.0])))
     return rep, orec
 
 
-def assert_pair_parity(rep):
+def assert_pair_parity(rep, widen_tol=BOX_TOL):
+    """widen_tol: how far a GPU machine edge may lie outside the oracle's; inside it, at most BOX_TOL."""
     assert rep["missing"] == 0, rep
     assert rep["extra_far"] == 0, rep
     assert rep["extra"] <= max(4, 1e-3 * rep["n"]), rep
     assert rep["flag_mismatch"] == 0, rep.get("mismatches")
     assert rep["flag_ambiguous"] <= max(2, 1e-3 * rep["n"]), rep
-    assert rep["box_diff_max"] <= BOX_TOL, rep
+    assert rep["box_inside_max"] <= BOX_TOL, rep
+    assert rep["box_diff_max"] <= widen_tol, rep
     assert rep["live"] > 0.3 * rep["n"], rep
 
 
@@ -151,7 +157,10 @@ def test_pair_fp64_mode_matches_oracle(B, orc):
 
 @pytest.mark.parametrize("n,depth,amp,k", [(4, 1, 0.06, 30), (3, 0, 0.1, 60)])
 def test_pair_gpu_boxes_contain_dense_sweep(B, orc, n, depth, amp, k):
-    sc = S.config("slab", n=n, depth=depth, amp=amp)
+    check_gpu_containment(B, orc, S.config("slab", n=n, depth=depth, amp=amp), k)
+
+
+def check_gpu_containment(B, orc, sc, k):
     _, _, g = gpu_pairs(B, sc)
     recs = {k: i for i, k in enumerate(keys_of(g["emitter"], g["tri0"], g["cell"], g["tri1"]))}
     viol = checked = 0
@@ -226,6 +235,57 @@ def test_flat_slab_render_closed_form_gpu(B):
         assert E[p] == pytest.approx(e_closed(r), rel=1e-5)
         ok += 1
     assert ok > 500
+
+
+# Reflection at T1, then a second mirror (periscope) or a refracting interface (mirror_glass).  These
+# chains reach the receiver over longer legs, so u2's degree-reduction remainder, and with it the
+# second-order product-rule term (2 r_a r_b per product), is larger than through the slab: the
+# oracle re-run with the GPU's rule widens these boxes by 3.97e-3 (periscope) and 4.06e-3
+# (mirror_glass).  The GPU machines must hold the oracle's and stay within REFL_WIDEN of them; the
+# dense sweep below checks them against the true chains.
+REFL_WIDEN = 1e-2
+
+
+@pytest.mark.parametrize("name", ["periscope", "mirror_glass"])
+def test_reflecting_chain_bounds_match_oracle(B, orc, name):
+    sc = S.config(name, n=4, depth=1, amp=0.04)
+    _, _, g = gpu_pairs(B, sc)
+    rep, _ = compare_pairs(orc, sc, g)
+    assert_pair_parity(rep, widen_tol=REFL_WIDEN)
+
+
+@pytest.mark.parametrize("name,amp", [("periscope", 0.04), ("mirror_glass", 0.04), ("periscope", 0.12)])
+def test_reflecting_chain_gpu_boxes_contain_dense_sweep(B, orc, name, amp):
+    check_gpu_containment(B, orc, S.config(name, n=4, depth=1, amp=amp), 30)
+
+
+@pytest.mark.parametrize("name", ["periscope", "mirror_glass"])
+def test_reflecting_chain_render_matches_oracle(B, orc, name):
+    sc = S.config(name, n=6, depth=1, amp=0.04, points=48)
+    _, _, res = render_gpu(B, sc)
+    out = orc.render_pairs(sc, gamma=1.0, seed=1, n_threads=8)
+    E, Eo = res.E.cpu().numpy().astype(np.float64), out["E"]
+    assert np.count_nonzero(Eo) > 600
+    rel = np.abs(E - Eo) / np.maximum(np.abs(Eo), 1e-30)
+    bad = (rel > E_REL) & ((Eo > 0) | (E > 0))
+    assert bad.sum() <= max(1, 0.002 * E.shape[0]), (bad.sum(), np.sort(rel)[-5:])
+
+
+def test_flat_periscope_render_closed_form_gpu(B):
+    """Two flat mirrors (z = 0 up, z = 1 down), light (0,0,2), receiver z = 0.5: the chain unfolds to
+    the straight ray from the double image (0,0,4), x1 = X / 1.75, x2 = 1.5 x1 and
+    E = I0 3.5 / (|X|^2 + 3.5^2)^(3/2) wherever both hits fall inside the mirrors."""
+    from test_oracle_pairs import receiver_xy
+    sc = S.config("periscope", n=2, flat=True, extent=1.0, lights=[(0.0, 0.0, 2.0)], rec_half=1.5, points=48)
+    _, _, res = render_gpu(B, sc, seed=3)
+    E = res.E.cpu().numpy().astype(np.float64)
+    X = receiver_xy(sc, sc.su.astype(np.float64), sc.sv.astype(np.float64))
+    x2 = 1.5 * X / 1.75
+    inside = np.max(np.abs(x2), axis=1) < 1.0 - 1e-3
+    outside = np.max(np.abs(x2), axis=1) > 1.0 + 1e-3
+    assert inside.sum() > 1000
+    np.testing.assert_allclose(E[inside], 3.5 / (np.sum(X[inside] ** 2, axis=1) + 3.5 ** 2) ** 1.5, rtol=1e-5)
+    assert np.all(E[outside] == 0.0)
 
 
 @pytest.fixture(scope="module")
