@@ -2052,3 +2052,271 @@ int orc_solve_pair(const orc_surface* s1, const orc_surface* s2, const orc_recei
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Implicit differentiation for a single refraction (Sec. 4.4 "Implicit
+// differentiation"; the specular polynomials F, G of its footnote).
+//
+//   * Variables: u1 in the cell (the cell's barycentric coordinates, a 2-simplex) and the
+//     receiver coordinates u_k in the record's position box [u_lo, u_hi] x [v_lo, v_hi]
+//     (box coordinates s, t in [0, 1]), treated as independent: the 4D superset of the
+//     2D manifold of refracted paths.  Polynomials are classical Bernstein forms on
+//     simplex x interval x interval ("tensor" forms below), degree (n; p, q).
+//   * With d0 = x1 - x0, d1 = x_k - x1, n1 the interpolated normal and b a fixed vector,
+//     A = (d0 x n1).b and C = (d1 x n1).b, the constraints are
+//       F = eta'^2 |d1|^2 A^2 - |d0|^2 C^2   (Snell's law squared along b; the paper's
+//           eta is the transmitted-over-incident ratio 1/eta', and F is scaled by the
+//           constant eta'^2, which cancels in the Jacobian),
+//       G = (d0 x n1).d1                      (coplanarity).
+//   * Partial derivatives by the product rule with the constant derivative vectors:
+//     d x1/du1 = p1 - p0, d n1/du1 = n1 - n0 (and v1 likewise), d x_k/du_k = e1 of the
+//     receiver (v_k: e2).
+//   * The implicit-function theorem gives |d u1 / d u_k| = |det B| / |det A| with
+//     A = d(F, G)/d(u1, v1) (degree (7; 3, 3)) and B = d(F, G)/d(u_k, v_k) (degree (7; 1, 1),
+//     elevated to (7; 3, 3)); with Eq. eq_dwda the irradiance is
+//       E = I0 |C1| |det B| / (|d0|^3 |N_k| |det A|),  C1 = (p0 - x0).N1.
+//   * Bound (Eq. eq_bbound): when every coefficient of det A is non-zero with one sign,
+//     |det B / det A| lies in [min, max] of the coefficient ratios (0 below when they
+//     change sign); |d0|^2 lies in [min, max] of its coefficients.  E_hi is the smaller
+//     and E_lo the larger of the bounds from b1 = (1, 0, 0) and b2 = (0, 1, 0); with
+//     neither certified, E_hi = +inf and E_lo = 0.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TPl {  // classical Bernstein coefficients, index (simplex g) * (p+1)(q+1) + i (q+1) + j
+  int n = 0, p = 0, q = 0;
+  std::vector<double> c;
+};
+
+int tsize(int n, int p, int q) { return psize(2, n) * (p + 1) * (q + 1); }
+
+TPl tconst(double v) { return {0, 0, 0, {v}}; }
+
+TPl tmul(const TPl& a, const TPl& b) {
+  TPl r;
+  r.n = a.n + b.n;
+  r.p = a.p + b.p;
+  r.q = a.q + b.q;
+  r.c.assign(tsize(r.n, r.p, r.q), 0.0);
+  const int ba = (a.p + 1) * (a.q + 1), bb = (b.p + 1) * (b.q + 1), br = (r.p + 1) * (r.q + 1);
+  for_each_index(2, a.n, [&](int a1, int a2) {
+    for_each_index(2, b.n, [&](int b1, int b2) {
+      const double ws = multinom(a.n, a1, a2) * multinom(b.n, b1, b2) / multinom(r.n, a1 + b1, a2 + b2);
+      const int ia = pidx(2, a.n, a1, a2), ib = pidx(2, b.n, b1, b2), ir = pidx(2, r.n, a1 + b1, a2 + b2);
+      for (int i = 0; i <= a.p; ++i)
+        for (int k = 0; k <= b.p; ++k) {
+          const double wi = binom(a.p, i) * binom(b.p, k) / binom(r.p, i + k);
+          for (int j = 0; j <= a.q; ++j)
+            for (int l = 0; l <= b.q; ++l) {
+              const double wj = binom(a.q, j) * binom(b.q, l) / binom(r.q, j + l);
+              r.c[ir * br + (i + k) * (r.q + 1) + (j + l)] +=
+                  ws * wi * wj * a.c[ia * ba + i * (a.q + 1) + j] * b.c[ib * bb + k * (b.q + 1) + l];
+            }
+        }
+    });
+  });
+  return r;
+}
+
+// Elevation to (n; p, q): the product with the constant 1 of degree (n - a.n; p - a.p, q - a.q).
+TPl televate(const TPl& a, int n, int p, int q) {
+  if (a.n == n && a.p == p && a.q == q) return a;
+  TPl one{n - a.n, p - a.p, q - a.q, {}};
+  one.c.assign(tsize(one.n, one.p, one.q), 1.0);
+  return tmul(a, one);
+}
+
+TPl tadd(const TPl& a, const TPl& b, double sb = 1.0) {
+  const int n = std::max(a.n, b.n), p = std::max(a.p, b.p), q = std::max(a.q, b.q);
+  TPl r = televate(a, n, p, q);
+  const TPl e = televate(b, n, p, q);
+  for (size_t i = 0; i < r.c.size(); ++i) r.c[i] += sb * e.c[i];
+  return r;
+}
+
+TPl tscale(TPl a, double s) {
+  for (auto& v : a.c) v *= s;
+  return a;
+}
+
+struct TV {
+  TPl x, y, z;
+};
+TV tv_const(V3 a) { return {tconst(a.x), tconst(a.y), tconst(a.z)}; }
+TPl tv_dot(const TV& a, const TV& b) { return tadd(tadd(tmul(a.x, b.x), tmul(a.y, b.y)), tmul(a.z, b.z)); }
+TV tv_cross(const TV& a, const TV& b) {
+  return {tadd(tmul(a.y, b.z), tmul(a.z, b.y), -1.0), tadd(tmul(a.z, b.x), tmul(a.x, b.z), -1.0),
+          tadd(tmul(a.x, b.y), tmul(a.y, b.x), -1.0)};
+}
+TV tv_sub(const TV& a, const TV& b) { return {tadd(a.x, b.x, -1.0), tadd(a.y, b.y, -1.0), tadd(a.z, b.z, -1.0)}; }
+TV tv_add(const TV& a, const TV& b) { return {tadd(a.x, b.x), tadd(a.y, b.y), tadd(a.z, b.z)}; }
+
+// Degree (1; 0, 0) from the values at the cell corners.
+TV tv_simplex(V3 f0, V3 f1, V3 f2) {
+  auto one = [&](double a, double b, double c) {
+    TPl r{1, 0, 0, std::vector<double>(3)};
+    r.c[pidx(2, 1, 0, 0)] = a;
+    r.c[pidx(2, 1, 1, 0)] = b;
+    r.c[pidx(2, 1, 0, 1)] = c;
+    return r;
+  };
+  return {one(f0.x, f1.x, f2.x), one(f0.y, f1.y, f2.y), one(f0.z, f1.z, f2.z)};
+}
+
+// Degree (0; 1, 1): a0 + s es + t et on [0, 1]^2.
+TV tv_box(V3 a0, V3 es, V3 et) {
+  auto one = [&](double a, double s, double t) { return TPl{0, 1, 1, {a, a + t, a + s, a + s + t}}; };
+  return {one(a0.x, es.x, et.x), one(a0.y, es.y, et.y), one(a0.z, es.z, et.z)};
+}
+
+double teval(const TPl& a, double l1, double l2, double s, double t) {
+  double sum = 0.0;
+  const double l0 = 1.0 - l1 - l2;
+  const int bs = (a.p + 1) * (a.q + 1);
+  for_each_index(2, a.n, [&](int g1, int g2) {
+    const int g0 = a.n - g1 - g2;
+    const double bsx = multinom(a.n, g1, g2) * std::pow(l0, g0) * std::pow(l1, g1) * std::pow(l2, g2);
+    for (int i = 0; i <= a.p; ++i)
+      for (int j = 0; j <= a.q; ++j)
+        sum += bsx * binom(a.p, i) * std::pow(s, i) * std::pow(1.0 - s, a.p - i) * binom(a.q, j) * std::pow(t, j) *
+               std::pow(1.0 - t, a.q - j) * a.c[pidx(2, a.n, g1, g2) * bs + i * (a.q + 1) + j];
+  });
+  return sum;
+}
+
+struct ImplicitForms {
+  TPl F, G, detA, detB, L0;
+};
+
+// The forms of the implicit Jacobian for one cell C (corners in T's (u, v)), one receiver box and
+// one vector b; detA and detB at degree (7; 3, 3).
+ImplicitForms implicit_forms(const Tri& T, V3 x0, double eta, const Rec& R, const UV C[3], double ul, double uh,
+                             double vl, double vh, V3 b) {
+  const V3 Eu = T.p[1] - T.p[0], Ev = T.p[2] - T.p[0], Nu = T.n[1] - T.n[0], Nv = T.n[2] - T.n[0];
+  auto X = [&](const UV& c) { return T.p[0] + c.u * Eu + c.v * Ev; };
+  auto Nn = [&](const UV& c) { return T.n[0] + c.u * Nu + c.v * Nv; };
+  const TV x1 = tv_simplex(X(C[0]), X(C[1]), X(C[2]));
+  const TV n1 = tv_simplex(Nn(C[0]), Nn(C[1]), Nn(C[2]));
+  const TV xk = tv_box(R.p0 + ul * R.e1 + vl * R.e2, (uh - ul) * R.e1, (vh - vl) * R.e2);
+  const TV d0 = tv_sub(x1, tv_const(x0));
+  const TV d1 = tv_sub(xk, x1);
+  const TV B = tv_const(b);
+  const TV d0n = tv_cross(d0, n1);
+  const TPl A = tv_dot(d0n, B);
+  const TPl Cc = tv_dot(tv_cross(d1, n1), B);
+  const TPl L1 = tv_dot(d1, d1), L0 = tv_dot(d0, d0);
+  const double e2 = eta * eta;
+  ImplicitForms out;
+  out.F = tadd(tscale(tmul(L1, tmul(A, A)), e2), tmul(L0, tmul(Cc, Cc)), -1.0);
+  out.G = tv_dot(d0n, d1);
+  // derivatives along T's u or v (edge E, normal difference N)
+  auto dF_dG_1 = [&](V3 E, V3 N, TPl* dF, TPl* dG) {
+    const TV Ec = tv_const(E), Nc = tv_const(N);
+    const TV dd0n = tv_add(tv_cross(Ec, n1), tv_cross(d0, Nc));          // d(d0 x n1)
+    const TPl dA = tv_dot(dd0n, B);
+    const TPl dC = tv_dot(tv_sub(tv_cross(d1, Nc), tv_cross(Ec, n1)), B);  // d(d1 x n1).b, d d1 = -E
+    const TPl dL1 = tscale(tv_dot(d1, Ec), -2.0), dL0 = tscale(tv_dot(d0, Ec), 2.0);
+    *dF = tadd(tscale(tadd(tmul(dL1, tmul(A, A)), tscale(tmul(L1, tmul(A, dA)), 2.0)), e2),
+               tadd(tmul(dL0, tmul(Cc, Cc)), tscale(tmul(L0, tmul(Cc, dC)), 2.0)), -1.0);
+    *dG = tadd(tv_dot(dd0n, d1), tv_dot(d0n, Ec), -1.0);
+  };
+  // derivatives along the receiver's u_k or v_k (edge e)
+  auto dF_dG_k = [&](V3 e, TPl* dF, TPl* dG) {
+    const TV ec = tv_const(e);
+    const TPl dC = tv_dot(tv_cross(ec, n1), B);
+    const TPl dL1 = tscale(tv_dot(d1, ec), 2.0);
+    *dF = tadd(tscale(tmul(dL1, tmul(A, A)), e2), tscale(tmul(L0, tmul(Cc, dC)), 2.0), -1.0);
+    *dG = tv_dot(d0n, ec);
+  };
+  TPl Fu, Gu, Fv, Gv, Fuk, Guk, Fvk, Gvk;
+  dF_dG_1(Eu, Nu, &Fu, &Gu);
+  dF_dG_1(Ev, Nv, &Fv, &Gv);
+  dF_dG_k(R.e1, &Fuk, &Guk);
+  dF_dG_k(R.e2, &Fvk, &Gvk);
+  out.detA = televate(tadd(tmul(Fu, Gv), tmul(Fv, Gu), -1.0), 7, 3, 3);
+  out.detB = televate(tadd(tmul(Fuk, Gvk), tmul(Fvk, Guk), -1.0), 7, 3, 3);
+  out.L0 = L0;
+  return out;
+}
+
+// E_lo, E_hi of one refraction record by implicit differentiation (header comment above).
+void implicit_irradiance(const Tri& T, V3 x0, double I0, double eta, const Rec& R, const UV C[3], double ul,
+                         double uh, double vl, double vh, double* e_lo, double* e_hi) {
+  const double inf = std::numeric_limits<double>::infinity();
+  const V3 N1 = cross(T.p[1] - T.p[0], T.p[2] - T.p[0]);
+  const double k = I0 * std::fabs(dot(T.p[0] - x0, N1)) / norm(cross(R.e1, R.e2));
+  double hi = inf, lo = 0.0;
+  const V3 bs[2] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}};
+  for (const V3& b : bs) {
+    const ImplicitForms f = implicit_forms(T, x0, eta, R, C, ul, uh, vl, vh, b);
+    bool pos = true, neg = true;
+    for (double v : f.detA.c) {
+      if (!(v > 0.0)) pos = false;
+      if (!(v < 0.0)) neg = false;
+    }
+    if (!pos && !neg) continue;
+    double rmin = inf, rmax = -inf;
+    for (size_t i = 0; i < f.detA.c.size(); ++i) {
+      const double r = f.detB.c[i] / f.detA.c[i];
+      rmin = std::min(rmin, r);
+      rmax = std::max(rmax, r);
+    }
+    const double amax = std::max(std::fabs(rmin), std::fabs(rmax));
+    const double amin = rmin > 0.0 ? rmin : (rmax < 0.0 ? -rmax : 0.0);
+    const double s_lo = *std::min_element(f.L0.c.begin(), f.L0.c.end());
+    const double s_hi = *std::max_element(f.L0.c.begin(), f.L0.c.end());
+    hi = std::min(hi, s_lo > 0.0 ? k * amax / (s_lo * std::sqrt(s_lo)) : inf);
+    lo = std::max(lo, k * amin / (s_hi * std::sqrt(s_hi)));
+  }
+  *e_lo = lo;
+  *e_hi = hi;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Implicit-differentiation irradiance bounds of n single-refraction records (emitter, tri0,
+// cell id at depth, position box): e_lo[i], e_hi[i].
+int orc_implicit_bound(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, int64_t n,
+                       const int32_t* emitter, const int32_t* tri0, const uint32_t* cell, const int32_t* depth,
+                       const double* u_lo, const double* u_hi, const double* v_lo, const double* v_hi, double* e_lo,
+                       double* e_hi, int n_threads) {
+  if (s1->kind != 1) return -1;
+  const Rec R = get_rec(rec);
+  parallel_for(n, n_threads, [&](int, int64_t a, int64_t b) {
+    for (int64_t i = a; i < b; ++i) {
+      const int e = emitter[i];
+      UV C[3];
+      cell_corners(cell[i], depth[i], C);
+      const V3 x0 = {em->x[e], em->y[e], em->z[e]};
+      implicit_irradiance(get_tri(s1, tri0[i]), x0, em->intensity[e], s1->eta, R, C, u_lo[i], u_hi[i], v_lo[i],
+                          v_hi[i], &e_lo[i], &e_hi[i]);
+    }
+  });
+  return 0;
+}
+
+// The implicit forms of one record evaluated at n points (cell barycentrics l1, l2; box
+// coordinates s, t), for b = (1,0,0) (which_b 0) or (0,1,0) (1): out[5 i + 0..4] = F, G,
+// det A, det B, |d0|^2.
+int orc_implicit_eval(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, int32_t e, int32_t t,
+                      uint32_t cell, int32_t depth, double ul, double uh, double vl, double vh, int32_t which_b,
+                      int64_t n, const double* l1, const double* l2, const double* s, const double* tt, double* out) {
+  if (s1->kind != 1) return -1;
+  UV C[3];
+  cell_corners(cell, depth, C);
+  const V3 x0 = {em->x[e], em->y[e], em->z[e]};
+  const V3 b = which_b == 0 ? V3{1.0, 0.0, 0.0} : V3{0.0, 1.0, 0.0};
+  const ImplicitForms f = implicit_forms(get_tri(s1, t), x0, s1->eta, get_rec(rec), C, ul, uh, vl, vh, b);
+  for (int64_t i = 0; i < n; ++i) {
+    out[5 * i + 0] = teval(f.F, l1[i], l2[i], s[i], tt[i]);
+    out[5 * i + 1] = teval(f.G, l1[i], l2[i], s[i], tt[i]);
+    out[5 * i + 2] = teval(f.detA, l1[i], l2[i], s[i], tt[i]);
+    out[5 * i + 3] = teval(f.detB, l1[i], l2[i], s[i], tt[i]);
+    out[5 * i + 4] = teval(f.L0, l1[i], l2[i], s[i], tt[i]);
+  }
+  return 0;
+}
+
+}  // extern "C"

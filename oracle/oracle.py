@@ -98,6 +98,9 @@ def lib():
             L.orc_bound_pairs.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, vp, i32]
             L.orc_eval_pair.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i64, vp]
             L.orc_solve_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32, i32, f64, vp, vp, vp, vp, i32]
+            L.orc_implicit_bound.argtypes = [vp, vp, vp, i64] + [vp] * 10 + [i32]
+            L.orc_implicit_eval.argtypes = [vp, vp, vp, i32, i32, C.c_uint32, i32, f64, f64, f64, f64, i32, i64,
+                                            vp, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -359,6 +362,38 @@ def eval_path(scene, emitter: int, tri: int, u, v, direct: bool = False):
     fn = L.orc_eval_direct if direct else L.orc_eval_path
     fn(C.byref(V.surf), C.byref(V.rec), C.byref(V.em), emitter, tri, _p(u), _p(v), n, _p(uk), _p(vk), _p(E), _p(t))
     return uk, vk, E, t
+
+
+def implicit_bound(scene, emitter, tri0, cell, depth, u_lo, u_hi, v_lo, v_hi, n_threads: int = 1):
+    """Implicit-differentiation irradiance bounds (Sec. 4.4) of single-refraction records given by
+    (emitter, tri0, cell id, depth, position box): (e_lo, e_hi) float64 arrays."""
+    L = lib()
+    V = _SceneViews(scene)
+    a = [np.ascontiguousarray(x, dt) for x, dt in [(emitter, np.int32), (tri0, np.int32), (cell, np.uint32),
+                                                   (depth, np.int32), (u_lo, np.float64), (u_hi, np.float64),
+                                                   (v_lo, np.float64), (v_hi, np.float64)]]
+    n = a[0].shape[0]
+    lo, hi = np.zeros(n), np.zeros(n)
+    rc = L.orc_implicit_bound(C.byref(V.surf), C.byref(V.rec), C.byref(V.em), n, *[_p(x) for x in a], _p(lo),
+                              _p(hi), n_threads)
+    if rc != 0:
+        raise RuntimeError(f"orc_implicit_bound failed: {rc}")
+    return lo, hi
+
+
+def implicit_eval(scene, emitter: int, tri0: int, cell: int, depth: int, box, which_b: int, l1, l2, s, t) -> dict:
+    """The implicit forms F, G, det A, det B and |d0|^2 of one record at cell barycentrics (l1, l2)
+    and box coordinates (s, t) in [0, 1]^2, for b = (1,0,0) (which_b 0) or (0,1,0) (1)."""
+    L = lib()
+    V = _SceneViews(scene)
+    l1, l2, s, t = (np.ascontiguousarray(x, np.float64) for x in (l1, l2, s, t))
+    n = l1.shape[0]
+    out = np.zeros((n, 5))
+    rc = L.orc_implicit_eval(C.byref(V.surf), C.byref(V.rec), C.byref(V.em), emitter, tri0, cell, depth, *map(float, box),
+                             which_b, n, _p(l1), _p(l2), _p(s), _p(t), _p(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_implicit_eval failed: {rc}")
+    return dict(F=out[:, 0], G=out[:, 1], detA=out[:, 2], detB=out[:, 3], L0=out[:, 4])
 
 
 def tuple_key(emitter, tri0, tri1=-1):

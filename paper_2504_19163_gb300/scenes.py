@@ -342,6 +342,20 @@ def config(name: str, **kw) -> Scene:
         rec = receiver_square(-1.0, 2.0, half_y=1.125)
         su, sv = shading_points(kw.get("points_x", 1920), kw.get("points_y", 1080), 1003)
         return Scene(name, s1, None, rec, em, kw.get("depth", 3), su, sv)
+    if name == "tir_wall":
+        # near total internal reflection: a light under water (eta' 1.33, normals facing down, the
+        # incident side) below an n^2 heightfield at z=0 over [-1,1]^2; the critical angle is reached
+        # at ~0.57 from the light's foot, and the grazing transmitted rays hit a vertical wall
+        # receiver at x=1.2 (y in [-1,1], z in [0,1])
+        n = kw.get("n", 4)
+        s1 = heightfield(n, kw.get("seed", 5), n_waves=4, amp_total=kw.get("amp", 0.02), extent=1.0,
+                         flip_normals=True, kind=SURFACE_REFRACT, eta=1.33)
+        em = point_emitters(kw.get("lights", [(0.02, -0.01, -0.5)]), 1.0)
+        rec = Receiver(np.array([1.2, -1.0, 0.0], np.float32), np.array([0.0, 2.0, 0.0], np.float32),
+                       np.array([0.0, 0.0, 1.0], np.float32))
+        p = kw.get("points", 32)
+        su, sv = shading_points(p, p, 1008)
+        return Scene(name, s1, None, rec, em, kw.get("depth", 3), su, sv)
     if name == "water":
         # small refraction case: n^2 Gerstner water on [-ext,ext]^2, floor 1 below
         n = kw.get("n", 8)
