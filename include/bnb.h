@@ -97,7 +97,11 @@ typedef struct bnb_emitters {
 typedef struct bnb_bound_cfg {
   int32_t depth;           /* base 4-way subdivision depth D of T1's domain: 4^D cells per tuple (0..10) */
   int32_t max_extra_split; /* extra splits of a cell whose denominator sign test fails (0..4) */
-  int32_t irradiance;      /* 1: irradiance bound (Sec. 4.4); 0: position only, e_hi = +inf */
+  int32_t irradiance;      /* 1: irradiance bound (Sec. 4.4); 0: position only, e_hi = +inf;
+                            * 2 (single refraction only, else BNB_ERR_UNSUPPORTED): the bound of 1
+                            * intersected with the implicit-differentiation bound of every live
+                            * record (bnb_implicit_irradiance, mode 1), after the whole pass;
+                            * adaptive stopping decisions use the bound of 1 */
   int32_t fp64;            /* 1: the whole bound pass in float64 (same arithmetic, u = 2^-53) */
   /* Adaptive subdivision (Sec. 6.1 "Domain subdivision"), on when adapt_depth > depth: a live cell
    * with a bounded box at depth < adapt_depth is subdivided again unless its receiver box has area
@@ -357,7 +361,25 @@ size_t bnb_bound_tuples_batched_ws(int32_t max_jobs);
 const char *bnb_status_string(int32_t status);
 
 /* ABI version of this header (increments on any struct or signature change). */
-int32_t bnb_abi_version(void);  /* 9 */
+/* Implicit-differentiation irradiance bound (Sec. 4.4 "Implicit differentiation", with the
+ * specular polynomials F, G of its footnote) of single-refraction records, on the stream.
+ * For every record r < n (n = -1: min(*cells->count, capacity), read on the device) that is
+ * BNB_CELL_LIVE with tri1 < 0: the cell's barycentric coordinates and the receiver
+ * coordinates of its box [u_lo, u_hi] x [v_lo, v_hi] are independent variables (the 4D
+ * superset of the path manifold); |du1/du_k| = |det B| / |det A| with A = d(F,G)/d(u1,v1),
+ * B = d(F,G)/d(u_k,v_k), and E = I0 |C1| |det B| / (|d0|^3 |N_k| |det A|) (Eq. eq_dwda) is
+ * bounded by coefficient ratios (Eq. eq_bbound) in float64 with tracked rounding error; the
+ * tighter of b = (1,0,0) and (0,1,0) is kept, +inf / 0 when neither certifies det A's sign.
+ *   mode 0: e_hi (and e_lo when non-NULL) receive the implicit bound, rounded outward;
+ *   mode 1: e_hi = min(e_hi, implicit), e_lo = max(e_lo, implicit).
+ * Other records are left unchanged.  s1: BNB_REFRACT with eta in (0, 1e6), else
+ * BNB_ERR_UNSUPPORTED / BNB_ERR_INVALID.  The records' emitter, tri0, tri1, cell, flags and
+ * box arrays must be valid device arrays; record indices outside the scene are skipped.
+ * No workspace; one warp per record (48 KB of shared memory per 64-thread block). */
+int32_t bnb_implicit_irradiance(const bnb_surface *s1, const bnb_receiver *rec, const bnb_emitters *em,
+                                const bnb_cell_bounds *cells, int64_t n, int32_t mode, void *stream);
+
+int32_t bnb_abi_version(void);  /* 10 */
 
 #ifdef __cplusplus
 }

@@ -96,7 +96,8 @@ _lib = None
 EXPORTS = ["bnb_bound_tuples", "bnb_bound_tuples_ws", "bnb_bound_tuples_noalloc", "bnb_build_index",
            "bnb_build_index_ws", "bnb_sample_and_solve", "bnb_sample_and_solve_ws", "bnb_status_string",
            "bnb_abi_version", "bnb_pack_surface", "bnb_pack_surface_bytes", "bnb_sample_and_solve_batched",
-           "bnb_sample_and_solve_batched_ws", "bnb_bound_tuples_batched", "bnb_bound_tuples_batched_ws"]
+           "bnb_sample_and_solve_batched_ws", "bnb_bound_tuples_batched", "bnb_bound_tuples_batched_ws",
+           "bnb_implicit_irradiance"]
 
 
 def lib():
@@ -125,6 +126,9 @@ def lib():
                                            vp, sz, vp]
         L.bnb_sample_and_solve_ws.restype = sz
         L.bnb_sample_and_solve_ws.argtypes = [P(bnb_surface), P(bnb_surface), i64, i64]
+        L.bnb_implicit_irradiance.restype = i32
+        L.bnb_implicit_irradiance.argtypes = [P(bnb_surface), P(bnb_receiver), P(bnb_emitters), P(bnb_cell_bounds),
+                                              i64, i32, vp]
         L.bnb_status_string.restype = C.c_char_p
         L.bnb_status_string.argtypes = [i32]
         L.bnb_abi_version.restype = i32
@@ -195,6 +199,10 @@ def bnb_bound_tuples_batched(*a):
 
 def bnb_bound_tuples_batched_ws(*a):
     return lib().bnb_bound_tuples_batched_ws(*a)
+
+
+def bnb_implicit_irradiance(*a):
+    return lib().bnb_implicit_irradiance(*a)
 
 
 def bnb_status_string(s: int) -> str:
@@ -354,14 +362,25 @@ class Index:
 
 
 # ----------------------------------------------------------------------------- high-level calls
-def bound_tuples(ds: DeviceScene, depth: int, max_extra_split: int = 4, irradiance: bool = True,
+def implicit_irradiance(ds: DeviceScene, cells: CellBounds, n: int = -1, mode: int = 0, stream=None) -> None:
+    """Implicit-differentiation irradiance bounds (Sec. 4.4) of the live single-refraction records
+    [0, n) of `cells` (n = -1: all the pass produced), in place: mode 0 writes them, mode 1
+    intersects them with the stored bounds."""
+    rc = bnb_implicit_irradiance(C.byref(ds.s1), C.byref(ds.rec), C.byref(ds.em), C.byref(cells.c), n, mode,
+                                        _stream(stream))
+    _check(rc, "bnb_implicit_irradiance")
+
+
+def bound_tuples(ds: DeviceScene, depth: int, max_extra_split: int = 4, irradiance=True,
                  fp64: bool = False, capacity: Optional[int] = None, out: Optional[CellBounds] = None,
                  ws: Optional[torch.Tensor] = None, stream=None, sync_check: bool = True,
                  with_e_hi_min: bool = False, with_e_lo: bool = True, adapt_depth: int = 0, sigma: float = 0.0,
                  alpha: float = 0.0, split_capacity: int = 0) -> CellBounds:
     """Bound pass (one or two specular vertices).  adapt_depth > depth: adaptive subdivision
     (Sec. 6.1) down to adapt_depth, a cell stopping when its box area is below sigma or
-    E_hi < alpha E_lo; split_capacity sizes the per-level split queue (0: the library default)."""
+    E_hi < alpha E_lo; split_capacity sizes the per-level split queue (0: the library default).
+    irradiance: False / True, or 2 (single refraction) to intersect each bound with the
+    implicit-differentiation bound (Sec. 4.4)."""
     n_base = ds.scene.emitters.n * ds.s1.n_tris * 4 ** depth
     adaptive = adapt_depth > depth
     if adaptive and split_capacity == 0:

@@ -20,6 +20,8 @@ size_t pair_ws_bytes(int64_t n_tris1, int64_t n_tris2, int64_t n_base);
 cudaError_t launch_bound_pairs(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
                                const bnb_emitters* em, int32_t depth, bool fp64, bnb_cell_bounds* out, void* ws,
                                cudaStream_t st);
+cudaError_t launch_implicit(const bnb_surface* s1, const bnb_receiver* rec, const bnb_emitters* em,
+                            const bnb_cell_bounds* cells, int64_t n, int32_t mode, cudaStream_t st);
 size_t batch_ws_bytes(const bnb_batch_cfg* c);
 size_t bound_batch_ws_bytes(int32_t max_jobs);
 cudaError_t launch_bound_batched(const bnb_bound_job* jobs, const int32_t* n_jobs, int32_t max_jobs, void* ws,
@@ -101,7 +103,7 @@ BoundWs carve_bound_ws(void* base, int64_t n_tris, int64_t qcap) {
 
 extern "C" {
 
-int32_t bnb_abi_version(void) { return 9; }
+int32_t bnb_abi_version(void) { return 10; }
 
 const char* bnb_status_string(int32_t s) {
   switch (s) {
@@ -150,6 +152,8 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
   }
   if (s1->kind != BNB_REFLECT && s1->kind != BNB_REFRACT) return BNB_ERR_INVALID;
   if (s1->kind == BNB_REFRACT && !(s1->eta > 0.0f && s1->eta < 1e6f)) return BNB_ERR_INVALID;
+  if (cfg->irradiance < 0 || cfg->irradiance > 2) return BNB_ERR_INVALID;
+  if (cfg->irradiance == 2 && s1->kind != BNB_REFRACT) return BNB_ERR_UNSUPPORTED;
   if (cfg->depth < 0 || cfg->depth > kMaxBaseDepth || cfg->max_extra_split < 0 || cfg->max_extra_split > kMaxExtra ||
       cfg->depth + cfg->max_extra_split > kMaxDepth || !adapt_ok(cfg))
     return BNB_ERR_INVALID;
@@ -222,7 +226,23 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
     P.q_out_count = w.qcount + nxt;
     if (launch_bound_split(P, w.q[cur], w.qcount + cur, fp64, st) != cudaSuccess) return BNB_ERR_CUDA;
   }
+  // implicit differentiation: intersect each live record's bound with the implicit one
+  if (cfg->irradiance == 2 && launch_implicit(s1, rec, em, out, -1, 1, st) != cudaSuccess) return BNB_ERR_CUDA;
   return BNB_OK;
+}
+
+int32_t bnb_implicit_irradiance(const bnb_surface* s1, const bnb_receiver* rec, const bnb_emitters* em,
+                                const bnb_cell_bounds* cells, int64_t n, int32_t mode, void* stream) {
+  if (!surface_ok(s1) || !emitters_ok(em) || !rec || !cells) return BNB_ERR_INVALID;
+  if (s1->kind != BNB_REFRACT) return BNB_ERR_UNSUPPORTED;
+  if (!(s1->eta > 0.0f && s1->eta < 1e6f)) return BNB_ERR_INVALID;
+  if (mode != 0 && mode != 1) return BNB_ERR_INVALID;
+  if (n < -1 || n > cells->capacity || (n < 0 && !cells->count)) return BNB_ERR_INVALID;
+  if (n == 0 || cells->capacity == 0) return BNB_OK;
+  if (!cells->u_lo || !cells->u_hi || !cells->v_lo || !cells->v_hi || !cells->e_hi || !cells->emitter ||
+      !cells->tri0 || !cells->tri1 || !cells->cell || !cells->flags)
+    return BNB_ERR_INVALID;
+  return launch_implicit(s1, rec, em, cells, n, mode, (cudaStream_t)stream) == cudaSuccess ? BNB_OK : BNB_ERR_CUDA;
 }
 
 size_t bnb_build_index_ws(const bnb_cell_bounds* cells, int32_t grid_res, int64_t pre_capacity) {

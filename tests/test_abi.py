@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(bnb):
 def test_status_strings_and_version(bnb):
     assert bnb.bnb_status_string(0) == "ok"
     assert "capacity" in bnb.bnb_status_string(-2)
-    assert bnb.lib().bnb_abi_version() == 9
+    assert bnb.lib().bnb_abi_version() == 10
 
 
 def test_workspace_queries_are_host_only(bnb):
@@ -204,3 +204,43 @@ def test_batched_queries_and_rejections_are_host_only(bnb):
         bnb.BNB_ERR_INVALID
     assert bnb.bnb_sample_and_solve_batched(4100, 4096, C.byref(cfg), C.byref(stats), 4096, ws, None) == \
         bnb.BNB_ERR_INVALID  # job table not 8-byte aligned
+
+
+def test_implicit_irradiance_arguments(bnb):
+    """Argument checks of the implicit-differentiation pass, all before any launch."""
+    s = bnb.bnb_surface()
+    s.n_tris, s.n_verts = 8, 9
+    for f in ("px", "py", "pz", "nx", "ny", "nz", "i0", "i1", "i2"):
+        setattr(s, f, 4096)
+    rec = bnb.bnb_receiver()
+    em = bnb.bnb_emitters(1, 4096, 4096, 4096, 4096)
+    cells = bnb.bnb_cell_bounds()
+    cells.capacity = 16
+    s.kind = bnb.BNB_REFLECT
+    assert bnb.bnb_implicit_irradiance(C.byref(s), C.byref(rec), C.byref(em), C.byref(cells), 0, 0, None) == \
+        bnb.BNB_ERR_UNSUPPORTED
+    s.kind, s.eta = bnb.BNB_REFRACT, 0.75
+    assert bnb.bnb_implicit_irradiance(C.byref(s), C.byref(rec), C.byref(em), C.byref(cells), 0, 2, None) == \
+        bnb.BNB_ERR_INVALID
+    assert bnb.bnb_implicit_irradiance(C.byref(s), C.byref(rec), C.byref(em), C.byref(cells), 17, 0, None) == \
+        bnb.BNB_ERR_INVALID
+    assert bnb.bnb_implicit_irradiance(C.byref(s), C.byref(rec), C.byref(em), C.byref(cells), -1, 0, None) == \
+        bnb.BNB_ERR_INVALID  # n = -1 needs the device count
+    assert bnb.bnb_implicit_irradiance(C.byref(s), C.byref(rec), C.byref(em), C.byref(cells), 0, 1, None) == \
+        bnb.BNB_OK
+    assert bnb.bnb_implicit_irradiance(C.byref(s), C.byref(rec), C.byref(em), C.byref(cells), 4, 0, None) == \
+        bnb.BNB_ERR_INVALID  # record arrays missing
+    # the bound pass: irradiance 2 needs a refracting surface, 3 is not a mode
+    out = bnb.bnb_cell_bounds()
+    out.capacity = 1 << 20
+    out.count = 4096
+    out.status = 4096
+    for f in ("u_lo", "u_hi", "v_lo", "v_hi", "e_hi", "emitter", "tri0", "tri1", "cell", "flags"):
+        setattr(out, f, 4096)
+    cfg = bnb.bnb_bound_cfg(1, 0, 3, 0)
+    assert bnb.bnb_bound_tuples(C.byref(s), None, C.byref(rec), C.byref(em), C.byref(cfg), C.byref(out), None, 0,
+                                None) == bnb.BNB_ERR_INVALID
+    s.kind = bnb.BNB_REFLECT
+    cfg = bnb.bnb_bound_cfg(1, 0, 2, 0)
+    assert bnb.bnb_bound_tuples(C.byref(s), None, C.byref(rec), C.byref(em), C.byref(cfg), C.byref(out), None, 0,
+                                None) == bnb.BNB_ERR_UNSUPPORTED
