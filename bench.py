@@ -414,6 +414,11 @@ def run_gpu(args):
             line["adaptive"] = adaptive_summary(dev, args.adaptive_steps)
         except Exception as ex:  # reported in the line; the bound benchmark above stands
             line["adaptive"] = {"error": f"{type(ex).__name__}: {ex}"}
+    if args.implicit_steps > 0 and rank == 0 and world == 1 and not args.emitters:
+        try:
+            line["implicit"] = implicit_summary(dev, args.implicit_steps)
+        except Exception as ex:  # reported in the line; the bound benchmark above stands
+            line["implicit"] = {"error": f"{type(ex).__name__}: {ex}"}
     if args.pairs_steps > 0 and rank == 0 and world == 1:
         try:
             line["pairs"] = pairs_summary(dev, args.pairs_steps, not args.no_cpu_baseline and not args.emitters)
@@ -598,6 +603,69 @@ def pairs_summary(dev, steps: int, oracle_too: bool) -> dict:
 ADAPT = dict(depth=0, adapt_depth=6, sigma=1e-6, alpha=2.0)
 
 
+def implicit_fma_per_record() -> int:
+    """FMAs of one record of the implicit-differentiation pass: a scaled-Bernstein product of forms
+    with m and n coefficients is m * n FMAs, an elevation a product with the constant 1, a scaling
+    one FMA per coefficient (the operation sequence of the kernel, both vectors b)."""
+    T = lambda n, p, q: (n + 1) * (n + 2) // 2 * (p + 1) * (q + 1)
+    mul = lambda a, b: T(*a) * T(*b)
+    elev = lambda a, to: T(*a) * T(to[0] - a[0], to[1] - a[1], to[2] - a[2])
+    s1, b11, s2 = (1, 0, 0), (0, 1, 1), (2, 0, 0)
+    x1e = (1, 1, 1)
+    base = 3 * (3 + elev(s1, x1e) + elev(b11, x1e) + 2 * T(*x1e))        # d0, d1
+    base += 6 * mul(s1, s1) + 6 * mul(x1e, s1) + 3 * mul(x1e, x1e) + 3 * mul(s1, s1)  # d0n, d1n, L1, L0
+    per_dir = 6 * 3 + 12 * 3 + 4 * T(*x1e) + 4 * 3 + 3 * mul(s1, x1e) + 3 * T(*s2) + elev(s2, (2, 1, 1)) + T(2, 1, 1)
+    per_rec = 6 * 3 + 4 * T(*x1e) + 3 * T(*s2)
+    base += 2 * per_dir + 2 * per_rec
+    A, C = s2, (2, 1, 1)
+    fd = (2 * T(*x1e) + elev(s1, x1e) + T(*x1e) + mul(x1e, (4, 0, 0)) + elev((5, 1, 1), (5, 2, 2)) + mul(A, s1)
+          + T(3, 0, 0) + mul((2, 2, 2), (3, 0, 0)) + mul(s1, (4, 2, 2)) + mul(C, x1e) + mul(s2, (3, 2, 2)))
+    fk = mul(x1e, (4, 0, 0)) + mul(C, s1) + mul(s2, (3, 1, 1))
+    per_b = (mul(A, A) + T(4, 0, 0) + mul(C, C) + 2 * fd + 2 * fk + 2 * mul((5, 2, 2), (2, 1, 1))
+             + 2 * mul((5, 1, 1), s2) + elev((7, 1, 1), (7, 3, 3)))
+    return base + 2 * per_b
+
+
+def implicit_summary(dev, steps: int) -> dict:
+    """Implicit-differentiation irradiance bound (Sec. 4.4) near total internal reflection: a
+    light under water below a 32^2 heightfield (2048 triangles), a wall receiver, depth 4
+    (524,288 base cells); the explicit bound pass, then the intersecting implicit pass over its
+    live records, timed alone with CUDA events (L2 flushed between launches)."""
+    import torch
+    from paper_2504_19163_gb300 import bnb
+    from paper_2504_19163_gb300 import scenes as S
+    sc = S.config("tir_wall", n=32, depth=4)
+    ds = bnb.DeviceScene(sc, dev)
+    stream = torch.cuda.current_stream(dev)
+    cb = bnb.bound_tuples(ds, sc.depth, irradiance=True)
+    torch.cuda.synchronize()
+    n_rec = cb.n_records()
+    e_hi0 = cb.e_hi[:n_rec].clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3 + steps)]
+    for i in range(3 + steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        bnb.implicit_irradiance(ds, cb, n=-1, mode=1, stream=stream)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs[3:]]))
+    fl = cb.flags[:n_rec]
+    live = (fl & 1) != 0
+    n_live = int(live.sum().item())
+    e1 = cb.e_hi[:n_rec]
+    tighter = int(((e1 < 0.5 * e_hi0) & live).sum().item())
+    inf_to_finite = int((torch.isinf(e_hi0) & torch.isfinite(e1) & live).sum().item())
+    fma = implicit_fma_per_record()
+    tflops = 2.0 * fma * n_live / (ms * 1e-3) / 1e12
+    return {"workload": "tir_wall 32^2 (2048 tris), depth 4, wall receiver; implicit pass (mode 1) over the live "
+                        "records of the explicit pass", "steps": steps, "records": n_rec, "live_records": n_live,
+            "ms": round(ms, 3), "live_records_per_s": round(n_live / (ms * 1e-3), 1),
+            "fma_per_record": fma, "fp64_tflops": round(tflops, 4),
+            "fp64_frac_of_nominal": round(tflops / 1.25, 4), "fp64_peak_note": "nominal 1.25 TFLOP/s FP64 (not measured)",
+            "bounds_halved_or_better": tighter, "infinite_to_finite": inf_to_finite}
+
+
 def adaptive_summary(dev, steps: int) -> dict:
     """Adaptive subdivision (Sec. 6.1) on the benchmark mirror: every triangle and light sample
     starts as one cell and is subdivided down to depth 6 until its receiver box has area below
@@ -716,6 +784,8 @@ def main():
                     help="requests of the serving workload reported under 'serving' (0: skip)")
     ap.add_argument("--adaptive-steps", type=int, default=5,
                     help="timed steps of the adaptive-subdivision mirror256 pass reported under 'adaptive' (0: skip)")
+    ap.add_argument("--implicit-steps", type=int, default=5,
+                    help="timed launches of the implicit-differentiation irradiance pass (0: skip)")
     ap.add_argument("--pairs-steps", type=int, default=10,
                     help="timed steps of the two-vertex slab48 workload reported under 'pairs' (0: skip)")
     args = ap.parse_args()
