@@ -24,10 +24,15 @@
 //   * Sec. 5.3, Algorithm 1, and Sec. 5.4: independent selection of each tuple
 //     with P = min(gamma * E~, 1), estimate sum E(T)/P over selected tuples.
 //   * Sec. 6.1 "Root-finding": Newton's method with deterministic initialization.
-//   * Two specular vertices (refraction at both, the TT chains of Table "tab:perf"):
-//     Sec. 6.1 "Tuple construction" (candidate T2 of a cell from the bound of x1 and
-//     of the direction ratios) and "Degree reduction" (u2 reduced to degree 1 plus a
-//     remainder, then the second vertex), and a direct-geometry chain evaluator.
+//   * Two specular vertices (each reflecting or refracting; the TT chains of Table
+//     "tab:perf"): Sec. 6.1 "Tuple construction" (candidate T2 of a cell from the bound
+//     of x1 and of the direction ratios) and "Degree reduction" (u2 reduced to degree 1
+//     plus a remainder, then the second vertex), and a direct-geometry chain evaluator.
+//   * Sec. 4.4 "Implicit differentiation": the irradiance of a single refraction from
+//     the specular polynomials F, G of the section's footnote over the cell and the
+//     receiver box, |du1/du_k| = |det B| / |det A|, bounded by coefficient ratios.
+//   * Sec. 6.1 "Domain subdivision" (adaptive stopping), Sec. 5.3 bin packing and the
+//     stochastic Newton starts ("Stoc") with their reciprocal weighting.
 //
 // Readings where the paper is silent (cell split order, chord closed form,
 // forward culling, grid inclusion, RNG, Newton details) are listed in the
