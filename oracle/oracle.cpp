@@ -2246,13 +2246,15 @@ ImplicitForms implicit_forms(const Tri& T, V3 x0, double eta, const Rec& R, cons
 
 // E_lo, E_hi of one refraction record by implicit differentiation (header comment above).
 void implicit_irradiance(const Tri& T, V3 x0, double I0, double eta, const Rec& R, const UV C[3], double ul,
-                         double uh, double vl, double vh, double* e_lo, double* e_hi) {
+                         double uh, double vl, double vh, int b_mask, double* e_lo, double* e_hi) {
   const double inf = std::numeric_limits<double>::infinity();
   const V3 N1 = cross(T.p[1] - T.p[0], T.p[2] - T.p[0]);
   const double k = I0 * std::fabs(dot(T.p[0] - x0, N1)) / norm(cross(R.e1, R.e2));
   double hi = inf, lo = 0.0;
   const V3 bs[2] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}};
-  for (const V3& b : bs) {
+  for (int ib = 0; ib < 2; ++ib) {
+    if (!(b_mask & (1 << ib))) continue;
+    const V3& b = bs[ib];
     const ImplicitForms f = implicit_forms(T, x0, eta, R, C, ul, uh, vl, vh, b);
     bool pos = true, neg = true;
     for (double v : f.detA.c) {
@@ -2282,11 +2284,12 @@ void implicit_irradiance(const Tri& T, V3 x0, double I0, double eta, const Rec& 
 extern "C" {
 
 // Implicit-differentiation irradiance bounds of n single-refraction records (emitter, tri0,
-// cell id at depth, position box): e_lo[i], e_hi[i].
+// cell id at depth, position box): e_lo[i], e_hi[i].  b_mask: 1 = b (1,0,0) only, 2 = (0,1,0)
+// only, 3 = both (the tighter of the two).
 int orc_implicit_bound(const orc_surface* s1, const orc_receiver* rec, const orc_emitters* em, int64_t n,
                        const int32_t* emitter, const int32_t* tri0, const uint32_t* cell, const int32_t* depth,
                        const double* u_lo, const double* u_hi, const double* v_lo, const double* v_hi, double* e_lo,
-                       double* e_hi, int n_threads) {
+                       double* e_hi, int n_threads, int b_mask) {
   if (s1->kind != 1) return -1;
   const Rec R = get_rec(rec);
   parallel_for(n, n_threads, [&](int, int64_t a, int64_t b) {
@@ -2296,7 +2299,7 @@ int orc_implicit_bound(const orc_surface* s1, const orc_receiver* rec, const orc
       cell_corners(cell[i], depth[i], C);
       const V3 x0 = {em->x[e], em->y[e], em->z[e]};
       implicit_irradiance(get_tri(s1, tri0[i]), x0, em->intensity[e], s1->eta, R, C, u_lo[i], u_hi[i], v_lo[i],
-                          v_hi[i], &e_lo[i], &e_hi[i]);
+                          v_hi[i], b_mask, &e_lo[i], &e_hi[i]);
     }
   });
   return 0;

@@ -98,7 +98,7 @@ def lib():
             L.orc_bound_pairs.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, vp, i32]
             L.orc_eval_pair.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i64, vp]
             L.orc_solve_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32, i32, f64, vp, vp, vp, vp, i32]
-            L.orc_implicit_bound.argtypes = [vp, vp, vp, i64] + [vp] * 10 + [i32]
+            L.orc_implicit_bound.argtypes = [vp, vp, vp, i64] + [vp] * 10 + [i32, i32]
             L.orc_implicit_eval.argtypes = [vp, vp, vp, i32, i32, C.c_uint32, i32, f64, f64, f64, f64, i32, i64,
                                             vp, vp, vp, vp, vp]
             _lib = L
@@ -364,9 +364,10 @@ def eval_path(scene, emitter: int, tri: int, u, v, direct: bool = False):
     return uk, vk, E, t
 
 
-def implicit_bound(scene, emitter, tri0, cell, depth, u_lo, u_hi, v_lo, v_hi, n_threads: int = 1):
+def implicit_bound(scene, emitter, tri0, cell, depth, u_lo, u_hi, v_lo, v_hi, n_threads: int = 1, b_mask: int = 3):
     """Implicit-differentiation irradiance bounds (Sec. 4.4) of single-refraction records given by
-    (emitter, tri0, cell id, depth, position box): (e_lo, e_hi) float64 arrays."""
+    (emitter, tri0, cell id, depth, position box): (e_lo, e_hi) float64 arrays.  b_mask: 1 = b
+    (1,0,0) only, 2 = (0,1,0) only, 3 = the tighter of both."""
     L = lib()
     V = _SceneViews(scene)
     a = [np.ascontiguousarray(x, dt) for x, dt in [(emitter, np.int32), (tri0, np.int32), (cell, np.uint32),
@@ -375,7 +376,7 @@ def implicit_bound(scene, emitter, tri0, cell, depth, u_lo, u_hi, v_lo, v_hi, n_
     n = a[0].shape[0]
     lo, hi = np.zeros(n), np.zeros(n)
     rc = L.orc_implicit_bound(C.byref(V.surf), C.byref(V.rec), C.byref(V.em), n, *[_p(x) for x in a], _p(lo),
-                              _p(hi), n_threads)
+                              _p(hi), n_threads, b_mask)
     if rc != 0:
         raise RuntimeError(f"orc_implicit_bound failed: {rc}")
     return lo, hi

@@ -6,7 +6,9 @@ differentiation", with the specular polynomials F, G of its footnote) in the ora
   forward derivatives, an independent route), for both vectors b;
 * every true path's irradiance in a cell lies in [E_lo, E_hi];
 * near total internal reflection the explicit bound is loose or infinite while the implicit one is
-  finite and tighter (the claim of Fig. fig_refraction), and the implicit bound tightens with depth.
+  finite and tighter (the claim of Fig. fig_refraction), and the implicit bound tightens with depth;
+* each of the footnote's two vectors b certifies cells where the other's det A changes sign, and the
+  combined bound is the tighter of the two.
 """
 import numpy as np
 import pytest
@@ -130,3 +132,19 @@ def test_implicit_bound_tightens_with_depth():
     med = [np.median(tightness(S.config("tir_wall", depth=d))[1]) for d in (2, 3, 4)]
     assert med[0] > med[1] > med[2] >= 1.0, med
     assert med[2] < 1.5, med
+
+
+def test_two_vectors_b_cover_each_others_degenerate_cells():
+    """The footnote's reason for intersecting the bounds of b1 = (1,0,0) and b2 = (0,1,0): where
+    (d0 x n1).b vanishes inside a cell, det A of that b changes sign and its bound is +inf; the
+    other b certifies most such cells.  The combined bound is the smaller E_hi and larger E_lo."""
+    sc = S.config("water", n=4, depth=2)
+    live = live_records(sc)
+    args = (sc, live["emitter"], live["tri0"], live["cell"], depth_of(live), live["u_lo"], live["u_hi"],
+            live["v_lo"], live["v_hi"])
+    (lo1, hi1), (lo2, hi2), (lo, hi) = (O.implicit_bound(*args, n_threads=8, b_mask=m) for m in (1, 2, 3))
+    f1, f2 = np.isfinite(hi1), np.isfinite(hi2)
+    assert np.sum(f1 & ~f2) >= 20 and np.sum(f2 & ~f1) >= 20
+    np.testing.assert_array_equal(hi, np.minimum(hi1, hi2))
+    np.testing.assert_array_equal(lo, np.maximum(lo1, lo2))
+    assert np.sum(np.isfinite(hi)) > max(f1.sum(), f2.sum())
