@@ -218,3 +218,29 @@ def test_estimator_equals_exhaustive_enumeration(name):
     assert st.sum() > 50
     assert np.count_nonzero(out["E"]) > 50
     np.testing.assert_allclose(out["E"], E_all, rtol=1e-12, atol=0.0)
+
+
+@pytest.mark.parametrize("name", ["slab", "periscope"])
+def test_pair_gap_agrees_with_candidates_and_is_a_distance(name):
+    """The gap by which T2's xy box misses a cell's footprint (the measure the GPU parity tests use
+    for GPU-only candidates): <= 0 exactly for the enumerated candidates; shifting s2 by delta
+    along x moves T2's box and not the footprint (same z-range), so every finite gap changes by at
+    most |delta|, and by exactly |delta| where the x separation decides it."""
+    import dataclasses
+    sc = S.config(name, n=4, depth=1, amp=0.04)
+    cand = set(zip(*[a.tolist() for a in O.pair_candidates(sc)]))
+    n_c = 4 ** sc.depth
+    items = [(0, t, c, b) for t in range(sc.s1.n_tris) for c in range(n_c) for b in range(sc.s2.n_tris)]
+    e, t1, cell, t2 = (np.array(x) for x in zip(*items))
+    gap = O.pair_gap(sc, e, t1, cell, t2)
+    is_cand = np.array([it in cand for it in items])
+    assert is_cand.sum() > 50 and (~is_cand).sum() > 50
+    np.testing.assert_array_equal(gap <= 0, is_cand)
+    delta = 0.013
+    s2 = dataclasses.replace(sc.s2, px=(sc.s2.px + np.float32(delta)).astype(np.float32))
+    gap2 = O.pair_gap(dataclasses.replace(sc, s2=s2), e, t1, cell, t2)
+    fin = np.isfinite(gap) & np.isfinite(gap2)
+    assert fin.sum() > 100
+    d = np.abs(gap2[fin] - gap[fin])
+    assert np.all(d <= delta + 1e-6)
+    assert np.sum(np.abs(d - delta) < 1e-6) > 20
