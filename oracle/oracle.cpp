@@ -2328,3 +2328,186 @@ int orc_implicit_eval(const orc_surface* s1, const orc_receiver* rec, const orc_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Implicit differentiation for two-vertex chains whose first vertex reflects (Sec. 4.4
+// "Implicit differentiation": the specular constraint at the last specular vertex x2 in u1
+// and u_k, with u2 substituted by its rational function of u1).
+//
+//   * First vertex (reflection, Eq. eq_refr_rational): d~1 = (n1.n1) d0 - 2 (d0.n1) n1, exact
+//     (no square root), so u2 = U2/Q2, v2 = V2/Q2 on T2's plane (Eq. eq_rct, Moller form) is
+//     an exact rational function of u1, and x2 = X2/Q2, n2 = N2/Q2 with
+//     X2 = p20 Q2 + U2 e21 + V2 e22, N2 = n20 Q2 + U2 (n21 - n20) + V2 (n22 - n20).
+//   * Constraints at x2 with d1 = x2 - x1 = D1/Q2, d2 = x_k - x2 = D2/Q2 (D1 = X2 - x1 Q2,
+//     D2 = x_k Q2 - X2) and A = (D1 x N2).b, C = (D2 x N2).b:
+//       F~ = eta2'^2 |D2|^2 A^2 - |D1|^2 C^2  (eta2' = 1 for a reflecting second vertex),
+//       G~ = (D1 x N2).D2,
+//     the section's F and G times powers of Q2 (functions of u1 alone): on the path manifold,
+//     where F = G = 0, the derivatives scale by the same factors and |du1/du_k| is unchanged.
+//   * Derivatives along u1 are taken in the cell's barycentric coordinates (Bernstein
+//     differencing), then det d(F,G)/d(u1,v1) = det d(F,G)/d(l1,l2) / det M with M the cell's
+//     edge matrix in T1's (u, v); along u_k by the product rule (d D2/du_k = e1 Q2, v_k: e2 Q2).
+//   * E = I0 |C1| |det B| |det M| / (|d0|^3 |N_k| |det A_l|), bounded like the single-vertex
+//     case over the cell x the record's receiver box; the tighter of b = x and y.
+// ---------------------------------------------------------------------------
+namespace {
+
+// d/d l_j (j = 1, 2) of a tensor form in the simplex's barycentric coordinates (l0 = 1 - l1 - l2):
+// degree n - 1 with classical coefficients n (c_{g + e_j} - c_{g + e_0}).
+TPl tderiv_simplex(const TPl& a, int j) {
+  TPl r{a.n - 1, a.p, a.q, {}};
+  r.c.assign(tsize(r.n, r.p, r.q), 0.0);
+  const int bs = (a.p + 1) * (a.q + 1);
+  for_each_index(2, r.n, [&](int g1, int g2) {
+    const int ij = j == 1 ? pidx(2, a.n, g1 + 1, g2) : pidx(2, a.n, g1, g2 + 1);
+    const int i0 = pidx(2, a.n, g1, g2);
+    const int ir = pidx(2, r.n, g1, g2);
+    for (int k = 0; k < bs; ++k) r.c[ir * bs + k] = a.n * (a.c[ij * bs + k] - a.c[i0 * bs + k]);
+  });
+  return r;
+}
+
+TV tv_scale_poly(const TPl& s, const TV& a) { return {tmul(s, a.x), tmul(s, a.y), tmul(s, a.z)}; }
+TV tv_constmul(const TPl& s, V3 c) { return {tscale(s, c.x), tscale(s, c.y), tscale(s, c.z)}; }
+TPl tv_comp(const TV& a, int c) { return c == 0 ? a.x : (c == 1 ? a.y : a.z); }
+
+struct ChainForms {
+  TPl F, G, detA, detB, L0;
+  double detM;
+};
+
+// Forms of one reflecting-first chain record (cell C of T1 = A, second vertex on T2 = Bt with the
+// law eta2 (< 0: mirror), receiver box) for the vector component b (0: x, 1: y).
+ChainForms chain_forms(const Tri& A, const Tri& Bt, V3 x0, double eta2, const Rec& R, const UV C[3], double ul,
+                       double uh, double vl, double vh, int bc) {
+  const V3 Eu = A.p[1] - A.p[0], Ev = A.p[2] - A.p[0], Nu = A.n[1] - A.n[0], Nv = A.n[2] - A.n[0];
+  auto X = [&](const UV& c) { return A.p[0] + c.u * Eu + c.v * Ev; };
+  auto Nn = [&](const UV& c) { return A.n[0] + c.u * Nu + c.v * Nv; };
+  const TV x1 = tv_simplex(X(C[0]), X(C[1]), X(C[2]));
+  const TV n1 = tv_simplex(Nn(C[0]), Nn(C[1]), Nn(C[2]));
+  const TV d0 = tv_sub(x1, tv_const(x0));
+  const TPl nn = tv_dot(n1, n1), dn = tv_dot(d0, n1);
+  const TV dt = tv_sub(tv_scale_poly(nn, d0), tv_scale_poly(tscale(dn, 2.0), n1));  // reflected, degree 3
+  const V3 p20 = Bt.p[0], e21 = Bt.p[1] - p20, e22 = Bt.p[2] - p20;
+  const V3 n20 = Bt.n[0], dn21 = Bt.n[1] - n20, dn22 = Bt.n[2] - n20;
+  const TV w2 = tv_sub(x1, tv_const(p20));
+  const TV dxe = tv_cross(dt, tv_const(e22));
+  const TPl Q2 = tv_dot(dxe, tv_const(e21));
+  const TPl U2 = tv_dot(dxe, w2);
+  const TPl V2 = tv_dot(tv_cross(w2, tv_const(e21)), dt);
+  const TV X2 = tv_add(tv_add(tv_constmul(Q2, p20), tv_constmul(U2, e21)), tv_constmul(V2, e22));
+  const TV N2 = tv_add(tv_add(tv_constmul(Q2, n20), tv_constmul(U2, dn21)), tv_constmul(V2, dn22));
+  const TV D1 = tv_sub(X2, tv_scale_poly(Q2, x1));
+  const TV xk = tv_box(R.p0 + ul * R.e1 + vl * R.e2, (uh - ul) * R.e1, (vh - vl) * R.e2);
+  const TV D2 = tv_sub(tv_scale_poly(Q2, xk), X2);
+  const TV D1N = tv_cross(D1, N2), D2N = tv_cross(D2, N2);
+  const TPl Ab = tv_comp(D1N, bc), Cb = tv_comp(D2N, bc);
+  const TPl L1 = tv_dot(D2, D2), L1b = tv_dot(D1, D1);
+  const double e2 = eta2 < 0.0 ? 1.0 : eta2 * eta2;
+  ChainForms out;
+  out.F = tadd(tscale(tmul(L1, tmul(Ab, Ab)), e2), tmul(L1b, tmul(Cb, Cb)), -1.0);
+  out.G = tv_dot(D1N, D2);
+  const TPl F1 = tderiv_simplex(out.F, 1), F2 = tderiv_simplex(out.F, 2);
+  const TPl G1 = tderiv_simplex(out.G, 1), G2 = tderiv_simplex(out.G, 2);
+  out.detA = televate(tadd(tmul(F1, G2), tmul(F2, G1), -1.0), 34, 3, 3);
+  auto dk = [&](V3 e, TPl* dF, TPl* dG) {
+    const TV eQ = tv_constmul(Q2, e);  // d D2 / d u_k
+    const TPl dC = tv_comp(tv_cross(eQ, N2), bc);
+    *dF = tadd(tscale(tmul(tscale(tv_dot(D2, eQ), 2.0), tmul(Ab, Ab)), e2), tmul(L1b, tscale(tmul(Cb, dC), 2.0)),
+               -1.0);
+    *dG = tv_dot(D1N, eQ);
+  };
+  TPl Fu, Gu, Fv, Gv;
+  dk(R.e1, &Fu, &Gu);
+  dk(R.e2, &Fv, &Gv);
+  out.detB = televate(tadd(tmul(Fu, Gv), tmul(Fv, Gu), -1.0), 34, 3, 3);
+  out.L0 = tv_dot(d0, d0);
+  out.detM = (C[1].u - C[0].u) * (C[2].v - C[0].v) - (C[2].u - C[0].u) * (C[1].v - C[0].v);
+  return out;
+}
+
+double chain_k(const Tri& A, V3 x0, double I0, const Rec& R) {
+  const V3 N1 = cross(A.p[1] - A.p[0], A.p[2] - A.p[0]);
+  return I0 * std::fabs(dot(A.p[0] - x0, N1)) / norm(cross(R.e1, R.e2));
+}
+
+}  // namespace
+
+extern "C" {
+
+// Implicit-differentiation irradiance bounds of n chain records (emitter, tri0 on s1, cell at
+// depth, tri1 on s2, receiver box) whose first vertex reflects: e_lo[i], e_hi[i].  b_mask as in
+// orc_implicit_bound.  Returns -1 unless s1 reflects.
+int orc_implicit_bound_pairs(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec,
+                             const orc_emitters* em, int64_t n, const int32_t* emitter, const int32_t* tri0,
+                             const uint32_t* cell, const int32_t* depth, const int32_t* tri1, const double* u_lo,
+                             const double* u_hi, const double* v_lo, const double* v_hi, double* e_lo, double* e_hi,
+                             int n_threads, int b_mask) {
+  if (s1->kind != 0) return -1;
+  const Rec R = get_rec(rec);
+  const double inf = std::numeric_limits<double>::infinity();
+  parallel_for(n, n_threads, [&](int, int64_t a, int64_t b) {
+    for (int64_t i = a; i < b; ++i) {
+      const int e = emitter[i];
+      UV C[3];
+      cell_corners(cell[i], depth[i], C);
+      const V3 x0 = {em->x[e], em->y[e], em->z[e]};
+      const Tri A = get_tri(s1, tri0[i]), Bt = get_tri(s2, tri1[i]);
+      const double k = chain_k(A, x0, em->intensity[e], R);
+      double hi = inf, lo = 0.0;
+      for (int bc = 0; bc < 2; ++bc) {
+        if (!(b_mask & (1 << bc))) continue;
+        const ChainForms f = chain_forms(A, Bt, x0, law(s2), R, C, u_lo[i], u_hi[i], v_lo[i], v_hi[i], bc);
+        bool pos = true, neg = true;
+        for (double v : f.detA.c) {
+          if (!(v > 0.0)) pos = false;
+          if (!(v < 0.0)) neg = false;
+        }
+        if (!pos && !neg) continue;
+        double rmin = inf, rmax = -inf;
+        for (size_t j = 0; j < f.detA.c.size(); ++j) {
+          const double r = f.detB.c[j] / f.detA.c[j];
+          rmin = std::min(rmin, r);
+          rmax = std::max(rmax, r);
+        }
+        const double amax = std::max(std::fabs(rmin), std::fabs(rmax));
+        const double amin = rmin > 0.0 ? rmin : (rmax < 0.0 ? -rmax : 0.0);
+        const double s_lo = *std::min_element(f.L0.c.begin(), f.L0.c.end());
+        const double s_hi = *std::max_element(f.L0.c.begin(), f.L0.c.end());
+        const double m = std::fabs(f.detM);
+        hi = std::min(hi, s_lo > 0.0 ? k * m * amax / (s_lo * std::sqrt(s_lo)) : inf);
+        lo = std::max(lo, k * m * amin / (s_hi * std::sqrt(s_hi)));
+      }
+      e_lo[i] = lo;
+      e_hi[i] = hi;
+    }
+  });
+  return 0;
+}
+
+// The chain forms of one record at n points (cell barycentrics l1, l2; box coordinates s, t), for
+// b component which_b: out[3 i + 0..2] = F~, G~ and the irradiance I0 |C1| |det B| |det M| /
+// (|d0|^3 |N_k| |det A_l|).
+int orc_implicit_eval_pair(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec,
+                           const orc_emitters* em, int32_t e, int32_t t1, uint32_t cell, int32_t depth, int32_t t2,
+                           double ul, double uh, double vl, double vh, int32_t which_b, int64_t n, const double* l1,
+                           const double* l2, const double* s, const double* tt, double* out) {
+  if (s1->kind != 0) return -1;
+  UV C[3];
+  cell_corners(cell, depth, C);
+  const V3 x0 = {em->x[e], em->y[e], em->z[e]};
+  const Rec R = get_rec(rec);
+  const Tri A = get_tri(s1, t1), Bt = get_tri(s2, t2);
+  const ChainForms f = chain_forms(A, Bt, x0, law(s2), R, C, ul, uh, vl, vh, which_b);
+  const double k = chain_k(A, x0, em->intensity[e], R);
+  for (int64_t i = 0; i < n; ++i) {
+    const double L0 = teval(f.L0, l1[i], l2[i], s[i], tt[i]);
+    out[3 * i + 0] = teval(f.F, l1[i], l2[i], s[i], tt[i]);
+    out[3 * i + 1] = teval(f.G, l1[i], l2[i], s[i], tt[i]);
+    out[3 * i + 2] = k * std::fabs(teval(f.detB, l1[i], l2[i], s[i], tt[i]) * f.detM) /
+                     (L0 * std::sqrt(L0) * std::fabs(teval(f.detA, l1[i], l2[i], s[i], tt[i])));
+  }
+  return 0;
+}
+
+}  // extern "C"

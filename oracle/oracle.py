@@ -101,6 +101,9 @@ def lib():
             L.orc_implicit_bound.argtypes = [vp, vp, vp, i64] + [vp] * 10 + [i32, i32]
             L.orc_implicit_eval.argtypes = [vp, vp, vp, i32, i32, C.c_uint32, i32, f64, f64, f64, f64, i32, i64,
                                             vp, vp, vp, vp, vp]
+            L.orc_implicit_bound_pairs.argtypes = [vp, vp, vp, vp, i64] + [vp] * 11 + [i32, i32]
+            L.orc_implicit_eval_pair.argtypes = [vp, vp, vp, vp, i32, i32, C.c_uint32, i32, i32, f64, f64, f64, f64,
+                                                 i32, i64, vp, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -395,6 +398,41 @@ def implicit_eval(scene, emitter: int, tri0: int, cell: int, depth: int, box, wh
     if rc != 0:
         raise RuntimeError(f"orc_implicit_eval failed: {rc}")
     return dict(F=out[:, 0], G=out[:, 1], detA=out[:, 2], detB=out[:, 3], L0=out[:, 4])
+
+
+def implicit_bound_pairs(scene, emitter, tri0, cell, depth, tri1, u_lo, u_hi, v_lo, v_hi, n_threads: int = 1,
+                         b_mask: int = 3):
+    """Implicit-differentiation irradiance bounds (Sec. 4.4) of chain records whose first vertex
+    reflects: (e_lo, e_hi) float64 arrays.  b_mask as in implicit_bound."""
+    L = lib()
+    V = _SceneViews(scene)
+    a = [np.ascontiguousarray(x, dt) for x, dt in [(emitter, np.int32), (tri0, np.int32), (cell, np.uint32),
+                                                   (depth, np.int32), (tri1, np.int32), (u_lo, np.float64),
+                                                   (u_hi, np.float64), (v_lo, np.float64), (v_hi, np.float64)]]
+    n = a[0].shape[0]
+    lo, hi = np.zeros(n), np.zeros(n)
+    rc = L.orc_implicit_bound_pairs(C.byref(V.surf), C.byref(V.surf2), C.byref(V.rec), C.byref(V.em), n,
+                                    *[_p(x) for x in a], _p(lo), _p(hi), n_threads, b_mask)
+    if rc != 0:
+        raise RuntimeError(f"orc_implicit_bound_pairs failed: {rc}")
+    return lo, hi
+
+
+def implicit_eval_pair(scene, emitter: int, tri0: int, cell: int, depth: int, tri1: int, box, which_b: int, l1, l2,
+                       s, t) -> dict:
+    """The chain forms F~, G~ and the implicit irradiance of one reflecting-first chain record at
+    cell barycentrics (l1, l2) and box coordinates (s, t)."""
+    L = lib()
+    V = _SceneViews(scene)
+    l1, l2, s, t = (np.ascontiguousarray(x, np.float64) for x in (l1, l2, s, t))
+    n = l1.shape[0]
+    out = np.zeros((n, 3))
+    rc = L.orc_implicit_eval_pair(C.byref(V.surf), C.byref(V.surf2), C.byref(V.rec), C.byref(V.em), emitter, tri0,
+                                  cell, depth, tri1, *map(float, box), which_b, n, _p(l1), _p(l2), _p(s), _p(t),
+                                  _p(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_implicit_eval_pair failed: {rc}")
+    return dict(F=out[:, 0], G=out[:, 1], E=out[:, 2])
 
 
 def tuple_key(emitter, tri0, tri1=-1):
