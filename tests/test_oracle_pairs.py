@@ -244,3 +244,36 @@ def test_pair_gap_agrees_with_candidates_and_is_a_distance(name):
     d = np.abs(gap2[fin] - gap[fin])
     assert np.all(d <= delta + 1e-6)
     assert np.sum(np.abs(d - delta) < 1e-6) > 20
+
+
+def test_flat_mirror_glass_closed_form():
+    """A flat mirror at z = 0 (light (0,0,2)) and a flat glass interface at z = 1 (eta' = 1/1.5 from
+    the air below), receiver z = 1.5: rotationally symmetric about the light's axis.  A ray leaving
+    at theta0 from the vertical meets the mirror at r = 2 tan(theta0), the interface at 1.5 r and
+    the receiver at rho = 3 tan(theta0) + 0.5 tan(theta_t), sin(theta_t) = sin(theta0) / 1.5, and
+    the irradiance is I0 dOmega0 / dA = I0 sin(theta0) / (rho drho/dtheta0)."""
+    sc = S.config("mirror_glass", n=2, flat=True, extent=1.0, lights=[(0.0, 0.0, 2.0)], rec_half=1.5)
+    eta = float(np.float32(1.0 / 1.5))  # the surface stores eta' in float32
+    rng = np.random.default_rng(5)
+    checked = 0
+    for t in range(sc.s1.n_tris):
+        u = rng.uniform(0, 1, 40)
+        v = rng.uniform(0, 1, 40) * (1 - u)
+        x1 = tri_points(sc.s1, t, u, v)[:, :2]
+        r = np.linalg.norm(x1, axis=1)
+        ok = (np.max(np.abs(1.5 * x1), axis=1) < 1.0 - 1e-6) & (r > 1e-3)  # the interface hit is on T2's face
+        for b in range(sc.s2.n_tris):
+            P = O.eval_pair(sc, 0, t, b, u, v)
+            hit = ok & through_t2(P) & (P["t2"] > 0)
+            if not hit.any():
+                continue
+            th0 = np.arctan(r[hit] / 2.0)
+            tht = np.arcsin(eta * np.sin(th0))
+            rho = 3.0 * np.tan(th0) + 0.5 * np.tan(tht)
+            drho = 3.0 / np.cos(th0) ** 2 + 0.5 / np.cos(tht) ** 2 * eta * np.cos(th0) / np.cos(tht)
+            X = receiver_xy(sc, P["uk"][hit], P["vk"][hit])
+            np.testing.assert_allclose(np.linalg.norm(X, axis=1), rho, rtol=1e-9)
+            np.testing.assert_allclose(X / np.linalg.norm(X, axis=1)[:, None], x1[hit] / r[hit][:, None], atol=1e-9)
+            np.testing.assert_allclose(P["E"][hit], np.sin(th0) / (rho * drho), rtol=1e-9)
+            checked += int(hit.sum())
+    assert checked > 30
