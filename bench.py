@@ -470,31 +470,9 @@ def launches_per_step(n_points: int, G: int) -> int:
 
 
 def calibrate_gamma(bnb, ds, idx, target: float) -> float:
-    """gamma such that the mean expected |S| = mean sum_U min(gamma E~, 1) is `target` (Sec. 5.4:
-    one-to-one map between gamma and E|S|), by bisection on log gamma over the device index."""
-    import torch
-    off = idx.offsets
-    su, sv = ds.t["su"], ds.t["sv"]
-    G = idx.grid_res
-    gi = torch.clamp(torch.floor(su * G), 0, G - 1).long()
-    gj = torch.clamp(torch.floor(sv * G), 0, G - 1).long()
-    g = gj * G + gi
-    cnt = (off[1:] - off[:-1])
-    n = int(idx.count[0].item())
-    et = idx.etilde[:n].double()
-    cell_of = torch.repeat_interleave(torch.arange(G * G, device=off.device), cnt)
-    w = torch.bincount(g, minlength=G * G).double()
-    lo, hi = -60.0, 60.0
-    for _ in range(80):
-        mid = 0.5 * (lo + hi)
-        p = torch.clamp(et * (2.0 ** mid), max=1.0)
-        per_cell = torch.zeros(G * G, dtype=torch.float64, device=off.device).index_add_(0, cell_of, p)
-        mean = float((per_cell * w).sum() / w.sum())
-        if mean < target:
-            lo = mid
-        else:
-            hi = mid
-    return float(2.0 ** hi)
+    """gamma such that the mean expected |S| over the workload's shading points is `target`
+    (Sec. 5.4: one-to-one map between gamma and E|S|), by the library's device bisection."""
+    return float(bnb.gamma_for_target(idx, target, ds.t["su"], ds.t["sv"]).item())
 
 
 def serving_summary(n_requests: int, dev) -> dict:

@@ -31,7 +31,8 @@
  *     output struct (0 = ok, BNB_ERR_CAPACITY) and the device counters hold the
  *     size that was needed; the outputs are then incomplete and the caller
  *     re-calls with larger buffers.  The library does not reset `*status`: the
- *     caller zeroes it (and the counters) before a call.
+ *     caller zeroes it (and the counters) before a call.  The same codes also
+ *     go to a device error word that bnb_stream_status() reads and clears.
  *   - No C++ exception crosses the ABI.  Calls on different streams with
  *     disjoint outputs and workspaces may run concurrently.
  */
@@ -179,6 +180,14 @@ typedef struct bnb_sample_stats {
                          |B| summed (groups drawn; bins = 1 only, else 0) */
   int32_t *status;    /* device int32: BNB_OK or BNB_ERR_CAPACITY */
   int32_t *sel_count; /* optional device int32[n_points]: |S| per shading point (NULL: not written) */
+  /* Optional per-selection outputs (NULL: not written), worklist_capacity entries each, in worklist
+   * order: points ascending, and within a point its selected tuples in index (key) order.  Entries
+   * [0, min(counters[1], worklist_capacity)) are written. */
+  int64_t *sel_point; /* shading point of the selection */
+  uint64_t *sel_key;  /* its tuple key */
+  double *root_u1;    /* 2 per selection: the barycentric coordinates (u, v) in T1 of the accepted root
+                         (the polished float64 iterate; the first accepted start with stoc_trials > 0),
+                         or (NaN, NaN) when the selection contributes no root */
 } bnb_sample_stats;
 
 /* Precomputation pass.  Bounds every (emitter, triangle of s1, cell) with
@@ -222,9 +231,16 @@ size_t bnb_bound_tuples_ws(const bnb_surface *s1, const bnb_surface *s2, const b
  * scratch comes from a fixed 8 MiB array inside the library (each GPU that loads the library holds
  * it until the process exits) instead of a caller workspace.
  *   - Returns BNB_ERR_CAPACITY, launching nothing, when bnb_bound_tuples_ws() for these arguments
- *     exceeds 8 MiB (e.g. up to ~50k triangles with ~2M base cells).
- *   - The first call on a device, with that device current, looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture on that device.
+ *     exceeds 8 MiB; that query is the exact test.  One surface: 80 B per triangle plus two split
+ *     queues of 16 B per entry (default 4096 + n_base / 32 entries each), e.g. up to ~50k
+ *     triangles with ~2M base cells.  Two surfaces: 80 B per triangle of each surface, about
+ *     20 B per triangle of s2 for its grid, and 16 B per base cell of s1, so at most ~0.45M
+ *     base cells (a 48^2 slab face at depth 2, 73,728 base cells, needs about 2 MB).
+ *   - The first call in a CUDA context, with that context current, looks up the array's device
+ *     address in it (cudaGetSymbolAddress) and caches it per context (by the driver's context id),
+ *     so calls from another device, from a context created through the driver API, or after
+ *     cudaDeviceReset look it up again; make the first call in each context before any stream
+ *     capture there.
  *   - All calls share the one array, which keeps the last call's contents; each call clears what
  *     must start at zero on its stream.  Calls whose kernels overlap on the GPU (on different
  *     streams, or from different threads) race on the array: serialize them.
@@ -256,6 +272,22 @@ int32_t bnb_sample_and_solve(const bnb_surface *s1, const bnb_surface *s2, const
                              bnb_sample_stats *stats, void *ws, size_t ws_bytes, void *stream);
 size_t bnb_sample_and_solve_ws(const bnb_surface *s1, const bnb_surface *s2, int64_t n_points,
                                int64_t worklist_capacity);
+
+/* gamma for a target expected sample count (Sec. 5.4: gamma and E|S| are in one-to-one
+ * correspondence, so the sampling density is set by E|S|).  With the selection rule of
+ * bnb_sample_and_solve (a 24-bit draw below P = min(gamma (x) E~, 1), product rounded up) a listed
+ * tuple is selected with probability exactly ceil(P 2^24) / 2^24, and
+ *     E|S|(gamma) = sum over grid cells g of w_g * sum over g's listed tuples of that probability, / W,
+ * with w_g the number of shading points (su, sv: device float arrays of n_points >= 1) whose grid
+ * cell is g and W = n_points; su = sv = NULL weighs every grid cell once (W = G^2, n_points
+ * ignored).  The sum is formed in integers on the device and bisected over the bit patterns of
+ * the non-negative finite floats: *gamma_out (device float) receives the smallest gamma with
+ * E|S|(gamma) >= target, or FLT_MAX when no gamma reaches it.  Deterministic.  target >= 0.
+ * ws: bnb_gamma_for_target_ws(grid_res) bytes (the weights and the bisection state); ~65 small
+ * launches on the stream, no host synchronization. */
+int32_t bnb_gamma_for_target(const bnb_index *index, const float *su, const float *sv, int64_t n_points,
+                             double target, float *gamma_out, void *ws, size_t ws_bytes, void *stream);
+size_t bnb_gamma_for_target_ws(int32_t grid_res);
 
 /* ---- Batched rendering pass ------------------------------------------------
  * The paper renders one frame at a time; these calls serve many rendering
@@ -315,7 +347,7 @@ typedef struct bnb_batch_cfg {
  * Device-side overflows (sum of n_points > max_points, *n_jobs > max_jobs,
  * more selections than worklist_capacity) set *stats->status =
  * BNB_ERR_CAPACITY; stats->counters as bnb_sample_and_solve, summed over the
- * batch; stats->sel_count is not written.  The caller zeroes status and
+ * batch; stats->sel_count, sel_point, sel_key and root_u1 are not written.  The caller zeroes status and
  * counters before each batch.  ws: bnb_sample_and_solve_batched_ws(cfg) bytes. */
 int32_t bnb_sample_and_solve_batched(const bnb_job *jobs, const int32_t *n_jobs, const bnb_batch_cfg *cfg,
                                      bnb_sample_stats *stats, void *ws, size_t ws_bytes, void *stream);
@@ -360,6 +392,20 @@ size_t bnb_bound_tuples_batched_ws(int32_t max_jobs);
 /* Human-readable name of a status code (static string). */
 const char *bnb_status_string(int32_t status);
 
+/* Reads and clears the device error word (no counterpart in the paper: the error reporting of this
+ * GPU library).  Every kernel that meets a condition only the
+ * device can see (BNB_ERR_CAPACITY: an output, split queue, index or worklist too small) raises it
+ * both in the status word of its call's output struct and in a device error word that keeps the
+ * first code raised since the last read.  This call synchronizes `stream` (all work enqueued on it
+ * has finished when it returns), then takes the word with an atomic exchange against 0, so a code
+ * raised concurrently is reported either now or by the next call, never lost.  Returns BNB_OK when
+ * no kernel raised anything since the last read, the first code raised otherwise, or BNB_ERR_CUDA
+ * when the stream itself failed (a launch or fault error).  The word belongs to the CUDA context
+ * current on the calling thread, not to the stream: it collects codes from every stream and call
+ * in that context, so callers that share a context also share the word.  The per-struct status
+ * words are not touched.  Not for use during stream capture (it synchronizes). */
+int32_t bnb_stream_status(void *stream);
+
 /* ABI version of this header (increments on any struct or signature change). */
 /* Implicit-differentiation irradiance bound (Sec. 4.4 "Implicit differentiation", with the
  * specular polynomials F, G of its footnote) of single-refraction records, on the stream.
@@ -379,7 +425,7 @@ const char *bnb_status_string(int32_t status);
 int32_t bnb_implicit_irradiance(const bnb_surface *s1, const bnb_receiver *rec, const bnb_emitters *em,
                                 const bnb_cell_bounds *cells, int64_t n, int32_t mode, void *stream);
 
-int32_t bnb_abi_version(void);  /* 10 */
+int32_t bnb_abi_version(void);  /* 11 */
 
 #ifdef __cplusplus
 }

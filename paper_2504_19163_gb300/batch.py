@@ -33,38 +33,13 @@ JOB_BYTES = C.sizeof(bnb.bnb_job)
 
 
 def gamma_for_target(index: bnb.Index, target: float, su: Optional[torch.Tensor] = None,
-                     sv: Optional[torch.Tensor] = None) -> float:
-    """gamma such that the mean over shading points of the expected number of selected tuples,
-    sum over the listed tuples of min(gamma E~, 1), equals `target` (Sec. 5.4: gamma and E|S| are
-    in one-to-one correspondence).  Points default to a uniform density over [0,1]^2 (every grid
-    cell weighted equally).  Bisection on log2 gamma; a parameter choice made on the host, not a
-    step of the rendering pass."""
-    off = index.offsets
-    G = index.grid_res
-    dev = off.device
-    n = int(index.count[0].item())
-    if n == 0:
-        return 1.0
-    cnt = off[1:] - off[:-1]
-    et = index.etilde[:n].double()
-    cell_of = torch.repeat_interleave(torch.arange(G * G, device=dev), cnt)
-    if su is None:
-        w = torch.ones(G * G, dtype=torch.float64, device=dev)
-    else:
-        gi = torch.clamp(torch.floor(su * G), 0, G - 1).long()
-        gj = torch.clamp(torch.floor(sv * G), 0, G - 1).long()
-        w = torch.bincount(gj * G + gi, minlength=G * G).double()
-    lo, hi = -60.0, 60.0
-    for _ in range(80):
-        mid = 0.5 * (lo + hi)
-        p = torch.clamp(et * (2.0 ** mid), max=1.0)
-        per_cell = torch.zeros(G * G, dtype=torch.float64, device=dev).index_add_(0, cell_of, p)
-        mean = float((per_cell * w).sum() / w.sum())
-        if mean < target:
-            lo = mid
-        else:
-            hi = mid
-    return float(2.0 ** hi)
+                     sv: Optional[torch.Tensor] = None, stream=None) -> float:
+    """gamma such that the mean over shading points of the expected number of selected tuples
+    equals `target` (Sec. 5.4: gamma and E|S| are in one-to-one correspondence), computed on the
+    device by bnb_gamma_for_target.  Points default to a uniform density over [0,1]^2 (every grid
+    cell weighted equally).  Synchronizes the stream to return the value."""
+    g = bnb.gamma_for_target(index, target, su, sv, stream=stream)
+    return float(g.item())
 
 
 class ResidentScene:

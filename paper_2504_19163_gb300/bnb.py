@@ -68,7 +68,8 @@ class bnb_sample_cfg(C.Structure):
 
 
 class bnb_sample_stats(C.Structure):
-    _fields_ = [("counters", vp), ("status", vp), ("sel_count", vp)]
+    _fields_ = [("counters", vp), ("status", vp), ("sel_count", vp), ("sel_point", vp), ("sel_key", vp),
+                ("root_u1", vp)]
 
 
 class bnb_job(C.Structure):
@@ -97,7 +98,7 @@ EXPORTS = ["bnb_bound_tuples", "bnb_bound_tuples_ws", "bnb_bound_tuples_noalloc"
            "bnb_build_index_ws", "bnb_sample_and_solve", "bnb_sample_and_solve_ws", "bnb_status_string",
            "bnb_abi_version", "bnb_pack_surface", "bnb_pack_surface_bytes", "bnb_sample_and_solve_batched",
            "bnb_sample_and_solve_batched_ws", "bnb_bound_tuples_batched", "bnb_bound_tuples_batched_ws",
-           "bnb_implicit_irradiance"]
+           "bnb_implicit_irradiance", "bnb_stream_status", "bnb_gamma_for_target", "bnb_gamma_for_target_ws"]
 
 
 def lib():
@@ -129,6 +130,12 @@ def lib():
         L.bnb_implicit_irradiance.restype = i32
         L.bnb_implicit_irradiance.argtypes = [P(bnb_surface), P(bnb_receiver), P(bnb_emitters), P(bnb_cell_bounds),
                                               i64, i32, vp]
+        L.bnb_gamma_for_target.restype = i32
+        L.bnb_gamma_for_target.argtypes = [P(bnb_index), vp, vp, i64, C.c_double, vp, vp, sz, vp]
+        L.bnb_gamma_for_target_ws.restype = sz
+        L.bnb_gamma_for_target_ws.argtypes = [i32]
+        L.bnb_stream_status.restype = i32
+        L.bnb_stream_status.argtypes = [vp]
         L.bnb_status_string.restype = C.c_char_p
         L.bnb_status_string.argtypes = [i32]
         L.bnb_abi_version.restype = i32
@@ -203,6 +210,42 @@ def bnb_bound_tuples_batched_ws(*a):
 
 def bnb_implicit_irradiance(*a):
     return lib().bnb_implicit_irradiance(*a)
+
+
+def bnb_gamma_for_target(*a):
+    return lib().bnb_gamma_for_target(*a)
+
+
+def bnb_gamma_for_target_ws(*a):
+    return lib().bnb_gamma_for_target_ws(*a)
+
+
+def gamma_for_target(index: "Index", target: float, su: Optional[torch.Tensor] = None,
+                     sv: Optional[torch.Tensor] = None, stream=None, out: Optional[torch.Tensor] = None,
+                     ws: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """gamma whose expected |S| per shading point is `target` (Sec. 5.4), computed by
+    bnb_gamma_for_target on the device; returns a one-element device float tensor (not synchronized).
+    su, sv: the shading points that weigh the grid cells (None: every grid cell once)."""
+    dev = index.offsets.device
+    out = out if out is not None else torch.empty(1, dtype=torch.float32, device=dev)
+    need = bnb_gamma_for_target_ws(index.grid_res)
+    if ws is None or ws.numel() < need + 256:
+        ws = _ws(need, dev)
+    n = 0 if su is None else int(su.shape[0])
+    rc = bnb_gamma_for_target(C.byref(index.c), _ptr(su), _ptr(sv), n, float(target), _ptr(out), _align(ws),
+                              C.c_size_t(need), _stream(stream))
+    _check(rc, "bnb_gamma_for_target")
+    return out
+
+
+def bnb_stream_status(*a):
+    return lib().bnb_stream_status(*a)
+
+
+def stream_status(stream=None) -> int:
+    """Synchronizes the stream and returns (and clears) the device error word: BNB_OK, or the first
+    code a kernel raised since the last read."""
+    return int(bnb_stream_status(_stream(stream)))
 
 
 def bnb_status_string(s: int) -> str:
@@ -456,6 +499,15 @@ class SampleResult:
     counters: torch.Tensor
     status: torch.Tensor
     sel_count: Optional[torch.Tensor] = None
+    sel_point: Optional[torch.Tensor] = None  # with_roots: per selection, worklist order
+    sel_key: Optional[torch.Tensor] = None
+    root_u1: Optional[torch.Tensor] = None    # with_roots: (n, 2) float64, NaN where no root
+
+    def roots(self):
+        """(point, key, u, v) of the selections, as numpy arrays (with_roots only)."""
+        n = min(int(self.counters[1].item()), int(self.sel_point.shape[0]))
+        return (self.sel_point[:n].cpu().numpy(), self.sel_key[:n].cpu().numpy().view(np.uint64),
+                self.root_u1[:n].cpu().numpy())
 
 
 def sample_and_solve(ds: DeviceScene, index: Index, gamma: float, seed: int, newton_iters: int = 16,
@@ -463,10 +515,12 @@ def sample_and_solve(ds: DeviceScene, index: Index, gamma: float, seed: int, new
                      su: Optional[torch.Tensor] = None, sv: Optional[torch.Tensor] = None,
                      E_out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None, stream=None,
                      sync_check: bool = True, with_sel_count: bool = False, bins: bool = False,
-                     stoc_trials: int = 0) -> SampleResult:
+                     stoc_trials: int = 0, with_roots: bool = False) -> SampleResult:
     """Rendering pass.  bins: the bin-packed selection (one draw per group of Sec. 5.3) instead of
     Algorithm 1's draw per tuple; counters[3] then holds |B|.  stoc_trials > 0: stochastic Newton
-    starts with the reciprocal weighting (Sec. 6.1 "Stoc"), weights capped at stoc_trials."""
+    starts with the reciprocal weighting (Sec. 6.1 "Stoc"), weights capped at stoc_trials.
+    with_roots: also return, per selection, its point, key and the accepted root's barycentric
+    coordinates in T1 (NaN where the selection has no root)."""
     su = ds.t["su"] if su is None else su
     sv = ds.t["sv"] if sv is None else sv
     n_points = int(su.shape[0])
@@ -482,12 +536,17 @@ def sample_and_solve(ds: DeviceScene, index: Index, gamma: float, seed: int, new
             ws = _ws(need, ds.device)
         counters.zero_()
         status.zero_()
-        stats = bnb_sample_stats(_ptr(counters), _ptr(status), _ptr(sel))
+        sp = sk = ru = None
+        if with_roots:
+            sp = torch.empty(max(1, wl), dtype=torch.int64, device=ds.device)
+            sk = torch.empty(max(1, wl), dtype=torch.int64, device=ds.device)
+            ru = torch.empty((max(1, wl), 2), dtype=torch.float64, device=ds.device)
+        stats = bnb_sample_stats(_ptr(counters), _ptr(status), _ptr(sel), _ptr(sp), _ptr(sk), _ptr(ru))
         rc = bnb_sample_and_solve(C.byref(ds.s1), ds.s2_ref(), C.byref(ds.rec), C.byref(ds.em), C.byref(index.c),
                                   _ptr(su), _ptr(sv), n_points, C.byref(cfg), _ptr(E), C.byref(stats), _align(ws),
                                   C.c_size_t(need), _stream(stream))
         _check(rc, "bnb_sample_and_solve")
         if not sync_check or int(status.item()) == BNB_OK:
-            return SampleResult(E, counters, status, sel)
+            return SampleResult(E, counters, status, sel, sp, sk, ru)
         wl = int(counters[1].item()) + 1024
     raise BnbError("bnb_sample_and_solve: worklist capacity exceeded twice")

@@ -22,6 +22,9 @@ cudaError_t launch_bound_pairs(const bnb_surface* s1, const bnb_surface* s2, con
                                cudaStream_t st);
 cudaError_t launch_implicit(const bnb_surface* s1, const bnb_receiver* rec, const bnb_emitters* em,
                             const bnb_cell_bounds* cells, int64_t n, int32_t mode, cudaStream_t st);
+size_t gamma_ws_bytes(int32_t G);
+cudaError_t launch_gamma_for_target(const bnb_index* idx, const float* su, const float* sv, int64_t n_points,
+                                    double target, float* gamma_out, void* ws, cudaStream_t st);
 size_t batch_ws_bytes(const bnb_batch_cfg* c);
 size_t bound_batch_ws_bytes(int32_t max_jobs);
 cudaError_t launch_bound_batched(const bnb_bound_job* jobs, const int32_t* n_jobs, int32_t max_jobs, void* ws,
@@ -103,7 +106,7 @@ BoundWs carve_bound_ws(void* base, int64_t n_tris, int64_t qcap) {
 
 extern "C" {
 
-int32_t bnb_abi_version(void) { return 10; }
+int32_t bnb_abi_version(void) { return 11; }
 
 const char* bnb_status_string(int32_t s) {
   switch (s) {
@@ -295,6 +298,27 @@ int32_t bnb_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2, const
   if (ws_bytes < need || !ws || !aligned256(ws)) return BNB_ERR_INVALID;
   return launch_sample_and_solve(s1, s2, rec, em, index, su, sv, n_points, cfg, E_out, stats, ws,
                                  (cudaStream_t)stream) == cudaSuccess
+             ? BNB_OK
+             : BNB_ERR_CUDA;
+}
+
+size_t bnb_gamma_for_target_ws(int32_t grid_res) {
+  if (grid_res < 1 || grid_res > 4096) return 0;
+  return gamma_ws_bytes(grid_res);
+}
+
+int32_t bnb_gamma_for_target(const bnb_index* index, const float* su, const float* sv, int64_t n_points,
+                             double target, float* gamma_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!index || !gamma_out || !index->offsets) return BNB_ERR_INVALID;
+  if (index->grid_res < 1 || index->grid_res > 4096 || index->capacity < 0) return BNB_ERR_INVALID;
+  if (index->capacity > 0 && !index->etilde) return BNB_ERR_INVALID;
+  if (!(target >= 0.0) || !(target < 1e300)) return BNB_ERR_INVALID;  // NaN fails
+  if ((su == nullptr) != (sv == nullptr) || n_points < 0) return BNB_ERR_INVALID;
+  if (su != nullptr && n_points == 0) return BNB_ERR_INVALID;
+  const size_t need = gamma_ws_bytes(index->grid_res);
+  if (ws_bytes < need || !ws || !aligned256(ws)) return BNB_ERR_INVALID;
+  return launch_gamma_for_target(index, su, sv, n_points, target, gamma_out, ws, (cudaStream_t)stream) ==
+                 cudaSuccess
              ? BNB_OK
              : BNB_ERR_CUDA;
 }

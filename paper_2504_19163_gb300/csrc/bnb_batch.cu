@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kJobScanThreads) job_offsets_k(const bnb_job* 
     job_off[j + 1] = acc;
   }
   if (threadIdx.x == kJobScanThreads - 1 && (warp_sum[31] > max_points || n_req > max_jobs || n_req < 0))
-    atomicCAS(status, 0, BNB_ERR_CAPACITY);
+    raise_status(status, BNB_ERR_CAPACITY);
 }
 
 __device__ __forceinline__ int job_of(const int64_t* __restrict__ job_off, int n_jobs, int64_t p) {
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(512) sample_b_k(BatchParams B) {
             B.wl_key[out] = key;
             B.wl_p[out] = Pt;
           } else {
-            atomicCAS(B.status, 0, BNB_ERR_CAPACITY);
+            raise_status(B.status, BNB_ERR_CAPACITY);
           }
           ++out;
         }

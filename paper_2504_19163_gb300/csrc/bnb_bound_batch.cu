@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kJobThreads) bound_jobs_k(const bnb_bound_job*
       const int64_t c = cells_of(j);
       acc += c;
       if (c > jobs[j].capacity) {
-        atomicCAS(jobs[j].status, 0, BNB_ERR_CAPACITY);
+        raise_status(jobs[j].status, BNB_ERR_CAPACITY);
       } else if (c > 0) {
         atomicAdd((unsigned long long*)jobs[j].count, (unsigned long long)c);
       }

@@ -538,7 +538,7 @@ __device__ __forceinline__ void chord_remainder(T sl, T sh, T& a, T& b, T& dlo, 
 }
 
 // ------------------------------------------------------------------ records
-__device__ __forceinline__ void raise_status(int32_t* st, int32_t code) { atomicCAS(st, 0, code); }
+// raise_status (bnb_internal.cuh): the record's status word and the device error word
 
 template <typename T>
 __device__ __forceinline__ float f_dn(T x) {

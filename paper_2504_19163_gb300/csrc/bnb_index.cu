@@ -144,7 +144,7 @@ __device__ __forceinline__ void emit(const IndexParams& P, int64_t slot, int g, 
     P.pre_e[slot] = e;
     atomicAdd((unsigned long long*)(P.gcount + g), 1ull);
   } else {
-    atomicCAS(P.status, 0, BNB_ERR_CAPACITY);
+    raise_status(P.status, BNB_ERR_CAPACITY);
   }
 }
 
@@ -405,7 +405,7 @@ __global__ void compact_k(const int64_t* __restrict__ goff, const uint64_t* __re
   const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (g == 0 && lane == 0) {
     count[0] = offsets[n_cells];
-    if (offsets[n_cells] > capacity) atomicCAS(status, 0, BNB_ERR_CAPACITY);
+    if (offsets[n_cells] > capacity) raise_status(status, BNB_ERR_CAPACITY);
   }
   if (g >= n_cells) return;
   const int64_t src = goff[g], dst = offsets[g], n = offsets[g + 1] - dst;

@@ -56,4 +56,34 @@ cudaError_t launch_exclusive_scan(const int64_t* in, int64_t* out, int64_t n, vo
 
 __host__ __device__ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// ---- device error word (read and cleared by bnb_stream_status)
+// Each translation unit holds its own word (the library is built without relocatable device code,
+// so a __device__ variable cannot be shared between units).  A kernel that meets a condition only
+// the device can see records it in the status word of the call's output struct and in its unit's
+// word; the first code since the last read is kept.  Every unit registers, at load time, a host
+// function that takes its word on a stream (an atomic exchange with 0 in a one-thread kernel, then
+// a copy of the old value to the host), so a read never loses a code raised concurrently.
+static __device__ int32_t g_device_error;
+static __device__ int32_t g_device_error_taken;
+
+__device__ __forceinline__ void raise_status(int32_t* status, int32_t code) {
+  if (status) atomicCAS(status, 0, code);
+  atomicCAS(&g_device_error, 0, code);
+}
+
+static __global__ void take_device_error_k() { g_device_error_taken = atomicExch(&g_device_error, 0); }
+
+// Enqueues the exchange on `st` and copies the taken code to *host_out (a pageable copy: it returns
+// once the value is on the host).
+static cudaError_t take_device_error(cudaStream_t st, int32_t* host_out) {
+  take_device_error_k<<<1, 1, 0, st>>>();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyFromSymbolAsync(host_out, g_device_error_taken, sizeof(int32_t), 0, cudaMemcpyDeviceToHost, st);
+}
+
+typedef cudaError_t (*TakeErrorFn)(cudaStream_t, int32_t*);
+int register_error_word(TakeErrorFn f);  // bnb_status.cu
+static const int g_error_word_registered = register_error_word(&take_device_error);
+
 }  // namespace bnb

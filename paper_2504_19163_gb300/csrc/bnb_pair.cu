@@ -449,7 +449,7 @@ __global__ void pair_total_k(const int64_t* __restrict__ cand_off, int64_t n_bas
                              int64_t* __restrict__ count, int32_t* __restrict__ status) {
   const int64_t total = cand_off[n_base];
   *count = total;
-  if (total > capacity) atomicCAS(status, 0, BNB_ERR_CAPACITY);
+  if (total > capacity) raise_status(status, BNB_ERR_CAPACITY);
 }
 
 // ------------------------------------------------------------------ composite bound

@@ -537,7 +537,7 @@ __device__ __forceinline__ Hit2<T> eval_pair_value(const PairGeom& G, T u, T v) 
 // root known to ~1e-6 with a Jacobian accurate to ~1e-6, one step leaves ~1e-12).  Acceptance
 // tests in float64 at the polished root; E from the float32 derivatives there.
 __device__ __forceinline__ double polish64_pair(const PairGeom& G, float tuf, float tvf, int polish_iters, float tol,
-                                                float u, float v) {
+                                                float u, float v, double* ur = nullptr, double* vr = nullptr) {
   const Path2<float> Pf = eval_pair<float>(G, u, v);
   const double J00 = Pf.J00, J01 = Pf.J01, J10 = Pf.J10, J11 = Pf.J11;
   const double det = J00 * J11 - J01 * J10;
@@ -551,6 +551,8 @@ __device__ __forceinline__ double polish64_pair(const PairGeom& G, float tuf, fl
     vd -= (-J10 * fu + J00 * fv) / det;
     if (!isfinite(ud) || !isfinite(vd)) return -1.0;
   }
+  if (ur) *ur = ud;
+  if (vr) *vr = vd;
   const Hit2<double> H = eval_pair_value<double>(G, ud, vd);
   if (!H.ok) return -1.0;
   const double fu = H.uk - (double)tuf, fv = H.vk - (double)tvf;

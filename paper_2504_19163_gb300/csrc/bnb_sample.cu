@@ -47,6 +47,8 @@ struct SampleParams {
   int64_t* counters;   // device int64[4]
   int32_t* status;
   int32_t* sel_count;  // optional, per point
+  int64_t* sel_point;  // optional, per selection (worklist order)
+  uint64_t* sel_key;   // optional, per selection
   int32_t bins;        // 1: bin-packed selection (one draw per group), 0: one draw per tuple
 };
 
@@ -86,8 +88,10 @@ __global__ void __launch_bounds__(256) sample_k(SampleParams P) {
             P.wl_point[out] = p;
             P.wl_key[out] = k;
             P.wl_p[out] = Pt;
+            if (P.sel_point) P.sel_point[out] = p;
+            if (P.sel_key) P.sel_key[out] = k;
           } else {
-            atomicCAS(P.status, 0, BNB_ERR_CAPACITY);
+            raise_status(P.status, BNB_ERR_CAPACITY);
           }
           ++out;
         }
@@ -139,11 +143,23 @@ struct SolveParams {
   int32_t kind1, kind2;
   float* contrib;
   int64_t* counters;
+  double* root_u1;  // optional: (u, v) of the accepted root per selection, NaN when none
   // tuples handed from the float32 phase to the float64 polish
   int64_t* pl_count;
   int64_t* pl_idx;
   float *pl_u, *pl_v;
 };
+
+__device__ __forceinline__ void put_root(const SolveParams& S, int64_t i, double u, double v) {
+  if (S.root_u1) {
+    S.root_u1[2 * i] = u;
+    S.root_u1[2 * i + 1] = v;
+  }
+}
+
+__device__ __forceinline__ void put_no_root(const SolveParams& S, int64_t i) {
+  put_root(S, i, __longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
+}
 
 // float32 Newton phase over every selection: contributions of the tuples without an admissible
 // root are 0 now; the others go to the polish list with their float32 root.
@@ -163,7 +179,10 @@ __global__ void __launch_bounds__(256) solve32_k(SolveParams S) {
       need = newton32<REFRACT>(pf, nf, x0, __ldg(S.ei + e), S.rp0, S.re1, S.re2, S.su[pt], S.sv[pt], S.newton_iters,
                                S.eta, u, v);
     }
-    if (!need) S.contrib[i] = 0.0f;
+    if (!need) {
+      S.contrib[i] = 0.0f;
+      put_no_root(S, i);
+    }
     const int64_t j = warp_append(need, S.pl_count);
     if (need) {
       S.pl_idx[j] = i;
@@ -186,12 +205,16 @@ __global__ void __launch_bounds__(256) polish_k(SolveParams S) {
     load_tri_s(S.tri, t, pf, nf);
     const float x0[3] = {__ldg(S.ex + e), __ldg(S.ey + e), __ldg(S.ez + e)};
     const int64_t pt = S.wl_point[i];
+    double ur = 0.0, vr = 0.0;
     const double E = polish64<REFRACT>(pf, nf, x0, __ldg(S.ei + e), S.rp0, S.re1, S.re2, S.su[pt], S.sv[pt],
-                                       S.polish_iters, S.tol, S.eta, S.pl_u[j], S.pl_v[j]);
+                                       S.polish_iters, S.tol, S.eta, S.pl_u[j], S.pl_v[j], &ur, &vr);
     float c = 0.0f;
     if (E >= 0.0) {
       c = (float)(E / (double)S.wl_p[i]);
       ++roots;
+      put_root(S, i, ur, vr);
+    } else {
+      put_no_root(S, i);
     }
     S.contrib[i] = c;
   }
@@ -238,7 +261,12 @@ __global__ void __launch_bounds__(256) solve_stoc_k(SolveParams S) {
         }
         c = (float)(E * (double)nw / (double)S.wl_p[i]);
         ++roots;
+        put_root(S, i, ur, vr);
+      } else {
+        put_no_root(S, i);
       }
+    } else {
+      put_no_root(S, i);
     }
     S.contrib[i] = c;
   }
@@ -280,7 +308,10 @@ __global__ void __launch_bounds__(256) solve32_pair_k(SolveParams S) {
       const int64_t pt = S.wl_point[i];
       need = newton32_pair(G, S.su[pt], S.sv[pt], S.newton_iters, u, v);
     }
-    if (!need) S.contrib[i] = 0.0f;
+    if (!need) {
+      S.contrib[i] = 0.0f;
+      put_no_root(S, i);
+    }
     const int64_t j = warp_append(need, S.pl_count);
     if (need) {
       S.pl_idx[j] = i;
@@ -298,11 +329,15 @@ __global__ void __launch_bounds__(256) polish_pair_k(SolveParams S) {
     PairGeom G;
     pair_geom(S, S.wl_key[i], G);  // listed by solve32_pair_k: the key is valid
     const int64_t pt = S.wl_point[i];
-    const double E = polish64_pair(G, S.su[pt], S.sv[pt], S.polish_iters, S.tol, S.pl_u[j], S.pl_v[j]);
+    double ur = 0.0, vr = 0.0;
+    const double E = polish64_pair(G, S.su[pt], S.sv[pt], S.polish_iters, S.tol, S.pl_u[j], S.pl_v[j], &ur, &vr);
     float c = 0.0f;
     if (E >= 0.0) {
       c = (float)(E / (double)S.wl_p[i]);
       ++roots;
+      put_root(S, i, ur, vr);
+    } else {
+      put_no_root(S, i);
     }
     S.contrib[i] = c;
   }
@@ -399,6 +434,8 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2
   P.counters = stats->counters;
   P.status = stats->status;
   P.sel_count = stats->sel_count;
+  P.sel_point = stats->sel_point;
+  P.sel_key = stats->sel_key;
   P.bins = cfg->bins;
   const int64_t pblocks = std::min<int64_t>((n_points + 255) / 256, (int64_t)sms * 32);
   sample_k<false><<<(unsigned)pblocks, 256, 0, st>>>(P);
@@ -429,6 +466,7 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2
   S.tol = cfg->tol;
   S.contrib = w.contrib;
   S.counters = stats->counters;
+  S.root_u1 = stats->root_u1;
   S.pl_count = w.pl_count;
   S.pl_idx = w.pl_idx;
   S.pl_u = w.pl_u;

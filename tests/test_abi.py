@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(bnb):
 def test_status_strings_and_version(bnb):
     assert bnb.bnb_status_string(0) == "ok"
     assert "capacity" in bnb.bnb_status_string(-2)
-    assert bnb.lib().bnb_abi_version() == 10
+    assert bnb.lib().bnb_abi_version() == 11
 
 
 def test_workspace_queries_are_host_only(bnb):
@@ -244,3 +244,25 @@ def test_implicit_irradiance_arguments(bnb):
     cfg = bnb.bnb_bound_cfg(1, 0, 2, 0)
     assert bnb.bnb_bound_tuples(C.byref(s), None, C.byref(rec), C.byref(em), C.byref(cfg), C.byref(out), None, 0,
                                 None) == bnb.BNB_ERR_UNSUPPORTED
+
+
+def test_gamma_for_target_arguments(bnb):
+    """Argument checks of the gamma <-> E|S| call (Sec. 5.4), all before any launch."""
+    assert bnb.bnb_gamma_for_target_ws(512) >= 512 * 512 * 4
+    assert bnb.bnb_gamma_for_target_ws(0) == 0
+    idx = bnb.bnb_index()
+    idx.grid_res, idx.capacity, idx.count, idx.status, idx.offsets, idx.key, idx.etilde = 512, 16, 4096, 4096, 4096, \
+        4096, 4096
+    ws = bnb.bnb_gamma_for_target_ws(512)
+    g = C.c_void_p(4096)
+    call = bnb.bnb_gamma_for_target
+    assert call(None, None, None, 0, 4.0, g, 4096, ws, None) == bnb.BNB_ERR_INVALID            # no index
+    assert call(C.byref(idx), None, None, 0, 4.0, None, 4096, ws, None) == bnb.BNB_ERR_INVALID  # no output
+    assert call(C.byref(idx), None, None, 0, float("nan"), g, 4096, ws, None) == bnb.BNB_ERR_INVALID
+    assert call(C.byref(idx), None, None, 0, -1.0, g, 4096, ws, None) == bnb.BNB_ERR_INVALID
+    assert call(C.byref(idx), 4096, None, 10, 4.0, g, 4096, ws, None) == bnb.BNB_ERR_INVALID    # su without sv
+    assert call(C.byref(idx), 4096, 4096, 0, 4.0, g, 4096, ws, None) == bnb.BNB_ERR_INVALID     # no points
+    assert call(C.byref(idx), None, None, 0, 4.0, g, 4096, ws - 1, None) == bnb.BNB_ERR_INVALID  # small workspace
+    assert call(C.byref(idx), None, None, 0, 4.0, g, 4100, ws, None) == bnb.BNB_ERR_INVALID     # misaligned
+    idx.grid_res = 0
+    assert call(C.byref(idx), None, None, 0, 4.0, g, 4096, ws, None) == bnb.BNB_ERR_INVALID
