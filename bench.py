@@ -82,6 +82,35 @@ def pair_fma_per_record() -> int:
 PAIR_FLOP_PER_RECORD = 2 * pair_fma_per_record()
 
 
+def refract_fma_per_cell():
+    """(position, irradiance) FMAs of the value chain of one single-refraction cell, in the kernel's
+    order (products as convolutions: nc(M)*nc(N) FMAs; a pair p0 + W p1 with W^2 -> beta costs the
+    four cross products plus the beta product), excluding error tracking and ratio logic.  Every
+    cell not in total internal reflection pays the position part; live cells pay the irradiance
+    part (the derivative-aware degree-17 bound over four faces)."""
+    mac = lambda m, n: nc(m) * nc(n)
+
+    def wp(m, n):
+        return mac(m, n) + mac(m - 2, n - 2) + mac(m + n - 4, 4) + mac(m, n - 2) + mac(m - 2, n)
+    pos = 3 * 3 * mac(1, 1) + 2 * mac(2, 2) + 2 * nc(4)             # n.n, d0.n, d0.d0, beta
+    pos += 3 * (2 * mac(2, 1) + nc(3))                              # eta' ((n.n) d0 - (d0.n) n)
+    pos += 3 * 4 * nc(1)                                            # receiver h_u, h_v
+    pos += 2 * (nc(4) + 3 * (mac(4, 1) + nc(5) + 2 * mac(5, 1)))    # both faces: W_j, d~, Q, A, B
+    pos += 3 * nc(1)                                                # forward cull
+    per_edge = 3 * 4 * nc(1) + 2 * mac(1, 2) + nc(3) + mac(2, 1) + nc(3)
+    per_edge += 3 * (2 * mac(1, 1) + 2 * mac(2, 0) + nc(2) + mac(3, 1) + nc(4))  # 2W-scaled d d~
+    irr = 2 * per_edge
+    irr += 3 * (nc(3) + nc(1) + 2 * (mac(3, 1) + mac(1, 1)))        # Q, A, B as pairs
+    irr += 2 * 3 * (nc(4) + nc(2) + 2 * (mac(4, 1) + mac(2, 1)) + nc(1) + 2 * nc(1) + 2 * mac(1, 4) + 2 * nc(3))
+    irr += 2 * wp(5, 5) + wp(3, 10) + 2 * wp(5, 4) + wp(4, 9) + 2 * wp(4, 5) + wp(4, 9)  # M'
+    irr += wp(3, 3) + wp(6, 3) + 2 * nc(2)                          # Q^3, s^-3/2 chord faces
+    irr += 2 * (nc(4) + mac(4, 11) + mac(4, 7) + mac(11, 4) + 2 * mac(15, 2))  # W faces, N, den
+    return pos, irr
+
+
+REFRACT_FMA_POS, REFRACT_FMA_IRR = refract_fma_per_cell()
+
+
 # Algorithmic bytes of the HBM-bound stages: the index reads a live cell's box, E_hi, keys and flags
 # (36 B; 4 B of flags for the others) and writes 12 B (key, E~) per (grid cell, tuple) entry plus the
 # offsets; the sampling pass reads 12 B per listed entry and writes 16 B per selection (point, key,
@@ -200,7 +229,9 @@ def run_reference(args):
     n_threads = os.cpu_count() or 1
     n_cells_full = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
     n_points_full = sc.su.shape[0]
-    cells, points = 64 * 256, 256
+    per = 4 ** sc.depth
+    cells = -(-n_cells_full // 100 // per) * per  # >= 1% of the cells per step, whole tuples
+    points = 1024
     for i in range(args.warmup):
         oracle_step_sample(sc, cells, points, 100 + i, n_threads)
     acc = np.zeros(3)
@@ -211,7 +242,11 @@ def run_reference(args):
     t_cell, t_draw, t_solve = acc / args.steps
     step_s = oracle_step_seconds(sc, t_cell, t_draw, t_solve)
     value = n_cells_full / step_s
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+    line = {"impl": "reference", "extrapolated": True,
+            "extrapolation": f"each step times the oracle on {cells} seeded contiguous base cells ({cells / n_cells_full:.2%} "
+                             f"of the workload) and on the draws and solves of {points} points; the step time is "
+                             f"extrapolated to all {n_cells_full} cells and {n_points_full} points",
+            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD},
@@ -351,6 +386,9 @@ def run_gpu(args):
                  "stoc_trials": 64, "per_point": {"S": cs_n[1] / n_points, "roots": cs_n[2] / n_points},
                  "status_ok": int(rs.status.item()) == 0}
 
+    # ---- measured FP32 FMA throughput (the ALU roofline's measured denominator)
+    peak_info = fp32_peak_summary(dev, local)
+
     # ---- roofline of the dominant kernel (bound pass)
     bound_ms = float(stage[:, 0].mean())
     props = torch.cuda.get_device_properties(dev)
@@ -398,15 +436,26 @@ def run_gpu(args):
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                          "flop_per_cell": BOUND_FLOP_PER_CELL,
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                                       f"(max SM clock of MEASURED_PEAKS.json)"},
+                                       f"(max SM clock of MEASURED_PEAKS.json)",
+                         "peak_measured": peak_info["peak"], "frac_of_measured": achieved / peak_info["peak"],
+                         "peak_measured_basis": "bnb_ffma_probe: FFMA and paired FFMA2 chains over 8 x 256-thread "
+                                                "blocks per SM, ~1 s each (the larger; see fp32_peak)"},
+            "fp32_peak": peak_info,
             "bins": bins_line,
             "stoc": stoc_line,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": launches_per_step(n_points, sc.grid_res) * args.steps,
             "clocks": clk.summary()}
+    if not args.no_cpu_baseline and rank == 0 and world == 1 and not args.emitters:
+        try:  # part of the CPU-baseline leg: the oracle runs in a spawned child
+            cb = None
+            torch.cuda.empty_cache()
+            line["accuracy"] = accuracy_summary(bnb, ds, sc, idx, gamma, dev)
+        except Exception as ex:  # reported in the line; the bound benchmark above stands
+            line["accuracy"] = {"error": f"{type(ex).__name__}: {ex}"}
     if args.serving_requests > 0 and rank == 0 and world == 1 and not args.emitters:
-        del cb, idx, cb_ws, ix_ws, sm_ws, flush
+        cb = idx = cb_ws = ix_ws = sm_ws = flush = None
         torch.cuda.empty_cache()
         line["serving"] = serving_summary(args.serving_requests, dev)
     if args.adaptive_steps > 0 and rank == 0 and world == 1 and not args.emitters:
@@ -424,6 +473,16 @@ def run_gpu(args):
             line["pairs"] = pairs_summary(dev, args.pairs_steps, not args.no_cpu_baseline and not args.emitters)
         except Exception as ex:  # reported in the line; the bound benchmark above stands
             line["pairs"] = {"error": f"{type(ex).__name__}: {ex}"}
+    if args.refraction_steps > 0 and rank == 0 and world == 1 and not args.emitters:
+        try:
+            line["refraction"] = refraction_summary(dev, args.refraction_steps, peak, peak_info["peak"])
+        except Exception as ex:  # reported in the line; the bound benchmark above stands
+            line["refraction"] = {"error": f"{type(ex).__name__}: {ex}"}
+    if args.rough_steps > 0 and rank == 0 and world == 1 and not args.emitters:
+        try:
+            line["rough"] = rough_summary(dev, args.rough_steps)
+        except Exception as ex:  # reported in the line; the bound benchmark above stands
+            line["rough"] = {"error": f"{type(ex).__name__}: {ex}"}
     if not args.no_cpu_baseline and rank == 0 and world == 1 and not args.emitters:
         line["cpu_baseline"] = cpu_baseline(counters[0] / n_points, counters[1] / n_points)
     if rank == 0:
@@ -581,6 +640,133 @@ def pairs_summary(dev, steps: int, oracle_too: bool) -> dict:
 ADAPT = dict(depth=0, adapt_depth=6, sigma=1e-6, alpha=2.0)
 
 
+def fp32_peak_summary(dev, gpu_index: int) -> dict:
+    """Measured FP32 FMA throughput (bnb_ffma_probe, scalar FFMA and paired FFMA2 over a resident
+    grid, ~1 s each, CUDA events) with the SM clocks sampled while it ran."""
+    from paper_2504_19163_gb300 import bnb
+    with ClockSampler(gpu_index) as clk:
+        r = bnb.fp32_fma_peak(dev, seconds=1.0)
+    r["clocks"] = clk.summary()
+    return r
+
+
+def refraction_summary(dev, steps: int, peak_tflops: float, peak_measured) -> dict:
+    """The refraction workload (water420: 420^2 Gerstner water, 352,800 triangles, eta' = 1/1.33, 4
+    point lights, pool floor 1 below, 1920x1080 shading points, depth 3: 90,316,800 cells per step):
+    bound pass with irradiance, index, gamma for E|S| = 4 (library bisection), rendering pass; each
+    stage timed with CUDA events over `steps` steps after 3 warm-up steps, L2 flushed between steps."""
+    import torch
+    from paper_2504_19163_gb300 import bnb
+    from paper_2504_19163_gb300 import scenes as S
+    sc = S.config("water420")
+    ds = bnb.DeviceScene(sc, dev)
+    stream = torch.cuda.current_stream(dev)
+    cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False)
+    idx = bnb.build_index(cb, grid_res=sc.grid_res)
+    gamma = calibrate_gamma(bnb, ds, idx, target=4.0)
+    res = bnb.sample_and_solve(ds, idx, gamma, 1)
+    torch.cuda.synchronize()
+    n_points = ds.n_points
+    n_cells = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
+    wl_cap = int(res.counters[1].item()) * 2 + 4096
+    cb_ws = bnb._ws(bnb.bnb_bound_tuples_ws(bnb.C.byref(ds.s1), None, bnb.C.byref(ds.em),
+                                            bnb.C.byref(bnb.bnb_bound_cfg(sc.depth, 4, 1, 0))), dev)
+    pre_cap = int(idx.count[1].item()) + int(idx.count[1].item()) // 4 + 4096
+    ix_ws = bnb._ws(bnb.bnb_build_index_ws(bnb.C.byref(cb.c), sc.grid_res, pre_cap), dev)
+    idx = bnb.Index(sc.grid_res, pre_cap, dev)
+    sm_ws = bnb._ws(bnb.bnb_sample_and_solve_ws(bnb.C.byref(ds.s1), None, n_points, wl_cap), dev)
+    E_out = torch.empty(n_points, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(seed, ev):
+        ev[0].record(stream)
+        bnb.bound_tuples(ds, sc.depth, out=cb, ws=cb_ws, sync_check=False)
+        ev[1].record(stream)
+        bnb.build_index(cb, grid_res=sc.grid_res, pre_capacity=pre_cap, capacity=pre_cap, out=idx, ws=ix_ws,
+                        sync_check=False)
+        ev[2].record(stream)
+        r = bnb.sample_and_solve(ds, idx, gamma, seed, worklist_capacity=wl_cap, E_out=E_out, ws=sm_ws,
+                                 sync_check=False)
+        ev[3].record(stream)
+        return r
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(3 + steps)]
+    for i in range(3 + steps):
+        if i == 3:
+            torch.cuda.nvtx.range_push("refraction")
+        flush.zero_()
+        r = step(i, evs[i])
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    st = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])] for e in evs[3:]])
+    ms = st.mean(axis=0)
+    ok = int(cb.status.item()) == 0 and int(idx.status.item()) == 0 and int(r.status.item()) == 0
+    n_rec = cb.n_records()
+    fl = cb.flags[:n_rec]
+    n_tir = int(((fl & 128) != 0).sum().item())
+    live = (fl & 1) != 0
+    n_live = int(live.sum().item())
+    n_live_finite = int((live & torch.isfinite(cb.e_hi[:n_rec])).sum().item())
+    fma = REFRACT_FMA_POS * (n_rec - n_tir) + REFRACT_FMA_IRR * n_live
+    achieved = 2.0 * fma / (ms[0] / 1e3) / 1e12
+    c = r.counters.cpu().numpy()
+    out = {"workload": "water420: 420^2 Gerstner water (352,800 tris, 16 waves), eta' 1/1.33, 4 point lights at "
+                       "(+-0.5,+-0.5,2), pool floor z=-1, 1920x1080 shading points, depth 3 (90,316,800 cells/step), "
+                       "grid 512, FP32 with outward rounding",
+           "status_ok": ok, "steps": steps, "cells_per_step": n_cells, "records": n_rec, "live_records": n_live,
+           "live_finite_e_hi": n_live_finite, "tir_records": n_tir, "gamma": gamma,
+           "stage_ms": {"bound": float(ms[0]), "index": float(ms[1]), "sample_solve": float(ms[2])},
+           "ms_per_step": float(ms.sum()), "cells_per_s": n_cells / (float(ms.sum()) / 1e3),
+           "bound_cells_per_s": n_cells / (ms[0] / 1e3), "shading_samples_per_s": n_points / (float(ms.sum()) / 1e3),
+           "per_point": {"U": c[0] / n_points, "S": c[1] / n_points, "roots": c[2] / n_points},
+           "roofline": {"bound": "alu", "kernel": "bound_base_k<float, refraction> (+ its split levels)",
+                        "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                        "fma_position_per_cell": REFRACT_FMA_POS, "fma_irradiance_per_live_cell": REFRACT_FMA_IRR,
+                        "flop_per_launch": 2.0 * fma}}
+    if peak_measured:
+        out["roofline"]["peak_measured"] = peak_measured
+        out["roofline"]["frac_of_measured"] = achieved / peak_measured
+    del cb, idx, cb_ws, ix_ws, sm_ws, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def rough_summary(dev, steps: int) -> dict:
+    """The bound pass alone on mirror256_rough, the literal per-vertex reading of the noise
+    (independent U[-0.01, 0.01] per vertex, slopes up to ~2.5; the index of this reading would hold
+    ~1e11 entries, so only the bound pass is timed), beside the smooth-noise benchmark mirror."""
+    import torch
+    from paper_2504_19163_gb300 import bnb
+    from paper_2504_19163_gb300 import scenes as S
+    sc = S.config("mirror256_rough")
+    ds = bnb.DeviceScene(sc, dev)
+    stream = torch.cuda.current_stream(dev)
+    cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False)
+    torch.cuda.synchronize()
+    cb_ws = bnb._ws(bnb.bnb_bound_tuples_ws(bnb.C.byref(ds.s1), None, bnb.C.byref(ds.em),
+                                            bnb.C.byref(bnb.bnb_bound_cfg(sc.depth, 4, 1, 0))), dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3 + steps)]
+    for i in range(3 + steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        bnb.bound_tuples(ds, sc.depth, out=cb, ws=cb_ws, sync_check=False)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs[3:]]))
+    n_cells = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
+    n_rec = cb.n_records()
+    fl = cb.flags[:n_rec]
+    out = {"workload": "mirror256_rough: as mirror256 but noise U[-0.01,0.01] independent per vertex; bound pass only",
+           "status_ok": int(cb.status.item()) == 0, "steps": steps, "bound_ms": ms,
+           "bound_cells_per_s": n_cells / (ms / 1e3), "records": n_rec,
+           "split_records": int(((fl & 2) != 0).sum().item()), "fold_records": int(((fl & 16) != 0).sum().item()),
+           "live_records": int(((fl & 1) != 0).sum().item())}
+    del cb, cb_ws, flush
+    torch.cuda.empty_cache()
+    return out
+
+
 def implicit_fma_per_record() -> int:
     """FMAs of one record of the implicit-differentiation pass: a scaled-Bernstein product of forms
     with m and n coefficients is m * n FMAs, an elevation a product with the constant 1, a scaling
@@ -713,6 +899,229 @@ def adaptive_summary(dev, steps: int) -> dict:
     return out
 
 
+# ----------------------------------------------------------------------------- accuracy vs the oracle
+# Part of the CPU-baseline leg (the oracle runs in a spawned child process; skipped with
+# --no-cpu-baseline): the error of the timed path's results against the FP64 oracle on seeded
+# samples of the benchmark workload.
+ACC_CELLS = 100_000      # seeded base cells whose records are compared
+ACC_CLUSTERS = 64        # seeded clusters of 4 x 4 adjacent grid cells: 1024 grid cells, ~4096 points
+ACC_SEED = 77
+
+
+def accuracy_gpu_side(bnb, ds, sc, idx, dev) -> dict:
+    """GPU records of ACC_CELLS seeded base cells (plus the children of those that split), from a
+    bound pass that also writes e_hi_min; the shading points of ACC_CLUSTERS x 16 seeded grid cells
+    and every cell of every tuple the GPU index lists there (the oracle's index is exact on those
+    grid cells: the GPU's boxes contain the oracle's, so any tuple the oracle lists there is one of
+    them)."""
+    import torch
+    cbx = bnb.bound_tuples(ds, sc.depth, with_e_hi_min=True, with_e_lo=False)
+    n_base = cbx.c.n_base
+    rng = np.random.default_rng(11)
+    work = np.sort(rng.choice(n_base, ACC_CELLS, replace=False))
+    fields = ("u_lo", "u_hi", "v_lo", "v_hi", "e_hi", "e_hi_min", "emitter", "tri0", "cell", "flags")
+    wt = torch.as_tensor(work, device=dev)
+    g = {k: getattr(cbx, k)[wt].cpu().numpy() for k in fields}
+    n_rec = cbx.n_records()
+    if n_rec > n_base:  # children of the sampled cells that split
+        ch = {k: getattr(cbx, k)[n_base:n_rec].cpu().numpy() for k in fields}
+        cd = (ch["flags"].view(np.uint32).astype(np.int64) >> 24) & 63
+        parent = ch["cell"].view(np.uint32).astype(np.int64) >> (2 * (cd - sc.depth))
+        sk = set(zip(g["emitter"].tolist(), g["tri0"].tolist(), g["cell"].view(np.uint32).tolist()))
+        keep = np.array([(int(a), int(b), int(c)) in sk for a, b, c in zip(ch["emitter"], ch["tri0"], parent)],
+                        dtype=bool)
+        for k in fields:
+            g[k] = np.concatenate([g[k], ch[k][keep]])
+    g["cell"] = g["cell"].view(np.uint32)
+    g["flags"] = g["flags"].view(np.uint32)
+    del cbx
+    torch.cuda.empty_cache()
+    G = sc.grid_res
+    rng = np.random.default_rng(12)
+    cx, cy = rng.integers(0, G - 4, ACC_CLUSTERS), rng.integers(0, G - 4, ACC_CLUSTERS)
+    cells = np.unique(np.array([(y + dy) * G + (x + dx) for x, y in zip(cx, cy) for dy in range(4) for dx in range(4)]))
+    gi = np.clip(np.floor(np.clip(sc.su, 0, 1).astype(np.float32) * np.float32(G)), 0, G - 1).astype(np.int64)
+    gj = np.clip(np.floor(np.clip(sc.sv, 0, 1).astype(np.float32) * np.float32(G)), 0, G - 1).astype(np.int64)
+    pts = np.nonzero(np.isin(gj * G + gi, cells))[0]
+    off = idx.offsets.cpu().numpy()
+    n_ent = int(idx.count[0].item())
+    segs = [idx.key[off[c]:min(off[c + 1], n_ent)] for c in cells]
+    keys = np.unique(torch.cat(segs).cpu().numpy().view(np.uint64)) if segs else np.zeros(0, np.uint64)
+    e = (keys >> np.uint64(48)).astype(np.int64)
+    t = (keys & np.uint64(0xFFFFFF)).astype(np.int64)
+    per = 4 ** sc.depth
+    tuple_work = (((e * sc.s1.n_tris + t) * per)[:, None] + np.arange(per)[None, :]).ravel()
+    return {"records": g, "work": work, "points": pts, "tuple_work": tuple_work, "n_tuples": int(keys.shape[0])}
+
+
+def _compare_records(g: dict, o) -> dict:
+    """GPU records against the oracle's, matched by (emitter, triangle, cell, depth): flags (outside
+    the ambiguity bands), box containment and widening, E_hi never below the oracle's, the relative
+    excess of E_hi (all finite cells, and the well-conditioned ones: min |b(M)| / max |b(M)| >= 1e-3),
+    and the certified enclosure [e_hi_min, e_hi] holding the oracle's float64 bound."""
+    gd = (g["flags"].astype(np.int64) >> 24) & 63
+    od = (o["flags"].astype(np.int64) >> 24) & 63
+    gk = {(int(a), int(b), int(c), int(d)): i for i, (a, b, c, d) in
+          enumerate(zip(g["emitter"], g["tri0"], g["cell"], gd))}
+    rep = dict(oracle_records=int(len(o)), missing=0, flag_mismatch=0, flag_ambiguous=0, live=0,
+               containment_violations=0, e_hi_below_oracle=0, enclosure_violations=0, e_finite=0)
+    widen, rel, rel_wc = [], [], []
+    for j in range(len(o)):
+        i = gk.get((int(o["emitter"][j]), int(o["tri0"][j]), int(o["cell"][j]), int(od[j])))
+        if i is None:
+            rep["missing"] += 1
+            continue
+        gf, of = int(g["flags"][i]) & 0xBF, int(o["flags"][j]) & 0xFF
+        if gf != of:
+            amb = o["q_cond"][j] < 1e-10 or ((gf & 16) and not (of & 16) and o["m_cond"][j] < 1e-3
+                                             and (gf & ~16) == (of & ~16))
+            rep["flag_ambiguous" if amb else "flag_mismatch"] += 1
+            continue
+        if not (of & 1):
+            continue
+        rep["live"] += 1
+        for a in ("u", "v"):
+            gl, gh = float(g[a + "_lo"][i]), float(g[a + "_hi"][i])
+            ol, oh = float(o[a + "_lo"][j]), float(o[a + "_hi"][j])
+            if gl > ol + 1e-12 or gh < oh - 1e-12:
+                rep["containment_violations"] += 1
+            widen.append(max(ol - gl, gh - oh))
+        oe, ge, gm = float(o["e_hi"][j]), float(g["e_hi"][i]), float(g["e_hi_min"][i])
+        if np.isfinite(oe) and np.isfinite(ge):
+            rep["e_finite"] += 1
+            r = (ge - oe) / oe
+            rel.append(r)
+            if o["m_cond"][j] >= 1e-3:
+                rel_wc.append(r)
+            if ge < oe * (1 - 1e-6):
+                rep["e_hi_below_oracle"] += 1
+            if oe < gm * (1 - 1e-6) or oe > ge * (1 + 1e-6):
+                rep["enclosure_violations"] += 1
+        elif np.isfinite(ge):
+            rep["e_hi_below_oracle"] += 1
+    w = np.array(widen or [0.0])
+    r = np.array(rel or [0.0])
+    rw = np.array(rel_wc or [0.0])
+    rep.update(box_widen_max=float(w.max()), box_widen_p99=float(np.percentile(w, 99)),
+               e_hi_rel_excess_median=float(np.median(r)), e_hi_rel_excess_p99=float(np.percentile(r, 99)),
+               e_hi_rel_excess_max=float(r.max()), well_conditioned_cells=len(rel_wc),
+               well_conditioned_e_hi_rel_excess_max=float(rw.max()),
+               well_conditioned_e_hi_rel_excess_p99=float(np.percentile(rw, 99)))
+    return rep
+
+
+def _accuracy_worker(name, gside, gamma, seed):
+    sys.path.insert(0, ROOT)
+    import copy
+
+    import oracle
+    from paper_2504_19163_gb300 import scenes as S
+    oracle.build()
+    sc = S.config(name)
+    n_threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    o = oracle.bound(sc, work=gside["work"], n_threads=n_threads)
+    cells = _compare_records(gside["records"], o)
+    o2 = oracle.bound(sc, work=gside["tuple_work"], n_threads=n_threads)
+    f = oracle.records_to_f32(o2)
+    off, key, et = oracle.index(f["u_lo"], f["u_hi"], f["v_lo"], f["v_hi"], f["e_hi"], f["emitter"], f["tri0"],
+                                f["tri1"], f["flags"], sc.grid_res)
+    pts = gside["points"]
+    sub = copy.copy(sc)
+    sub.su, sub.sv = sc.su[pts], sc.sv[pts]
+    out = {"cells": cells, "off": off, "key": key, "et": et, "oracle_cells": int(len(o) + len(o2))}
+    for tag, gm in (("sampled", gamma), ("all", float("inf"))):
+        wp, wk, wP, n_u = oracle.sample(off, key, et, sc.grid_res, sub.su, sub.sv, gm, seed)
+        contrib, ru, rv, st = oracle.solve(sub, wp, wk, wP, n_threads=n_threads)
+        out[tag] = {"wp": wp, "wk": wk, "ru": ru, "rv": rv, "st": st,
+                    "E": oracle.accumulate(pts.shape[0], wp, contrib), "n_u": n_u}
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
+def _x1(s1, tri, u, v):
+    P = lambda i: np.stack([s1.px[i], s1.py[i], s1.pz[i]], axis=-1).astype(np.float64)
+    p0 = P(s1.i0[tri])
+    return p0 + u[:, None] * (P(s1.i1[tri]) - p0) + v[:, None] * (P(s1.i2[tri]) - p0)
+
+
+def _point_errors(E_g, E_o) -> dict:
+    E_g = np.asarray(E_g, np.float64)
+    pos = E_o > 0
+    rel = np.abs(E_g[pos] - E_o[pos]) / E_o[pos]
+    return {"points": int(E_o.shape[0]), "lit_points": int(pos.sum()),
+            "E_rel_max": float(rel.max(initial=0.0)), "E_rel_p99": float(np.percentile(rel, 99)) if rel.size else 0.0,
+            "points_above_1e-4": int(np.sum(rel > 1e-4) + np.sum(E_g[~pos] != 0))}
+
+
+def _root_errors(s1, gp, gk, guv, o) -> dict:
+    gmap = {(int(p), int(k)): i for i, (p, k) in enumerate(zip(gp, gk))}
+    oi, gi, one_side, missing = [], [], 0, 0
+    for j, (p, k) in enumerate(zip(o["wp"], o["wk"])):
+        i = gmap.pop((int(p), int(k)), None)
+        if i is None:
+            missing += 1
+            continue
+        gr, orr = bool(np.isfinite(guv[i, 0])), bool(o["st"][j])
+        if gr and orr:
+            oi.append(j)
+            gi.append(i)
+        elif gr != orr:
+            one_side += 1
+    extra_roots = int(sum(np.isfinite(guv[i, 0]) for i in gmap.values()))
+    d = 0.0
+    if oi:
+        oi, gi = np.array(oi), np.array(gi)
+        tri = (o["wk"][oi] & np.uint64(0xFFFFFF)).astype(np.int64)
+        d = float(np.max(np.linalg.norm(_x1(s1, tri, guv[gi, 0], guv[gi, 1]) -
+                                        _x1(s1, tri, o["ru"][oi], o["rv"][oi]), axis=1)))
+    return {"roots": int(len(oi)), "root_dist_max": d, "root_on_one_side": one_side,
+            "oracle_selections_missing": missing, "gpu_only_selections": len(gmap), "gpu_only_roots": extra_roots}
+
+
+def accuracy_summary(bnb, ds, sc, idx, gamma, dev) -> dict:
+    """Error of the timed path against the FP64 oracle (Sec. 8 parity, measured on the benchmark
+    workload): (1) records of 100,000 seeded base cells; (2) ~4096 seeded points: the rendering pass
+    on the oracle's index with the benchmark's gamma (selections, per-point estimates, roots); (3) the
+    same points with every listed tuple selected (gamma = inf), the GPU's own index against the
+    oracle's: the whole path, deterministic."""
+    import multiprocessing as mp
+
+    import torch
+    gside = accuracy_gpu_side(bnb, ds, sc, idx, dev)
+    with mp.get_context("spawn").Pool(1) as pool:
+        o = pool.apply(_accuracy_worker, (sc.name, gside, gamma, ACC_SEED))
+    pts = gside["points"]
+    su = ds.t["su"][torch.as_tensor(pts, device=dev)]
+    sv = ds.t["sv"][torch.as_tensor(pts, device=dev)]
+    G = sc.grid_res
+    io = bnb.Index(G, max(1, o["key"].shape[0]), dev)
+    io.offsets.copy_(torch.as_tensor(o["off"]))
+    if o["key"].shape[0]:
+        io.key[: o["key"].shape[0]] = torch.as_tensor(o["key"].view(np.int64))
+        io.etilde[: o["key"].shape[0]] = torch.as_tensor(o["et"])
+    io.count[0] = o["key"].shape[0]
+    r = bnb.sample_and_solve(ds, io, gamma, ACC_SEED, su=su, sv=sv, with_roots=True)
+    gp, gk, guv = r.roots()
+    sampled = {"gamma": gamma, "seed": ACC_SEED,
+               "selections_equal": bool(np.array_equal(gp, o["sampled"]["wp"]) and
+                                        np.array_equal(gk, o["sampled"]["wk"])),
+               "selections": int(gp.shape[0])}
+    sampled.update(_point_errors(r.E.cpu().numpy(), o["sampled"]["E"]))
+    sampled.update(_root_errors(sc.s1, gp, gk, guv, o["sampled"]))
+    r2 = bnb.sample_and_solve(ds, idx, float("inf"), ACC_SEED, su=su, sv=sv, with_roots=True)
+    gp2, gk2, guv2 = r2.roots()
+    whole = {"gamma": "inf", "selections_gpu": int(gp2.shape[0]), "selections_oracle": int(o["all"]["wp"].shape[0])}
+    whole.update(_point_errors(r2.E.cpu().numpy(), o["all"]["E"]))
+    whole.update(_root_errors(sc.s1, gp2, gk2, guv2, o["all"]))
+    return {"cells": dict(o["cells"], sampled_base_cells=ACC_CELLS, seed=11),
+            "points_on_oracle_index": dict(sampled, grid_cells=16 * ACC_CLUSTERS,
+                                           tuples_bounded_by_oracle=gside["n_tuples"]),
+            "whole_path_every_tuple": whole,
+            "tolerances": {"E_rel": 1e-4, "root_scene_units": 1e-5, "box": "GPU box contains the oracle's"},
+            "oracle_seconds": round(o["seconds"], 2), "oracle_cells_bounded": o["oracle_cells"]}
+
+
 def _pairs_oracle_worker():
     sys.path.insert(0, ROOT)
     import oracle
@@ -742,7 +1151,9 @@ def _cpu_baseline_worker(name, u_per_point, s_per_point):
     oracle.build()
     sc = S.config(name)
     n_threads = os.cpu_count() or 1
-    t_cell, t_draw, t_solve, desc = oracle_step_sample(sc, 64 * 2048, 1024, 7, n_threads)
+    per = 4 ** sc.depth
+    n_sample = -(-sc.emitters.n * sc.s1.n_tris * per // 100 // per) * per  # >= 1% of the cells, whole tuples
+    t_cell, t_draw, t_solve, desc = oracle_step_sample(sc, n_sample, 1024, 7, n_threads)
     step_s = oracle_step_seconds(sc, t_cell, t_draw, t_solve, u_per_point, s_per_point)
     n_cells = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
     return {"value": n_cells / step_s, "unit": "cells/s", "cores": n_threads, "kind": "oracle",
@@ -766,6 +1177,10 @@ def main():
                     help="timed launches of the implicit-differentiation irradiance pass (0: skip)")
     ap.add_argument("--pairs-steps", type=int, default=10,
                     help="timed steps of the two-vertex slab48 workload reported under 'pairs' (0: skip)")
+    ap.add_argument("--refraction-steps", type=int, default=5,
+                    help="timed steps of the water420 refraction workload reported under 'refraction' (0: skip)")
+    ap.add_argument("--rough-steps", type=int, default=3,
+                    help="timed bound passes of mirror256_rough reported under 'rough' (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

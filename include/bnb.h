@@ -425,6 +425,16 @@ int32_t bnb_stream_status(void *stream);
 int32_t bnb_implicit_irradiance(const bnb_surface *s1, const bnb_receiver *rec, const bnb_emitters *em,
                                 const bnb_cell_bounds *cells, int64_t n, int32_t mode, void *stream);
 
+/* FP32 FMA throughput probe (no counterpart in the paper): the measured denominator of the
+ * roofline of the ALU-bound bound kernels.  Launches grid_blocks x block_threads threads
+ * (block_threads a multiple of 32, at most 1024) on the stream; each runs `iters` rounds of 16
+ * independent FMA chains, as scalar FFMA (paired = 0) or paired FFMA2 (paired = 1, two FMAs per
+ * instruction), and writes one float to sink[thread] (device, grid_blocks * block_threads floats,
+ * caller-owned) so that no chain is dead code.  FLOPs per launch = grid_blocks * block_threads *
+ * iters * 32 * (paired ? 2 : 1).  The caller times it (CUDA events on the stream). */
+int32_t bnb_ffma_probe(int32_t grid_blocks, int32_t block_threads, int32_t iters, int32_t paired, float *sink,
+                       void *stream);
+
 int32_t bnb_abi_version(void);  /* 11 */
 
 #ifdef __cplusplus

@@ -98,7 +98,8 @@ EXPORTS = ["bnb_bound_tuples", "bnb_bound_tuples_ws", "bnb_bound_tuples_noalloc"
            "bnb_build_index_ws", "bnb_sample_and_solve", "bnb_sample_and_solve_ws", "bnb_status_string",
            "bnb_abi_version", "bnb_pack_surface", "bnb_pack_surface_bytes", "bnb_sample_and_solve_batched",
            "bnb_sample_and_solve_batched_ws", "bnb_bound_tuples_batched", "bnb_bound_tuples_batched_ws",
-           "bnb_implicit_irradiance", "bnb_stream_status", "bnb_gamma_for_target", "bnb_gamma_for_target_ws"]
+           "bnb_implicit_irradiance", "bnb_stream_status", "bnb_gamma_for_target", "bnb_gamma_for_target_ws",
+           "bnb_ffma_probe"]
 
 
 def lib():
@@ -134,6 +135,8 @@ def lib():
         L.bnb_gamma_for_target.argtypes = [P(bnb_index), vp, vp, i64, C.c_double, vp, vp, sz, vp]
         L.bnb_gamma_for_target_ws.restype = sz
         L.bnb_gamma_for_target_ws.argtypes = [i32]
+        L.bnb_ffma_probe.restype = i32
+        L.bnb_ffma_probe.argtypes = [i32, i32, i32, i32, vp, vp]
         L.bnb_stream_status.restype = i32
         L.bnb_stream_status.argtypes = [vp]
         L.bnb_status_string.restype = C.c_char_p
@@ -235,6 +238,45 @@ def gamma_for_target(index: "Index", target: float, su: Optional[torch.Tensor] =
     rc = bnb_gamma_for_target(C.byref(index.c), _ptr(su), _ptr(sv), n, float(target), _ptr(out), _align(ws),
                               C.c_size_t(need), _stream(stream))
     _check(rc, "bnb_gamma_for_target")
+    return out
+
+
+def bnb_ffma_probe(*a):
+    return lib().bnb_ffma_probe(*a)
+
+
+def fp32_fma_peak(device=None, seconds: float = 1.0, stream=None) -> dict:
+    """Measured FP32 FMA throughput (TFLOP/s) of this GPU with bnb_ffma_probe: scalar FFMA and paired
+    FFMA2, a resident grid (8 blocks of 256 threads per SM), timed with CUDA events on the stream
+    over about `seconds` per form after a warm-up; returns both rates and the larger as "peak"."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = sms * 8, 256
+    sink = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    out = {"blocks": blocks, "threads": threads}
+    for paired in (0, 1):
+        iters = 4096
+        flops = lambda it: blocks * threads * it * 32 * (2 if paired else 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):  # warm-up, and grow iters until one launch takes ~20 ms
+            e0.record(st)
+            _check(bnb_ffma_probe(blocks, threads, iters, paired, _ptr(sink), _stream(st)), "bnb_ffma_probe")
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            iters = max(1, min(1 << 22, int(iters * 20.0 / max(ms, 1e-3))))
+        reps = max(3, int(seconds * 1e3 / 20.0))
+        e0.record(st)
+        for _ in range(reps):
+            _check(bnb_ffma_probe(blocks, threads, iters, paired, _ptr(sink), _stream(st)), "bnb_ffma_probe")
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out["ffma2_tflops" if paired else "ffma_tflops"] = flops(iters) / (ms / 1e3) / 1e12
+    if not bool(torch.isfinite(sink).all()):
+        raise BnbError("bnb_ffma_probe: non-finite chain")
+    out["peak"] = max(out["ffma_tflops"], out["ffma2_tflops"])
     return out
 
 

@@ -266,3 +266,9 @@ def test_gamma_for_target_arguments(bnb):
     assert call(C.byref(idx), None, None, 0, 4.0, g, 4100, ws, None) == bnb.BNB_ERR_INVALID     # misaligned
     idx.grid_res = 0
     assert call(C.byref(idx), None, None, 0, 4.0, g, 4096, ws, None) == bnb.BNB_ERR_INVALID
+
+
+def test_ffma_probe_arguments(bnb):
+    for args in ((0, 256, 1, 0), (8, 33, 1, 0), (8, 2048, 1, 0), (8, 256, 0, 0), (8, 256, 1, 2)):
+        assert bnb.bnb_ffma_probe(*args, 4096, None) == bnb.BNB_ERR_INVALID
+    assert bnb.bnb_ffma_probe(8, 256, 1, 0, None, None) == bnb.BNB_ERR_INVALID
