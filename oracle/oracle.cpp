@@ -1175,6 +1175,7 @@ struct Vertex1 {
   bool tir = false;
   PV x1;
   PV dt[2];
+  double ca = 0.0, cb = 0.0, dlo = 0.0, dhi = 0.0;  // refraction: chord of sqrt(beta) and its remainder range
 };
 
 Vertex1 first_vertex(const Tri& T, V3 x0, int kind, double eta, const UV C[3]) {
@@ -1202,6 +1203,10 @@ Vertex1 first_vertex(const Tri& T, V3 x0, int kind, double eta, const UV C[3]) {
   }
   double a, b, dlo, dhi;
   chord_sqrt(std::max(blo, 0.0), bhi, &a, &b, &dlo, &dhi);
+  S.ca = a;
+  S.cb = b;
+  S.dlo = dlo;
+  S.dhi = dhi;
   PV tang = pv_elev(pv_scale(pv_sub(pv_mul(nn, d0), pv_mul(dn, n1)), eta), 5);
   for (int j = 0; j < 2; ++j) {
     Poly W = padd(pscale(beta, a), pconst(2, 4, b + (j == 0 ? dlo : dhi)));
@@ -1404,7 +1409,23 @@ void centroid_hit(const Ctx2& cx, const Tri& A, const Tri& B, V3 x0, const UV C[
   *vc = std::nearbyint(b * 65536.0) / 65536.0;
 }
 
-void bound_cell_pair(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int t2, orc_record& r) {
+// Intermediate quantities of one pair record, for the pins that evaluate the remainder forms
+// pointwise (the bound must hold over the whole product domain of the cell and the remainder
+// variables, not only on true chains).
+struct PairDiag {
+  double chord1[4];      // vertex 1: a, b, delta_lo, delta_hi of W1 = a beta1 + b + delta (0 for reflection)
+  double rx[2], ry[2];   // ratio bounds of d~1x / d~1z, d~1y / d~1z over both xi1 faces (tuple construction)
+  double u2box[4];       // ratio bounds of u2, v2 over the cell and both xi1 faces
+  double lu[3], lv[3];   // degree-1 interpolant of u2, v2 at the cell corners (barycentric order of C)
+  double rho[4];         // remainder ranges: u2 - l_u in [rho0, rho1], v2 - l_v in [rho2, rho3]
+  double chord2[4];      // vertex 2: a, b, delta_lo, delta_hi of W2 (0 for reflection)
+  double uc, vc;         // expansion point of the receiver forms
+  int32_t stage;         // 0: no intermediate, 1: vertex 1 only, 2: through u2, 3: complete
+  int32_t pad;
+};
+
+void bound_cell_pair(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int t2, orc_record& r,
+                     PairDiag* dg = nullptr) {
   UV C[3];
   cell_corners(id, depth, C);
   const Tri A = get_tri(cx.s1, t1), B = get_tri(cx.s2, t2);
@@ -1424,6 +1445,19 @@ void bound_cell_pair(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int 
     r.flags |= F_LIVE | F_POS_UNBOUNDED;
   };
   const Vertex1 S = first_vertex(A, x0, cx.s1->kind, cx.s1->eta, C);
+  if (dg) {
+    std::memset(dg, 0, sizeof(*dg));
+    dg->chord1[0] = S.ca;
+    dg->chord1[1] = S.cb;
+    dg->chord1[2] = S.dlo;
+    dg->chord1[3] = S.dhi;
+    const Bundle Bd = ray_bundle(S);
+    dg->rx[0] = Bd.rx[0];
+    dg->rx[1] = Bd.rx[1];
+    dg->ry[0] = Bd.ry[0];
+    dg->ry[1] = Bd.ry[1];
+    dg->stage = Bd.kind == 1 ? 1 : 0;
+  }
   if (S.tir) {
     r.flags |= F_TIR;
     return;
@@ -1484,6 +1518,21 @@ void bound_cell_pair(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int 
     rvl = std::min(rvl, l);
     rvh = std::max(rvh, h);
   }
+  if (dg) {
+    dg->u2box[0] = u2l;
+    dg->u2box[1] = u2h;
+    dg->u2box[2] = v2l;
+    dg->u2box[3] = v2h;
+    for (int k = 0; k < 3; ++k) {
+      dg->lu[k] = lu[k];
+      dg->lv[k] = lv[k];
+    }
+    dg->rho[0] = rul;
+    dg->rho[1] = ruh;
+    dg->rho[2] = rvl;
+    dg->rho[3] = rvh;
+    dg->stage = 2;
+  }
   const MP U2 = {mp_shift(MP{Lu, 0.0}, 0.5 * (rul + ruh)).p, 0.5 * (ruh - rul)};
   const MP V2 = {mp_shift(MP{Lv, 0.0}, 0.5 * (rvl + rvh)).p, 0.5 * (rvh - rvl)};
   // Second vertex: x2, n2 (Eqs. eq_xi, eq_ni on T2) affine in (U2, V2), d1 = x2 - x1
@@ -1506,6 +1555,12 @@ void bound_cell_pair(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int 
     }
     double a, b, dlo, dhi;
     chord_sqrt(std::max(blo, 0.0), bhi, &a, &b, &dlo, &dhi);
+    if (dg) {
+      dg->chord2[0] = a;
+      dg->chord2[1] = b;
+      dg->chord2[2] = dlo;
+      dg->chord2[3] = dhi;
+    }
     const MV tang = mv_elev(mv_scale(mv_sub(mv_mul(nn, d1), mv_mul(dn, n2)), eta), 5);
     for (int j = 0; j < 2; ++j) {
       const MP Wj = mp_shift(mp_scale(beta, a), b + (j == 0 ? dlo : dhi));
@@ -1514,6 +1569,11 @@ void bound_cell_pair(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int 
   }
   double uc, vc;
   centroid_hit(cx, A, B, x0, C, &uc, &vc);
+  if (dg) {
+    dg->uc = uc;
+    dg->vc = vc;
+    dg->stage = 3;
+  }
   const V3 pp = R.p0 + uc * R.e1 + vc * R.e2;
   const MV w3 = {mp_shift(x2.x, -pp.x), mp_shift(x2.y, -pp.y), mp_shift(x2.z, -pp.z)};
   MP Q3[2], A3[2], B3[2];
@@ -1977,6 +2037,17 @@ int orc_bound_pairs(const orc_surface* s1, const orc_surface* s2, const orc_rece
   });
   return 0;
 }
+
+// Records of the given pair items with their intermediate quantities (one PairDiag each).
+int orc_bound_pairs_diag(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec,
+                         const orc_emitters* em, int32_t depth, const int32_t* e, const int32_t* t1,
+                         const uint32_t* cell, const int32_t* t2, int64_t n, orc_record* out, PairDiag* diag) {
+  if (s1->kind < 0 || s1->kind > 1 || s2->kind < 0 || s2->kind > 1) return -4;
+  Ctx2 cx{s1, s2, get_rec(rec), em};
+  for (int64_t i = 0; i < n; ++i) bound_cell_pair(cx, e[i], t1[i], cell[i], depth, t2[i], out[i], &diag[i]);
+  return 0;
+}
+int orc_pair_diag_size(void) { return (int)sizeof(PairDiag); }
 
 // Direct chain evaluation at (u1, v1): out[i*8 + 0..7] = uk, vk, E, u2, v2, t1, t2, detJ (NaN: no path).
 int orc_eval_pair(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec, const orc_emitters* em,

@@ -96,6 +96,8 @@ def lib():
             L.orc_pair_candidates.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, i64, vp, i32]
             L.orc_pair_gap.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, i64, vp]
             L.orc_bound_pairs.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, vp, i32]
+            L.orc_bound_pairs_diag.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, vp, vp]
+            L.orc_pair_diag_size.restype = i32
             L.orc_eval_pair.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i64, vp]
             L.orc_solve_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32, i32, f64, vp, vp, vp, vp, i32]
             L.orc_implicit_bound.argtypes = [vp, vp, vp, i64] + [vp] * 10 + [i32, i32]
@@ -502,6 +504,33 @@ def bound_pairs(scene, e, t1, cell, t2, depth: Optional[int] = None, n_threads: 
     if rc != 0:
         raise RuntimeError(f"orc_bound_pairs failed: {rc}")
     return out
+
+
+# Intermediate quantities of a pair record (the oracle's PairDiag): the chord of sqrt(beta) at each
+# vertex (a, b, delta_lo, delta_hi), the direction-ratio bounds of tuple construction, the u2 box,
+# the degree-1 interpolant of u2 at the cell corners and its remainder ranges, the receiver forms'
+# expansion point, and how far the record's computation got (stage 3: complete).
+PAIR_DIAG_DTYPE = np.dtype([("chord1", np.float64, 4), ("rx", np.float64, 2), ("ry", np.float64, 2),
+                            ("u2box", np.float64, 4), ("lu", np.float64, 3), ("lv", np.float64, 3),
+                            ("rho", np.float64, 4), ("chord2", np.float64, 4), ("uc", np.float64),
+                            ("vc", np.float64), ("stage", np.int32), ("pad", np.int32)])
+
+
+def bound_pairs_diag(scene, e, t1, cell, t2, depth: Optional[int] = None):
+    """Records (RECORD_DTYPE) of the given pair items and their intermediates (PAIR_DIAG_DTYPE)."""
+    L = lib()
+    assert PAIR_DIAG_DTYPE.itemsize == L.orc_pair_diag_size()
+    V = _SceneViews(scene)
+    d = scene.depth if depth is None else depth
+    arr = [np.ascontiguousarray(a, dt) for a, dt in ((e, np.int32), (t1, np.int32), (cell, np.uint32), (t2, np.int32))]
+    n = arr[0].shape[0]
+    out = np.zeros(n, RECORD_DTYPE)
+    diag = np.zeros(n, PAIR_DIAG_DTYPE)
+    rc = L.orc_bound_pairs_diag(C.byref(V.surf), C.byref(V.surf2), C.byref(V.rec), C.byref(V.em), d,
+                                *[_p(a) for a in arr], n, _p(out), _p(diag))
+    if rc != 0:
+        raise RuntimeError(f"orc_bound_pairs_diag failed: {rc}")
+    return out, diag
 
 
 def bound_pair_scene(scene, depth: Optional[int] = None, n_threads: int = 1) -> np.ndarray:

@@ -277,3 +277,126 @@ def test_flat_mirror_glass_closed_form():
             np.testing.assert_allclose(P["E"][hit], np.sin(th0) / (rho * drho), rtol=1e-9)
             checked += int(hit.sum())
     assert checked > 30
+
+
+# ----------------------------------------------------------------------------- remainder-form sweeps
+# The bound of a pair record holds over the whole product domain of the cell and the remainder
+# variables (Sec. 4.3 "Remainder variables"; Sec. 6.1 "Degree reduction"), not only on true chains:
+# with W1 = a1 beta1 + b1 + delta1(xi1) at the first vertex, u2 replaced by its degree-1 interpolant
+# plus any (rho_u, rho_v) in the reduction's remainder ranges, and W2 = a2 beta2 + b2 + delta2(xi2)
+# at the second, every point of that domain must land in the record's box.  These sweeps evaluate
+# the remainder forms pointwise (the textbook ray-plane intersection, no Bernstein arithmetic) at
+# both ends of every remainder interval, so a bound that drops one xi face or one end of a
+# reduction remainder misses points of the domain by the width of that remainder, which on coarse,
+# steep cells under grazing light is far above the bound's slack.
+
+
+def _tri(s, t):
+    i = [int(s.i0[t]), int(s.i1[t]), int(s.i2[t])]
+    P = np.stack([s.px, s.py, s.pz], 1).astype(np.float64)[i]
+    N = np.stack([s.nx, s.ny, s.nz], 1).astype(np.float64)[i]
+    return P, N
+
+
+def _scatter(d, n, kind, eta, chord, xi):
+    """Direction leaving a vertex with incoming d and (un-normalized) normal n: reflection
+    (n.n) d - 2 (d.n) n; refraction eta' ((n.n) d - (d.n) n) - W n with W the remainder form
+    a beta + b + delta_lo + xi (delta_hi - delta_lo) of sqrt(beta), beta = (1 - eta'^2)(n.n)(d.d)
+    + eta'^2 (d.n)^2 (Eq. eq_refr_rational and the chord remainder of Sec. 4.3)."""
+    nn = np.sum(n * n, -1)[..., None]
+    dn = np.sum(d * n, -1)[..., None]
+    if kind == 0:
+        return nn * d - 2.0 * dn * n
+    ss = np.sum(d * d, -1)[..., None]
+    beta = (1.0 - eta * eta) * nn * ss + eta * eta * dn * dn
+    a, b, dlo, dhi = chord
+    W = a * beta + b + dlo + xi * (dhi - dlo)
+    return eta * (nn * d - dn * n) - W * n
+
+
+def _plane_coords(x, d, p0, e1, e2):
+    """(u, v) with x + s d = p0 + u e1 + v e2 (Cramer's rule)."""
+    M = np.stack([np.broadcast_to(e1, d.shape), np.broadcast_to(e2, d.shape), -d], -1)
+    sol = np.linalg.solve(M, (x - p0)[..., None])[..., 0]
+    return sol[..., 0], sol[..., 1]
+
+
+def remainder_sweep(sc, depth, k=12):
+    """Count the points of every live, bounded record's remainder domain (cell x xi1 x rho x xi2,
+    remainder variables at both ends and the middle) that fall outside its intermediate bounds or
+    its box.  Returns (violations by stage, points checked)."""
+    e, t1, cell, t2 = O.pair_candidates(sc)
+    rec, dg = O.bound_pairs_diag(sc, e, t1, cell, t2)
+    s1, s2, R = sc.s1, sc.s2, sc.receiver
+    p0r, e1r, e2r = (np.asarray(a, np.float64) for a in (R.p0, R.e1, R.e2))
+    eta1, eta2 = float(np.float32(s1.eta)), float(np.float32(s2.eta))  # stored as float32 in the scene views
+    viol = {"ratios": 0, "u2box": 0, "corner_interp": 0, "rho": 0, "box": 0}
+    checked = 0
+    tol = 1e-9
+    for i in range(rec.shape[0]):
+        r, g = rec[i], dg[i]
+        if not (r["flags"] & O.LIVE) or (r["flags"] & O.POS_UNBOUNDED) or g["stage"] != 3:
+            continue
+        C = O.cell_corners(int(r["cell"]), depth)
+        a, b = np.meshgrid(np.linspace(0, 1, k), np.linspace(0, 1, k))
+        m = a + b <= 1 + 1e-12
+        lam1, lam2 = a[m], b[m]
+        u1 = C[0, 0] + lam1 * (C[1, 0] - C[0, 0]) + lam2 * (C[2, 0] - C[0, 0])
+        v1 = C[0, 1] + lam1 * (C[1, 1] - C[0, 1]) + lam2 * (C[2, 1] - C[0, 1])
+        P1, N1 = _tri(s1, int(r["tri0"]))
+        P2, N2 = _tri(s2, int(r["tri1"]))
+        x0 = np.array([sc.emitters.x[int(r["emitter"])], sc.emitters.y[int(r["emitter"])],
+                       sc.emitters.z[int(r["emitter"])]], np.float64)
+        x1 = P1[0] + u1[:, None] * (P1[1] - P1[0]) + v1[:, None] * (P1[2] - P1[0])
+        n1 = N1[0] + u1[:, None] * (N1[1] - N1[0]) + v1[:, None] * (N1[2] - N1[0])
+        d0 = x1 - x0
+        lu = g["lu"][0] * (1 - lam1 - lam2) + g["lu"][1] * lam1 + g["lu"][2] * lam2
+        lv = g["lv"][0] * (1 - lam1 - lam2) + g["lv"][1] * lam1 + g["lv"][2] * lam2
+        e21, e22 = P2[1] - P2[0], P2[2] - P2[0]
+        for xi1 in (0.0, 0.5, 1.0):
+            d1t = _scatter(d0, n1, s1.kind, eta1, g["chord1"], xi1)
+            rx, ry = d1t[:, 0] / d1t[:, 2], d1t[:, 1] / d1t[:, 2]
+            viol["ratios"] += int(np.sum((rx < g["rx"][0] - tol) | (rx > g["rx"][1] + tol) |
+                                         (ry < g["ry"][0] - tol) | (ry > g["ry"][1] + tol)))
+            u2, v2 = _plane_coords(x1, d1t, P2[0], e21, e22)
+            viol["u2box"] += int(np.sum((u2 < g["u2box"][0] - tol) | (u2 > g["u2box"][1] + tol) |
+                                        (v2 < g["u2box"][2] - tol) | (v2 > g["u2box"][3] + tol)))
+            viol["rho"] += int(np.sum((u2 - lu < g["rho"][0] - tol) | (u2 - lu > g["rho"][1] + tol) |
+                                      (v2 - lv < g["rho"][2] - tol) | (v2 - lv > g["rho"][3] + tol)))
+            if xi1 == 0.5:  # the interpolant takes u2's values at the corners at xi1 = 1/2
+                corner = (np.abs(lam1) + np.abs(lam2) < 1e-12) | (np.abs(lam1 - 1) < 1e-12) | \
+                    (np.abs(lam2 - 1) < 1e-12)
+                viol["corner_interp"] += int(np.sum(corner & ((np.abs(u2 - lu) > 1e-9) | (np.abs(v2 - lv) > 1e-9))))
+            checked += u1.shape[0]
+        for ru in np.linspace(g["rho"][0], g["rho"][1], 3):
+            for rv in np.linspace(g["rho"][2], g["rho"][3], 3):
+                u2, v2 = lu + ru, lv + rv
+                x2 = P2[0] + u2[:, None] * e21 + v2[:, None] * e22
+                n2 = N2[0] + u2[:, None] * (N2[1] - N2[0]) + v2[:, None] * (N2[2] - N2[0])
+                for xi2 in (0.0, 0.5, 1.0):
+                    d2t = _scatter(x2 - x1, n2, s2.kind, eta2, g["chord2"], xi2)
+                    uk, vk = _plane_coords(x2, d2t, p0r, e1r, e2r)
+                    inu = (uk >= 0) & (uk <= 1)
+                    inv = (vk >= 0) & (vk <= 1)
+                    viol["box"] += int(np.sum(inu & ((uk < r["u_lo"] - tol) | (uk > r["u_hi"] + tol))))
+                    viol["box"] += int(np.sum(inv & ((vk < r["v_lo"] - tol) | (vk > r["v_hi"] + tol))))
+                    checked += int(np.sum(inu | inv))
+    return viol, checked
+
+
+# coarse, steep slabs lit from the side (large sqrt chords at both vertices, exits near the
+# critical angle at the bottom face, large reduction remainders), the workloads' gentle slab, and a
+# mirror followed by a refracting interface.  A planted copy of the oracle in which one xi face is
+# dropped (in the direction ratios, the u2 bounds, the reduction remainder, either vertex's W, or the
+# receiver ratio bound) fails this test on each of the three slab cases.
+@pytest.mark.parametrize("name,kw", [("slab", dict(n=3, depth=1, amp=0.1, lights=[(0.9, -0.5, 1.0)], rec_half=3.0)),
+                                     ("slab", dict(n=3, depth=1, amp=0.15, lights=[(0.5, 0.3, 1.2)], rec_half=3.0)),
+                                     ("slab", dict(n=4, depth=1, amp=0.04)),
+                                     ("mirror_glass", dict(n=4, depth=1, amp=0.04))])
+def test_pair_bound_holds_over_the_remainder_domain(name, kw):
+    depth = kw["depth"]
+    sc = S.config(name, **kw)
+    viol, checked = remainder_sweep(sc, depth)
+    print(name, kw, viol, checked)
+    assert checked > 5000
+    assert all(v == 0 for v in viol.values()), viol
