@@ -1621,6 +1621,227 @@ void bound_cell_pair(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int 
   r.e_hi = inf;
 }
 
+// ---------------------------------------------------------------------------
+// Irradiance of two-vertex chains (Eq. eq_dwda through both vertices).  The irradiance at the
+// receiver is E = I0 |d0.N1| / |d0|^3 * |det du1/du_k| / |N_k| (the direct evaluator's GGT form);
+// here both factors are enclosed over the whole cell by evaluating the chain map of
+// eval_pair_direct (unit normals, vector Snell or mirror law at each vertex, ray/plane hits) in
+// interval arithmetic with forward-mode derivatives along T1's two barycentric directions: the
+// cell's barycentric bounding box is the input interval, every operation rounds outward by one ulp,
+// and the hit on T2's plane is intersected with T2's closed domain (only chains through T2 count).
+// The Jacobian du_k/du1 of every chain of the cell lies in the resulting interval matrix, so when its
+// interval determinant excludes 0, E_hi = I0 |C1| / (s_lo^(3/2) |N_k| min |det|) bounds the
+// irradiance of every chain of the record from above (and E_lo from below); otherwise, or when a
+// division or square root cannot be certified, E_hi = +inf.  (The paper bounds chain irradiance by
+// implicit differentiation with Bernstein forms; its details are in the unavailable supplement.)
+struct Iv {
+  double lo, hi;
+};
+double out_dn(double x) { return std::nextafter(x, -std::numeric_limits<double>::infinity()); }
+double out_up(double x) { return std::nextafter(x, std::numeric_limits<double>::infinity()); }
+Iv ic(double a) { return {a, a}; }
+Iv iadd(Iv a, Iv b) { return {out_dn(a.lo + b.lo), out_up(a.hi + b.hi)}; }
+Iv isub(Iv a, Iv b) { return {out_dn(a.lo - b.hi), out_up(a.hi - b.lo)}; }
+Iv imul(Iv a, Iv b) {
+  const double p0 = a.lo * b.lo, p1 = a.lo * b.hi, p2 = a.hi * b.lo, p3 = a.hi * b.hi;
+  return {out_dn(std::min(std::min(p0, p1), std::min(p2, p3))), out_up(std::max(std::max(p0, p1), std::max(p2, p3)))};
+}
+// a / b; ok = false when b contains 0
+Iv idiv(Iv a, Iv b, bool& ok) {
+  if (!(b.lo > 0.0 || b.hi < 0.0)) {
+    ok = false;
+    return {-std::numeric_limits<double>::infinity(), std::numeric_limits<double>::infinity()};
+  }
+  const double q0 = a.lo / b.lo, q1 = a.lo / b.hi, q2 = a.hi / b.lo, q3 = a.hi / b.hi;
+  return {out_dn(std::min(std::min(q0, q1), std::min(q2, q3))), out_up(std::max(std::max(q0, q1), std::max(q2, q3)))};
+}
+// sqrt of the non-negative part; ok = false when a has none
+Iv isqrt(Iv a, bool& ok) {
+  if (!(a.hi >= 0.0)) {
+    ok = false;
+    return {0.0, 0.0};
+  }
+  return {std::max(0.0, out_dn(std::sqrt(std::max(a.lo, 0.0)))), out_up(std::sqrt(a.hi))};
+}
+
+struct ID {  // interval value and its derivatives along T1's barycentric directions u, v
+  Iv v, d[2];
+};
+ID idc(double a) { return {ic(a), {ic(0.0), ic(0.0)}}; }
+ID operator+(ID a, ID b) { return {iadd(a.v, b.v), {iadd(a.d[0], b.d[0]), iadd(a.d[1], b.d[1])}}; }
+ID operator-(ID a, ID b) { return {isub(a.v, b.v), {isub(a.d[0], b.d[0]), isub(a.d[1], b.d[1])}}; }
+ID operator*(ID a, ID b) {
+  return {imul(a.v, b.v),
+          {iadd(imul(a.d[0], b.v), imul(a.v, b.d[0])), iadd(imul(a.d[1], b.v), imul(a.v, b.d[1]))}};
+}
+ID idivd(ID a, ID b, bool& ok) {
+  const Iv q = idiv(a.v, b.v, ok);
+  return {q, {idiv(isub(a.d[0], imul(q, b.d[0])), b.v, ok), idiv(isub(a.d[1], imul(q, b.d[1])), b.v, ok)}};
+}
+ID isqrtd(ID a, bool& ok) {
+  const Iv r = isqrt(a.v, ok);
+  const Iv r2 = imul(ic(2.0), r);
+  return {r, {idiv(a.d[0], r2, ok), idiv(a.d[1], r2, ok)}};
+}
+struct IV3 {
+  ID x, y, z;
+};
+IV3 operator+(IV3 a, IV3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+IV3 operator-(IV3 a, IV3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+IV3 operator*(ID s, IV3 a) { return {s * a.x, s * a.y, s * a.z}; }
+ID idot(IV3 a, IV3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+IV3 iconst(V3 a) { return {idc(a.x), idc(a.y), idc(a.z)}; }
+IV3 idivs(IV3 a, ID s, bool& ok) { return {idivd(a.x, s, ok), idivd(a.y, s, ok), idivd(a.z, s, ok)}; }
+
+// Unit normal, then the mirror law or vector Snell (as snell(); eta < 0: a mirror); ok = false
+// when the discriminant's range reaches 0 (total internal reflection on part of the cell).
+IV3 isnell(IV3 ih, IV3 n, double eta, bool& ok) {
+  const ID ln = isqrtd(idot(n, n), ok);
+  const IV3 nh = idivs(n, ln, ok);
+  if (eta < 0.0) return ih - (idc(2.0) * idot(ih, nh)) * nh;
+  const ID c1 = idc(0.0) - idot(ih, nh);
+  const ID k = idc(1.0) - idc(eta * eta) * (idc(1.0) - c1 * c1);
+  if (!(k.v.lo > 0.0)) ok = false;
+  return idc(eta) * ih + (idc(eta) * c1 - isqrtd(k, ok)) * nh;
+}
+
+void iplane_coords(IV3 rel, V3 a, V3 b, ID* U, ID* V, bool& ok) {  // as plane_coords
+  const double g11 = dot(a, a), g12 = dot(a, b), g22 = dot(b, b);
+  const double det = g11 * g22 - g12 * g12;
+  const ID pa = idot(rel, iconst(a)), pb = idot(rel, iconst(b));
+  *U = idivd(idc(g22) * pa - idc(g12) * pb, idc(det), ok);
+  *V = idivd(idc(g11) * pb - idc(g12) * pa, idc(det), ok);
+}
+
+// [E_lo, E_hi] of every chain of (emitter e, T1, T2) whose u1 lies in the box U x W of T1's
+// barycentric coordinates.  Returns 0 (bounds certified), 1 (no chain of the box meets T2's closed
+// domain: [0, 0]) or 2 (not certified: a division, square root or the Jacobian's sign undecided).
+int chain_box(const Ctx2& cx, const Tri& A, const Tri& B, V3 x0, double I0, Iv Ub, Iv Wb, double* elo, double* ehi,
+              double* diag = nullptr) {
+  const Rec& R = cx.rec;
+  bool ok = true;
+  const ID U = {Ub, {ic(1.0), ic(0.0)}};
+  const ID W = {Wb, {ic(0.0), ic(1.0)}};
+  const IV3 x1 = iconst(A.p[0]) + U * iconst(A.p[1] - A.p[0]) + W * iconst(A.p[2] - A.p[0]);
+  const IV3 n1 = iconst(A.n[0]) + U * iconst(A.n[1] - A.n[0]) + W * iconst(A.n[2] - A.n[0]);
+  const IV3 d0 = x1 - iconst(x0);
+  const ID s0 = idot(d0, d0);
+  const IV3 i1 = idivs(d0, isqrtd(s0, ok), ok);
+  const IV3 r1 = isnell(i1, n1, law(cx.s1), ok);
+  const V3 e21 = B.p[1] - B.p[0], e22 = B.p[2] - B.p[0], N2 = cross(e21, e22);
+  const ID t = idivd(idot(iconst(B.p[0]) - x1, iconst(N2)), idot(r1, iconst(N2)), ok);
+  const IV3 x2 = x1 + t * r1;
+  ID U2, V2;
+  iplane_coords(x2 - iconst(B.p[0]), e21, e22, &U2, &V2, ok);
+  if (!ok) return 2;
+  // only chains through the closed triangle T2 count: clip the values to its barycentric box
+  U2.v = {std::max(U2.v.lo, 0.0), std::min(U2.v.hi, 1.0)};
+  V2.v = {std::max(V2.v.lo, 0.0), std::min(V2.v.hi, 1.0)};
+  if (U2.v.lo > U2.v.hi || V2.v.lo > V2.v.hi || U2.v.lo + V2.v.lo > 1.0) return 1;
+  const IV3 n2 = iconst(B.n[0]) + U2 * iconst(B.n[1] - B.n[0]) + V2 * iconst(B.n[2] - B.n[0]);
+  const IV3 i2 = idivs(r1, isqrtd(idot(r1, r1), ok), ok);
+  const IV3 r2 = isnell(i2, n2, law(cx.s2), ok);
+  const V3 Nk = cross(R.e1, R.e2);
+  const ID t2h = idivd(idot(iconst(R.p0) - x2, iconst(Nk)), idot(r2, iconst(Nk)), ok);
+  const IV3 X = x2 + t2h * r2;
+  ID Uk, Vk;
+  iplane_coords(X - iconst(R.p0), R.e1, R.e2, &Uk, &Vk, ok);
+  if (!ok) return 2;
+  const Iv det = isub(imul(Uk.d[0], Vk.d[1]), imul(Uk.d[1], Vk.d[0]));
+  if (diag) {  // s = |d0|^2 and det du_k/du1 over the box
+    diag[0] = s0.v.lo;
+    diag[1] = s0.v.hi;
+    diag[2] = det.lo;
+    diag[3] = det.hi;
+  }
+  if (!(det.lo > 0.0 || det.hi < 0.0)) return 2;  // a fold may lie in the box
+  const double dmin = det.lo > 0.0 ? det.lo : -det.hi, dmax = det.lo > 0.0 ? det.hi : -det.lo;
+  const Iv s = s0.v;
+  if (!(s.lo > 0.0)) return 2;
+  // |C1| = |(p10 - x0).N1| (constant on T1) with its float64 rounding error, |N_k|
+  const V3 a1 = A.p[1] - A.p[0], b1 = A.p[2] - A.p[0], r0 = A.p[0] - x0;
+  const V3 N1 = cross(a1, b1);
+  const double c1 = std::fabs(dot(r0, N1)), nk = norm(Nk);
+  const double mag = std::fabs(r0.x) * (std::fabs(a1.y * b1.z) + std::fabs(a1.z * b1.y)) +
+                     std::fabs(r0.y) * (std::fabs(a1.z * b1.x) + std::fabs(a1.x * b1.z)) +
+                     std::fabs(r0.z) * (std::fabs(a1.x * b1.y) + std::fabs(a1.y * b1.x));
+  const double cerr = 2e-15 * mag;
+  const double num_hi = out_up(I0 * out_up(c1 + cerr));
+  const double num_lo = std::max(0.0, out_dn(I0 * out_dn(c1 - cerr)));
+  const double s32_lo = out_dn(s.lo * out_dn(std::sqrt(s.lo))), s32_hi = out_up(s.hi * out_up(std::sqrt(s.hi)));
+  *ehi = out_up(num_hi / out_dn(out_dn(s32_lo * out_dn(nk * (1.0 - 1e-15))) * dmin));
+  *elo = std::max(0.0, out_dn(num_lo / out_up(out_up(s32_hi * out_up(nk * (1.0 + 1e-15))) * dmax)));
+  return 0;
+}
+
+// Whether the box [u0, u1] x [v0, v1] meets the triangle with corners C (separating axes: the
+// coordinate axes and the triangle's edge normals); a box separated by at most 1e-6 counts as
+// meeting it, so boxes that touch the cell are always kept.
+bool box_meets_cell(const UV C[3], double u0, double u1, double v0, double v1) {
+  const double mu = std::min(std::min(C[0].u, C[1].u), C[2].u), Mu = std::max(std::max(C[0].u, C[1].u), C[2].u);
+  const double mv = std::min(std::min(C[0].v, C[1].v), C[2].v), Mv = std::max(std::max(C[0].v, C[1].v), C[2].v);
+  const double eps = 1e-6;
+  if (u0 > Mu + eps || u1 < mu - eps || v0 > Mv + eps || v1 < mv - eps) return false;
+  for (int k = 0; k < 3; ++k) {
+    const UV a = C[k], b = C[(k + 1) % 3], c = C[(k + 2) % 3];
+    const double nu = -(b.v - a.v), nv = b.u - a.u;  // normal of edge a-b
+    const double side = nu * (c.u - a.u) + nv * (c.v - a.v);  // the triangle's side
+    const double len = std::sqrt(nu * nu + nv * nv);
+    double mn = std::numeric_limits<double>::infinity(), mx = -mn;
+    for (int q = 0; q < 4; ++q) {
+      const double pu = (q & 1) ? u1 : u0, pv = (q & 2) ? v1 : v0;
+      const double d = nu * (pu - a.u) + nv * (pv - a.v);
+      mn = std::min(mn, d);
+      mx = std::max(mx, d);
+    }
+    if (side > 0.0 && mx < -eps * len) return false;
+    if (side < 0.0 && mn > eps * len) return false;
+  }
+  return true;
+}
+
+// [E_lo, E_hi] of every chain of (emitter e, cell of T1, T2); E_hi = +inf when not certified,
+// [0, 0] when no chain of the cell passes through T2's closed domain.  The cell's barycentric
+// bounding box is tried whole; when that is not certified, its 2 x 2 and then 4 x 4 sub-boxes that
+// meet the cell (interval widths shrink with the box): the bound is the hull over the sub-boxes
+// of the first level at which every kept sub-box is certified or meets no chain.
+void chain_irradiance(const Ctx2& cx, int e, int t1, uint32_t id, int depth, int t2, double* elo, double* ehi) {
+  const double inf = std::numeric_limits<double>::infinity();
+  UV C[3];
+  cell_corners(id, depth, C);
+  const Tri A = get_tri(cx.s1, t1), B = get_tri(cx.s2, t2);
+  const V3 x0 = {cx.em->x[e], cx.em->y[e], cx.em->z[e]};
+  const double I0 = cx.em->intensity[e];
+  const double u0 = std::min(std::min(C[0].u, C[1].u), C[2].u), u1 = std::max(std::max(C[0].u, C[1].u), C[2].u);
+  const double v0 = std::min(std::min(C[0].v, C[1].v), C[2].v), v1 = std::max(std::max(C[0].v, C[1].v), C[2].v);
+  for (int level = 0; level < 3; ++level) {
+    const int m = 1 << level;
+    double lo = inf, hi = 0.0;
+    bool certified = true;
+    for (int j = 0; j < m && certified; ++j) {
+      for (int i = 0; i < m && certified; ++i) {
+        const double a0 = u0 + (u1 - u0) * i / m, a1 = u0 + (u1 - u0) * (i + 1) / m;
+        const double b0 = v0 + (v1 - v0) * j / m, b1 = v0 + (v1 - v0) * (j + 1) / m;
+        if (level > 0 && !box_meets_cell(C, a0, a1, b0, b1)) continue;
+        double l = 0.0, h = 0.0;
+        const int rc = chain_box(cx, A, B, x0, I0, Iv{a0, a1}, Iv{b0, b1}, &l, &h);
+        if (rc == 2) certified = false;
+        if (rc == 0) {
+          lo = std::min(lo, l);
+          hi = std::max(hi, h);
+        }
+      }
+    }
+    if (certified) {
+      *elo = lo == inf ? 0.0 : lo;
+      *ehi = hi;
+      return;
+    }
+  }
+  *elo = 0.0;
+  *ehi = inf;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -2048,6 +2269,33 @@ int orc_bound_pairs_diag(const orc_surface* s1, const orc_surface* s2, const orc
   return 0;
 }
 int orc_pair_diag_size(void) { return (int)sizeof(PairDiag); }
+
+// Irradiance bounds [e_lo, e_hi] of the given pair items (chain_irradiance; +inf when not certified).
+int orc_chain_irradiance(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec,
+                         const orc_emitters* em, int32_t depth, const int32_t* e, const int32_t* t1,
+                         const uint32_t* cell, const int32_t* t2, int64_t n, double* e_lo, double* e_hi,
+                         int32_t n_threads) {
+  if (s1->kind < 0 || s1->kind > 1 || s2->kind < 0 || s2->kind > 1) return -4;
+  Ctx2 cx{s1, s2, get_rec(rec), em};
+  parallel_for(n, std::max(1, (int)n_threads), [&](int, int64_t a, int64_t b) {
+    for (int64_t i = a; i < b; ++i) chain_irradiance(cx, e[i], t1[i], cell[i], depth, t2[i], &e_lo[i], &e_hi[i]);
+  });
+  return 0;
+}
+
+// One box of the chain bound with its factors: out = {rc, s_lo, s_hi, det_lo, det_hi, e_lo, e_hi} for the
+// box [u0, u1] x [v0, v1] of T1's barycentric coordinates (rc: 0 certified, 1 no chain, 2 not certified).
+int orc_chain_box(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec, const orc_emitters* em,
+                  int32_t e, int32_t t1, int32_t t2, double u0, double u1, double v0, double v1, double* out) {
+  Ctx2 cx{s1, s2, get_rec(rec), em};
+  const Tri A = get_tri(s1, t1), B = get_tri(s2, t2);
+  const V3 x0 = {em->x[e], em->y[e], em->z[e]};
+  double d[4] = {0, 0, 0, 0}, l = 0.0, h = 0.0;
+  const int rc = chain_box(cx, A, B, x0, em->intensity[e], Iv{u0, u1}, Iv{v0, v1}, &l, &h, d);
+  const double vals[7] = {(double)rc, d[0], d[1], d[2], d[3], l, h};
+  for (int k = 0; k < 7; ++k) out[k] = vals[k];
+  return 0;
+}
 
 // Direct chain evaluation at (u1, v1): out[i*8 + 0..7] = uk, vk, E, u2, v2, t1, t2, detJ (NaN: no path).
 int orc_eval_pair(const orc_surface* s1, const orc_surface* s2, const orc_receiver* rec, const orc_emitters* em,

@@ -98,6 +98,8 @@ def lib():
             L.orc_bound_pairs.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, vp, i32]
             L.orc_bound_pairs_diag.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, vp, vp]
             L.orc_pair_diag_size.restype = i32
+            L.orc_chain_irradiance.argtypes = [vp, vp, vp, vp, i32, vp, vp, vp, vp, i64, vp, vp, i32]
+            L.orc_chain_box.argtypes = [vp, vp, vp, vp, i32, i32, i32, f64, f64, f64, f64, vp]
             L.orc_eval_pair.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp, i64, vp]
             L.orc_solve_pair.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, vp, vp, i32, i32, f64, vp, vp, vp, vp, i32]
             L.orc_implicit_bound.argtypes = [vp, vp, vp, i64] + [vp] * 10 + [i32, i32]
@@ -533,10 +535,46 @@ def bound_pairs_diag(scene, e, t1, cell, t2, depth: Optional[int] = None):
     return out, diag
 
 
-def bound_pair_scene(scene, depth: Optional[int] = None, n_threads: int = 1) -> np.ndarray:
-    """Candidates then their records, in candidate order."""
+def chain_irradiance(scene, e, t1, cell, t2, depth: Optional[int] = None, n_threads: int = 1):
+    """Irradiance bounds (e_lo, e_hi) of the given pair items: the chain map in interval arithmetic
+    with forward-mode derivatives over the cell (e_hi = +inf when not certified)."""
+    L = lib()
+    V = _SceneViews(scene)
+    d = scene.depth if depth is None else depth
+    arr = [np.ascontiguousarray(a, dt) for a, dt in ((e, np.int32), (t1, np.int32), (cell, np.uint32), (t2, np.int32))]
+    n = arr[0].shape[0]
+    lo, hi = np.zeros(n), np.zeros(n)
+    rc = L.orc_chain_irradiance(C.byref(V.surf), C.byref(V.surf2), C.byref(V.rec), C.byref(V.em), d,
+                                *[_p(a) for a in arr], n, _p(lo), _p(hi), n_threads)
+    if rc != 0:
+        raise RuntimeError(f"orc_chain_irradiance failed: {rc}")
+    return lo, hi
+
+
+def chain_box(scene, emitter: int, tri0: int, tri1: int, u0: float, u1: float, v0: float, v1: float) -> dict:
+    """One box of the chain irradiance bound with its factors: rc (0 certified, 1 no chain, 2 not
+    certified), the intervals of s = |x1 - x0|^2 and det du_k/du1 over the box, and [e_lo, e_hi]."""
+    L = lib()
+    V = _SceneViews(scene)
+    out = np.zeros(7)
+    L.orc_chain_box(C.byref(V.surf), C.byref(V.surf2), C.byref(V.rec), C.byref(V.em), emitter, tri0, tri1, u0, u1,
+                    v0, v1, _p(out))
+    return dict(rc=int(out[0]), s=(out[1], out[2]), det=(out[3], out[4]), e_lo=out[5], e_hi=out[6])
+
+
+def bound_pair_scene(scene, depth: Optional[int] = None, n_threads: int = 1,
+                     irradiance: bool = False) -> np.ndarray:
+    """Candidates then their records, in candidate order.  irradiance: live records receive the chain
+    irradiance bounds (chain_irradiance); otherwise e_hi = +inf (P = 1 in Algorithm 1)."""
     e, t1, cell, t2 = pair_candidates(scene, depth, n_threads)
-    return bound_pairs(scene, e, t1, cell, t2, depth, n_threads)
+    rec = bound_pairs(scene, e, t1, cell, t2, depth, n_threads)
+    if irradiance and rec.shape[0]:
+        live = (rec["flags"] & LIVE) != 0
+        lo, hi = chain_irradiance(scene, rec["emitter"][live], rec["tri0"][live], rec["cell"][live],
+                                  rec["tri1"][live], depth, n_threads)
+        rec["e_lo"][live] = lo
+        rec["e_hi"][live] = hi
+    return rec
 
 
 def eval_pair(scene, emitter: int, tri0: int, tri1: int, u, v) -> dict:
@@ -571,9 +609,10 @@ def solve_pair(scene, wl_point, wl_key, wl_p, newton_iters: int = 16, polish_ite
 
 
 def render_pairs(scene, gamma: float, seed: int, depth: Optional[int] = None, newton_iters: int = 16,
-                 polish_iters: int = 1, tol: float = 1e-5, n_threads: int = 1):
-    """Whole two-vertex path on the CPU: candidates -> pair bounds -> index -> Algorithm 1 -> Newton."""
-    rec = bound_pair_scene(scene, depth, n_threads)
+                 polish_iters: int = 1, tol: float = 1e-5, n_threads: int = 1, irradiance: bool = False):
+    """Whole two-vertex path on the CPU: candidates -> pair bounds (irradiance: with the chain
+    irradiance bounds) -> index -> Algorithm 1 -> Newton."""
+    rec = bound_pair_scene(scene, depth, n_threads, irradiance)
     f = records_to_f32(rec)
     off, key, et = index(f["u_lo"], f["u_hi"], f["v_lo"], f["v_hi"], f["e_hi"], f["emitter"], f["tri0"],
                          f["tri1"], f["flags"], scene.grid_res)
