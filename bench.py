@@ -557,9 +557,10 @@ def serving_summary(n_requests: int, dev) -> dict:
 
 def pairs_summary(dev, steps: int, oracle_too: bool) -> dict:
     """The two-vertex workload (slab48: glass slab, two 48^2 faces, 512^2 points, depth 2), run after
-    the main timed region: bound pass (s2 grid, tuple construction, composite bounds), index,
-    rendering pass (chains carry no irradiance bound: P = 1), each timed with CUDA events over
-    `steps` steps after 3 warm-up steps, with a 256 MiB L2 flush between steps."""
+    the main timed region: bound pass (s2 grid, tuple construction, composite position bounds, chain
+    irradiance bounds), index, rendering pass with gamma for E|S| = |U| / 2 (the chain bounds make
+    P < 1), each timed with CUDA events over `steps` steps after 3 warm-up steps, with a 256 MiB L2
+    flush between steps; then the bound pass without the irradiance post-pass, timed the same way."""
     import torch
     from paper_2504_19163_gb300 import bnb
     from paper_2504_19163_gb300 import scenes as S
@@ -568,12 +569,14 @@ def pairs_summary(dev, steps: int, oracle_too: bool) -> dict:
     stream = torch.cuda.current_stream(dev)
     cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False)
     idx = bnb.build_index(cb, grid_res=sc.grid_res)
-    res = bnb.sample_and_solve(ds, idx, 1.0, 1)
+    res = bnb.sample_and_solve(ds, idx, float("inf"), 1)
     torch.cuda.synchronize()
     n_points = ds.n_points
     n_base = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
     wl_cap = int(res.counters[1].item()) * 2 + 4096
-    cfg = bnb.bnb_bound_cfg(sc.depth, 0, 0, 0)
+    U_all = float(res.counters[0].item()) / n_points
+    gamma = calibrate_gamma(bnb, ds, idx, target=0.5 * U_all)
+    cfg = bnb.bnb_bound_cfg(sc.depth, 0, 1, 0)
     cb_ws = bnb._ws(bnb.bnb_bound_tuples_ws(bnb.C.byref(ds.s1), ds.s2_ref(), bnb.C.byref(ds.em),
                                             bnb.C.byref(cfg)), dev)
     pre_cap = int(idx.count[1].item()) + int(idx.count[1].item()) // 4 + 4096
@@ -590,7 +593,7 @@ def pairs_summary(dev, steps: int, oracle_too: bool) -> dict:
         bnb.build_index(cb, grid_res=sc.grid_res, pre_capacity=pre_cap, capacity=pre_cap, out=idx, ws=ix_ws,
                         sync_check=False)
         ev[2].record(stream)
-        r = bnb.sample_and_solve(ds, idx, 1.0, seed, worklist_capacity=wl_cap, E_out=E_out, ws=sm_ws,
+        r = bnb.sample_and_solve(ds, idx, gamma, seed, worklist_capacity=wl_cap, E_out=E_out, ws=sm_ws,
                                  sync_check=False)
         ev[3].record(stream)
         return r
@@ -610,22 +613,35 @@ def pairs_summary(dev, steps: int, oracle_too: bool) -> dict:
     live = int(((flags & 1) != 0).sum().item())
     c = r.counters.cpu().numpy()
     ms = st.mean(axis=0)
+    n_finite = int((((flags & 1) != 0) & torch.isfinite(cb.e_hi[:n_rec])).sum().item())
+    # the bound pass without the chain irradiance post-pass (position bounds only)
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3 + steps)]
+    for i in range(3 + steps):
+        flush.zero_()
+        pev[i][0].record(stream)
+        bnb.bound_tuples(ds, sc.depth, out=cb, ws=cb_ws, sync_check=False, irradiance=False)
+        pev[i][1].record(stream)
+    torch.cuda.synchronize()
+    pos_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in pev[3:]]))
     props = torch.cuda.get_device_properties(dev)
     try:
         sm_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0))
     except Exception:
         sm_max = 2070.0
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
-    achieved = PAIR_FLOP_PER_RECORD * n_rec / (ms[0] / 1e3) / 1e12
+    achieved = PAIR_FLOP_PER_RECORD * n_rec / (pos_ms / 1e3) / 1e12
     out = {"workload": "slab48: glass slab (ior 1.5), two 48^2 heightfield faces (4608 tris each), point light "
                        "(0,0,2), receiver z=-1, 512^2 shading points, depth 2 (73,728 base cells), FP32",
            "status_ok": ok, "steps": steps, "base_cells": n_base, "pair_records": n_rec, "live_records": live,
+           "live_records_finite_e_hi": n_finite, "gamma": gamma, "gamma_target": "E|S| = |U| / 2",
+           "bound_position_only_ms": pos_ms, "chain_irradiance_ms": float(ms[0]) - pos_ms,
            "records_per_base_cell": n_rec / n_base,
            "stage_ms": {"bound": float(ms[0]), "index": float(ms[1]), "sample_solve": float(ms[2])},
            "pair_records_per_s": n_rec / (ms[0] / 1e3), "base_cells_per_s": n_base / (ms[0] / 1e3),
            "shading_samples_per_s": n_points / (ms[2] / 1e3),
            "per_point": {"U": c[0] / n_points, "S": c[1] / n_points, "roots": c[2] / n_points},
-           "roofline": {"bound": "alu", "kernel": "pair bound stage (s2 grid, candidates, pair_bound_k<float>)",
+           "roofline": {"bound": "alu", "kernel": "pair bound stage without the irradiance post-pass (s2 grid, "
+                                                 "candidates, pair_bound_k<float>)",
                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                         "flop_per_record": PAIR_FLOP_PER_RECORD}}
     del cb, idx, cb_ws, ix_ws, sm_ws, flush

@@ -210,11 +210,17 @@ typedef struct bnb_sample_stats {
  * candidates; each candidate is one record (tri1 = T2), records of one cell
  * contiguous, cells in base order.  Its box is the composite position bound:
  * u2 reduced to degree 1 plus a remainder (Sec. 6.1 "Degree reduction"), then
- * the second reflection or refraction and the receiver forms.  e_hi = +inf for every record
- * (chains carry no irradiance bound; P = 1 in the rendering pass).  A float32
+ * the second reflection or refraction and the receiver forms.  Irradiance (cfg->irradiance = 1;
+ * 0: e_hi = +inf, so P = 1 in the rendering pass; 2 is not supported for chains): per live
+ * record, E = I0 |C1| / (|x1 - x0|^3 |N_k| |det du_k/du1|) (Eq. eq_dwda through both vertices) is
+ * bounded by evaluating the chain map (unit normals, mirror law or vector Snell, ray/plane hits)
+ * in float32 interval arithmetic rounded outward, with forward-mode derivatives, over the cell's
+ * barycentric bounding box (then its 2 x 2 and 4 x 4 sub-boxes that meet the cell when the whole
+ * box is not certified); e_hi = +inf where the Jacobian's determinant cannot be kept away from 0,
+ * e_lo (when given) the matching lower bound, e_hi_min = 0.  A float32
  * sign test that cannot decide is redone in float64 (QSIGN_FP64); a certified
  * mixed-sign denominator gives the full box (POS_UNBOUNDED; no splits:
- * max_extra_split is ignored, and so is irradiance).  *count receives the number
+ * max_extra_split is ignored).  *count receives the number
  * of candidates; when it exceeds out->capacity, status = BNB_ERR_CAPACITY and the
  * records are invalid: re-call with capacity >= *count.  Host fields: n_base = 0
  * and depth = 0 (the index pass takes every record on its own). */

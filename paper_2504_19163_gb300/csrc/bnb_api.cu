@@ -18,8 +18,8 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2
                                     bnb_sample_stats* stats, void* ws, cudaStream_t st);
 size_t pair_ws_bytes(int64_t n_tris1, int64_t n_tris2, int64_t n_base);
 cudaError_t launch_bound_pairs(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
-                               const bnb_emitters* em, int32_t depth, bool fp64, bnb_cell_bounds* out, void* ws,
-                               cudaStream_t st);
+                               const bnb_emitters* em, int32_t depth, bool fp64, bool irradiance, bnb_cell_bounds* out,
+                               void* ws, cudaStream_t st);
 cudaError_t launch_implicit(const bnb_surface* s1, const bnb_receiver* rec, const bnb_emitters* em,
                             const bnb_cell_bounds* cells, int64_t n, int32_t mode, cudaStream_t st);
 size_t gamma_ws_bytes(int32_t G);
@@ -148,7 +148,9 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
     out->depth = 0;
     out->n_emitters = em->n;
     out->n_tris = s1->n_tris;
-    return launch_bound_pairs(s1, s2, rec, em, cfg->depth, cfg->fp64 != 0, out, ws, (cudaStream_t)stream) ==
+    if (cfg->irradiance < 0 || cfg->irradiance > 1) return BNB_ERR_INVALID;
+    return launch_bound_pairs(s1, s2, rec, em, cfg->depth, cfg->fp64 != 0, cfg->irradiance != 0, out, ws,
+                              (cudaStream_t)stream) ==
                    cudaSuccess
                ? BNB_OK
                : BNB_ERR_CUDA;

@@ -870,9 +870,13 @@ size_t pair_ws_bytes(int64_t n_tris1, int64_t n_tris2, int64_t n_base) {
   return carve_pair_ws(nullptr, n_tris1, n_tris2, n_base).bytes;
 }
 
+cudaError_t launch_chain_irradiance(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
+                                    const bnb_emitters* em, int32_t depth, const float4* tri1, const float4* tri2,
+                                    const bnb_cell_bounds* out, cudaStream_t st);  // bnb_chain.cu
+
 cudaError_t launch_bound_pairs(const bnb_surface* s1, const bnb_surface* s2, const bnb_receiver* rec,
-                               const bnb_emitters* em, int32_t depth, bool fp64, bnb_cell_bounds* out, void* ws,
-                               cudaStream_t st) {
+                               const bnb_emitters* em, int32_t depth, bool fp64, bool irradiance, bnb_cell_bounds* out,
+                               void* ws, cudaStream_t st) {
   const int64_t n_base = (int64_t)em->n * s1->n_tris * ((int64_t)1 << (2 * depth));
   PairWs w = carve_pair_ws(ws, s1->n_tris, s2->n_tris, n_base);
   const int G = pair_grid_res(s2->n_tris);
@@ -948,7 +952,10 @@ cudaError_t launch_bound_pairs(const bnb_surface* s1, const bnb_surface* s2, con
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_bound_k<false>, kPairThreads, 0);
     pair_bound_k<false><<<sms * std::max(1, per_sm), kPairThreads, 0, st>>>(P);
   }
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // chain irradiance bounds of the live records (a post-pass; otherwise e_hi stays +inf)
+  if (irradiance) return launch_chain_irradiance(s1, s2, rec, em, depth, w.tri1, w.tri2, out, st);
+  return cudaSuccess;
 }
 
 }  // namespace bnb

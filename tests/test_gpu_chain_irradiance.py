@@ -1,0 +1,148 @@
+"""GPU parity of the irradiance bound of two-vertex chains (Eq. eq_dwda through both vertices;
+the chain map in interval arithmetic with forward-mode derivatives over each record's cell).
+
+* Records: the GPU's float32 interval evaluation, rounded outward, against the oracle's float64 one
+  on the same (emitter, T1, cell, T2) items: the same records certified (finite E_hi), and there the
+  GPU's E_hi at or above the oracle's and within 1e-4 of it (the two differ by rounding only), E_lo
+  at or below it; a record certified at a different sub-box level on the two sides (float32 vs
+  float64 deciding a sign) is allowed on at most 0.1% of records and must hold its swept chains.
+* Containment: every swept chain of a sample of GPU records lies in its [E_lo, E_hi].
+* Sampling with P < 1 (Sec. 5.3): on the oracle's index with the bounds, the GPU's selections are
+  bit-exact and its estimates within 1e-4 per point; the mean of the GPU's P < 1 estimates over
+  seeds equals the P = 1 render (unbiasedness) within its standard error.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2504_19163_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2504_19163_gb300 import build
+    build.build()
+    from paper_2504_19163_gb300 import bnb
+    return bnb
+
+
+def gpu_records(B, sc):
+    ds = B.DeviceScene(sc)
+    cb = B.bound_tuples(ds, sc.depth, irradiance=True)
+    torch.cuda.synchronize()
+    assert int(cb.status.item()) == 0
+    return ds, cb, cb.to_numpy()
+
+
+def compare_chain_bounds(orc, sc, g, max_records=None, seed=0):
+    live = np.nonzero((g["flags"] & 1) != 0)[0]
+    if max_records is not None and live.shape[0] > max_records:
+        live = np.sort(np.random.default_rng(seed).choice(live, max_records, replace=False))
+    lo, hi = orc.chain_irradiance(sc, g["emitter"][live], g["tri0"][live], g["cell"][live], g["tri1"][live],
+                                  n_threads=16)
+    ge, gl = g["e_hi"][live].astype(np.float64), g["e_lo"][live].astype(np.float64)
+    both = np.isfinite(hi) & np.isfinite(ge) & (hi > 0)
+    rel = (ge[both] - hi[both]) / hi[both]
+    off = (rel < -1e-6) | (rel > REL) | (gl[both] > lo[both] * (1 + 1e-6))
+    rep = dict(records=int(live.shape[0]), oracle_finite=int(np.isfinite(hi).sum()), gpu_finite=int(np.isfinite(ge).sum()),
+               both_finite=int(both.sum()), finite_mismatch=int(np.sum(np.isfinite(hi) != np.isfinite(ge))),
+               off=int(off.sum()), rel_max=float(np.abs(rel).max(initial=0.0)),
+               rel_median=float(np.median(rel)) if rel.size else 0.0)
+    odd = live[np.isfinite(hi) != np.isfinite(ge)].tolist() + live[both][off].tolist()
+    return rep, odd
+
+
+def sweep_violations(orc, sc, g, idx, k=12):
+    from test_oracle_pairs import sweep_cell, through_t2
+    viol = checked = 0
+    for i in idx:
+        if not np.isfinite(g["e_hi"][i]):
+            continue
+        u, v = sweep_cell(sc.depth, g["cell"][i], k)
+        P = orc.eval_pair(sc, int(g["emitter"][i]), int(g["tri0"][i]), int(g["tri1"][i]), u, v)
+        h = through_t2(P) & (P["t2"] > 0) & np.isfinite(P["E"])
+        E = P["E"][h]
+        checked += E.size
+        viol += int(np.sum((E > g["e_hi"][i] * (1 + 1e-6)) | (E < g["e_lo"][i] * (1 - 1e-6))))
+    return viol, checked
+
+
+@pytest.mark.parametrize("name,kw", [("slab", dict(n=6, depth=2, amp=0.02)),
+                                     ("slab", dict(n=4, depth=3, amp=0.08)),
+                                     ("mirror_glass", dict(n=4, depth=2, amp=0.04)),
+                                     ("periscope", dict(n=4, depth=2, amp=0.04))])
+def test_chain_bounds_match_oracle(B, orc, name, kw):
+    sc = S.config(name, **kw)
+    _, _, g = gpu_records(B, sc)
+    rep, odd = compare_chain_bounds(orc, sc, g)
+    print(name, kw, rep)
+    assert rep["both_finite"] > 100
+    assert rep["finite_mismatch"] + rep["off"] <= max(1, 1e-3 * rep["records"]), rep
+    viol, _ = sweep_violations(orc, sc, g, odd)
+    assert viol == 0
+    live = np.nonzero((g["flags"] & 1) != 0)[0]
+    sample = np.random.default_rng(2).choice(live, min(200, live.shape[0]), replace=False)
+    viol, checked = sweep_violations(orc, sc, g, sample)
+    assert viol == 0 and checked > 1000
+
+
+def test_slab48_chain_bounds(B, orc):
+    """The workload slab at full size: every live record certified, 20,000 sampled records against
+    the oracle, 300 swept."""
+    sc = S.config("slab48")
+    _, cb, g = gpu_records(B, sc)
+    live = (g["flags"] & 1) != 0
+    assert np.isfinite(g["e_hi"][live]).mean() > 0.999
+    rep, odd = compare_chain_bounds(orc, sc, g, max_records=20000, seed=4)
+    print("slab48", rep)
+    assert rep["finite_mismatch"] + rep["off"] <= max(2, 1e-3 * rep["records"]), rep
+    assert sweep_violations(orc, sc, g, odd)[0] == 0
+    idx = np.random.default_rng(5).choice(np.nonzero(live)[0], 300, replace=False)
+    viol, checked = sweep_violations(orc, sc, g, idx)
+    assert viol == 0 and checked > 3000
+
+
+def upload_index(B, off, key, et, G):
+    idx = B.Index(G, max(1, key.shape[0]), torch.device("cuda"))
+    idx.offsets.copy_(torch.as_tensor(off))
+    if key.shape[0]:
+        idx.key[: key.shape[0]] = torch.as_tensor(key.view(np.int64))
+        idx.etilde[: key.shape[0]] = torch.as_tensor(et)
+    idx.count[0] = key.shape[0]
+    return idx
+
+
+def test_chain_sampling_below_one_on_oracle_index(B, orc):
+    """gamma for E|S| = |U| / 2: selections bit-exact and estimates within 1e-4 per point on the
+    oracle's index (the oracle's chain bounds), then unbiasedness of the GPU's P < 1 estimates."""
+    sc = S.config("slab", n=6, depth=2, amp=0.02, points=40)
+    out = orc.render_pairs(sc, gamma=float("inf"), seed=1, n_threads=16, irradiance=True)
+    off, key, et = out["offsets"], out["key"], out["etilde"]
+    assert np.isfinite(et).mean() > 0.99
+    ds = B.DeviceScene(sc)
+    idx = upload_index(B, off, key, et, sc.grid_res)
+    U = out["n_U"] / sc.su.shape[0]
+    gamma = float(B.gamma_for_target(idx, 0.5 * U, ds.t["su"], ds.t["sv"]).item())
+    o = orc.render_pairs(sc, gamma=gamma, seed=9, n_threads=16, irradiance=True)
+    assert np.array_equal(o["offsets"], off) and np.array_equal(o["key"], key)
+    r = B.sample_and_solve(ds, idx, gamma, 9, with_sel_count=True)
+    torch.cuda.synchronize()
+    assert np.mean(o["wl_p"] < 1.0) > 0.5  # the bounds make most selections probabilistic
+    assert np.array_equal(r.sel_count.cpu().numpy(), np.bincount(o["wl_point"], minlength=sc.su.shape[0]))
+    E_g, E_o = r.E.cpu().numpy().astype(np.float64), o["E"]
+    pos = E_o > 0
+    assert pos.sum() > 100
+    assert np.max(np.abs(E_g[pos] - E_o[pos]) / E_o[pos]) <= REL
+    assert np.all(E_g[~pos] == 0)
+    # unbiased: the mean over seeds of the P < 1 estimate is the P = 1 (every listed chain) render
+    E_all = out["E"]
+    est = np.stack([B.sample_and_solve(ds, idx, gamma, s).E.cpu().numpy().astype(np.float64) for s in range(64)])
+    tot, tot_all = est.sum(axis=1), E_all.sum()
+    se = tot.std(ddof=1) / np.sqrt(tot.shape[0])
+    assert abs(tot.mean() - tot_all) <= 5 * se + 1e-4 * tot_all, (tot.mean(), tot_all, se)

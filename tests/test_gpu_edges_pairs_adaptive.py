@@ -33,7 +33,7 @@ def test_pairs_with_an_empty_second_surface(B):
     cb = B.bound_tuples(ds, sc.depth)
     assert int(cb.count.item()) == 0 and int(cb.status.item()) == 0
     idx = B.build_index(cb, sc.grid_res)
-    r = B.sample_and_solve(ds, idx, 1.0, 1)
+    r = B.sample_and_solve(ds, idx, float("inf"), 1)
     torch.cuda.synchronize()
     assert int(r.status.item()) == 0 and float(r.E.abs().sum().item()) == 0.0
 
@@ -46,7 +46,7 @@ def test_smallest_slab_matches_oracle(B, orc):
     gk = set(zip(g["emitter"].tolist(), g["tri0"].tolist(), g["cell"].tolist(), g["tri1"].tolist()))
     ok = set(zip(o["emitter"].tolist(), o["tri0"].tolist(), o["cell"].tolist(), o["tri1"].tolist()))
     assert ok <= gk and len(gk - ok) <= 1
-    r = B.sample_and_solve(ds, B.build_index(B.bound_tuples(ds, sc.depth), sc.grid_res), 1.0, 1)
+    r = B.sample_and_solve(ds, B.build_index(B.bound_tuples(ds, sc.depth), sc.grid_res), float("inf"), 1)
     out = orc.render_pairs(sc, 1.0, 1)
     E = r.E.cpu().numpy().astype(np.float64)
     pos = out["E"] > 0

@@ -190,7 +190,7 @@ def render_gpu(B, sc, ds=None, seed=1):
     ds = ds or B.DeviceScene(sc)
     cb = B.bound_tuples(ds, sc.depth)
     idx = B.build_index(cb, sc.grid_res)
-    res = B.sample_and_solve(ds, idx, gamma=1.0, seed=seed)
+    res = B.sample_and_solve(ds, idx, gamma=float("inf"), seed=seed)
     torch.cuda.synchronize()
     return cb, idx, res
 

@@ -193,7 +193,7 @@ def test_slab_whole_path_every_point_and_roots(B, orc, kw):
     ds = B.DeviceScene(sc)
     cb = B.bound_tuples(ds, sc.depth)
     idx = B.build_index(cb, sc.grid_res)
-    r = B.sample_and_solve(ds, idx, gamma=1.0, seed=1, with_roots=True)
+    r = B.sample_and_solve(ds, idx, gamma=float("inf"), seed=1, with_roots=True)
     torch.cuda.synchronize()
     out = orc.render_pairs(sc, gamma=1.0, seed=1, n_threads=os.cpu_count())
     assert_every_point(r.E.cpu().numpy(), out["E"])
