@@ -1020,7 +1020,8 @@ def _compare_records(g: dict, o) -> dict:
     rw = np.array(rel_wc or [0.0])
     rep.update(box_widen_max=float(w.max()), box_widen_p99=float(np.percentile(w, 99)),
                e_hi_rel_excess_median=float(np.median(r)), e_hi_rel_excess_p99=float(np.percentile(r, 99)),
-               e_hi_rel_excess_max=float(r.max()), well_conditioned_cells=len(rel_wc),
+               e_hi_rel_excess_max=float(r.max()), e_hi_within_1e-4_frac=float(np.mean(np.abs(r) <= 1e-4)),
+               well_conditioned_cells=len(rel_wc),
                well_conditioned_e_hi_rel_excess_max=float(rw.max()),
                well_conditioned_e_hi_rel_excess_p99=float(np.percentile(rw, 99)))
     return rep

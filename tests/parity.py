@@ -84,11 +84,21 @@ def compare_bounds(g, o, fp64=False):
     er = np.array(rep.pop("e_rel") or [0.0])
     rep.update(box_widen_max=float(w.max()), box_widen_p99=float(np.percentile(w, 99)),
                slack_median=float(np.median(sl)), slack_p99=float(np.percentile(sl, 99)), slack_max=float(sl.max()),
-               e_rel_median=float(np.median(er)), e_rel_max=float(np.abs(er).max()))
+               e_rel_median=float(np.median(er)), e_rel_max=float(np.abs(er).max()),
+               e_within_frac=float(np.mean(np.abs(er) <= E_REL_CELL)))
     return rep
 
 
-def assert_bounds_parity(rep, allow_ambiguous_frac=1e-3, slack_median=2e-4, slack_p99=5e-3):
+# E_hi against the oracle's: the float32 bound exceeds the float64 one by at most its certified
+# enclosure width, which cancellation while the Jacobian numerator is formed widens on a few
+# percent of cells; on the smooth workloads at least E_WITHIN of the finite cells are within
+# E_REL_CELL, with the median excess at most E_REL_MEDIAN (every cell is held to the enclosure).
+E_REL_CELL = 1e-4
+E_WITHIN = 0.95
+E_REL_MEDIAN = 5e-5
+
+
+def assert_bounds_parity(rep, allow_ambiguous_frac=1e-3, slack_median=2e-4, slack_p99=5e-3, e_within=E_WITHIN):
     assert rep["missing"] == 0, rep
     assert rep["extra"] <= 4 * rep["flag_ambiguous"], rep
     assert rep["flag_mismatch"] == 0, rep
@@ -102,6 +112,8 @@ def assert_bounds_parity(rep, allow_ambiguous_frac=1e-3, slack_median=2e-4, slac
         assert rep["box_widen_max"] <= BOX_TOL32, rep
         assert rep["encl_viol"] == 0, rep
         assert rep["slack_median"] <= slack_median and rep["slack_p99"] <= slack_p99, rep
+        if e_within is not None and rep["e_checked"] > 0:
+            assert rep["e_within_frac"] >= e_within and rep["e_rel_median"] <= E_REL_MEDIAN, rep
     assert rep["e_checked"] > 0.9 * rep["live"], rep
 
 
