@@ -1020,7 +1020,7 @@ def _compare_records(g: dict, o) -> dict:
     rw = np.array(rel_wc or [0.0])
     rep.update(box_widen_max=float(w.max()), box_widen_p99=float(np.percentile(w, 99)),
                e_hi_rel_excess_median=float(np.median(r)), e_hi_rel_excess_p99=float(np.percentile(r, 99)),
-               e_hi_rel_excess_max=float(r.max()), e_hi_within_1e-4_frac=float(np.mean(np.abs(r) <= 1e-4)),
+               e_hi_rel_excess_max=float(r.max()), e_hi_frac_within_1e4=float(np.mean(np.abs(r) <= 1e-4)),
                well_conditioned_cells=len(rel_wc),
                well_conditioned_e_hi_rel_excess_max=float(rw.max()),
                well_conditioned_e_hi_rel_excess_p99=float(np.percentile(rw, 99)))
@@ -1178,6 +1178,67 @@ def _cpu_baseline_worker(name, u_per_point, s_per_point):
                       f"points x ({u_per_point:.1f} draws + {s_per_point:.2f} solves, this run's |U|, |S|)"}
 
 
+def profile_case(args):
+    """Small cases of single stages for ncu captures (no JSON line): `--warmup` + `--steps` launches of
+    the stage named by --profile-case, inputs larger than L2 but a few GB on the device at most.
+      refraction  water420 with its first light (22.6M cells): the refraction bound pass
+      index       mirror256 with 4 of its 16 light samples (33.6M cells): the index pass
+      sample      mirror256 with 8 light samples: the rendering pass over its index (1024^2 points)
+      chain       slab48: the two-vertex bound pass with the chain irradiance post-pass
+      implicit    tir_wall 32^2, depth 4: the implicit-differentiation pass"""
+    import torch
+    from paper_2504_19163_gb300 import bnb, build
+    from paper_2504_19163_gb300 import scenes as S
+    build.build()
+    dev = torch.device("cuda", 0)
+    case = args.profile_case
+
+    def subset(sc, n):
+        e = sc.emitters
+        sc.emitters = S.Emitters(e.x[:n], e.y[:n], e.z[:n], e.intensity[:n])
+        return sc
+
+    n = args.warmup + args.steps
+    if case == "refraction":
+        sc = subset(S.config("water420"), 1)
+        ds = bnb.DeviceScene(sc, dev)
+        cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False)
+        for _ in range(n):
+            bnb.bound_tuples(ds, sc.depth, out=cb, sync_check=False)
+    elif case in ("index", "sample"):
+        sc = subset(S.config("mirror256"), 4 if case == "index" else 8)
+        ds = bnb.DeviceScene(sc, dev)
+        cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False)
+        idx = bnb.build_index(cb, grid_res=sc.grid_res)
+        if case == "index":
+            for _ in range(n):
+                bnb.build_index(cb, grid_res=sc.grid_res, pre_capacity=int(idx.count[1].item()) + 4096,
+                                capacity=int(idx.count[1].item()) + 4096, out=idx, sync_check=False)
+        else:
+            del cb
+            torch.cuda.empty_cache()
+            gamma = calibrate_gamma(bnb, ds, idx, target=4.0)
+            for i in range(n):
+                bnb.sample_and_solve(ds, idx, gamma, i)
+    elif case == "chain":
+        sc = S.config("slab48")
+        ds = bnb.DeviceScene(sc, dev)
+        cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False)
+        for _ in range(n):
+            bnb.bound_tuples(ds, sc.depth, out=cb, sync_check=False)
+    elif case == "implicit":
+        sc = S.config("tir_wall", n=32, depth=4)
+        ds = bnb.DeviceScene(sc, dev)
+        cb = bnb.bound_tuples(ds, sc.depth, irradiance=True)
+        for _ in range(n):
+            bnb.implicit_irradiance(ds, cb, n=-1, mode=1)
+    else:
+        raise SystemExit(f"unknown profile case {case}")
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": case, "launches": n, "stream_status": bnb.stream_status()}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1198,9 +1259,13 @@ def main():
                     help="timed steps of the water420 refraction workload reported under 'refraction' (0: skip)")
     ap.add_argument("--rough-steps", type=int, default=3,
                     help="timed bound passes of mirror256_rough reported under 'rough' (0: skip)")
+    ap.add_argument("--profile-case", default="", choices=["", "refraction", "index", "sample", "chain", "implicit"],
+                    help="run one stage's small profiling case (for ncu) instead of the benchmark")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.profile_case:
+        return profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
