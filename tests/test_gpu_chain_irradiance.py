@@ -3,11 +3,14 @@ the chain map in interval arithmetic with forward-mode derivatives over each rec
 
 * Records: the GPU's float32 interval evaluation, rounded outward, against the oracle's float64 one
   on the same (emitter, T1, cell, T2) items: the same records certified (finite E_hi), and there the
-  GPU's E_hi at or above the oracle's and within CHAIN_REL = 2e-3 of it, median within 1e-4 (the two
-  differ by outward rounding only: one float32 ulp per operation over a few hundred operations,
-  amplified by the cancellation in the Jacobian's determinant), E_lo at or below it; a record
-  certified at a different sub-box level on the two sides (float32 vs float64 deciding a sign) is
-  allowed on at most 0.1% of records and must hold its swept chains.
+  GPU's E_hi at or above the oracle's, E_lo at or below it, and the median gap within 1e-4.  The two
+  differ by outward rounding only (one float32 ulp per operation over a few hundred operations), and
+  that rounding moves the determinant's lower end min|det| by a small multiple of its magnitude
+  ~max|det|, so E_hi moves by ~(max|det| / min|det|) times the rounding: the gap on each record is
+  held to CHAIN_REL * max(2, E_hi / E_lo) (E_hi / E_lo >= max|det| / min|det| on the oracle's
+  record), CHAIN_REL = 1e-3.  A record certified at a different sub-box level on the two sides
+  (float32 vs float64 deciding a sign) or outside that gap is allowed on at most 0.1% of records and
+  must hold its swept chains.
 * Containment: every swept chain of a sample of GPU records lies in its [E_lo, E_hi].
 * Sampling with P < 1 (Sec. 5.3): on the oracle's index with the bounds, the GPU's selections are
   bit-exact and its estimates within 1e-4 per point; the mean of the GPU's P < 1 estimates over
@@ -24,7 +27,7 @@ from paper_2504_19163_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 REL = 1e-4          # per-point estimates
-CHAIN_REL = 2e-3    # chain irradiance bound: float32 vs float64 outward rounding of the same enclosure
+CHAIN_REL = 1e-3    # chain irradiance bound: float32 vs float64 rounding, per unit of E_hi / E_lo
 
 
 @pytest.fixture(scope="module")
@@ -52,7 +55,8 @@ def compare_chain_bounds(orc, sc, g, max_records=None, seed=0):
     ge, gl = g["e_hi"][live].astype(np.float64), g["e_lo"][live].astype(np.float64)
     both = np.isfinite(hi) & np.isfinite(ge) & (hi > 0)
     rel = (ge[both] - hi[both]) / hi[both]
-    off = (rel < -1e-6) | (rel > CHAIN_REL) | (gl[both] > lo[both] * (1 + 1e-6))
+    spread = hi[both] / np.maximum(lo[both], 1e-300)
+    off = (rel < -1e-6) | (rel > CHAIN_REL * np.maximum(2.0, spread)) | (gl[both] > lo[both] * (1 + 1e-6))
     rep = dict(records=int(live.shape[0]), oracle_finite=int(np.isfinite(hi).sum()), gpu_finite=int(np.isfinite(ge).sum()),
                both_finite=int(both.sum()), finite_mismatch=int(np.sum(np.isfinite(hi) != np.isfinite(ge))),
                off=int(off.sum()), rel_max=float(np.abs(rel).max(initial=0.0)),
