@@ -282,8 +282,12 @@ def run_gpu(args):
     n_points = ds.n_points
     stream = torch.cuda.current_stream(dev)
 
+    # Block size of the bound pass: the autotuner times its compiled schedules on this workload.
+    from paper_2504_19163_gb300 import batch as BA
+    sched = BA.autotune_bound(ds, sc.depth, use_cache=False, with_e_lo=False)
+    bt = int(sched["block_threads"])
     # Buffers sized once (first call discovers the capacities), then reused every step.
-    cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False)  # the index needs E_hi only
+    cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False, block_threads=bt)  # the index needs E_hi only
     idx = bnb.build_index(cb, grid_res=sc.grid_res)
     # gamma: expected |S| of about 4 per shading point (paper's Plane scene: |S| = 3.4)
     gamma = calibrate_gamma(bnb, ds, idx, target=4.0)
@@ -302,7 +306,7 @@ def run_gpu(args):
     def step(seed, ev=None):
         if ev is not None:
             ev[0].record(stream)
-        bnb.bound_tuples(ds, sc.depth, out=cb, ws=cb_ws, sync_check=False)
+        bnb.bound_tuples(ds, sc.depth, out=cb, ws=cb_ws, sync_check=False, block_threads=bt)
         if ev is not None:
             ev[1].record(stream)
         bnb.build_index(cb, grid_res=sc.grid_res, pre_capacity=pre_cap, capacity=pre_cap, out=idx, ws=ix_ws,
@@ -427,6 +431,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "l2": "flushed between steps (256 MiB write, outside the events)",
                        "gamma": gamma, "cells_per_step": n_cells, "points_per_step": n_points,
+                       "bound_schedule": sched,
                        "status_ok": st_ok},
             "shading_samples_per_s": n_points * world / (ms_max / 1e3),
             "stage_ms": stage_ms,

@@ -112,7 +112,9 @@ typedef struct bnb_bound_cfg {
   int32_t adapt_depth;     /* 0 or depth..15 (adapt_depth + max_extra_split <= 15) */
   float sigma;             /* >= 0 */
   float alpha;             /* >= 0 */
-  int32_t reserved;        /* 0 */
+  int32_t block_threads;   /* block size of the float32 reflection pass (one persistent block per SM):
+                              0 (the default, 384), 256, 320 or 384; other passes ignore it.  The
+                              records do not depend on it (the autotuner picks the fastest). */
   int64_t split_capacity;  /* split-queue entries per level (0: 4096 + n_base / 32); a level that
                               queues more raises BNB_ERR_CAPACITY */
 } bnb_bound_cfg;

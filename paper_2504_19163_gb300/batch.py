@@ -339,3 +339,45 @@ def autotune(jobs: Sequence[Job], worklist_capacity: int, reps: int = 3, device=
     if use_cache:
         store_cache(key, entry)
     return entry
+
+
+BOUND_SCHEDULES = (256, 320, 384)  # block sizes the float32 reflection bound pass is compiled for
+
+
+def autotune_bound(ds: bnb.DeviceScene, depth: int, reps: int = 3, use_cache: bool = True,
+                   candidates: Sequence[int] = BOUND_SCHEDULES, **bound_kw) -> dict:
+    """Fastest block size of the bound pass for scenes like `ds` at `depth`; cached per (device,
+    size class = log2 of the base cells).  Every candidate bounds the scene `reps` times after one
+    warm-up into the same outputs; the median CUDA-event time decides.  Only the float32 reflection
+    pass has schedules: other passes return the default (0) without timing."""
+    if ds.s2 is not None or ds.s1.kind != bnb.BNB_REFLECT or bound_kw.get("fp64"):
+        return {"block_threads": 0, "ms": None, "candidates": []}
+    n_base = ds.scene.emitters.n * ds.s1.n_tris * 4 ** depth
+    name = torch.cuda.get_device_name(ds.device).replace(" ", "_")
+    key = f"{name}|bound_tuples_reflect|cells_2^{size_class(n_base)}"
+    if use_cache:
+        hit = load_cache().get(key)
+        if hit is not None:
+            return hit
+    out = bnb.bound_tuples(ds, depth, **bound_kw)
+    stream = torch.cuda.current_stream(ds.device)
+    timings = []
+    for bt in candidates:
+        ts = []
+        for k in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bnb.bound_tuples(ds, depth, out=out, sync_check=False, block_threads=bt, **bound_kw)
+            b.record(stream)
+            b.synchronize()
+            if k > 0:
+                ts.append(a.elapsed_time(b))
+        if int(out.status.item()) != bnb.BNB_OK:
+            raise bnb.BnbError("autotune_bound: bound pass status not OK")
+        ts.sort()
+        timings.append((ts[len(ts) // 2], bt))
+    best = min(timings)
+    entry = {"block_threads": best[1], "ms": best[0], "candidates": [[bt, ms] for ms, bt in sorted(timings, key=lambda x: x[1])]}
+    if use_cache:
+        store_cache(key, entry)
+    return entry

@@ -47,7 +47,7 @@ class bnb_emitters(C.Structure):
 
 class bnb_bound_cfg(C.Structure):
     _fields_ = [("depth", i32), ("max_extra_split", i32), ("irradiance", i32), ("fp64", i32), ("adapt_depth", i32),
-                ("sigma", f32), ("alpha", f32), ("reserved", i32), ("split_capacity", i64)]
+                ("sigma", f32), ("alpha", f32), ("block_threads", i32), ("split_capacity", i64)]
 
 
 class bnb_cell_bounds(C.Structure):
@@ -460,12 +460,13 @@ def bound_tuples(ds: DeviceScene, depth: int, max_extra_split: int = 4, irradian
                  fp64: bool = False, capacity: Optional[int] = None, out: Optional[CellBounds] = None,
                  ws: Optional[torch.Tensor] = None, stream=None, sync_check: bool = True,
                  with_e_hi_min: bool = False, with_e_lo: bool = True, adapt_depth: int = 0, sigma: float = 0.0,
-                 alpha: float = 0.0, split_capacity: int = 0) -> CellBounds:
+                 alpha: float = 0.0, split_capacity: int = 0, block_threads: int = 0) -> CellBounds:
     """Bound pass (one or two specular vertices).  adapt_depth > depth: adaptive subdivision
     (Sec. 6.1) down to adapt_depth, a cell stopping when its box area is below sigma or
     E_hi < alpha E_lo; split_capacity sizes the per-level split queue (0: the library default).
     irradiance: False / True, or 2 (single refraction) to intersect each bound with the
-    implicit-differentiation bound (Sec. 4.4)."""
+    implicit-differentiation bound (Sec. 4.4).  block_threads: block size of the float32 reflection
+    pass (0: the library default; see batch.autotune_bound)."""
     n_base = ds.scene.emitters.n * ds.s1.n_tris * 4 ** depth
     adaptive = adapt_depth > depth
     if adaptive and split_capacity == 0:
@@ -477,7 +478,7 @@ def bound_tuples(ds: DeviceScene, depth: int, max_extra_split: int = 4, irradian
         out = CellBounds(capacity if capacity is not None else default, ds.device, with_e_hi_min, with_e_lo)
     for _ in range(6):
         cfg = bnb_bound_cfg(depth, max_extra_split, int(irradiance), int(fp64), adapt_depth if adaptive else 0,
-                            sigma, alpha, 0, split_capacity)
+                            sigma, alpha, int(block_threads), split_capacity)
         need = bnb_bound_tuples_ws(C.byref(ds.s1), ds.s2_ref(), C.byref(ds.em), C.byref(cfg))
         if need == 0:
             raise BnbError("bnb_bound_tuples_ws: invalid configuration")

@@ -1743,10 +1743,13 @@ __device__ __forceinline__ void process_any(const BoundParams& P, int e, int t, 
 }
 
 // Refraction: the same kernel also bounds the children of queued split cells (q_in != nullptr), so
-// its long cell program is reachable from one kernel entry only.
-template <typename T, int KIND>
-__global__ void __launch_bounds__(kThreadsOf<KIND>, 1) bound_base_k(BoundParams P, const SplitItem* __restrict__ q_in,
-                                                                    const int64_t* __restrict__ q_in_count) {
+// its long cell program is reachable from one kernel entry only.  THREADS: the block size (one
+// resident block per SM), which sets the register budget per thread (65,536 / THREADS, at most
+// 255); the reflection pass is compiled for 256, 320 and 384 threads, the schedules the
+// autotuner chooses from.
+template <typename T, int KIND, int THREADS = kThreadsOf<KIND>>
+__global__ void __launch_bounds__(THREADS, 1) bound_base_k(BoundParams P, const SplitItem* __restrict__ q_in,
+                                                           const int64_t* __restrict__ q_in_count) {
   if constexpr (KIND == 1) {
     if (q_in != nullptr) {
       const int64_t n = min(*q_in_count, P.q_cap);
@@ -1761,11 +1764,11 @@ __global__ void __launch_bounds__(kThreadsOf<KIND>, 1) bound_base_k(BoundParams 
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)P.count, (unsigned long long)P.n_base);
   const int64_t per_tuple = (int64_t)1 << (2 * P.depth);
   const int64_t per_em = per_tuple * P.n_tris;
-  const int64_t stride = (int64_t)gridDim.x * kThreadsOf<KIND>;
+  const int64_t stride = (int64_t)gridDim.x * THREADS;
   const int64_t rounds = (P.n_base + stride - 1) / stride;
   for (int64_t r = 0; r < rounds; ++r) {
     __syncthreads();
-    const int64_t w = r * stride + (int64_t)blockIdx.x * kThreadsOf<KIND> + threadIdx.x;
+    const int64_t w = r * stride + (int64_t)blockIdx.x * THREADS + threadIdx.x;
     if (w < P.n_base) {
       const int e = (int)(w / per_em);
       const int64_t rr = w - (int64_t)e * per_em;
@@ -1796,9 +1799,9 @@ int grid_for_T(int64_t n, int block) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
 }
 
-template <typename T, int KIND>
+template <typename T, int KIND, int THREADS = kThreadsOf<KIND>>
 cudaError_t launch_bound_base_T(const BoundParams& p, cudaStream_t st) {
-  bound_base_k<T, KIND><<<grid_for_T<T>(p.n_base, kThreadsOf<KIND>), kThreadsOf<KIND>, 0, st>>>(p, nullptr, nullptr);
+  bound_base_k<T, KIND, THREADS><<<grid_for_T<T>(p.n_base, THREADS), THREADS, 0, st>>>(p, nullptr, nullptr);
   return cudaGetLastError();
 }
 

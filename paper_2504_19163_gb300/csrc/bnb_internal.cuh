@@ -28,6 +28,7 @@ struct BoundParams {
   int32_t kind;  // BNB_REFLECT or BNB_REFRACT
   float eta;     // refraction: eta' = incident / transmitted index
   int32_t adapt_depth;  // adaptive subdivision above this depth (0: off)
+  int32_t block_threads;  // block size of the float32 reflection base pass (0: the default, 384)
   float sigma, alpha;   // its stopping thresholds (box area, E_hi / E_lo)
   int64_t n_base;
   // outputs

@@ -272,3 +272,20 @@ def test_ffma_probe_arguments(bnb):
     for args in ((0, 256, 1, 0), (8, 33, 1, 0), (8, 2048, 1, 0), (8, 256, 0, 0), (8, 256, 1, 2)):
         assert bnb.bnb_ffma_probe(*args, 4096, None) == bnb.BNB_ERR_INVALID
     assert bnb.bnb_ffma_probe(8, 256, 1, 0, None, None) == bnb.BNB_ERR_INVALID
+
+
+def test_bound_block_threads_checked(bnb):
+    s = bnb.bnb_surface()
+    s.n_tris, s.n_verts = 8, 9
+    for f in ("px", "py", "pz", "nx", "ny", "nz", "i0", "i1", "i2"):
+        setattr(s, f, 4096)
+    em = bnb.bnb_emitters(1, 4096, 4096, 4096, 4096)
+    rec = bnb.bnb_receiver()
+    out = bnb.bnb_cell_bounds()
+    out.capacity = 1 << 20
+    out.count = out.status = 4096
+    for f in ("u_lo", "u_hi", "v_lo", "v_hi", "e_hi", "emitter", "tri0", "tri1", "cell", "flags"):
+        setattr(out, f, 4096)  # never dereferenced: the block size is refused before any launch
+    cfg = bnb.bnb_bound_cfg(1, 4, 1, 0, 0, 0.0, 0.0, 300, 0)  # not a compiled block size
+    assert bnb.bnb_bound_tuples(C.byref(s), None, C.byref(rec), C.byref(em), C.byref(cfg), C.byref(out), None, 0,
+                                None) == bnb.BNB_ERR_INVALID

@@ -139,3 +139,20 @@ def test_upper_bound_identical_without_optional_outputs(B):
     a, b = full.to_numpy(), lean.to_numpy()
     for k in ("u_lo", "u_hi", "v_lo", "v_hi", "e_hi", "emitter", "tri0", "cell", "flags"):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def test_bound_schedules_give_identical_records_and_autotune_picks_one(B):
+    """The float32 reflection pass compiled for 256, 320 and 384 threads per block: the records do not
+    depend on the block size (bit for bit), and the autotuner returns one of them."""
+    from paper_2504_19163_gb300 import batch as BA
+    sc = S.config("mirror32")
+    ds = B.DeviceScene(sc)
+    ref = B.bound_tuples(ds, sc.depth, with_e_hi_min=True).to_numpy()
+    for bt in BA.BOUND_SCHEDULES:
+        got = B.bound_tuples(ds, sc.depth, with_e_hi_min=True, block_threads=bt).to_numpy()
+        order_r = np.lexsort((ref["cell"], ref["flags"] >> np.uint32(24), ref["tri0"], ref["emitter"]))
+        order_g = np.lexsort((got["cell"], got["flags"] >> np.uint32(24), got["tri0"], got["emitter"]))
+        for k in ref:
+            assert np.array_equal(ref[k][order_r], got[k][order_g]), (bt, k)
+    entry = BA.autotune_bound(ds, sc.depth, use_cache=False)
+    assert entry["block_threads"] in BA.BOUND_SCHEDULES and len(entry["candidates"]) == 3
