@@ -682,7 +682,10 @@ def refraction_summary(dev, steps: int, peak_tflops: float, peak_measured) -> di
     sc = S.config("water420")
     ds = bnb.DeviceScene(sc, dev)
     stream = torch.cuda.current_stream(dev)
-    cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False)
+    from paper_2504_19163_gb300 import batch as BA
+    sched = BA.autotune_bound(ds, sc.depth, reps=2, use_cache=False, with_e_lo=False)
+    bt = int(sched["block_threads"])
+    cb = bnb.bound_tuples(ds, sc.depth, with_e_lo=False, block_threads=bt)
     idx = bnb.build_index(cb, grid_res=sc.grid_res)
     gamma = calibrate_gamma(bnb, ds, idx, target=4.0)
     res = bnb.sample_and_solve(ds, idx, gamma, 1)
@@ -701,7 +704,7 @@ def refraction_summary(dev, steps: int, peak_tflops: float, peak_measured) -> di
 
     def step(seed, ev):
         ev[0].record(stream)
-        bnb.bound_tuples(ds, sc.depth, out=cb, ws=cb_ws, sync_check=False)
+        bnb.bound_tuples(ds, sc.depth, out=cb, ws=cb_ws, sync_check=False, block_threads=bt)
         ev[1].record(stream)
         bnb.build_index(cb, grid_res=sc.grid_res, pre_capacity=pre_cap, capacity=pre_cap, out=idx, ws=ix_ws,
                         sync_check=False)
@@ -735,7 +738,7 @@ def refraction_summary(dev, steps: int, peak_tflops: float, peak_measured) -> di
                        "(+-0.5,+-0.5,2), pool floor z=-1, 1920x1080 shading points, depth 3 (90,316,800 cells/step), "
                        "grid 512, FP32 with outward rounding",
            "status_ok": ok, "steps": steps, "cells_per_step": n_cells, "records": n_rec, "live_records": n_live,
-           "live_finite_e_hi": n_live_finite, "tir_records": n_tir, "gamma": gamma,
+           "live_finite_e_hi": n_live_finite, "tir_records": n_tir, "gamma": gamma, "bound_schedule": sched,
            "stage_ms": {"bound": float(ms[0]), "index": float(ms[1]), "sample_solve": float(ms[2])},
            "ms_per_step": float(ms.sum()), "cells_per_s": n_cells / (float(ms.sum()) / 1e3),
            "bound_cells_per_s": n_cells / (ms[0] / 1e3), "shading_samples_per_s": n_points / (float(ms.sum()) / 1e3),

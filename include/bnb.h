@@ -112,9 +112,12 @@ typedef struct bnb_bound_cfg {
   int32_t adapt_depth;     /* 0 or depth..15 (adapt_depth + max_extra_split <= 15) */
   float sigma;             /* >= 0 */
   float alpha;             /* >= 0 */
-  int32_t block_threads;   /* block size of the float32 reflection pass (one persistent block per SM):
-                              0 (the default, 384), 256, 320 or 384; other passes ignore it.  The
-                              records do not depend on it (the autotuner picks the fastest). */
+  int32_t block_threads;   /* block size of the float32 base pass (one persistent block per SM):
+                              reflection 256, 320 or 384 (0: 384), refraction 128 or 256 (0: 256);
+                              other values of the set are ignored by the other pass, and the
+                              float64 and two-vertex passes ignore it.  The records do not depend
+                              on it (the autotuner picks the fastest); values outside {0, 128, 256,
+                              320, 384} are BNB_ERR_INVALID. */
   int64_t split_capacity;  /* split-queue entries per level (0: 4096 + n_base / 32); a level that
                               queues more raises BNB_ERR_CAPACITY */
 } bnb_bound_cfg;

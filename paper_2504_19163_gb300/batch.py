@@ -341,20 +341,24 @@ def autotune(jobs: Sequence[Job], worklist_capacity: int, reps: int = 3, device=
     return entry
 
 
-BOUND_SCHEDULES = (256, 320, 384)  # block sizes the float32 reflection bound pass is compiled for
+BOUND_SCHEDULES = (256, 320, 384)       # block sizes the float32 reflection bound pass is compiled for
+REFRACT_SCHEDULES = (128, 256)          # ... and the float32 refraction pass
 
 
 def autotune_bound(ds: bnb.DeviceScene, depth: int, reps: int = 3, use_cache: bool = True,
-                   candidates: Sequence[int] = BOUND_SCHEDULES, **bound_kw) -> dict:
+                   candidates: Optional[Sequence[int]] = None, **bound_kw) -> dict:
     """Fastest block size of the bound pass for scenes like `ds` at `depth`; cached per (device,
-    size class = log2 of the base cells).  Every candidate bounds the scene `reps` times after one
-    warm-up into the same outputs; the median CUDA-event time decides.  Only the float32 reflection
-    pass has schedules: other passes return the default (0) without timing."""
-    if ds.s2 is not None or ds.s1.kind != bnb.BNB_REFLECT or bound_kw.get("fp64"):
+    kind, size class = log2 of the base cells).  Every candidate bounds the scene `reps` times after
+    one warm-up into the same outputs; the median CUDA-event time decides.  Only the float32
+    one-vertex passes have schedules: the others return the default (0) without timing."""
+    if ds.s2 is not None or bound_kw.get("fp64"):
         return {"block_threads": 0, "ms": None, "candidates": []}
+    refract = ds.s1.kind == bnb.BNB_REFRACT
+    if candidates is None:
+        candidates = REFRACT_SCHEDULES if refract else BOUND_SCHEDULES
     n_base = ds.scene.emitters.n * ds.s1.n_tris * 4 ** depth
     name = torch.cuda.get_device_name(ds.device).replace(" ", "_")
-    key = f"{name}|bound_tuples_reflect|cells_2^{size_class(n_base)}"
+    key = f"{name}|bound_tuples_{'refract' if refract else 'reflect'}|cells_2^{size_class(n_base)}"
     if use_cache:
         hit = load_cache().get(key)
         if hit is not None:

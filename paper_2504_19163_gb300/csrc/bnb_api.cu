@@ -159,7 +159,8 @@ int32_t bnb_bound_tuples(const bnb_surface* s1, const bnb_surface* s2, const bnb
   if (s1->kind == BNB_REFRACT && !(s1->eta > 0.0f && s1->eta < 1e6f)) return BNB_ERR_INVALID;
   if (cfg->irradiance < 0 || cfg->irradiance > 2) return BNB_ERR_INVALID;
   if (cfg->irradiance == 2 && s1->kind != BNB_REFRACT) return BNB_ERR_UNSUPPORTED;
-  if (cfg->block_threads != 0 && cfg->block_threads != 256 && cfg->block_threads != 320 && cfg->block_threads != 384)
+  if (cfg->block_threads != 0 && cfg->block_threads != 128 && cfg->block_threads != 256 &&
+      cfg->block_threads != 320 && cfg->block_threads != 384)
     return BNB_ERR_INVALID;
   if (cfg->depth < 0 || cfg->depth > kMaxBaseDepth || cfg->max_extra_split < 0 || cfg->max_extra_split > kMaxExtra ||
       cfg->depth + cfg->max_extra_split > kMaxDepth || !adapt_ok(cfg))

@@ -20,6 +20,7 @@ extern template cudaError_t launch_bound_split_T<double, 1>(const BoundParams&, 
 // block-size schedules of the float32 reflection pass (bnb_bound_t256.cu, bnb_bound_t320.cu)
 extern template cudaError_t launch_bound_base_T<float, 0, 256>(const BoundParams&, cudaStream_t);
 extern template cudaError_t launch_bound_base_T<float, 0, 320>(const BoundParams&, cudaStream_t);
+extern template cudaError_t launch_bound_base_T<float, 1, 128>(const BoundParams&, cudaStream_t);  // bnb_bound_refract_t128.cu
 
 __global__ void pack_tris_k(const float* __restrict__ px, const float* __restrict__ py, const float* __restrict__ pz,
                             const float* __restrict__ nx, const float* __restrict__ ny, const float* __restrict__ nz,
@@ -53,8 +54,11 @@ cudaError_t launch_pack_tris(const bnb_surface* s, float4* out, cudaStream_t st)
 }
 
 cudaError_t launch_bound_base(const BoundParams& p, bool fp64, cudaStream_t st) {
-  if (p.kind == BNB_REFRACT)
-    return fp64 ? launch_bound_base_T<double, 1>(p, st) : launch_bound_base_T<float, 1>(p, st);
+  if (p.kind == BNB_REFRACT) {
+    if (fp64) return launch_bound_base_T<double, 1>(p, st);
+    if (p.block_threads == 128) return launch_bound_base_T<float, 1, 128>(p, st);
+    return launch_bound_base_T<float, 1>(p, st);
+  }
   if (fp64) return launch_bound_base_T<double, 0>(p, st);
   if (p.block_threads == 256) return launch_bound_base_T<float, 0, 256>(p, st);
   if (p.block_threads == 320) return launch_bound_base_T<float, 0, 320>(p, st);

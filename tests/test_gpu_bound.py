@@ -156,3 +156,19 @@ def test_bound_schedules_give_identical_records_and_autotune_picks_one(B):
             assert np.array_equal(ref[k][order_r], got[k][order_g]), (bt, k)
     entry = BA.autotune_bound(ds, sc.depth, use_cache=False)
     assert entry["block_threads"] in BA.BOUND_SCHEDULES and len(entry["candidates"]) == 3
+
+
+def test_refraction_schedules_give_identical_records(B):
+    """The float32 refraction pass compiled for 128 and 256 threads per block: identical records."""
+    from paper_2504_19163_gb300 import batch as BA
+    sc = S.config("water", n=8, depth=1)
+    ds = B.DeviceScene(sc)
+    ref = B.bound_tuples(ds, sc.depth).to_numpy()
+    for bt in BA.REFRACT_SCHEDULES:
+        got = B.bound_tuples(ds, sc.depth, block_threads=bt).to_numpy()
+        order_r = np.lexsort((ref["cell"], ref["flags"] >> np.uint32(24), ref["tri0"], ref["emitter"]))
+        order_g = np.lexsort((got["cell"], got["flags"] >> np.uint32(24), got["tri0"], got["emitter"]))
+        for k in ref:
+            assert np.array_equal(ref[k][order_r], got[k][order_g]), (bt, k)
+    entry = BA.autotune_bound(ds, sc.depth, use_cache=False)
+    assert entry["block_threads"] in BA.REFRACT_SCHEDULES
