@@ -111,12 +111,12 @@ def refract_fma_per_cell():
 REFRACT_FMA_POS, REFRACT_FMA_IRR = refract_fma_per_cell()
 
 
-# Algorithmic bytes of the HBM-bound stages: the index reads a live cell's box, E_hi, keys and flags
-# (36 B; 4 B of flags for the others) and writes 12 B (key, E~) per (grid cell, tuple) entry plus the
-# offsets; the sampling pass reads 12 B per listed entry and writes 16 B per selection (point, key,
-# P), the solve reads 72 B of geometry + 12 B of emitter per selection and writes 4 B; per point
-# 8 B of coordinates + 4 B of estimate.
-INDEX_BYTES_LIVE, INDEX_BYTES_ENTRY = 36, 12
+# Algorithmic bytes of the HBM-bound stages: the index reads a live cell's box, E_hi and flags
+# (24 B; 4 B of flags for the others), a tuple's key once (12 B), and writes 12 B (key, E~) per
+# (grid cell, tuple) entry plus the offsets; the sampling pass reads 12 B per listed entry and
+# writes 16 B per selection (point, key, P), the solve reads 72 B of geometry + 12 B of emitter per
+# selection and writes 4 B; per point 8 B of coordinates + 4 B of estimate.
+INDEX_BYTES_LIVE, INDEX_BYTES_TUPLE, INDEX_BYTES_ENTRY = 24, 12, 12
 SAMPLE_BYTES_LISTED, SOLVE_BYTES_SELECTED, SAMPLE_BYTES_POINT = 12, 16 + 72 + 12 + 4, 12
 
 
@@ -410,8 +410,9 @@ def run_gpu(args):
     n_rec = cb.n_records()
     n_live = int(((cb.flags[:n_rec] & 1) != 0).sum().item())
     n_entries = int(idx.count[0].item())
-    index_bytes = INDEX_BYTES_LIVE * n_live + 4 * (n_rec - n_live) + INDEX_BYTES_ENTRY * n_entries + \
-        8 * (sc.grid_res ** 2 + 1)
+    n_tuples = sc.emitters.n * sc.s1.n_tris
+    index_bytes = INDEX_BYTES_LIVE * n_live + 4 * (n_rec - n_live) + INDEX_BYTES_TUPLE * n_tuples + \
+        INDEX_BYTES_ENTRY * n_entries + 8 * (sc.grid_res ** 2 + 1)
     ss_bytes = SAMPLE_BYTES_LISTED * float(counters[0]) + SOLVE_BYTES_SELECTED * float(counters[1]) + \
         SAMPLE_BYTES_POINT * n_points
     stage_ms = {"bound": bound_ms, "index": float(stage[:, 1].mean()), "sample_solve": float(stage[:, 2].mean())}

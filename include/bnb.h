@@ -263,7 +263,13 @@ int32_t bnb_bound_tuples_noalloc(const bnb_surface *s1, const bnb_surface *s2, c
 /* Bound storage (Sec. 6.1) over the records of one bnb_bound_tuples call (its
  * host fields must be set).  m multiplies the bound (Eq. eq_pertuple_b; the
  * paper uses m = 1).  pre_capacity: pre-merge (grid cell, tuple) entries the
- * workspace holds; bnb_build_index_ws(cells, grid_res, pre_capacity) bytes. */
+ * workspace holds; bnb_build_index_ws(cells, grid_res, pre_capacity) bytes
+ * (32 B per pre-merge entry plus 40 B per grid cell).  The pre-merge entries are
+ * kept in 64 partitions of pre_capacity / 64 (tuple T, or a record emitted on
+ * its own, in the partition given by a hash of T); out->count[1] reports 64 x
+ * the largest partition's count, the pre_capacity these records need (it
+ * depends on the records only).  Entries that do not fit are dropped and status
+ * is BNB_ERR_CAPACITY. */
 int32_t bnb_build_index(const bnb_cell_bounds *cells, float m, int64_t pre_capacity, bnb_index *out,
                         void *ws, size_t ws_bytes, void *stream);
 size_t bnb_build_index_ws(const bnb_cell_bounds *cells, int32_t grid_res, int64_t pre_capacity);

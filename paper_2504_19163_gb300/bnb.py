@@ -529,7 +529,7 @@ def build_index(cells: CellBounds, grid_res: int = 512, m: float = 1.0, pre_capa
         pre = max(pre, int(out.count[1].item()) + 1024)
         cap = max(cap, int(out.count[0].item()) + 1024, pre)
         free, _ = torch.cuda.mem_get_info(dev)
-        if (pre * 28 + cap * 12) > free:
+        if (pre * 32 + cap * 12) > free:
             raise BnbError(f"bnb_build_index: needs {pre} pre-merge and {cap} index entries, more than the "
                            f"free device memory ({free} bytes)")
         out = None

@@ -117,3 +117,35 @@ def test_index_of_nothing(B):
     torch.cuda.synchronize()
     off, key, et = idx.to_numpy()
     assert off.shape[0] == 32 * 32 + 1 and off.max() == 0 and key.shape[0] == 0
+
+
+@pytest.mark.parametrize("n_emitters,vary_t1", [(1, False), (4, False), (400, False), (3, True)])
+def test_index_direct_mode_crowded(B, orc, n_emitters, vary_t1):
+    """No per-record emission (no split children, every footprint within the merge tile), so the
+    per-cell ordering writes the CSR directly; grid cells of <= 128 (rank), 129..512 (warp bitonic
+    sort), 513..1024 (block sort) and > 1024 entries; keys spanning < 2^32, one second-triangle
+    field over < 256 emitters, and neither (400 emitters, or varied second triangles), which
+    select the 32- and 64-bit orderings."""
+    rec = S.synthetic_cell_records(5000, 1, n_tris=20000, n_emitters=n_emitters, n_overflow=0, seed=21 + n_emitters,
+                                   grid_res=64)
+    rng = np.random.default_rng(n_emitters)
+    if vary_t1:
+        rec["tri1"] = np.repeat(rng.integers(-1, 5000, 5000), 4).astype(np.int32)
+    group = rng.random(5000)
+    for sel, lo, hi in ((group < 0.15, 0.1, 0.3), ((group >= 0.15) & (group < 0.4), 0.5, 0.7),
+                        ((group >= 0.4) & (group < 0.46), 0.75, 0.9)):
+        r = np.repeat(sel, 4)
+        for k in ("u_lo", "v_lo"):
+            rec[k][r] = np.float32(lo)
+        for k in ("u_hi", "v_hi"):
+            rec[k][r] = np.float32(hi)
+        rec["flags"][r] = (rec["flags"][r] & np.uint32(0xFF000000)) | np.uint32(1)
+    cb = upload_records(B, rec)
+    idx = B.build_index(cb, grid_res=64)
+    torch.cuda.synchronize()
+    assert int(idx.status.item()) == 0
+    off, key, et = idx.to_numpy()
+    n_per = np.diff(off)
+    for lo, hi in ((1, 128), (129, 512), (513, 1024), (1025, 1 << 40)):
+        assert np.any((n_per >= lo) & (n_per <= hi)), (lo, hi)
+    assert_same_index((off, key, et), oracle_index(orc, rec, 64))
