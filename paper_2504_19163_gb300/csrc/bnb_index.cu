@@ -270,14 +270,91 @@ __global__ void __launch_bounds__(32 * kMergeWarps) tuple_merge_k(IndexParams P)
   }
 }
 
+// One tuple of at most 64 records held two per lane (record lane + 32 c in slot c): footprint,
+// rasterization into the warp's tile with the max E_hi per grid cell, and emission of one entry
+// per covered grid cell.  The key comes from the tuple's first record (all 4^D records of a tuple
+// share it) unless that record is dead.
+__device__ __forceinline__ void merge_tuple64(const IndexParams& P, int64_t T, int64_t r0, uint32_t* loc,
+                                              const float (&ulo)[2], const float (&uhi)[2], const float (&vlo)[2],
+                                              const float (&vhi)[2], const float (&eh)[2], const uint32_t (&fl)[2],
+                                              int e0, int t0, int t1) {
+  const int lane = threadIdx.x & 31;
+  int ci0[2], ci1[2], cj0[2], cj1[2];
+  int bi0 = 1 << 30, bi1 = -1, bj0 = 1 << 30, bj1 = -1;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    ci0[c] = grid_col(ulo[c], P.G);
+    ci1[c] = grid_col(uhi[c], P.G);
+    cj0[c] = grid_col(vlo[c], P.G);
+    cj1[c] = grid_col(vhi[c], P.G);
+    if (fl[c] & BNB_CELL_LIVE) {
+      bi0 = min(bi0, ci0[c]);
+      bi1 = max(bi1, ci1[c]);
+      bj0 = min(bj0, cj0[c]);
+      bj1 = max(bj1, cj1[c]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bi0 = min(bi0, __shfl_xor_sync(0xffffffffu, bi0, o));
+    bi1 = max(bi1, __shfl_xor_sync(0xffffffffu, bi1, o));
+    bj0 = min(bj0, __shfl_xor_sync(0xffffffffu, bj0, o));
+    bj1 = max(bj1, __shfl_xor_sync(0xffffffffu, bj1, o));
+  }
+  if (bi1 < 0) return;  // no live record in this tuple
+  const int W = bi1 - bi0 + 1, H = bj1 - bj0 + 1;
+  if ((int64_t)W * H > kMergeTile) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      if (fl[c] & BNB_CELL_LIVE) emit_record(P, r0 + lane + 32 * c);
+    return;
+  }
+  for (int k = lane; k < W * H; k += 32) loc[k] = 0u;
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (!(fl[c] & BNB_CELL_LIVE)) continue;
+    // E_hi >= 0: the float bit pattern orders like the value; +1 marks "covered".
+    const uint32_t bits = __float_as_uint(fmaxf(eh[c], 0.0f)) + 1u;
+    for (int j = cj0[c] - bj0; j <= cj1[c] - bj0; ++j)
+      for (int i = ci0[c] - bi0; i <= ci1[c] - bi0; ++i) atomicMax(&loc[j * W + i], bits);
+  }
+  __syncwarp();
+  // the key of the tuple's first live record (the first record's, loaded above, unless it is dead)
+  uint64_t key = tuple_key(e0, t0, t1);
+  const unsigned l0 = __ballot_sync(0xffffffffu, (fl[0] & BNB_CELL_LIVE) != 0u);
+  const unsigned l1 = __ballot_sync(0xffffffffu, (fl[1] & BNB_CELL_LIVE) != 0u);
+  const int first = l0 ? __ffs(l0) - 1 : 32 + __ffs(l1) - 1;
+  if (first != 0) key = tuple_key(P.emitter[r0 + first], P.tri0[r0 + first], P.tri1[r0 + first]);
+  int cnt = 0;
+  for (int k = lane; k < W * H; k += 32) cnt += loc[k] != 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  const int part = part_of(T);
+  long long base = 0;
+  if (lane == 0) base = (long long)reserve(P, part, cnt);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  int done = 0;
+  for (int k0 = 0; k0 < W * H; k0 += 32) {
+    const int k = k0 + lane;
+    const uint32_t b = k < W * H ? loc[k] : 0u;
+    const unsigned m = __ballot_sync(0xffffffffu, b != 0u);
+    if (b != 0u) {
+      const int pos = done + __popc(m & ((1u << lane) - 1u));
+      const int g = (bj0 + k / W) * P.G + (bi0 + k % W);
+      emit(P, part, base + pos, g, key, __uint_as_float(b - 1u));
+    }
+    done += __popc(m);
+  }
+  __syncwarp();
+}
+
 // Tuples of at most 64 records: each lane holds two records in registers, loaded in one round
 // (box, E_hi and flags of both at once), so the footprint and the rasterization need no second
-// read; the tuple's key is loaded beside them from its first record (all 4^D records of a tuple
-// share it).
+// read; the tuple's key is loaded beside them from its first record.
 __global__ void __launch_bounds__(32 * kMergeWarps) tuple_merge64_k(IndexParams P) {
   __shared__ uint32_t tile[kMergeWarps][kMergeTile];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t* loc = tile[wid];
   const int cpt = P.cells_per_tuple;
   for (int64_t T = (int64_t)blockIdx.x * kMergeWarps + wid; T < P.n_tuples; T += (int64_t)gridDim.x * kMergeWarps) {
     const int64_t r0 = T * cpt;
@@ -294,76 +371,63 @@ __global__ void __launch_bounds__(32 * kMergeWarps) tuple_merge64_k(IndexParams 
       vhi[c] = P.v_hi[r];
       eh[c] = P.e_hi[r];
     }
-    const int e0 = P.emitter[r0], t0 = P.tri0[r0], t1 = P.tri1[r0];
-    int ci0[2], ci1[2], cj0[2], cj1[2];
-    int bi0 = 1 << 30, bi1 = -1, bj0 = 1 << 30, bj1 = -1;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      ci0[c] = grid_col(ulo[c], P.G);
-      ci1[c] = grid_col(uhi[c], P.G);
-      cj0[c] = grid_col(vlo[c], P.G);
-      cj1[c] = grid_col(vhi[c], P.G);
-      if (fl[c] & BNB_CELL_LIVE) {
-        bi0 = min(bi0, ci0[c]);
-        bi1 = max(bi1, ci1[c]);
-        bj0 = min(bj0, cj0[c]);
-        bj1 = max(bj1, cj1[c]);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      bi0 = min(bi0, __shfl_xor_sync(0xffffffffu, bi0, o));
-      bi1 = max(bi1, __shfl_xor_sync(0xffffffffu, bi1, o));
-      bj0 = min(bj0, __shfl_xor_sync(0xffffffffu, bj0, o));
-      bj1 = max(bj1, __shfl_xor_sync(0xffffffffu, bj1, o));
-    }
-    if (bi1 < 0) continue;  // no live record in this tuple
-    const int W = bi1 - bi0 + 1, H = bj1 - bj0 + 1;
-    if ((int64_t)W * H > kMergeTile) {
-#pragma unroll
-      for (int c = 0; c < 2; ++c)
-        if (fl[c] & BNB_CELL_LIVE) emit_record(P, r0 + lane + 32 * c);
-      continue;
-    }
-    for (int k = lane; k < W * H; k += 32) loc[k] = 0u;
-    __syncwarp();
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      if (!(fl[c] & BNB_CELL_LIVE)) continue;
-      // E_hi >= 0: the float bit pattern orders like the value; +1 marks "covered".
-      const uint32_t bits = __float_as_uint(fmaxf(eh[c], 0.0f)) + 1u;
-      for (int j = cj0[c] - bj0; j <= cj1[c] - bj0; ++j)
-        for (int i = ci0[c] - bi0; i <= ci1[c] - bi0; ++i) atomicMax(&loc[j * W + i], bits);
-    }
-    __syncwarp();
-    // the key of the tuple's first live record (the first record's, loaded above, unless it is dead)
-    uint64_t key = tuple_key(e0, t0, t1);
-    const unsigned l0 = __ballot_sync(0xffffffffu, (fl[0] & BNB_CELL_LIVE) != 0u);
-    const unsigned l1 = __ballot_sync(0xffffffffu, (fl[1] & BNB_CELL_LIVE) != 0u);
-    const int first = l0 ? __ffs(l0) - 1 : 32 + __ffs(l1) - 1;
-    if (first != 0) key = tuple_key(P.emitter[r0 + first], P.tri0[r0 + first], P.tri1[r0 + first]);
-    int cnt = 0;
-    for (int k = lane; k < W * H; k += 32) cnt += loc[k] != 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    const int part = part_of(T);
-    long long base = 0;
-    if (lane == 0) base = (long long)reserve(P, part, cnt);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    int done = 0;
-    for (int k0 = 0; k0 < W * H; k0 += 32) {
-      const int k = k0 + lane;
-      const uint32_t b = k < W * H ? loc[k] : 0u;
-      const unsigned m = __ballot_sync(0xffffffffu, b != 0u);
-      if (b != 0u) {
-        const int pos = done + __popc(m & ((1u << lane) - 1u));
-        const int g = (bj0 + k / W) * P.G + (bi0 + k % W);
-        emit(P, part, base + pos, g, key, __uint_as_float(b - 1u));
-      }
-      done += __popc(m);
-    }
-    __syncwarp();
+    merge_tuple64(P, T, r0, tile[wid], ulo, uhi, vlo, vhi, eh, fl, P.emitter[r0], P.tri0[r0], P.tri1[r0]);
   }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Tuples of exactly 64 records with 16-byte aligned record arrays: each warp double-buffers its
+// tuples' records (box, E_hi, flags: 6 x 256 B) in shared memory with cp.async, so the next
+// tuple's records are in flight while this one is rasterized.
+__global__ void __launch_bounds__(32 * kMergeWarps) tuple_merge64_async_k(IndexParams P) {
+  __shared__ uint32_t tile[kMergeWarps][kMergeTile];
+  __shared__ __align__(16) float rec[kMergeWarps][2][6][64];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t step = (int64_t)gridDim.x * kMergeWarps;
+  auto fetch = [&](int64_t T, int b) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {  // 6 arrays x 16 chunks of 16 B, 3 chunks per lane
+      const int c = lane + 32 * q, a = c >> 4, o = (c & 15) * 4;
+      const float* g = a == 0 ? P.u_lo
+                              : a == 1 ? P.u_hi
+                                       : a == 2 ? P.v_lo : a == 3 ? P.v_hi : a == 4 ? P.e_hi : (const float*)P.flags;
+      cp_async16(&rec[wid][b][a][o], g + T * 64 + o);
+    }
+  };
+  int64_t T = (int64_t)blockIdx.x * kMergeWarps + wid;
+  if (T < P.n_tuples) fetch(T, 0);
+  cp_async_commit();
+  for (int b = 0; T < P.n_tuples; T += step, b ^= 1) {
+    if (T + step < P.n_tuples) fetch(T + step, b ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();  // this tuple's group has landed (the next one may be in flight)
+    __syncwarp();
+    const int64_t r0 = T * 64;
+    float ulo[2], uhi[2], vlo[2], vhi[2], eh[2];
+    uint32_t fl[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int k = lane + 32 * c;
+      ulo[c] = rec[wid][b][0][k];
+      uhi[c] = rec[wid][b][1][k];
+      vlo[c] = rec[wid][b][2][k];
+      vhi[c] = rec[wid][b][3][k];
+      eh[c] = rec[wid][b][4][k];
+      fl[c] = __float_as_uint(rec[wid][b][5][k]);
+    }
+    merge_tuple64(P, T, r0, tile[wid], ulo, uhi, vlo, vhi, eh, fl, P.emitter[r0], P.tri0[r0], P.tri1[r0]);
+    __syncwarp();  // every lane has read buffer b before it is refilled
+  }
+  cp_async_wait<0>();
 }
 
 __global__ void overflow_k(IndexParams P) {
@@ -1022,7 +1086,11 @@ cudaError_t launch_build_index(const bnb_cell_bounds* c, float m, int64_t pre_ca
   const int sms = sm_count();
   if (P.n_tuples > 0) {
     const int64_t blocks = std::min<int64_t>((P.n_tuples + kMergeWarps - 1) / kMergeWarps, (int64_t)sms * 64);
-    if (P.cells_per_tuple <= 64)
+    auto al16 = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
+    if (P.cells_per_tuple == 64 && al16(P.u_lo) && al16(P.u_hi) && al16(P.v_lo) && al16(P.v_hi) && al16(P.e_hi) &&
+        al16(P.flags))
+      tuple_merge64_async_k<<<(unsigned)blocks, 32 * kMergeWarps, 0, st>>>(P);
+    else if (P.cells_per_tuple <= 64)
       tuple_merge64_k<<<(unsigned)blocks, 32 * kMergeWarps, 0, st>>>(P);
     else
       tuple_merge_k<<<(unsigned)blocks, 32 * kMergeWarps, 0, st>>>(P);
