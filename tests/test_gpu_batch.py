@@ -297,3 +297,44 @@ def test_serving_prefetch_builds_scenes_in_one_batch(B):
             assert same_bits(r.E, mixed[r.rid]), r.rid
     finally:
         cache.close()
+
+
+def test_batched_bound_encloses_the_single_pass_split_cells(B, BA):
+    """Steep water at depth 2: the single pass splits the cells whose position denominator has no
+    certified sign (up to 4 extra levels); the batched pass takes no extra level and bounds such a
+    cell at once (reciprocal rule or the receiver box).  Where the single pass did not split, the
+    records are bit-identical; where it did, the batched record is live and holds the box and the
+    E_hi of every live descendant the single pass produced (looser, still a valid bound)."""
+    sc = S.config("water", n=8, depth=2, steep=0.3, lights=[(0.8, 0.2, 0.6)])
+    ds = B.DeviceScene(sc)
+    nb = sc.emitters.n * sc.s1.n_tris * 4 ** sc.depth
+    out = B.CellBounds(nb, ds.device)
+    BA.bound_batched([(ds, sc.depth, out)])
+    single = B.bound_tuples(ds, sc.depth)
+    torch.cuda.synchronize()
+    assert int(out.status.item()) == 0 and int(single.status.item()) == 0
+    a, s = out.to_numpy(), single.to_numpy()
+    assert a["u_lo"].shape[0] == nb and s["u_lo"].shape[0] > nb
+    split = (s["flags"][:nb] & 2) != 0
+    assert split.sum() > 20
+    keep = ~split
+    for k in ("u_lo", "u_hi", "v_lo", "v_hi", "e_hi"):
+        assert np.array_equal(a[k][keep].view(np.uint32), s[k][:nb][keep].view(np.uint32)), k
+    for k in ("emitter", "tri0", "cell", "flags"):
+        assert np.array_equal(a[k][keep], s[k][:nb][keep]), k
+    # descendants of each split base cell: same (emitter, triangle), cell id prefix = the base id
+    d = s["flags"][nb:] >> np.uint32(24)
+    live = (s["flags"][nb:] & 1) != 0
+    anc = s["cell"][nb:].astype(np.int64) >> (2 * (d.astype(np.int64) - sc.depth))
+    base_of = {(int(e), int(t), int(c)): i for i, (e, t, c) in
+               enumerate(zip(a["emitter"], a["tri0"], a["cell"]))}
+    checked = 0
+    for j in np.nonzero(live)[0]:
+        i = base_of[(int(s["emitter"][nb + j]), int(s["tri0"][nb + j]), int(anc[j]))]
+        assert split[i]
+        assert a["flags"][i] & 1, i
+        assert a["u_lo"][i] <= s["u_lo"][nb + j] and a["u_hi"][i] >= s["u_hi"][nb + j]
+        assert a["v_lo"][i] <= s["v_lo"][nb + j] and a["v_hi"][i] >= s["v_hi"][nb + j]
+        assert a["e_hi"][i] >= s["e_hi"][nb + j]
+        checked += 1
+    assert checked > 20
