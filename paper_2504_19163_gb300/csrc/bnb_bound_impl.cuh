@@ -1207,7 +1207,7 @@ __device__ __forceinline__ void refract_irradiance(const Leaves<T>& L, const TP<
     tp_zero(dt[c].p1);
     mac_s<true>(dt[c].p1, T(1), L.N[c]);
   }
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < 2; ++j) {
     // d(n.n) = 2 n.dn, d(d0.n) = dx.n + d0.dn, d(d0.d0) = 2 d0.dx   (degree 1)
     TP<T, 1> dNN, dDN, dSS;
@@ -1265,7 +1265,7 @@ __device__ __forceinline__ void refract_irradiance(const Leaves<T>& L, const TP<
   wp_zero(Qw);
   wp_zero(Aw);
   wp_zero(Bw);
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < 2; ++j) {
     wp_zero(Qt[j]);
     wp_zero(At[j]);
@@ -1278,7 +1278,7 @@ __device__ __forceinline__ void refract_irradiance(const Leaves<T>& L, const TP<
     wp_mac_p(Aw, dt[c], hu[c]);
     wp_mac_p(Bw, dt[c], hv[c]);
   }
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < 2; ++j) {
     const TP<T, 0> dhu[3] = {cross_comp<T>(e2[1], L.DX[j][2].c[0], e2[2], L.DX[j][1].c[0]),
                              cross_comp<T>(e2[2], L.DX[j][0].c[0], e2[0], L.DX[j][2].c[0]),
@@ -1380,7 +1380,9 @@ __device__ __forceinline__ void refract_irradiance(const Leaves<T>& L, const TP<
   scale2(beta4);
   T mn = F::inf(), mx = -F::inf();
   int sm0 = 0;
-#pragma unroll
+  // the face loops stay rolled: one copy of their long bodies keeps the program within reach of
+  // the instruction caches (unrolled, the four copies made the kernel wait on instruction fetch)
+#pragma unroll 1
   for (int j = 0; j < 2; ++j) {
     TP<T, 4> Wj;
     tp_zero(Wj);
@@ -1409,7 +1411,7 @@ __device__ __forceinline__ void refract_irradiance(const Leaves<T>& L, const TP<
     tp_zero(Nb);
     mac(Nb, Q3j, beta4);
     renorm(Nb);
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < 2; ++k) {
       TP<T, 17> Nm;
       tp_zero(Nm);
@@ -1589,7 +1591,7 @@ __device__ __forceinline__ void process_cell_refract(const BoundParams& P, int e
   // the two xi faces: W_j = a beta + b + d_j, d~ = TG - W_j n, Q, A = d~.h_u, B = d~.h_v
   TP<T, 5> Qf[2];
   TP<T, 6> Af[2], Bf[2];
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < 2; ++j) {
     TP<T, 4> Wj;
     tp_zero(Wj);
@@ -1655,7 +1657,7 @@ __device__ __forceinline__ void process_cell_refract(const BoundParams& P, int e
     }
   }
   T umn = F::inf(), umx = -F::inf(), vmn = F::inf(), vmx = -F::inf();
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < 2; ++j) {
     TP<T, 6> Q6;
     elevate(Q6, Qf[j]);
