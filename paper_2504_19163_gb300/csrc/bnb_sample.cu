@@ -10,7 +10,9 @@
 //                     packed greedily into groups of probability sum <= 1 and
 //                     one draw per group selects at most one of its tuples.
 //   scan              -> worklist offsets (point order, then key order).
-//   sample_k (fill)   the same draws, writing (point, key, P).
+//   sample_k (fill)   the same selections, writing (point, key, P): the count pass keeps
+//                     the list positions of a point's first kSelCache selections,
+//                     so only points with more selections walk their list again.
 //   solve32_k         per selected tuple: Newton's method in T1's barycentric
 //                     coordinates from the centroid (deterministic init), float32
 //                     damped steps; tuples left with a possible root are listed.
@@ -50,7 +52,10 @@ struct SampleParams {
   int64_t* sel_point;  // optional, per selection (worklist order)
   uint64_t* sel_key;   // optional, per selection
   int32_t bins;        // 1: bin-packed selection (one draw per group), 0: one draw per tuple
+  int32_t* sel_cache;  // [kSelCache][n_points]: list positions (from the cell's start) of the selections
 };
+
+constexpr int kSelCache = 8;
 
 template <bool FILL>
 __global__ void __launch_bounds__(256) sample_k(SampleParams P) {
@@ -62,6 +67,26 @@ __global__ void __launch_bounds__(256) sample_k(SampleParams P) {
     const int64_t e = min(P.offsets[g + 1], P.index_capacity);
     int64_t cnt = 0;
     int64_t out = FILL ? P.woff[p] : 0;
+    if (FILL) {
+      const int64_t c = P.n_sel[p];
+      if (c <= kSelCache) {  // the count pass kept every selection's list position
+        for (int q = 0; q < (int)c; ++q) {
+          const int64_t j = s + P.sel_cache[(int64_t)q * P.n_points + p];
+          const uint64_t k = P.key[j];
+          if (out < P.wl_cap) {
+            P.wl_point[out] = p;
+            P.wl_key[out] = k;
+            P.wl_p[out] = fminf(__fmul_ru(P.gamma, P.etilde[j]), 1.0f);
+            if (P.sel_point) P.sel_point[out] = p;
+            if (P.sel_key) P.sel_key[out] = k;
+          } else {
+            raise_status(P.status, BNB_ERR_CAPACITY);
+          }
+          ++out;
+        }
+        continue;
+      }
+    }
     // bins: the current group's running probability sum and draw (groups are runs of the list)
     float acc = 0.0f, rb = 0.0f;
     bool open = false;
@@ -94,6 +119,8 @@ __global__ void __launch_bounds__(256) sample_k(SampleParams P) {
             raise_status(P.status, BNB_ERR_CAPACITY);
           }
           ++out;
+        } else if (cnt < kSelCache) {
+          P.sel_cache[cnt * P.n_points + p] = (int32_t)(j - s);
         }
         ++cnt;
       }
@@ -369,6 +396,7 @@ struct SampleWs {
   int64_t* pl_count;
   int64_t* pl_idx;
   float *pl_u, *pl_v;
+  int32_t* sel_cache;
   void* scan;
   size_t bytes;
 };
@@ -393,6 +421,7 @@ static SampleWs carve_sample_ws(void* base, int64_t n_tris, int64_t n_tris2, int
   w.pl_idx = (int64_t*)take((size_t)wl_cap * 8);
   w.pl_u = (float*)take((size_t)wl_cap * 4);
   w.pl_v = (float*)take((size_t)wl_cap * 4);
+  w.sel_cache = (int32_t*)take((size_t)n_points * kSelCache * 4);
   w.scan = take(scan_ws_bytes(n_points));
   w.bytes = o;
   return w;
@@ -437,6 +466,7 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2
   P.sel_point = stats->sel_point;
   P.sel_key = stats->sel_key;
   P.bins = cfg->bins;
+  P.sel_cache = w.sel_cache;
   const int64_t pblocks = std::min<int64_t>((n_points + 255) / 256, (int64_t)sms * 32);
   sample_k<false><<<(unsigned)pblocks, 256, 0, st>>>(P);
   if ((e = launch_exclusive_scan(w.n_sel, w.woff, n_points, w.scan, st)) != cudaSuccess) return e;
