@@ -955,8 +955,13 @@ __device__ __forceinline__ void process_cell(const BoundParams& P, int e, int t,
     mac<true>(Z, DQ[1], DB[0]);
     renorm(Z);
     mac(M, Q, X);
-    mac<true>(M, B, Y);
-    mac<true>(M, A, Z);
+    // B Y and A Z (the largest products) as one rolled loop, negated copies of B and A
+#pragma unroll 1
+    for (int t = 0; t < 2; ++t) {
+      TP<T, 4> a = t ? A : B;
+      negate(a);
+      mac(M, a, t ? Z : Y);
+    }
   }
   renorm(M);
   const int sm = cert_sign(M);
@@ -1172,6 +1177,12 @@ __device__ __forceinline__ void wp_mac_p(WPr<T, M + N>& r, const WPr<T, M>& a, c
 }
 
 template <typename T, int N>
+__device__ __forceinline__ void wp_negate(WPr<T, N>& r) {  // exact: coefficients only
+  negate(r.p0);
+  negate(r.p1);
+}
+
+template <typename T, int N>
 __device__ __forceinline__ void wp_renorm(WPr<T, N>& r) {
   renorm(r.p0);
   renorm(r.p1);
@@ -1315,32 +1326,43 @@ __device__ __forceinline__ void refract_irradiance(const Leaves<T>& L, const TP<
   wp_renorm(Qw);
   wp_renorm(Aw);
   wp_renorm(Bw);
-  // M' = Q (A1 B2 - A2 B1) - B (A1 Q2 - A2 Q1) - A (Q1 B2 - Q2 B1)
+  // M' = Q (A1 B2 - A2 B1) - B (A1 Q2 - A2 Q1) - A (Q1 B2 - Q2 B1).  The two products of each
+  // difference run as one rolled loop, the subtracted one through an exactly negated copy of an
+  // operand (the same FMAs, term for term), so each product shape is compiled once.
+  WPr<T, 10> X;
+  wp_zero(X);
+#pragma unroll 1
+  for (int t = 0; t < 2; ++t) {
+    WPr<T, 5> b = Bt[1 - t];
+    if (t) wp_negate(b);
+    wp_mac(X, At[t], b, beta);
+  }
+  wp_renorm(X);
+  WPr<T, 9> Y, Z;
+  wp_zero(Y);
+  wp_zero(Z);
+#pragma unroll 1
+  for (int t = 0; t < 2; ++t) {
+    WPr<T, 4> q = Qt[1 - t];
+    if (t) wp_negate(q);
+    wp_mac(Y, At[t], q, beta);
+  }
+#pragma unroll 1
+  for (int t = 0; t < 2; ++t) {
+    WPr<T, 5> b = Bt[1 - t];
+    if (t) wp_negate(b);
+    wp_mac(Z, Qt[t], b, beta);
+  }
+  wp_renorm(Y);
+  wp_renorm(Z);
   WPr<T, 13> Mp;
   wp_zero(Mp);
-  {
-    WPr<T, 10> X;
-    wp_zero(X);
-    wp_mac(X, At[0], Bt[1], beta);
-    wp_mac<true>(X, At[1], Bt[0], beta);
-    wp_renorm(X);
-    wp_mac(Mp, Qw, X, beta);
-  }
-  {
-    WPr<T, 9> Y;
-    wp_zero(Y);
-    wp_mac(Y, At[0], Qt[1], beta);
-    wp_mac<true>(Y, At[1], Qt[0], beta);
-    wp_renorm(Y);
-    wp_mac<true>(Mp, Bw, Y, beta);
-  }
-  {
-    WPr<T, 9> Z;
-    wp_zero(Z);
-    wp_mac(Z, Qt[0], Bt[1], beta);
-    wp_mac<true>(Z, Qt[1], Bt[0], beta);
-    wp_renorm(Z);
-    wp_mac<true>(Mp, Aw, Z, beta);
+  wp_mac(Mp, Qw, X, beta);
+#pragma unroll 1
+  for (int t = 0; t < 2; ++t) {
+    WPr<T, 4> a = t ? Aw : Bw;
+    wp_negate(a);
+    wp_mac(Mp, a, t ? Z : Y, beta);
   }
   wp_renorm(Mp);
   WPr<T, 9> Q3;
