@@ -40,8 +40,24 @@ __device__ __forceinline__ int nsx(int n) { return (n + 1) * (n + 2) / 2; }
 __device__ __forceinline__ int tsz(int n, int p, int q) { return nsx(n) * (p + 1) * (q + 1); }
 __device__ __forceinline__ int sidx_of(int n, int g1, int g2) { return g1 * (n + 1) - g1 * (g1 - 1) / 2 + g2; }
 
-// Small binomials and multinomials (exact in double).
+// Small binomials and multinomials (exact in double): C(n, k) for n < 32 from a table built at
+// compile time by Pascal's rule (integers below 2^53, so every sum is exact), else the product
+// formula, whose every partial value is an integer too.
+struct BinomTable {
+  double v[32][32];
+};
+constexpr BinomTable binom_table() {
+  BinomTable t{};
+  for (int n = 0; n < 32; ++n) {
+    t.v[n][0] = 1.0;
+    for (int k = 1; k <= n; ++k) t.v[n][k] = t.v[n - 1][k - 1] + (k < n ? t.v[n - 1][k] : 0.0);
+  }
+  return t;
+}
+__device__ const BinomTable g_binom = binom_table();
+
 __device__ __forceinline__ double dbinom(int n, int k) {
+  if (n < 32) return __ldg(&g_binom.v[n][k]);
   double r = 1.0;
   for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
   return r;
@@ -105,6 +121,7 @@ __device__ void tmul(Ten& r, const Ten& a, const double* bc, int bn, int bp, int
     *r.err = 1;
     return;
   }
+  const double isgn = 1.0 / sgn;
   for (int o = lane; o < rs; o += 32) {
     const int si = o / rbox, bx = o - si * rbox;
     const int i = bx / (rq + 1), j = bx - i * (rq + 1);
@@ -114,7 +131,9 @@ __device__ void tmul(Ten& r, const Ten& a, const double* bc, int bn, int bp, int
       ++g1;
     }
     const int g2 = t;
-    double s = acc ? r.c[o] : 0.0;
+    // sgn is +-1 or +-2: scaling by it is exact and commutes with rounding, so the chain runs on
+    // s / sgn with the plain products and is scaled back once (the same value as scaling each term)
+    double s = acc ? r.c[o] * isgn : 0.0;
     for (int a1 = max(0, g1 - bn); a1 <= min(g1, a.n); ++a1) {
       const int b1 = g1 - a1;
       for (int a2 = max(0, g2 - (bn - b1)); a2 <= min(g2, a.n - a1); ++a2) {
@@ -127,12 +146,12 @@ __device__ void tmul(Ten& r, const Ten& a, const double* bc, int bn, int bp, int
           for (int ja = max(0, j - bq); ja <= min(j, a.q); ++ja) {
             const int jb = j - ja;
             const double bv = bc ? bc[bsi * bbox + ib * (bq + 1) + jb] : wb * dbinom(bp, ib) * dbinom(bq, jb);
-            s = fma(sgn * ap[ia * (a.q + 1) + ja], bv, s);
+            s = fma(ap[ia * (a.q + 1) + ja], bv, s);
           }
         }
       }
     }
-    r.c[o] = s;
+    r.c[o] = s * sgn;
   }
   __syncwarp();
   const int K = nsx(min(a.n, bn)) * (min(a.p, bp) + 1) * (min(a.q, bq) + 1);
