@@ -467,6 +467,8 @@ def run_gpu(args):
     if args.adaptive_steps > 0 and rank == 0 and world == 1 and not args.emitters:
         try:
             line["adaptive"] = adaptive_summary(dev, args.adaptive_steps)
+            if args.adaptive_sweep_steps > 0:
+                line["adaptive_sweep"] = adaptive_sweep(dev, args.adaptive_sweep_steps)
         except Exception as ex:  # reported in the line; the bound benchmark above stands
             line["adaptive"] = {"error": f"{type(ex).__name__}: {ex}"}
     if args.implicit_steps > 0 and rank == 0 and world == 1 and not args.emitters:
@@ -856,18 +858,19 @@ def implicit_summary(dev, steps: int) -> dict:
             "bounds_halved_or_better": tighter, "infinite_to_finite": inf_to_finite}
 
 
-def adaptive_summary(dev, steps: int) -> dict:
+def adaptive_summary(dev, steps: int, sigma: float = ADAPT["sigma"], alpha: float = ADAPT["alpha"]) -> dict:
     """Adaptive subdivision (Sec. 6.1) on the benchmark mirror: every triangle and light sample
     starts as one cell and is subdivided down to depth 6 until its receiver box has area below
-    1e-6 (a quarter of a 512^2 grid cell) or E_hi < 2 E_lo (the paper's alpha for single
-    scattering); then the index and the rendering pass at E|S| = 4.  Timed like the main steps."""
+    sigma (1e-6: a quarter of a 512^2 grid cell) or E_hi < alpha E_lo (2: the paper's alpha for
+    single scattering); then the index and the rendering pass at E|S| = 4.  Timed like the main
+    steps."""
     import torch
     from paper_2504_19163_gb300 import bnb
     from paper_2504_19163_gb300 import scenes as S
     sc = S.config("mirror256")
     ds = bnb.DeviceScene(sc, dev)
     stream = torch.cuda.current_stream(dev)
-    kw = dict(adapt_depth=ADAPT["adapt_depth"], sigma=ADAPT["sigma"], alpha=ADAPT["alpha"], with_e_lo=False)
+    kw = dict(adapt_depth=ADAPT["adapt_depth"], sigma=sigma, alpha=alpha, with_e_lo=False)
     cb = bnb.bound_tuples(ds, ADAPT["depth"], **kw)
     split_cap = cb.capacity
     idx = bnb.build_index(cb, grid_res=sc.grid_res)
@@ -876,7 +879,7 @@ def adaptive_summary(dev, steps: int) -> dict:
     torch.cuda.synchronize()
     n_points = ds.n_points
     wl_cap = int(res.counters[1].item()) * 2 + 4096
-    cfg = bnb.bnb_bound_cfg(ADAPT["depth"], 4, 1, 0, ADAPT["adapt_depth"], ADAPT["sigma"], ADAPT["alpha"], 0, split_cap)
+    cfg = bnb.bnb_bound_cfg(ADAPT["depth"], 4, 1, 0, ADAPT["adapt_depth"], sigma, alpha, 0, split_cap)
     cb_ws = bnb._ws(bnb.bnb_bound_tuples_ws(bnb.C.byref(ds.s1), None, bnb.C.byref(ds.em), bnb.C.byref(cfg)), dev)
     pre_cap = int(idx.count[1].item()) + int(idx.count[1].item()) // 4 + 4096
     ix_ws = bnb._ws(bnb.bnb_build_index_ws(bnb.C.byref(cb.c), sc.grid_res, pre_cap), dev)
@@ -914,7 +917,7 @@ def adaptive_summary(dev, steps: int) -> dict:
     c = r.counters.cpu().numpy()
     n_base = sc.emitters.n * sc.s1.n_tris * 4 ** ADAPT["depth"]
     out = {"workload": "mirror256 (131,072 tris x 16 area-light samples) from depth 0, adaptive to depth "
-                       f"{ADAPT['adapt_depth']}: sigma {ADAPT['sigma']} (box area), alpha {ADAPT['alpha']}; "
+                       f"{ADAPT['adapt_depth']}: sigma {sigma} (box area), alpha {alpha}; "
                        "1024^2 points, E|S| = 4", "status_ok": ok, "steps": steps, "base_cells": n_base,
            "records": n_rec, "live_leaves": live, "split_cells": split, "live_depth_histogram": hist,
            "gamma": gamma, "stage_ms": {"bound": float(ms[0]), "index": float(ms[1]), "sample_solve": float(ms[2])},
@@ -923,6 +926,27 @@ def adaptive_summary(dev, steps: int) -> dict:
     del cb, idx, cb_ws, ix_ws, sm_ws, flush
     torch.cuda.empty_cache()
     return out
+
+
+ADAPT_SWEEP = [(sg, al) for al in (1.25, 2.0, 10.0) for sg in (1e-5, 1e-6, 1e-7)]
+
+
+def adaptive_sweep(dev, steps: int) -> list:
+    """The stopping parameters of adaptive subdivision (Sec. 6.1, the sweep of Fig. fig_par) on
+    the benchmark mirror: box area sigma and bound ratio alpha against the precomputation time
+    (bound + index), the tuples listed per point |U| and the roots found per point at E|S| = 4."""
+    rows = []
+    for sg, al in ADAPT_SWEEP:
+        try:
+            r = adaptive_summary(dev, steps, sigma=sg, alpha=al)
+        except Exception as ex:  # a configuration that does not fit is reported, the rest stand
+            rows.append({"sigma": sg, "alpha": al, "error": f"{type(ex).__name__}: {ex}"})
+            continue
+        rows.append({"sigma": sg, "alpha": al, "status_ok": r["status_ok"], "records": r["records"],
+                     "live_leaves": r["live_leaves"], "precompute_ms": r["stage_ms"]["bound"] + r["stage_ms"]["index"],
+                     "stage_ms": r["stage_ms"], "U": r["per_point"]["U"], "S": r["per_point"]["S"],
+                     "roots": r["per_point"]["roots"]})
+    return rows
 
 
 # ----------------------------------------------------------------------------- accuracy vs the oracle
@@ -1259,6 +1283,8 @@ def main():
     ap.add_argument("--emitters", type=int, default=0, help="use only the first N area-light samples (profiling case)")
     ap.add_argument("--serving-requests", type=int, default=256,
                     help="requests of the serving workload reported under 'serving' (0: skip)")
+    ap.add_argument("--adaptive-sweep-steps", type=int, default=2,
+                    help="timed steps per (sigma, alpha) of the adaptive parameter sweep (0: skip)")
     ap.add_argument("--adaptive-steps", type=int, default=5,
                     help="timed steps of the adaptive-subdivision mirror256 pass reported under 'adaptive' (0: skip)")
     ap.add_argument("--implicit-steps", type=int, default=5,
