@@ -172,3 +172,25 @@ def test_selection_probability_positive_when_bound_positive(orc):
     assert n_u == 3
     assert 3 in wk.tolist()  # E~ = inf -> P = 1, always selected
     assert np.all(wP > 0)
+
+
+@pytest.mark.parametrize("name,kw", [("tiny", dict(n=6, depth=1, points=24)),
+                                     ("water", dict(n=6, depth=1, steep=0.08, points=24))])
+def test_one_polish_step_is_enough(orc, name, kw):
+    """Sec. 6.1 Newton: after the damped float32-level phase leaves a root within ~1e-6, one
+    quadratically convergent float64 step reaches the float64 limit.  Every (point, tuple) pair
+    solved with 1 and with 2 float64 polish steps: the same roots accepted, contributions within
+    1e-12 relative, roots within 1e-12 in barycentric coordinates (the oracle's polish count)."""
+    sc = S.config(name, **kw)
+    n_p = sc.su.shape[0]
+    keys = np.array([orc.tuple_key(e, t) for e in range(sc.emitters.n) for t in range(sc.s1.n_tris)], np.uint64)
+    wp = np.repeat(np.arange(n_p), keys.shape[0])
+    wk = np.tile(keys, n_p)
+    ones = np.ones(wp.shape[0], np.float32)
+    c1, u1, v1, s1 = orc.solve(sc, wp, wk, ones, polish_iters=1)
+    c2, u2, v2, s2 = orc.solve(sc, wp, wk, ones, polish_iters=2)
+    acc1, acc2 = c1 > 0, c2 > 0
+    assert acc1.sum() > 20
+    assert np.array_equal(acc1, acc2)
+    assert np.max(np.abs(c1[acc1] - c2[acc1]) / c2[acc1]) <= 1e-12
+    assert np.max(np.abs(u1[acc1] - u2[acc1])) <= 1e-12 and np.max(np.abs(v1[acc1] - v2[acc1])) <= 1e-12
