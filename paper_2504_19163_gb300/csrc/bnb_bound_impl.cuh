@@ -1338,21 +1338,20 @@ __device__ __forceinline__ void refract_irradiance(const Leaves<T>& L, const TP<
     wp_mac(X, At[t], b, beta);
   }
   wp_renorm(X);
-  WPr<T, 9> Y, Z;
-  wp_zero(Y);
-  wp_zero(Z);
+  // Y = A1 Q2 - A2 Q1 and Z = Q1 B2 - Q2 B1 = B2 Q1 - B1 Q2: four products of one shape in one loop
+  WPr<T, 9> YZ[2];
+  wp_zero(YZ[0]);
+  wp_zero(YZ[1]);
 #pragma unroll 1
-  for (int t = 0; t < 2; ++t) {
-    WPr<T, 4> q = Qt[1 - t];
-    if (t) wp_negate(q);
-    wp_mac(Y, At[t], q, beta);
+  for (int t = 0; t < 4; ++t) {
+    const int h = t >> 1, k = t & 1;
+    const WPr<T, 5>& a = h == 0 ? At[k] : Bt[1 - k];
+    WPr<T, 4> q = h == 0 ? Qt[1 - k] : Qt[k];
+    if (k) wp_negate(q);
+    wp_mac(YZ[h], a, q, beta);
   }
-#pragma unroll 1
-  for (int t = 0; t < 2; ++t) {
-    WPr<T, 5> b = Bt[1 - t];
-    if (t) wp_negate(b);
-    wp_mac(Z, Qt[t], b, beta);
-  }
+  WPr<T, 9>& Y = YZ[0];
+  WPr<T, 9>& Z = YZ[1];
   wp_renorm(Y);
   wp_renorm(Z);
   WPr<T, 13> Mp;
