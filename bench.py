@@ -533,7 +533,9 @@ def launches_per_step(n_points: int, G: int) -> int:
     bound = 1 + 1 + 4                                # pack, base, 4 split levels
     # merge, overflow, scan, scatter, rank/warp sort, block sort, big-cell sort, scan, compact, count
     index = 2 + scan_launches(G * G) + 4 + scan_launches(G * G) + 2
-    sample = 1 + 1 + scan_launches(n_points) + 1 + 2 + 1  # pack, count, scan, fill, solve32 + polish, reduce
+    # pack, list-length mode, count (thread and warp forms: one returns at once), scan, fill (both
+    # forms), solve32 + polish, reduce
+    sample = 1 + 1 + 2 + scan_launches(n_points) + 2 + 2 + 1
     return bound + index + sample
 
 

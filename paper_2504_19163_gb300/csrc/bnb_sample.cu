@@ -10,6 +10,7 @@
 //                     packed greedily into groups of probability sum <= 1 and
 //                     one draw per group selects at most one of its tuples.
 //   scan              -> worklist offsets (point order, then key order).
+//   (bins = 0 and long lists: sample_warp_k, the same with a warp per point)
 //   sample_k (fill)   the same selections, writing (point, key, P): the count pass keeps
 //                     the list positions of a point's first kSelCache selections,
 //                     so only points with more selections walk their list again.
@@ -58,7 +59,8 @@ struct SampleParams {
 constexpr int kSelCache = 8;
 
 template <bool FILL>
-__global__ void __launch_bounds__(256) sample_k(SampleParams P) {
+__global__ void __launch_bounds__(256) sample_k(SampleParams P, const int32_t* __restrict__ mode) {
+  if (!P.bins && *mode != 0) return;  // the long-list form runs instead (sample_warp_k)
   long long nu = 0, ns = 0, nb = 0;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n_points;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -143,6 +145,103 @@ __global__ void __launch_bounds__(256) sample_k(SampleParams P) {
       if (nu) atomicAdd((unsigned long long*)&P.counters[0], (unsigned long long)nu);
       if (ns) atomicAdd((unsigned long long*)&P.counters[1], (unsigned long long)ns);
       if (nb) atomicAdd((unsigned long long*)&P.counters[3], (unsigned long long)nb);
+    }
+  }
+}
+
+// One draw per listed tuple (bins = 0) with a warp per shading point, for long lists: lane l
+// takes list entries l, l + 32, ... (coalesced loads, 32 draws at once); a ballot per 32 entries
+// keeps the selections in list order, so the counts, the kept positions and the worklist are
+// those of sample_k.  *mode (set by sample_mode_k) picks this kernel or sample_k; the other one
+// returns at once.
+constexpr int kLongList = 32;  // mean entries per grid cell from which the warp form runs
+
+__global__ void sample_mode_k(const int64_t* __restrict__ offsets, int32_t G, int64_t capacity,
+                              int32_t* __restrict__ mode) {
+  const int64_t cells = (int64_t)G * G;
+  const int64_t entries = min(offsets[cells], capacity);
+  *mode = entries >= (int64_t)kLongList * cells ? 1 : 0;
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(256) sample_warp_k(SampleParams P, const int32_t* __restrict__ mode) {
+  if (*mode == 0) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  long long nu = 0, ns = 0;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = (((int64_t)blockIdx.x * blockDim.x) >> 5) + (threadIdx.x >> 5); p < P.n_points; p += warps) {
+    const int g = grid_col_s(P.sv[p], P.G) * P.G + grid_col_s(P.su[p], P.G);
+    const int64_t s = P.offsets[g];
+    const int64_t e = min(P.offsets[g + 1], P.index_capacity);
+    int64_t out = FILL ? P.woff[p] : 0;
+    if (FILL) {
+      const int64_t c = P.n_sel[p];
+      if (c <= kSelCache) {  // the count pass kept every selection's list position
+        if (lane < (int)c) {
+          const int64_t j = s + P.sel_cache[(int64_t)lane * P.n_points + p];
+          const uint64_t k = P.key[j];
+          const int64_t o = out + lane;
+          if (o < P.wl_cap) {
+            P.wl_point[o] = p;
+            P.wl_key[o] = k;
+            P.wl_p[o] = fminf(__fmul_ru(P.gamma, P.etilde[j]), 1.0f);
+            if (P.sel_point) P.sel_point[o] = p;
+            if (P.sel_key) P.sel_key[o] = k;
+          } else {
+            raise_status(P.status, BNB_ERR_CAPACITY);
+          }
+        }
+        continue;
+      }
+    }
+    int64_t cnt = 0;
+    for (int64_t j0 = s; j0 < e; j0 += 32) {
+      const int64_t j = j0 + lane;
+      bool sel = false;
+      float Pt = 0.0f;
+      uint64_t k = 0;
+      if (j < e) {
+        Pt = fminf(__fmul_ru(P.gamma, P.etilde[j]), 1.0f);
+        k = P.key[j];
+        sel = uniform24(P.seed, p, k) < Pt;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, sel);
+      if (sel) {
+        const int64_t rank = cnt + __popc(m & below);
+        if (FILL) {
+          const int64_t o = out + rank;
+          if (o < P.wl_cap) {
+            P.wl_point[o] = p;
+            P.wl_key[o] = k;
+            P.wl_p[o] = Pt;
+            if (P.sel_point) P.sel_point[o] = p;
+            if (P.sel_key) P.sel_key[o] = k;
+          } else {
+            raise_status(P.status, BNB_ERR_CAPACITY);
+          }
+        } else if (rank < kSelCache) {
+          P.sel_cache[rank * P.n_points + p] = (int32_t)(j - s);
+        }
+      }
+      cnt += __popc(m);
+    }
+    if (!FILL && lane == 0) {
+      P.n_sel[p] = cnt;
+      if (P.sel_count) P.sel_count[p] = (int32_t)cnt;
+      nu += (e > s ? e - s : 0);
+      ns += cnt;
+    }
+  }
+  if (!FILL) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nu += __shfl_xor_sync(0xffffffffu, nu, o);
+      ns += __shfl_xor_sync(0xffffffffu, ns, o);
+    }
+    if (lane == 0) {
+      if (nu) atomicAdd((unsigned long long*)&P.counters[0], (unsigned long long)nu);
+      if (ns) atomicAdd((unsigned long long*)&P.counters[1], (unsigned long long)ns);
     }
   }
 }
@@ -397,6 +496,7 @@ struct SampleWs {
   int64_t* pl_idx;
   float *pl_u, *pl_v;
   int32_t* sel_cache;
+  int32_t* mode;
   void* scan;
   size_t bytes;
 };
@@ -422,6 +522,7 @@ static SampleWs carve_sample_ws(void* base, int64_t n_tris, int64_t n_tris2, int
   w.pl_u = (float*)take((size_t)wl_cap * 4);
   w.pl_v = (float*)take((size_t)wl_cap * 4);
   w.sel_cache = (int32_t*)take((size_t)n_points * kSelCache * 4);
+  w.mode = (int32_t*)take(4);
   w.scan = take(scan_ws_bytes(n_points));
   w.bytes = o;
   return w;
@@ -468,9 +569,13 @@ cudaError_t launch_sample_and_solve(const bnb_surface* s1, const bnb_surface* s2
   P.bins = cfg->bins;
   P.sel_cache = w.sel_cache;
   const int64_t pblocks = std::min<int64_t>((n_points + 255) / 256, (int64_t)sms * 32);
-  sample_k<false><<<(unsigned)pblocks, 256, 0, st>>>(P);
+  const int64_t wblocks = std::min<int64_t>((n_points * 32 + 255) / 256, (int64_t)sms * 64);
+  sample_mode_k<<<1, 1, 0, st>>>(idx->offsets, idx->grid_res, idx->capacity, w.mode);
+  sample_k<false><<<(unsigned)pblocks, 256, 0, st>>>(P, w.mode);
+  if (!P.bins) sample_warp_k<false><<<(unsigned)wblocks, 256, 0, st>>>(P, w.mode);
   if ((e = launch_exclusive_scan(w.n_sel, w.woff, n_points, w.scan, st)) != cudaSuccess) return e;
-  sample_k<true><<<(unsigned)pblocks, 256, 0, st>>>(P);
+  sample_k<true><<<(unsigned)pblocks, 256, 0, st>>>(P, w.mode);
+  if (!P.bins) sample_warp_k<true><<<(unsigned)wblocks, 256, 0, st>>>(P, w.mode);
   SolveParams S{};
   S.tri = w.tri;
   S.n_tris = s1->n_tris;
