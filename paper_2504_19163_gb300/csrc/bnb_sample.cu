@@ -447,7 +447,8 @@ __global__ void __launch_bounds__(256) solve32_pair_k(SolveParams S) {
   }
 }
 
-__global__ void __launch_bounds__(256) polish_pair_k(SolveParams S) {
+// Two blocks per SM (128 registers): more warps on the float64 chain polish than one block at 233.
+__global__ void __launch_bounds__(256, 2) polish_pair_k(SolveParams S) {
   const int64_t n = *S.pl_count;
   long long roots = 0;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
